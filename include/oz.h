@@ -1,0 +1,182 @@
+/*
+ * oz.h -- C ABI of the GB300 (sm_103a) Ozaki-II emulated FP64 GEMM library.
+ *
+ * The library computes C = op(A) op(B) for FP64 row-major matrices by the
+ * Ozaki-II scheme on the INT8 alphabet (Sec. "Ozaki II", Sec. "INT4 and INT8"):
+ *   1. Scale      one power-of-two shift per row of op(A) and per column of
+ *                 op(B) (eq. convert);
+ *   2. Reduce     truncate to integers below 2^bits and write the balanced
+ *                 residue planes modulo each of Q pairwise-coprime moduli
+ *                 (Sec. "Structure", phase 2);
+ *   3. GEMMs      one exact integer product per modulus (phase 3);
+ *   4. Epilogue   each product reduced modulo its modulus (phase 4, order R>C);
+ *   5. Reconstruct CRT back to the integer product, one rounding to binary64,
+ *                 unscale (phase 5).
+ *
+ * Conventions for every call below:
+ *   - Matrices are row-major. op(X) = X if trans == 0, X^T if trans == 1.
+ *     A is stored m x k (trans_a = 0) or k x m (trans_a = 1) with leading
+ *     dimension lda >= its column count; likewise B (k x n or n x k), C (m x n).
+ *   - A, B, C and the workspace are DEVICE pointers owned by the caller. The
+ *     library never allocates memory during a product call; a plan owns a small
+ *     table of constants (no device memory).
+ *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream). Nothing synchronises the host
+ *     except oz_query_status.
+ *   - Errors come back as oz_status codes; the library never exits, aborts or
+ *     traps. Argument errors are detected on the host before any launch.
+ *     Non-finite input is detected on the device, leaves C unspecified, and is
+ *     reported by the next oz_query_status on the same workspace.
+ *   - Nothing is thread-local: a plan is immutable after creation and may be
+ *     shared by threads; a workspace must not be used by two calls that
+ *     overlap on the GPU.
+ */
+#ifndef OZ_H_
+#define OZ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OZ_API __attribute__((visibility("default")))
+#else
+#define OZ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OZ_MAX_MODULI 20   /* largest Q the library accepts */
+#define OZ_MIN_MODULI 9    /* smallest Q the library accepts */
+#define OZ_MAX_BITS 64     /* largest bit budget beta (|A'| < 2^beta) */
+
+typedef enum {
+  OZ_OK = 0,
+  OZ_ERR_INVALID_ARG = 1,   /* bad size, leading dimension, pointer or flag */
+  OZ_ERR_K_TOO_LARGE = 2,   /* k above the plan's K_max (eq. caps) */
+  OZ_ERR_WORKSPACE = 3,     /* workspace NULL or shorter than oz_workspace_bytes */
+  OZ_ERR_NONFINITE = 4,     /* NaN or Inf in A or B (reported by oz_query_status) */
+  OZ_ERR_UNSUPPORTED = 5,   /* configuration or engine not available */
+  OZ_ERR_CUDA = 6           /* a CUDA runtime call or launch failed */
+} oz_status;
+
+typedef enum {
+  OZ_ENGINE_AUTO = 0,  /* the fastest engine available for the plan */
+  OZ_ENGINE_IMMA = 1,  /* INT8 residue planes, warp-level mma.sync s8 -> s32 */
+  OZ_ENGINE_TC = 2     /* BF16-held residue planes, tcgen05.mma into TMEM */
+} oz_engine;
+
+typedef struct oz_plan_s* oz_plan;
+
+/*
+ * oz_plan_create -- build an INT8 configuration (Sec. "Forms and Channels":
+ * one one-limb channel per modulus; Sec. "INT4 and INT8": moduli up to 239).
+ *   out          receives the plan (caller frees it with oz_plan_destroy).
+ *   num_moduli   Q in [OZ_MIN_MODULI, OZ_MAX_MODULI]; 0 picks the least Q whose
+ *                modulus product satisfies the window P > 2 K (2^53 - 1)^2
+ *                (eq. ov-crtgen) at K = k_hint.
+ *                The moduli are the Q pairwise-coprime integers <= 239 with the
+ *                largest product (for Q >= 9 these are prefixes of one list).
+ *   bits         beta, the bits kept per row/column maximum (eq. convert uses
+ *                53). 0 picks the largest beta <= OZ_MAX_BITS with
+ *                2 k_hint (2^beta - 1)^2 < P.
+ *   k_hint       the largest inner dimension the caller intends to use (>= 1).
+ *                The plan is refused with OZ_ERR_K_TOO_LARGE if the window
+ *                does not hold at k_hint.
+ *   engine       an oz_engine value.
+ * Returns OZ_OK, OZ_ERR_INVALID_ARG, OZ_ERR_K_TOO_LARGE or OZ_ERR_UNSUPPORTED.
+ */
+OZ_API oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int64_t k_hint, int engine);
+
+/*
+ * oz_plan_info -- report a plan: q = Q, bits = beta, k_max = K_max (the
+ * minimum of the reconstruction and accumulation caps of eq. caps at this
+ * beta), engine = the engine a call will use, moduli[0..Q-1] (decreasing).
+ * Any output pointer may be NULL. moduli, if given, must hold OZ_MAX_MODULI.
+ */
+OZ_API oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, int* engine, uint32_t* moduli);
+
+/* Release a plan (NULL is accepted). */
+OZ_API void oz_plan_destroy(oz_plan plan);
+
+/*
+ * oz_workspace_bytes -- device workspace a product of this shape needs: the
+ * shifts, the residue planes of both operands (Q (m_pad + n_pad) k_pad entries
+ * of 1 byte for IMMA, 2 bytes for TC) and the Q m n residues of the product.
+ * Returns 0 for an invalid plan or shape.
+ */
+OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
+
+/*
+ * oz_dgemm -- C = op(A) op(B) (Sec. "Emulation Problem"; five phases of
+ * Sec. "Structure"). No alpha/beta: C is overwritten.
+ *   m, n, k >= 0 (an empty product writes nothing; k = 0 writes zeros).
+ *   k must not exceed the plan's K_max (OZ_ERR_K_TOO_LARGE).
+ *   workspace: device memory of at least oz_workspace_bytes(plan, m, n, k)
+ *   bytes, 256-byte aligned.
+ * The result is C_ij = fl(2^-(s_i + t_j) (A'B')_ij), one round-to-nearest-even
+ * rounding of the exact integer product of the truncated operands, with
+ * gradual underflow and overflow to +-inf.
+ */
+OZ_API oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                   const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * oz_query_status -- wait for the stream, then report OZ_ERR_NONFINITE if the
+ * last oz_dgemm on this workspace met a NaN or Inf, OZ_ERR_CUDA if the stream
+ * has a CUDA error, else OZ_OK.
+ */
+OZ_API oz_status oz_query_status(void* workspace, void* stream);
+
+/* ---- The phases on their own, for parity checks and profiling. ---- */
+
+/*
+ * oz_split -- phases 1 and 2 for one operand (Sec. "Structure").
+ * The operand is viewed as nvec vectors of len entries: vector v, entry h is
+ * X[v*ld + h] if contiguous != 0 (rows of a row-major matrix: A, or B^T), else
+ * X[h*ld + v] (columns: B, or A^T). Writes:
+ *   shifts[v]  = beta - e_v, e_v the exponent with max_h |x| in [2^(e-1), 2^e)
+ *                (0 for a zero vector), int32, device;
+ *   planes     = Q planes of nvec_pad x k_pad entries, plane q row v entry h =
+ *                the balanced residue of trunc(x 2^shift) modulo m_q in
+ *                [-floor(m/2), ceil(m/2) - 1]; int8 for IMMA, bf16 for TC;
+ *                padding (v >= nvec or h >= len) is zero.
+ *   flag       (may be NULL) device int32; bit 0 set if an entry is not finite.
+ *   colmax     device scratch of nvec uint64 words, used when contiguous == 0
+ *              (may be NULL otherwise).
+ * nvec_pad and k_pad must be multiples of 256 and 128, >= nvec and len.
+ */
+OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t len, const double* X, int64_t ld,
+                   int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag,
+                   uint64_t* colmax, void* stream);
+
+/*
+ * oz_residue_gemm -- phases 3 and 4: for each modulus q,
+ * W_q = U_q V_q^T (exact, INT32) and
+ *   raw == 0: Y[q][i][j] = (W mod m_q) * ((P/m_q)^-1 mod m_q) mod m_q, the CRT
+ *             digit the reconstruct phase consumes;
+ *   raw != 0: Y[q][i][j] = W mod m_q in [0, m_q) (the paper's epilogue value).
+ * U, V: planes from oz_split (m_pad x k_pad and n_pad x k_pad per modulus),
+ * Y: uint8, Q planes of m x n (row pitch n). Device pointers.
+ */
+OZ_API oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                          const void* U, const void* V, uint8_t* Y, int raw, void* stream);
+
+/*
+ * oz_reconstruct -- phase 5 (Sec. "Around the GEMMs", Reconstruct): from the
+ * CRT digits Y (raw == 0 output of oz_residue_gemm) and the shifts s[m], t[n],
+ * C_ij = fl(2^-(s_i + t_j) X_ij), X_ij the integer in [-P/2, P/2) congruent
+ * to the digits. C row pitch ldc >= n. Device pointers.
+ */
+OZ_API oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+                         const int32_t* t, double* C, int64_t ldc, void* stream);
+
+/* Short English description of a status code (static string). */
+OZ_API const char* oz_status_str(oz_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZ_H_ */

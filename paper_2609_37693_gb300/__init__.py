@@ -1,0 +1,209 @@
+"""Python binding of liboz, the GB300 Ozaki-II emulated FP64 GEMM library.
+
+The functions named ``oz_*`` mirror the C ABI of ``include/oz.h`` one to one:
+they marshal arguments (device pointers as integers, the stream as a handle)
+and return the ``oz_status`` code. Every step of the computation runs in the
+library's CUDA kernels; nothing here computes. The library is built in-tree by
+``paper_2609_37693_gb300.build``; importing this package fails loudly if it is
+missing or cannot be loaded, and there is no fallback path.
+
+On top of the ABI sit small conveniences for torch tensors: ``Plan`` (owns an
+``oz_plan``), ``dgemm`` (allocates the workspace with torch and calls
+``oz_dgemm`` on the current stream) and ``EmuMatmul`` (autograd).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+OZ_OK = 0
+OZ_ERR_INVALID_ARG = 1
+OZ_ERR_K_TOO_LARGE = 2
+OZ_ERR_WORKSPACE = 3
+OZ_ERR_NONFINITE = 4
+OZ_ERR_UNSUPPORTED = 5
+OZ_ERR_CUDA = 6
+
+OZ_ENGINE_AUTO = 0
+OZ_ENGINE_IMMA = 1
+OZ_ENGINE_TC = 2
+
+OZ_MAX_MODULI = 20
+OZ_MIN_MODULI = 9
+OZ_MAX_BITS = 64
+
+EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_dgemm",
+            "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str")
+
+
+class OzError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {oz_status_str(status)} (status {status})")
+
+
+def _load_library():
+    path = _build.LIB
+    if not os.path.exists(path):
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    P, I64, I32, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "oz_plan_create": (I32, [ctypes.POINTER(P), I32, I32, I64, I32]),
+        "oz_plan_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I64),
+                               ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_uint32)]),
+        "oz_plan_destroy": (None, [P]),
+        "oz_workspace_bytes": (SZ, [P, I64, I64, I64]),
+        "oz_dgemm": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
+        "oz_query_status": (I32, [P, P]),
+        "oz_split": (I32, [P, I32, I64, I64, P, I64, I64, I64, P, P, P, P, P]),
+        "oz_residue_gemm": (I32, [P, I64, I64, I64, I64, I64, P, P, P, I32, P]),
+        "oz_reconstruct": (I32, [P, I64, I64, P, P, P, P, I64, P]),
+        "oz_status_str": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load_library()
+LIBRARY_PATH = _lib._name
+
+
+# ---------------------------------------------------------------------------
+# The C ABI, name for name
+# ---------------------------------------------------------------------------
+
+def oz_status_str(status: int) -> str:
+    return _lib.oz_status_str(int(status)).decode()
+
+
+def oz_plan_create(num_moduli: int = 16, bits: int = 0, k_hint: int = 8192, engine: int = OZ_ENGINE_AUTO):
+    """Returns (status, plan handle or None)."""
+    h = ctypes.c_void_p()
+    st = _lib.oz_plan_create(ctypes.byref(h), int(num_moduli), int(bits), int(k_hint), int(engine))
+    return st, (h.value if st == OZ_OK else None)
+
+
+def oz_plan_info(plan):
+    """Returns (status, dict(q, bits, k_max, engine, moduli))."""
+    q, b, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    km = ctypes.c_int64()
+    mods = (ctypes.c_uint32 * OZ_MAX_MODULI)()
+    st = _lib.oz_plan_info(plan, ctypes.byref(q), ctypes.byref(b), ctypes.byref(km), ctypes.byref(e), mods)
+    if st != OZ_OK:
+        return st, None
+    return st, {"q": q.value, "bits": b.value, "k_max": km.value, "engine": e.value,
+                "moduli": [int(x) for x in mods[: q.value]]}
+
+
+def oz_plan_destroy(plan) -> None:
+    _lib.oz_plan_destroy(plan)
+
+
+def oz_workspace_bytes(plan, m: int, n: int, k: int) -> int:
+    return int(_lib.oz_workspace_bytes(plan, int(m), int(n), int(k)))
+
+
+def oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream) -> int:
+    return _lib.oz_dgemm(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb), C,
+                         int(ldc), workspace, int(workspace_bytes), stream)
+
+
+def oz_query_status(workspace, stream) -> int:
+    return _lib.oz_query_status(workspace, stream)
+
+
+def oz_split(plan, contiguous, nvec, length, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, stream) -> int:
+    return _lib.oz_split(plan, int(contiguous), int(nvec), int(length), X, int(ld), int(nvec_pad), int(k_pad),
+                         shifts, planes, flag, colmax, stream)
+
+
+def oz_residue_gemm(plan, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, stream) -> int:
+    return _lib.oz_residue_gemm(plan, int(m), int(n), int(m_pad), int(n_pad), int(k_pad), U, V, Y, int(raw),
+                                stream)
+
+
+def oz_reconstruct(plan, m, n, Y, s, t, C, ldc, stream) -> int:
+    return _lib.oz_reconstruct(plan, int(m), int(n), Y, s, t, C, int(ldc), stream)
+
+
+# ---------------------------------------------------------------------------
+# torch conveniences
+# ---------------------------------------------------------------------------
+
+def _check(st: int, what: str):
+    if st != OZ_OK:
+        raise OzError(st, what)
+
+
+def round_up(x: int, r: int) -> int:
+    return (x + r - 1) // r * r
+
+
+class Plan:
+    """An oz_plan owned by Python. ``Plan(q=16, bits=0, k_hint=8192, engine=OZ_ENGINE_AUTO)``."""
+
+    def __init__(self, q: int = 16, bits: int = 0, k_hint: int = 8192, engine: int = OZ_ENGINE_AUTO):
+        st, h = oz_plan_create(q, bits, k_hint, engine)
+        _check(st, "oz_plan_create")
+        self.handle = h
+        _, info = oz_plan_info(h)
+        self.q, self.bits, self.k_max = info["q"], info["bits"], info["k_max"]
+        self.engine, self.moduli = info["engine"], info["moduli"]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            oz_plan_destroy(h)
+            self.handle = None
+
+    def workspace_bytes(self, m: int, n: int, k: int) -> int:
+        return oz_workspace_bytes(self.handle, m, n, k)
+
+    def __repr__(self):
+        return f"Plan(q={self.q}, bits={self.bits}, k_max={self.k_max}, engine={self.engine})"
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace(plan: Plan, m: int, n: int, k: int, device=None):
+    import torch
+    nbytes = plan.workspace_bytes(m, n, k)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def dgemm(A, B, plan: Plan | None = None, trans_a: bool = False, trans_b: bool = False, out=None, ws=None,
+          stream=None):
+    """C = op(A) op(B) for float64 CUDA tensors (row-major, unit inner stride)."""
+    import torch
+    if A.dtype != torch.float64 or B.dtype != torch.float64 or not A.is_cuda or not B.is_cuda:
+        raise TypeError("dgemm takes float64 CUDA tensors")
+    if A.dim() != 2 or B.dim() != 2 or A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("dgemm takes 2-D tensors with unit inner stride")
+    m, k = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
+    k2, n = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} vs {k2}")
+    if plan is None:
+        plan = Plan(16, 0, max(k, 1))
+    C = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(plan, m, n, k, A.device)
+    st = oz_dgemm(plan.handle, int(trans_a), int(trans_b), m, n, k, A.data_ptr(), max(A.stride(0), 1),
+                  B.data_ptr(), max(B.stride(0), 1), C.data_ptr(), max(C.stride(0), 1), ws.data_ptr(),
+                  ws.numel(), _stream_handle(stream))
+    _check(st, "oz_dgemm")
+    return C
+
+
+def query_status(ws, stream=None) -> int:
+    return oz_query_status(ws.data_ptr(), _stream_handle(stream))

@@ -1,0 +1,153 @@
+// oz_api.cu -- the C ABI entry points that run the phases (declared in
+// include/oz.h): argument checks, the workspace layout, and the launch order
+// Scale+Reduce (A), Scale+Reduce (B), GEMMs+Epilogue, Reconstruct of
+// Sec. "Structure". Every call is asynchronous on the caller's stream and
+// allocates nothing.
+#include <stdint.h>
+#include <string.h>
+
+#include "oz_internal.h"
+
+namespace {
+
+using oz::round_up;
+
+struct Layout {
+  int64_t m_pad, n_pad, k_pad;
+  size_t flag, s, t, colmax, u, v, y, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
+  if (!p || m < 0 || n < 0 || k < 0) return false;
+  const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;
+  L->m_pad = round_up(m > 0 ? m : 1, oz::kPadRows);
+  L->n_pad = round_up(n > 0 ? n : 1, oz::kPadRows);
+  L->k_pad = round_up(k > 0 ? k : 1, oz::kPadK);
+  size_t off = 0;
+  L->flag = off; off = align256(off + 16);
+  L->s = off; off = align256(off + 4 * (size_t)m);
+  L->t = off; off = align256(off + 4 * (size_t)n);
+  L->colmax = off; off = align256(off + 8 * (size_t)(m > n ? m : n));
+  L->u = off; off = align256(off + (size_t)p->Q * L->m_pad * L->k_pad * elem);
+  L->v = off; off = align256(off + (size_t)p->Q * L->n_pad * L->k_pad * elem);
+  L->y = off; off = align256(off + (size_t)p->Q * m * n);
+  L->total = off;
+  return true;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+oz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? OZ_OK : OZ_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k) {
+  Layout L;
+  if (!make_layout(plan, m, n, k, &L)) return 0;
+  return L.total;
+}
+
+extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                              const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  if (!plan || m < 0 || n < 0 || k < 0) return OZ_ERR_INVALID_ARG;
+  if ((trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1)) return OZ_ERR_INVALID_ARG;
+  const int64_t a_cols = trans_a ? m : k, b_cols = trans_b ? k : n;
+  if (lda < (a_cols > 1 ? a_cols : 1) || ldb < (b_cols > 1 ? b_cols : 1) || ldc < (n > 1 ? n : 1))
+    return OZ_ERR_INVALID_ARG;
+  if (k > plan->k_max) return OZ_ERR_K_TOO_LARGE;
+  if (m == 0 || n == 0) return OZ_OK;
+  if (!C || !aligned(C, 8)) return OZ_ERR_INVALID_ARG;
+  if (k > 0 && (!A || !B || !aligned(A, 8) || !aligned(B, 8))) return OZ_ERR_INVALID_ARG;
+  Layout L;
+  make_layout(plan, m, n, k, &L);
+  if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256)) return OZ_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  int32_t* flag = reinterpret_cast<int32_t*>(ws + L.flag);
+  cudaError_t e = cudaMemsetAsync(flag, 0, 16, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  if (k == 0) return cuda_status(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)n * 8, (size_t)m, st));
+
+  const OzTables& T = plan->tab;
+  const int bf16 = plan->engine == OZ_ENGINE_TC;
+  int32_t* s = reinterpret_cast<int32_t*>(ws + L.s);
+  int32_t* t = reinterpret_cast<int32_t*>(ws + L.t);
+  uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.colmax);
+  void* U = ws + L.u;
+  void* V = ws + L.v;
+  uint8_t* Y = reinterpret_cast<uint8_t*>(ws + L.y);
+
+  // Scale + Reduce, A side: vectors are the rows of op(A).
+  e = trans_a ? oz::launch_split_cols(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, colmax, st)
+              : oz::launch_split_rows(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  // B side: vectors are the columns of op(B).
+  e = trans_b ? oz::launch_split_rows(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, st)
+              : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  // GEMMs + epilogue
+  if (bf16) return OZ_ERR_UNSUPPORTED;
+  e = oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
+                           static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  // Reconstruct
+  e = oz::launch_reconstruct(T, m, n, Y, s, t, C, ldc, st);
+  return cuda_status(e);
+}
+
+extern "C" oz_status oz_query_status(void* workspace, void* stream) {
+  if (!workspace) return OZ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OZ_ERR_CUDA;
+  int32_t flag = 0;
+  if (cudaMemcpy(&flag, workspace, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess) return OZ_ERR_CUDA;
+  return (flag & 1) ? OZ_ERR_NONFINITE : OZ_OK;
+}
+
+extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t len, const double* X, int64_t ld,
+                              int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag,
+                              uint64_t* colmax, void* stream) {
+  if (!plan || nvec < 0 || len < 0) return OZ_ERR_INVALID_ARG;
+  if (nvec_pad < nvec || k_pad < len || nvec_pad % oz::kPadRows || k_pad % oz::kPadK || k_pad == 0)
+    return OZ_ERR_INVALID_ARG;
+  if (len > plan->k_max) return OZ_ERR_K_TOO_LARGE;
+  if (nvec > 0 && (!shifts || (len > 0 && (!X || !aligned(X, 8))))) return OZ_ERR_INVALID_ARG;
+  if (!planes || !aligned(planes, 16)) return OZ_ERR_INVALID_ARG;
+  if (contiguous ? ld < (len > 1 ? len : 1) : ld < (nvec > 1 ? nvec : 1)) return OZ_ERR_INVALID_ARG;
+  if (!contiguous && nvec > 0 && !colmax) return OZ_ERR_INVALID_ARG;
+  const int bf16 = plan->engine == OZ_ENGINE_TC;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = contiguous
+                      ? oz::launch_split_rows(plan->tab, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, bf16,
+                                              flag, st)
+                      : oz::launch_split_cols(plan->tab, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, bf16,
+                                              flag, colmax, st);
+  return cuda_status(e);
+}
+
+extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad,
+                                     int64_t k_pad, const void* U, const void* V, uint8_t* Y, int raw,
+                                     void* stream) {
+  if (!plan || m < 0 || n < 0) return OZ_ERR_INVALID_ARG;
+  if (m_pad < m || n_pad < n || m_pad % oz::kPadRows || n_pad % oz::kPadRows || k_pad <= 0 || k_pad % oz::kPadK)
+    return OZ_ERR_INVALID_ARG;
+  if (k_pad > oz::round_up(plan->k_max, oz::kPadK)) return OZ_ERR_K_TOO_LARGE;
+  if (m == 0 || n == 0) return OZ_OK;
+  if (!U || !V || !Y || !aligned(U, 16) || !aligned(V, 16)) return OZ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->engine == OZ_ENGINE_TC) return OZ_ERR_UNSUPPORTED;
+  return cuda_status(oz::launch_gemm_imma(plan->tab, m, n, k_pad, static_cast<const int8_t*>(U), m_pad * k_pad,
+                                          static_cast<const int8_t*>(V), n_pad * k_pad, Y, raw ? 1 : 0, st));
+}
+
+extern "C" oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+                                    const int32_t* t, double* C, int64_t ldc, void* stream) {
+  if (!plan || m < 0 || n < 0 || ldc < (n > 1 ? n : 1)) return OZ_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return OZ_OK;
+  if (!Y || !s || !t || !C || !aligned(C, 8)) return OZ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return cuda_status(oz::launch_reconstruct(plan->tab, m, n, Y, s, t, C, ldc, st));
+}

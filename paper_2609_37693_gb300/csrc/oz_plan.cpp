@@ -1,0 +1,218 @@
+// oz_plan.cpp -- host-side configuration builder (Sec. "Implementation": a
+// configuration is its moduli, its tables and its caps; building it checks the
+// accumulator bound and refuses K above the reconstruction cap).
+//
+// The INT8 alphabet is complete modulo every m <= 256 (Sec. "Forms and
+// Channels"), so each channel is one-limb with the balanced residue as both
+// tables and lambda = 1; its cost is one GEMM. The moduli are the Q
+// pairwise-coprime integers <= 239 of largest product; for 9 <= Q <= 20 these
+// are the first Q entries of kModuli below (Sec. "INT4 and INT8" fixes 16
+// moduli up to 239 with radius 119 and K_max = 151 647).
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "oz_internal.h"
+
+namespace {
+
+const uint32_t kModuli[OZ_MAX_MODULI] = {239, 237, 236, 235, 233, 229, 227, 223, 221, 217,
+                                         211, 209, 199, 197, 193, 191, 181, 179, 173, 167};
+
+// Unsigned big integer, 32-bit limbs, least significant first; 8 limbs = 256 bits.
+struct Big {
+  uint32_t w[8];
+  Big() { memset(w, 0, sizeof w); }
+  explicit Big(uint64_t v) {
+    memset(w, 0, sizeof w);
+    w[0] = (uint32_t)v;
+    w[1] = (uint32_t)(v >> 32);
+  }
+  Big mul(uint64_t s) const {  // s < 2^32
+    Big r;
+    uint64_t carry = 0;
+    for (int i = 0; i < 8; ++i) {
+      uint64_t t = (uint64_t)w[i] * s + carry;
+      r.w[i] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    return r;
+  }
+  Big mulbig(const Big& o) const {  // truncated to 256 bits
+    Big r;
+    for (int i = 0; i < 8; ++i) {
+      uint64_t carry = 0;
+      for (int j = 0; i + j < 8; ++j) {
+        uint64_t t = (uint64_t)w[i] * o.w[j] + r.w[i + j] + carry;
+        r.w[i + j] = (uint32_t)t;
+        carry = t >> 32;
+      }
+    }
+    return r;
+  }
+  uint32_t divmod(uint32_t d, Big* q) const {  // returns remainder
+    uint64_t rem = 0;
+    for (int i = 7; i >= 0; --i) {
+      uint64_t cur = (rem << 32) | w[i];
+      q->w[i] = (uint32_t)(cur / d);
+      rem = cur % d;
+    }
+    return (uint32_t)rem;
+  }
+  int cmp(const Big& o) const {
+    for (int i = 7; i >= 0; --i)
+      if (w[i] != o.w[i]) return w[i] < o.w[i] ? -1 : 1;
+    return 0;
+  }
+  int bitlen() const {
+    for (int i = 7; i >= 0; --i)
+      if (w[i]) return 32 * i + 32 - __builtin_clz(w[i]);
+    return 0;
+  }
+};
+
+Big product(int Q) {
+  Big P(1);
+  for (int i = 0; i < Q; ++i) P = P.mul(kModuli[i]);
+  return P;
+}
+
+// 2 K (2^beta - 1)^2, beta <= 96, K < 2^63
+Big window(int64_t K, int beta) {
+  Big b;  // 2^beta - 1
+  for (int i = 0; i < beta; ++i) b.w[i / 32] |= 1u << (i % 32);
+  Big sq = b.mulbig(b);
+  Big twoK((uint64_t)K * 2u);
+  return sq.mulbig(twoK);
+}
+
+bool window_holds(const Big& P, int64_t K, int beta) { return window(K, beta).cmp(P) < 0; }
+
+uint32_t inverse_mod(uint32_t a, uint32_t m) {  // extended Euclid, gcd(a, m) = 1
+  int64_t t = 0, newt = 1, r = m, newr = a % m;
+  while (newr) {
+    int64_t q = r / newr;
+    int64_t tmp = t - q * newt; t = newt; newt = tmp;
+    tmp = r - q * newr; r = newr; newr = tmp;
+  }
+  if (t < 0) t += m;
+  return (uint32_t)t;
+}
+
+uint32_t pow2_mod(int e, uint32_t m) {
+  uint64_t r = 1 % m;
+  for (int i = 0; i < e; ++i) r = (r * 2) % m;
+  return (uint32_t)r;
+}
+
+// Largest K (capped at 2^62) with 2 K (2^beta - 1)^2 < P: the reconstruction cap.
+int64_t kappa_rec(const Big& P, int beta) {
+  int64_t lo = 0, hi = (int64_t)1 << 62;
+  if (window_holds(P, hi, beta)) return hi;
+  while (hi - lo > 1) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (window_holds(P, mid, beta)) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace
+
+extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int64_t k_hint, int engine) {
+  if (!out) return OZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (k_hint < 1 || bits < 0 || bits > OZ_MAX_BITS) return OZ_ERR_INVALID_ARG;
+  if (engine < OZ_ENGINE_AUTO || engine > OZ_ENGINE_TC) return OZ_ERR_INVALID_ARG;
+  if (num_moduli != 0 && (num_moduli < OZ_MIN_MODULI || num_moduli > OZ_MAX_MODULI)) return OZ_ERR_UNSUPPORTED;
+
+  int Q = num_moduli;
+  if (Q == 0) {  // least Q meeting the window at beta = 53 (eq. ov-crtgen)
+    for (Q = OZ_MIN_MODULI; Q <= OZ_MAX_MODULI; ++Q)
+      if (window_holds(product(Q), k_hint, 53)) break;
+    if (Q > OZ_MAX_MODULI) return OZ_ERR_K_TOO_LARGE;
+  }
+  Big P = product(Q);
+  int beta = bits;
+  if (beta == 0) {
+    for (beta = OZ_MAX_BITS; beta >= 1; --beta)
+      if (window_holds(P, k_hint, beta)) break;
+    if (beta < 1) return OZ_ERR_K_TOO_LARGE;
+  } else if (!window_holds(P, k_hint, beta)) {
+    return OZ_ERR_K_TOO_LARGE;
+  }
+  int resolved = engine == OZ_ENGINE_AUTO ? OZ_ENGINE_IMMA : engine;
+  if (resolved == OZ_ENGINE_TC) return OZ_ERR_UNSUPPORTED;
+
+  oz_plan p = new (std::nothrow) oz_plan_s;
+  if (!p) return OZ_ERR_INVALID_ARG;
+  memset(p, 0, sizeof *p);
+  p->Q = Q;
+  p->bits = beta;
+  p->engine = resolved;
+  // eq. caps: K_max = min(kappa_rec, kappa_acc); the INT32 accumulator of one
+  // GEMM sums K products of two residues of magnitude <= r (eq. ov-acc).
+  uint32_t r = 0;
+  for (int i = 0; i < Q; ++i) r = kModuli[i] / 2 > r ? kModuli[i] / 2 : r;
+  int64_t k_acc = (int64_t)2147483647 / ((int64_t)r * r);
+  int64_t k_rec = kappa_rec(P, beta);
+  p->k_max = k_acc < k_rec ? k_acc : k_rec;
+  if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }
+
+  OzTables& t = p->tab;
+  t.Q = Q;
+  t.bits = beta;
+  // The reconstruct phase works modulo 2^(32 limbs) in two's complement. Its
+  // candidate X lies in (-1.5P, 1.5P) and it compares 2X with +-P, so 3P must
+  // stay below 2^(32 limbs - 1).
+  t.limbs = (P.bitlen() + 3 + 31) / 32;
+  if (t.limbs > OZ_MAX_LIMBS) { delete p; return OZ_ERR_UNSUPPORTED; }
+  for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.P[i] = P.w[i];
+  for (int q = 0; q < Q; ++q) {
+    uint32_t m = kModuli[q];
+    t.m[q] = m;
+    t.half[q] = (m + 1) / 2;
+    t.magic[q] = (uint32_t)((((uint64_t)1) << 32) / m);
+    t.c18[q] = pow2_mod(18, m);
+    t.c36[q] = pow2_mod(36, m);
+    t.c54[q] = pow2_mod(54, m);
+    Big Mk;
+    uint32_t rem = P.divmod(m, &Mk);
+    (void)rem;
+    Big dummy;
+    uint32_t mk_mod_m = Mk.divmod(m, &dummy);
+    t.inv[q] = inverse_mod(mk_mod_m, m);
+    t.invm[q] = 1.0f / (float)m;
+    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
+  }
+  *out = p;
+  return OZ_OK;
+}
+
+extern "C" oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, int* engine, uint32_t* moduli) {
+  if (!plan) return OZ_ERR_INVALID_ARG;
+  if (q) *q = plan->Q;
+  if (bits) *bits = plan->bits;
+  if (k_max) *k_max = plan->k_max;
+  if (engine) *engine = plan->engine;
+  if (moduli) {
+    for (int i = 0; i < OZ_MAX_MODULI; ++i) moduli[i] = i < plan->Q ? plan->tab.m[i] : 0;
+  }
+  return OZ_OK;
+}
+
+extern "C" void oz_plan_destroy(oz_plan plan) { delete plan; }
+
+extern "C" const char* oz_status_str(oz_status s) {
+  switch (s) {
+    case OZ_OK: return "ok";
+    case OZ_ERR_INVALID_ARG: return "invalid argument";
+    case OZ_ERR_K_TOO_LARGE: return "inner dimension above the configuration's K_max";
+    case OZ_ERR_WORKSPACE: return "workspace missing or too small";
+    case OZ_ERR_NONFINITE: return "non-finite entry in an operand";
+    case OZ_ERR_UNSUPPORTED: return "configuration or engine not supported";
+    case OZ_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,269 @@
+// oz_reconstruct.cu -- phase 5 of Sec. "Structure" (Reconstruct, Sec. "Around
+// the GEMMs"): the CRT sum in digits whose sums stay exact, the balanced
+// representative from one quotient estimate with an exact fallback, one
+// rounding, and the unscaling.
+//
+// Input per entry: the CRT digits y_q = (W_q mod m_q) (P/m_q)^-1 mod m_q in
+// [0, m_q), written by the GEMM epilogue. Then
+//   S = sum_q y_q (P/m_q) == X (mod P),  0 <= S < Q P,
+// formed in 32-bit limbs with 64-bit accumulators (each y_q (P/m_q)_limb is
+// below 2^40; twenty of them stay below 2^45). The quotient estimate is
+// round(sum_q y_q / m_q) in fp32 (error far below 1/2); X = S - qP is formed
+// modulo 2^(32 L) in two's complement and corrected once by +-P into
+// [-P/2, P/2). The window (eq. ov-crtgen) makes that X the exact integer
+// product (A'B')_ij.
+//
+// The binary64 result fl(X 2^-(s_i + t_j)) is assembled from integer fields:
+// the leading 53 bits (fewer below 2^-1022), round to nearest even from the
+// round bit and the sticky bits, overflow to +-inf. No floating-point
+// operation touches the value, so the rounding happens exactly once.
+#include <stdint.h>
+
+#include "oz_internal.h"
+
+namespace oz {
+namespace {
+
+template <int L>
+struct Limbs {
+  uint32_t w[L];
+};
+
+template <int L>
+__device__ __forceinline__ int bitlen(const Limbs<L>& x) {
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i)
+    if (x.w[i]) r = 32 * i + 32 - __clz(x.w[i]);
+  return r;
+}
+
+// bits [sh, sh + 64) of x (sh >= 0), with zeros above the top limb
+template <int L>
+__device__ __forceinline__ uint64_t bits64(const Limbs<L>& x, int sh) {
+  const int wi = sh >> 5, b = sh & 31;
+  uint32_t lo = 0, mid = 0, hi = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    if (i == wi) lo = x.w[i];
+    if (i == wi + 1) mid = x.w[i];
+    if (i == wi + 2) hi = x.w[i];
+  }
+  uint64_t v = ((uint64_t)mid << 32) | lo;
+  if (b) v = (v >> b) | ((uint64_t)hi << (64 - b));
+  return v;
+}
+
+// any bit of x below position p set (p >= 0)
+template <int L>
+__device__ __forceinline__ bool any_below(const Limbs<L>& x, int p) {
+  bool r = false;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    int lo = 32 * i;
+    if (lo + 32 <= p) r |= x.w[i] != 0;
+    else if (lo < p) r |= (x.w[i] & ((1u << (p - lo)) - 1u)) != 0;
+  }
+  return r;
+}
+
+template <int L>
+__device__ __forceinline__ bool bit_at(const Limbs<L>& x, int p) {
+  bool r = false;
+#pragma unroll
+  for (int i = 0; i < L; ++i)
+    if (p >= 32 * i && p < 32 * i + 32) r = (x.w[i] >> (p - 32 * i)) & 1u;
+  return r;
+}
+
+// x -= c * P (c >= 0 small), modulo 2^(32L)
+template <int L>
+__device__ __forceinline__ void sub_mul_P(Limbs<L>& x, uint32_t c, const uint32_t* P) {
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    uint64_t sub = (uint64_t)c * P[i] + borrow;           // < 2^32 * 2^5 + 2^37
+    uint64_t cur = x.w[i];
+    uint64_t subl = sub & 0xffffffffull;
+    x.w[i] = (uint32_t)(cur - subl);
+    borrow = (sub >> 32) + (cur < subl ? 1 : 0);
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void add_P(Limbs<L>& x, const uint32_t* P) {
+  uint64_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    uint64_t t = (uint64_t)x.w[i] + P[i] + carry;
+    x.w[i] = (uint32_t)t;
+    carry = t >> 32;
+  }
+}
+
+// sign of 2x - P (x two's complement): true if 2x >= P
+template <int L>
+__device__ __forceinline__ bool twice_ge_P(const Limbs<L>& x, const uint32_t* P) {
+  if (x.w[L - 1] >> 31) return false;     // x < 0
+  // compare 2x with P limb by limb from the top
+  Limbs<L> d;
+  uint32_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    d.w[i] = (x.w[i] << 1) | carry;
+    carry = x.w[i] >> 31;
+  }
+  int res = 0;                             // 0 equal, 1 greater, -1 less
+#pragma unroll
+  for (int i = L - 1; i >= 0; --i)
+    if (res == 0 && d.w[i] != P[i]) res = d.w[i] > P[i] ? 1 : -1;
+  return res >= 0;
+}
+
+// true if 2x < -P, i.e. -2x > P (x two's complement)
+template <int L>
+__device__ __forceinline__ bool twice_lt_minus_P(const Limbs<L>& x, const uint32_t* P) {
+  if (!(x.w[L - 1] >> 31)) return false;  // x >= 0
+  Limbs<L> nx;                             // -x
+  uint64_t carry = 1;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    uint64_t t = (uint64_t)(~x.w[i]) + carry;
+    nx.w[i] = (uint32_t)t;
+    carry = t >> 32;
+  }
+  Limbs<L> d;
+  uint32_t c2 = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    d.w[i] = (nx.w[i] << 1) | c2;
+    c2 = nx.w[i] >> 31;
+  }
+  int res = 0;
+#pragma unroll
+  for (int i = L - 1; i >= 0; --i)
+    if (res == 0 && d.w[i] != P[i]) res = d.w[i] > P[i] ? 1 : -1;
+  return res > 0;
+}
+
+// binary64 bits of (-1)^neg mag 2^e, rounded to nearest even
+template <int L>
+__device__ __forceinline__ uint64_t round_to_binary64(const Limbs<L>& mag, uint32_t neg, int e) {
+  const uint64_t sign = (uint64_t)neg << 63;
+  const int nb = bitlen(mag);
+  if (nb == 0) return 0ull;                               // X = 0 gives +0
+  const int E = nb - 1 + e;                               // exponent of the leading bit
+  if (E > 1023) return sign | 0x7ff0000000000000ull;
+  const int lsb = E >= -1022 ? E - 52 : -1074;            // exponent of the last kept bit
+  const int sh = lsb - e;                                 // low bits of mag dropped
+  uint64_t q;
+  if (sh <= 0) {
+    q = bits64(mag, 0) << (-sh);                          // nb - sh <= 53 bits
+  } else {
+    q = sh < 32 * L ? bits64(mag, sh) : 0ull;
+    const bool half = bit_at(mag, sh - 1);
+    const bool sticky = any_below(mag, sh - 1);
+    if (half && (sticky || (q & 1ull))) q += 1ull;
+  }
+  uint64_t b = E >= -1022 ? ((uint64_t)(E + 1022) << 52) + q : q;
+  if (b >= 0x7ff0000000000000ull) b = 0x7ff0000000000000ull;
+  return sign | b;
+}
+
+template <int L, int EPT>
+__global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n,
+                                                          const uint8_t* __restrict__ Y,
+                                                          const int32_t* __restrict__ s,
+                                                          const int32_t* __restrict__ t, double* __restrict__ C,
+                                                          int64_t ldc) {
+  const int64_t i = blockIdx.x;
+  const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
+  if (i >= m || j0 >= n) return;
+  const int Q = T.Q;
+  const int64_t plane = m * n;
+  const uint8_t* yp = Y + i * n + j0;
+  const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
+                   ((plane & 3) == 0);
+  uint64_t acc[EPT][L];
+  float f[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    f[e] = 0.f;
+#pragma unroll
+    for (int l = 0; l < L; ++l) acc[e][l] = 0;
+  }
+  for (int q = 0; q < Q; ++q) {
+    uint32_t d[EPT];
+    if (vec) {
+      uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(yp + q * plane));
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) d[e] = (w >> (8 * e)) & 0xff;
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) d[e] = (j0 + e < n) ? __ldg(yp + q * plane + e) : 0u;
+    }
+    const float im = T.invm[q];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      f[e] = fmaf((float)d[e], im, f[e]);
+#pragma unroll
+      for (int l = 0; l < L; ++l) acc[e][l] += (uint64_t)d[e] * T.Mk[q][l];
+    }
+  }
+  const int32_t si = s[i];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int64_t j = j0 + e;
+    if (j >= n) break;
+    Limbs<L> X;
+    uint64_t carry = 0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      uint64_t v = acc[e][l] + carry;
+      X.w[l] = (uint32_t)v;
+      carry = v >> 32;
+    }
+    const uint32_t qe = (uint32_t)__float2int_rn(f[e]);
+    sub_mul_P(X, qe, T.P);
+    if (twice_ge_P(X, T.P)) sub_mul_P(X, 1u, T.P);
+    else if (twice_lt_minus_P(X, T.P)) add_P(X, T.P);
+    const uint32_t neg = X.w[L - 1] >> 31;
+    if (neg) {
+      uint64_t c = 1;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        uint64_t v = (uint64_t)(~X.w[l]) + c;
+        X.w[l] = (uint32_t)v;
+        c = v >> 32;
+      }
+    }
+    const int ex = -(si + t[j]);
+    const uint64_t bits = round_to_binary64(X, neg, ex);
+    C[i * ldc + j] = __longlong_as_double((long long)bits);
+  }
+}
+
+template <int L>
+cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+                     const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int EPT = 4;
+  dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
+  reconstruct_kernel<L, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+                               const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  switch (T.limbs) {
+    case 3: return launch_L<3>(T, m, n, Y, s, t, C, ldc, st);
+    case 4: return launch_L<4>(T, m, n, Y, s, t, C, ldc, st);
+    case 5: return launch_L<5>(T, m, n, Y, s, t, C, ldc, st);
+    case 6: return launch_L<6>(T, m, n, Y, s, t, C, ldc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace oz

@@ -1,0 +1,321 @@
+// oz_split.cu -- phases 1 (Scale) and 2 (Reduce) of Sec. "Structure".
+//
+// Scale (eq. convert): per vector (row of A, column of B) the exponent e with
+// max|x| in [2^(e-1), 2^e), from the largest |x| bit pattern (for finite
+// doubles the order of |x| is the order of its bits), and the shift
+// s = beta - e (0 for a zero vector).
+//
+// Reduce: a' = trunc(x 2^s) taken straight from the IEEE fields: with the
+// 53-bit significand f and exponent E, x 2^s = f 2^(E - 1075 + s), so a'
+// is f shifted left or right (the right shift truncates toward zero). The
+// residue of |a'| modulo m uses only 32-bit integer work: |a'| < 2^64 is cut
+// into 18-bit pieces p0..p3, y = p0 + p1 (2^18 mod m) + p2 (2^36 mod m) +
+// p3 (2^54 mod m) < 2^32 is congruent to |a'|, and one Barrett step reduces y
+// (Sec. "Around the GEMMs": a one-byte modulus reduces in 32-bit Barrett
+// steps). The sign is applied modulo m and the result mapped to the
+// representative nearest zero, [-floor(m/2), ceil(m/2) - 1].
+//
+// Planes are written K-major, Q planes of nvec_pad x k_pad entries, int8
+// (two's complement, IMMA engine) or bf16 (TC engine; integers below 2^8 are
+// exact in bf16).
+#include <stdint.h>
+
+#include "oz_internal.h"
+
+namespace oz {
+namespace {
+
+constexpr uint64_t kAbsMask = 0x7fffffffffffffffull;
+constexpr uint32_t kM18 = (1u << 18) - 1;
+
+// Shift s from the largest |x| bit pattern.
+__device__ __forceinline__ int32_t shift_from_maxbits(uint64_t mb, int beta) {
+  if (mb == 0) return 0;
+  int eb = (int)(mb >> 52);
+  int e = eb ? eb - 1022 : (64 - __clzll((long long)mb)) - 1074;  // frexp exponent
+  return beta - e;
+}
+
+// Decoded truncated integer of one entry: |a'| and its sign.
+struct Trunc {
+  uint64_t mag;
+  uint32_t neg;
+};
+
+__device__ __forceinline__ Trunc truncate(uint64_t bits, int32_t s) {
+  Trunc t;
+  t.neg = (uint32_t)(bits >> 63);
+  int eb = (int)((bits >> 52) & 0x7ff);
+  uint64_t f = bits & ((1ull << 52) - 1);
+  uint64_t mant = eb ? (f | (1ull << 52)) : f;
+  int sh = (eb ? eb - 1075 : -1074) + s;   // a' = mant * 2^sh, |a'| < 2^beta <= 2^64
+  if (sh >= 0) t.mag = mant << sh;         // sh <= 11 when beta <= 64
+  else t.mag = (-sh) >= 64 ? 0ull : (mant >> (-sh));
+  return t;
+}
+
+// Balanced residue of (+-mag) modulo table entry q.
+__device__ __forceinline__ int32_t residue(const OzTables& T, int q, uint32_t p0, uint32_t p1, uint32_t p2,
+                                           uint32_t p3, uint32_t neg) {
+  uint32_t m = T.m[q];
+  uint32_t y = p0 + p1 * T.c18[q] + p2 * T.c36[q] + p3 * T.c54[q];
+  uint32_t r = mod_barrett(y, m, T.magic[q]);
+  r = neg ? m - r : r;                      // in (0, m]; m maps to 0 below
+  return (int32_t)r - (r >= T.half[q] ? (int32_t)m : 0);
+}
+
+// Exact bf16 bit pattern of an integer |r| < 2^22 (magic-number conversion:
+// the float 1.5*2^23 + r has r in its low significand bits; subtracting
+// 1.5*2^23 leaves r exactly, and an integer below 2^8 needs no more than
+// bf16's 8 significand bits, so the high half of the float is exact).
+__device__ __forceinline__ uint32_t bf16_bits(int32_t r) {
+  float f = __int_as_float(0x4B400000 + r) - 12582912.0f;
+  return __float_as_uint(f) >> 16;
+}
+
+// 64-bit max across a warp.
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Contiguous vectors (rows of A, or of B^T): one CTA of 256 threads per
+// vector. Pass 1 finds the max bits; pass 2 re-reads the row (from L2) and
+// writes 8 consecutive entries per thread per plane.
+// ---------------------------------------------------------------------------
+template <bool kBF16>
+__global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
+                                                         const double* __restrict__ X, int64_t ld,
+                                                         int64_t nvec_pad, int64_t k_pad,
+                                                         int32_t* __restrict__ shifts, void* __restrict__ planes,
+                                                         int32_t* __restrict__ flag) {
+  __shared__ uint64_t red[8];
+  __shared__ int32_t s_sh;
+  const int64_t v = blockIdx.x;
+  const int tid = threadIdx.x;
+  const bool live = v < nvec;
+  const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
+
+  uint64_t mx = 0;
+  uint32_t bad = 0;
+  if (live) {
+    for (int64_t h = tid; h < len; h += 256) {
+      uint64_t b = __ldg(row + h) & kAbsMask;
+      bad |= (uint32_t)((b >> 52) == 0x7ff);
+      mx = b > mx ? b : mx;
+    }
+  }
+  mx = warp_max_u64(mx);
+  bad = __any_sync(0xffffffffu, bad);
+  if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t m = 0, anybad = 0;
+    for (int w = 0; w < 8; ++w) {
+      anybad |= red[w] >> 63;
+      uint64_t x = red[w] & kAbsMask;
+      m = x > m ? x : m;
+    }
+    if (anybad && flag) atomicOr(flag, 1);
+    int32_t s = live ? shift_from_maxbits(anybad ? 0 : m, T.bits) : 0;
+    s_sh = s;
+    if (live) shifts[v] = s;
+  }
+  __syncthreads();
+  const int32_t s = s_sh;
+
+  const int Q = T.Q;
+  const int64_t plane = nvec_pad * k_pad;
+  for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
+    uint32_t p0[8], p1[8], p2[8], p3[8], ng[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      int64_t h = h0 + e;
+      uint64_t b = (live && h < len) ? __ldg(row + h) : 0ull;
+      if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;  // non-finite: flagged above
+      Trunc t = truncate(b, s);
+      p0[e] = (uint32_t)t.mag & kM18;
+      p1[e] = (uint32_t)(t.mag >> 18) & kM18;
+      p2[e] = (uint32_t)(t.mag >> 36) & kM18;
+      p3[e] = (uint32_t)(t.mag >> 54);
+      ng[e] = t.neg;
+    }
+    for (int q = 0; q < Q; ++q) {
+      int32_t r[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) r[e] = residue(T, q, p0[e], p1[e], p2[e], p3[e], ng[e]);
+      const int64_t off = (int64_t)q * plane + v * k_pad + h0;
+      if (kBF16) {
+        uint4 o;
+        o.x = bf16_bits(r[0]) | (bf16_bits(r[1]) << 16);
+        o.y = bf16_bits(r[2]) | (bf16_bits(r[3]) << 16);
+        o.z = bf16_bits(r[4]) | (bf16_bits(r[5]) << 16);
+        o.w = bf16_bits(r[6]) | (bf16_bits(r[7]) << 16);
+        *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
+      } else {
+        uint2 o;
+        o.x = (uint32_t)(r[0] & 0xff) | ((uint32_t)(r[1] & 0xff) << 8) | ((uint32_t)(r[2] & 0xff) << 16) |
+              ((uint32_t)(r[3] & 0xff) << 24);
+        o.y = (uint32_t)(r[4] & 0xff) | ((uint32_t)(r[5] & 0xff) << 8) | ((uint32_t)(r[6] & 0xff) << 16) |
+              ((uint32_t)(r[7] & 0xff) << 24);
+        *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Strided vectors (columns of B, or of A^T).
+// Pass 1: column maxima by atomicMax into colmax (zeroed by the launcher).
+// Block (32 x 8): 32 consecutive columns, 8 warps over rows; each CTA covers
+// 256 rows.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) colmax_kernel(int64_t nvec, int64_t len, const double* __restrict__ X,
+                                                     int64_t ld, uint64_t* __restrict__ colmax,
+                                                     int32_t* __restrict__ flag) {
+  __shared__ uint64_t red[8][32];
+  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t h0 = (int64_t)blockIdx.y * 256;
+  uint64_t mx = 0;
+  uint32_t bad = 0;
+  if (j < nvec) {
+    const uint64_t* col = reinterpret_cast<const uint64_t*>(X) + j;
+    for (int i = threadIdx.y; i < 256; i += 8) {
+      int64_t h = h0 + i;
+      if (h >= len) break;
+      uint64_t b = __ldg(col + h * ld) & kAbsMask;
+      bad |= (uint32_t)((b >> 52) == 0x7ff);
+      mx = b > mx ? b : mx;
+    }
+  }
+  if (bad && flag) atomicOr(flag, 1);
+  red[threadIdx.y][threadIdx.x] = bad ? 0 : mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < nvec) {
+    uint64_t m = 0;
+    for (int w = 0; w < 8; ++w) m = red[w][threadIdx.x] > m ? red[w][threadIdx.x] : m;
+    if (m) atomicMax(reinterpret_cast<unsigned long long*>(colmax + j), (unsigned long long)m);
+  }
+}
+
+__global__ void shifts_from_colmax_kernel(int64_t nvec, const uint64_t* __restrict__ colmax, int beta,
+                                          int32_t* __restrict__ shifts) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nvec) shifts[j] = shift_from_maxbits(colmax[j], beta);
+}
+
+// Pass 2: 64 (h) x 64 (vector) tiles; residues go through shared memory so
+// that the planes, which are K-major per vector, are written along h.
+// Thread t handles vector j = t % 64 and 16 consecutive h.
+template <bool kBF16>
+__global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
+                                                         const double* __restrict__ X, int64_t ld,
+                                                         int64_t nvec_pad, int64_t k_pad,
+                                                         const int32_t* __restrict__ shifts,
+                                                         void* __restrict__ planes) {
+  constexpr int kPitchWords = kBF16 ? 33 : 17;   // 64 entries + 4 bytes of padding per row
+  __shared__ uint32_t tile[2][64 * kPitchWords];
+  const int tid = threadIdx.x;
+  const int jl = tid & 63;
+  const int hg = tid >> 6;                         // 0..3: h = hg*16 .. hg*16+15
+  const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int64_t hbase = (int64_t)blockIdx.y * 64;
+  const int64_t j = j0 + jl;
+  const bool live = j < nvec;
+  const int32_t s = live ? shifts[j] : 0;
+
+  uint32_t p0[16], p1[16], p2[16], p3[16], ng[16];
+  const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    int64_t h = hbase + hg * 16 + e;
+    uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
+    if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
+    Trunc t = truncate(b, s);
+    p0[e] = (uint32_t)t.mag & kM18;
+    p1[e] = (uint32_t)(t.mag >> 18) & kM18;
+    p2[e] = (uint32_t)(t.mag >> 36) & kM18;
+    p3[e] = (uint32_t)(t.mag >> 54);
+    ng[e] = t.neg;
+  }
+  const int Q = T.Q;
+  const int64_t plane = nvec_pad * k_pad;
+  for (int q = 0; q < Q; ++q) {
+    uint32_t* tb = tile[q & 1];
+    int32_t r[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) r[e] = residue(T, q, p0[e], p1[e], p2[e], p3[e], ng[e]);
+    if (kBF16) {
+#pragma unroll
+      for (int w = 0; w < 8; ++w)
+        tb[jl * kPitchWords + hg * 8 + w] = bf16_bits(r[2 * w]) | (bf16_bits(r[2 * w + 1]) << 16);
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        tb[jl * kPitchWords + hg * 4 + w] = (uint32_t)(r[4 * w] & 0xff) | ((uint32_t)(r[4 * w + 1] & 0xff) << 8) |
+                                            ((uint32_t)(r[4 * w + 2] & 0xff) << 16) |
+                                            ((uint32_t)(r[4 * w + 3] & 0xff) << 24);
+    }
+    __syncthreads();
+    // write 64 rows of 64 entries: int8 -> 4 words of 16 B per row, bf16 -> 8
+    constexpr int kChunks = kBF16 ? 8 : 4;          // 16-byte chunks per row
+    for (int c = tid; c < 64 * kChunks; c += 256) {
+      int row = c / kChunks, ch = c % kChunks;
+      if (j0 + row >= nvec_pad) continue;
+      uint4 o;
+      o.x = tb[row * kPitchWords + ch * 4 + 0];
+      o.y = tb[row * kPitchWords + ch * 4 + 1];
+      o.z = tb[row * kPitchWords + ch * 4 + 2];
+      o.w = tb[row * kPitchWords + ch * 4 + 3];
+      const int64_t off = (int64_t)q * plane + (j0 + row) * k_pad + hbase;
+      char* dst = static_cast<char*>(planes) + (off * (kBF16 ? 2 : 1)) + ch * 16;
+      *reinterpret_cast<uint4*>(dst) = o;
+    }
+    // tile[q & 1] is rewritten two moduli later, after the next barrier
+  }
+}
+
+// Rows v in [nvec, nvec_pad) of the strided layout are covered by the grid
+// (grid.x spans nvec_pad), so no separate padding pass is needed.
+
+}  // namespace
+
+cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
+                              int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
+                              int32_t* flag, cudaStream_t st) {
+  if (nvec_pad == 0) return cudaSuccess;
+  dim3 grid((unsigned)nvec_pad);
+  if (bf16)
+    split_rows_kernel<true><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  else
+    split_rows_kernel<false><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
+                              int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
+                              int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+  if (nvec_pad == 0) return cudaSuccess;
+  if (nvec > 0) {
+    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * (size_t)nvec, st);
+    if (e != cudaSuccess) return e;
+    if (len > 0) {
+      dim3 g1((unsigned)((nvec + 31) / 32), (unsigned)((len + 255) / 256));
+      colmax_kernel<<<g1, dim3(32, 8), 0, st>>>(nvec, len, X, ld, colmax, flag);
+    }
+    shifts_from_colmax_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, st>>>(nvec, colmax, t.bits, shifts);
+  }
+  dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+  if (bf16)
+    split_cols_kernel<true><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  else
+    split_cols_kernel<false><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  return cudaGetLastError();
+}
+
+}  // namespace oz

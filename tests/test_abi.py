@@ -1,0 +1,109 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol the
+header declares, and its host-side logic (plans, caps, workspace sizes,
+argument checks) is right. No call here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2609_37693_gb300 as oz
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "oz.h")).read()
+    return sorted(set(re.findall(r"OZ_API\s+[\w\s\*]+?\b(oz_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared_symbols()
+    assert len(names) >= 10
+    lib = ctypes.CDLL(oz.LIBRARY_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(oz.EXPORTED)
+
+
+@pytest.mark.parametrize("q", range(9, 21))
+def test_plan_moduli_caps_and_bits_match_the_oracle(q):
+    for k_hint in (256, 4096, 8192):
+        st, h = oz.oz_plan_create(q, 0, k_hint, oz.OZ_ENGINE_IMMA)
+        mods = oracle.max_product_moduli(q, 239)
+        bmax = min(oracle.beta_max(mods, k_hint), oz.OZ_MAX_BITS)
+        if bmax < 1 or oracle.caps(mods, bmax)[2] < k_hint:
+            assert st == oz.OZ_ERR_K_TOO_LARGE
+            continue
+        assert st == oz.OZ_OK
+        _, info = oz.oz_plan_info(h)
+        assert info["moduli"] == mods
+        assert info["bits"] == bmax
+        assert info["k_max"] == oracle.caps(mods, bmax)[2]
+        oz.oz_plan_destroy(h)
+
+
+def test_paper_int8_plan():
+    st, h = oz.oz_plan_create(16, 53, 8192, oz.OZ_ENGINE_IMMA)
+    assert st == oz.OZ_OK
+    _, info = oz.oz_plan_info(h)
+    assert info["k_max"] == 151647 and max(info["moduli"]) == 239
+    oz.oz_plan_destroy(h)
+    # least Q at beta = 53 (num_moduli = 0): 15 up to K = 836, then 16
+    for k, q in ((800, 15), (836, 15), (837, 16), (151647, 16)):
+        st, h = oz.oz_plan_create(0, 53, k, oz.OZ_ENGINE_IMMA)
+        assert st == oz.OZ_OK
+        assert oz.oz_plan_info(h)[1]["q"] == q
+        oz.oz_plan_destroy(h)
+    # above K_max: refused (eq. caps), as the paper's builder refuses K above kappa_rec
+    assert oz.oz_plan_create(16, 53, 151648, oz.OZ_ENGINE_IMMA)[0] == oz.OZ_ERR_K_TOO_LARGE
+    # Q = 14 at beta = 53 is infeasible at K = 256 (kappa_rec = 4), feasible at beta = 50
+    assert oz.oz_plan_create(14, 53, 256, oz.OZ_ENGINE_IMMA)[0] == oz.OZ_ERR_K_TOO_LARGE
+    assert oz.oz_plan_create(14, 50, 256, oz.OZ_ENGINE_IMMA)[0] == oz.OZ_OK
+
+
+def test_bad_plans_are_refused():
+    assert oz.oz_plan_create(8, 0, 100)[0] == oz.OZ_ERR_UNSUPPORTED
+    assert oz.oz_plan_create(21, 0, 100)[0] == oz.OZ_ERR_UNSUPPORTED
+    assert oz.oz_plan_create(16, 65, 100)[0] == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_plan_create(16, 0, 0)[0] == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_plan_create(16, 0, 100, 7)[0] == oz.OZ_ERR_INVALID_ARG
+
+
+def test_workspace_bytes():
+    p = oz.Plan(16, 0, 1000, oz.OZ_ENGINE_IMMA)
+    m, n, k = 300, 200, 1000
+    ws = p.workspace_bytes(m, n, k)
+    planes = 16 * (512 + 256) * 1024
+    assert ws >= planes + 16 * m * n
+    assert ws < planes + 16 * m * n + 64 * 1024
+    assert p.workspace_bytes(-1, 2, 3) == 0
+
+
+def test_argument_errors_are_caught_on_the_host():
+    p = oz.Plan(16, 0, 1000, oz.OZ_ENGINE_IMMA)
+    h = p.handle
+    fake = 1 << 20  # never dereferenced: every case fails its checks before a launch
+    ws = p.workspace_bytes(8, 8, 8)
+    assert oz.oz_dgemm(h, 0, 0, -1, 8, 8, fake, 8, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(h, 2, 0, 8, 8, 8, fake, 8, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, fake, 7, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, fake, 8, fake, 8, fake, 7, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 200000, fake, 200000, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_K_TOO_LARGE
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, fake, 8, fake, 8, fake, 8, fake, ws - 1, None) == oz.OZ_ERR_WORKSPACE
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, fake, 8, fake, 8, fake, 8, None, ws, None) == oz.OZ_ERR_WORKSPACE
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, None, 8, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(h, 0, 0, 8, 8, 8, fake + 4, 8, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_dgemm(None, 0, 0, 8, 8, 8, fake, 8, fake, 8, fake, 8, fake, ws, None) == oz.OZ_ERR_INVALID_ARG
+    # empty products succeed without touching memory
+    assert oz.oz_dgemm(h, 0, 0, 0, 8, 8, None, 8, None, 8, None, 8, None, 0, None) == oz.OZ_OK
+    assert oz.oz_split(h, 1, 4, 4, fake, 4, 100, 128, fake, fake, None, None, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_split(h, 0, 4, 4, fake, 4, 256, 128, fake, fake, None, None, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_residue_gemm(h, 4, 4, 256, 256, 100, fake, fake, fake, 0, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_reconstruct(h, 4, 4, fake, fake, fake, fake, 3, None) == oz.OZ_ERR_INVALID_ARG
+
+
+def test_status_strings():
+    for s in range(7):
+        assert oz.oz_status_str(s) and oz.oz_status_str(s) != "unknown status"

@@ -1,0 +1,277 @@
+"""Parity of the CUDA path with the CPU oracle, phase by phase and end to end.
+
+Integer work (shifts, residue planes, W mod m) must match bit for bit; the
+FP64 output must match bit for bit too, because both sides round the same
+exact integer once (Sec. "Emulation Problem"). All calls go through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU hosts but never run there
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2609_37693_gb300 as oz  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _stream():
+    return oz._stream_handle()
+
+
+def _split(plan, X, contiguous, nvec, length, ld):
+    nvec_pad = oz.round_up(max(nvec, 1), 256)
+    k_pad = oz.round_up(max(length, 1), 128)
+    elem = torch.bfloat16 if plan.engine == oz.OZ_ENGINE_TC else torch.int8
+    planes = torch.full((plan.q, nvec_pad, k_pad), 7, dtype=elem, device=DEV)  # poison: padding must be zeroed
+    shifts = torch.zeros(max(nvec, 1), dtype=torch.int32, device=DEV)
+    flag = torch.zeros(4, dtype=torch.int32, device=DEV)
+    colmax = torch.zeros(max(nvec, 1), dtype=torch.int64, device=DEV)
+    st = oz.oz_split(plan.handle, contiguous, nvec, length, X.data_ptr(), ld, nvec_pad, k_pad, shifts.data_ptr(),
+                     planes.data_ptr(), flag.data_ptr(), colmax.data_ptr(), _stream())
+    assert st == oz.OZ_OK
+    torch.cuda.synchronize()
+    return shifts.cpu().numpy()[:nvec], planes.float().cpu().numpy().astype(np.int16), flag.cpu().numpy()
+
+
+@pytest.mark.parametrize("engine", [oz.OZ_ENGINE_IMMA])
+@pytest.mark.parametrize("m,k,phi", [(256, 256, 0.5), (300, 1000, 2.0), (1, 1, 1.0), (777, 129, 4.0)])
+def test_split_rows_and_cols_match_oracle(engine, m, k, phi):
+    plan = oz.Plan(16, 0, max(k, 1), engine)
+    A, _ = synth.phi_pair(m, 1, k, phi, seed=m + k)
+    # rows of A (contiguous)
+    s, P, flag = _split(plan, _dev(A), 1, m, k, k)
+    s_ref = oracle.scale(A, plan.bits, axis=1)
+    U_ref = oracle.planes(A, s_ref, plan.moduli, axis=1)
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(P[:, :m, :k], U_ref)
+    assert not P[:, m:, :].any() and not P[:, :, k:].any()
+    assert flag[0] == 0
+    # columns of A^T stored k x m (strided)
+    At = np.ascontiguousarray(A.T)
+    s2, P2, _ = _split(plan, _dev(At), 0, m, k, m)
+    assert np.array_equal(s2, s_ref)
+    assert np.array_equal(P2[:, :m, :k], U_ref)
+    assert not P2[:, m:, :].any() and not P2[:, :, k:].any()
+
+
+def test_split_special_values():
+    plan = oz.Plan(16, 53, 64, oz.OZ_ENGINE_IMMA)
+    A = np.array([[0.0] * 8, [1e-310, -3e-320, 5e-324, 0, 0, 0, 0, -2.5e-308], [1e300, -1e-300, 3.0, 0.5, 2**-1000,
+                                                                                 -7.0, 1.0, 0.0],
+                  [2.0**52, 2.0**53 - 1, -(2.0**52) - 1, 1.0, 0.75, -0.25, 3.5, 1e16]])
+    s, P, _ = _split(plan, _dev(A), 1, 4, 8, 8)
+    s_ref = oracle.scale(A, 53, axis=1)
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(P[:, :4, :8], oracle.planes(A, s_ref, plan.moduli, axis=1))
+
+
+def test_split_flags_nonfinite():
+    plan = oz.Plan(16, 53, 64, oz.OZ_ENGINE_IMMA)
+    A = np.ones((3, 5))
+    A[1, 2] = np.nan
+    _, _, flag = _split(plan, _dev(A), 1, 3, 5, 5)
+    assert flag[0] & 1
+    A[1, 2] = -np.inf
+    _, _, flag = _split(plan, _dev(np.ascontiguousarray(A.T)), 0, 3, 5, 3)
+    assert flag[0] & 1
+
+
+def _residues(plan, A, B):
+    """GPU W mod m (raw epilogue) through oz_split + oz_residue_gemm."""
+    m, k = A.shape
+    n = B.shape[1]
+    m_pad, n_pad, k_pad = oz.round_up(m, 256), oz.round_up(n, 256), oz.round_up(k, 128)
+    U = torch.zeros((plan.q, m_pad, k_pad), dtype=torch.int8, device=DEV)
+    V = torch.zeros((plan.q, n_pad, k_pad), dtype=torch.int8, device=DEV)
+    s = torch.zeros(m, dtype=torch.int32, device=DEV)
+    t = torch.zeros(n, dtype=torch.int32, device=DEV)
+    cm = torch.zeros(max(m, n), dtype=torch.int64, device=DEV)
+    Ad, Bd = _dev(A), _dev(B)
+    st = _stream()
+    assert oz.oz_split(plan.handle, 1, m, k, Ad.data_ptr(), k, m_pad, k_pad, s.data_ptr(), U.data_ptr(), None,
+                       None, st) == oz.OZ_OK
+    assert oz.oz_split(plan.handle, 0, n, k, Bd.data_ptr(), n, n_pad, k_pad, t.data_ptr(), V.data_ptr(), None,
+                       cm.data_ptr(), st) == oz.OZ_OK
+    Y = torch.zeros((plan.q, m, n), dtype=torch.uint8, device=DEV)
+    Yd = torch.zeros((plan.q, m, n), dtype=torch.uint8, device=DEV)
+    assert oz.oz_residue_gemm(plan.handle, m, n, m_pad, n_pad, k_pad, U.data_ptr(), V.data_ptr(), Y.data_ptr(), 1,
+                              st) == oz.OZ_OK
+    assert oz.oz_residue_gemm(plan.handle, m, n, m_pad, n_pad, k_pad, U.data_ptr(), V.data_ptr(), Yd.data_ptr(), 0,
+                              st) == oz.OZ_OK
+    C = torch.zeros((m, n), dtype=torch.float64, device=DEV)
+    assert oz.oz_reconstruct(plan.handle, m, n, Yd.data_ptr(), s.data_ptr(), t.data_ptr(), C.data_ptr(), n,
+                             st) == oz.OZ_OK
+    torch.cuda.synchronize()
+    return Y.cpu().numpy(), Yd.cpu().numpy(), C.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k,q,bits", [(256, 256, 256, 14, 50), (300, 200, 1000, 16, 0), (129, 513, 700, 16, 53),
+                                          (64, 300, 2048, 20, 0)])
+def test_residue_products_and_reconstruct_match_oracle(m, n, k, q, bits):
+    plan = oz.Plan(q, bits, k, oz.OZ_ENGINE_IMMA)
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=q + k)
+    Y, Yd, C = _residues(plan, A, B)
+    C_ref, W_ref, _, _ = oracle.dgemm(A, B, plan.moduli, plan.bits, want_residues=True)
+    assert np.array_equal(Y, W_ref)                    # W mod m, bit for bit
+    # the CRT digits are (W mod m) (P/m)^-1 mod m
+    P = oracle.modulus_product(plan.moduli)
+    for qq, mq in enumerate(plan.moduli):
+        inv = pow((P // mq) % mq, -1, mq)
+        assert np.array_equal(Yd[qq].astype(np.int64), (W_ref[qq].astype(np.int64) * inv) % mq)
+    assert np.array_equal(_bits(C), _bits(C_ref))
+
+
+def _digits(x, moduli):
+    P = oracle.modulus_product(moduli)
+    return [((x % mq) * pow((P // mq) % mq, -1, mq)) % mq for mq in moduli]
+
+
+@pytest.mark.parametrize("q", [14, 16, 20])
+def test_reconstruct_edge_integers(q):
+    """Integers at the window's edges, ties of the final rounding, subnormal and
+    overflowing results, fed as CRT digits straight to the reconstruct phase."""
+    plan = oz.Plan(q, 40, 4, oz.OZ_ENGINE_IMMA)
+    P = oracle.modulus_product(plan.moduli)
+    rng = np.random.default_rng(q)
+    xs = [0, 1, -1, P // 2 - 1, -(P // 2), P // 2 - 2**60, -(P // 2) + 3, (2**53 + 1) << 10, -((2**54 + 2) << 40),
+          3 << 70, (2**53 + 1), -(2**53 + 3)]
+    xs += [int(v) for v in rng.integers(-2**62, 2**62, size=20)]
+    xs += [int(rng.integers(1, 2**62)) << int(rng.integers(0, 60)) for _ in range(20)]
+    xs = [x for x in xs if -(P // 2) <= x < P // 2]
+    exps = [0, -1, 5, -1074, -1100, -1200, 1000, 900, 1023, -1022, -30, 60]
+    n = len(xs)
+    m = len(exps)
+    # C[i][j] = X_j * 2^-(s_i + t_j): take t = 0, s_i = -exps[i]
+    Ydig = np.zeros((plan.q, m, n), dtype=np.uint8)
+    for j, x in enumerate(xs):
+        d = _digits(x, plan.moduli)
+        for qq in range(plan.q):
+            Ydig[qq, :, j] = d[qq]
+    s = np.array([-e for e in exps], dtype=np.int32)
+    t = np.zeros(n, dtype=np.int32)
+    C = torch.zeros((m, n), dtype=torch.float64, device=DEV)
+    Yt, st_, tt = _dev(Ydig), _dev(s), _dev(t)
+    assert oz.oz_reconstruct(plan.handle, m, n, Yt.data_ptr(), st_.data_ptr(), tt.data_ptr(), C.data_ptr(), n,
+                             _stream()) == oz.OZ_OK
+    torch.cuda.synchronize()
+    ref = np.array([oracle.round_scaled(xs, [e] * n) for e in exps])
+    assert np.array_equal(_bits(C.cpu().numpy()), _bits(ref))
+
+
+def _dgemm(plan, A, B, trans_a=False, trans_b=False):
+    Ad, Bd = _dev(A), _dev(B)
+    C = oz.dgemm(Ad, Bd, plan, trans_a=trans_a, trans_b=trans_b)
+    torch.cuda.synchronize()
+    return C.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k,q,bits,phi", [(256, 256, 256, 14, 50, 0.5), (1000, 777, 300, 16, 53, 1.0),
+                                              (300, 1000, 4096, 16, 0, 2.0), (33, 17, 5000, 16, 0, 4.0),
+                                              (1, 1, 1, 16, 53, 1.0), (513, 129, 1, 9, 0, 1.0)])
+def test_dgemm_matches_oracle(m, n, k, q, bits, phi):
+    plan = oz.Plan(q, bits, k, oz.OZ_ENGINE_IMMA)
+    A, B = synth.phi_pair(m, n, k, phi, seed=m * 7 + k)
+    C = _dgemm(plan, A, B)
+    C_ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
+    assert np.array_equal(_bits(C), _bits(C_ref))
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
+def test_dgemm_transposed_operands(ta, tb):
+    m, n, k = 200, 300, 500
+    plan = oz.Plan(16, 0, k, oz.OZ_ENGINE_IMMA)
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=3)
+    C_ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
+    Ain = np.ascontiguousarray(A.T) if ta else A
+    Bin = np.ascontiguousarray(B.T) if tb else B
+    C = _dgemm(plan, Ain, Bin, bool(ta), bool(tb))
+    assert np.array_equal(_bits(C), _bits(C_ref))
+
+
+def test_dgemm_special_operands():
+    plan = oz.Plan(16, 53, 64, oz.OZ_ENGINE_IMMA)
+    A, B = synth.phi_pair(40, 30, 64, 1.0, seed=11)
+    A[3, :] = 0.0
+    B[:, 7] = 0.0
+    A[5, :] *= 1e-300
+    B[:, 9] *= 1e-20
+    A[6, :] *= 1e200
+    B[:, 11] *= 1e150                       # row 6 x column 11 overflows to +-inf
+    A[8, 3] = 2.0**-1074
+    C = _dgemm(plan, A, B)
+    C_ref = oracle.dgemm(A, B, plan.moduli, 53)
+    assert np.isinf(C_ref[6, 11])
+    assert np.array_equal(_bits(C), _bits(C_ref))
+
+
+def test_dgemm_lossless_is_fl_of_exact():
+    """Integer operands convert losslessly, so C = fl(AB) (Sec. 'Emulation Problem')."""
+    rng = np.random.default_rng(2)
+    A = rng.integers(-2**20, 2**20, size=(64, 200)).astype(np.float64)
+    B = rng.integers(-2**20, 2**20, size=(200, 48)).astype(np.float64)
+    plan = oz.Plan(16, 53, 200, oz.OZ_ENGINE_IMMA)
+    C = _dgemm(plan, A, B)
+    Ai = A.astype(object)
+    Bi = B.astype(object)
+    exact = Ai.dot(Bi)
+    ref = np.array([[float(v) for v in row] for row in exact])   # int -> float rounds to nearest even
+    assert np.array_equal(_bits(C), _bits(ref))
+
+
+def test_dgemm_k_zero_and_empty():
+    plan = oz.Plan(16, 0, 16, oz.OZ_ENGINE_IMMA)
+    A = torch.zeros((5, 0), dtype=torch.float64, device=DEV)
+    B = torch.zeros((0, 3), dtype=torch.float64, device=DEV)
+    C = torch.full((5, 3), 9.0, dtype=torch.float64, device=DEV)
+    oz.dgemm(A, B, plan, out=C)
+    torch.cuda.synchronize()
+    assert torch.all(C == 0)
+    E = oz.dgemm(torch.zeros((0, 4), dtype=torch.float64, device=DEV),
+                 torch.zeros((4, 3), dtype=torch.float64, device=DEV), plan)
+    assert E.shape == (0, 3)
+
+
+def test_dgemm_reports_nonfinite():
+    plan = oz.Plan(16, 0, 64, oz.OZ_ENGINE_IMMA)
+    A, B = synth.phi_pair(20, 20, 64, 1.0, seed=1)
+    A[4, 5] = np.nan
+    Ad, Bd = _dev(A), _dev(B)
+    ws = oz.workspace(plan, 20, 20, 64)
+    oz.dgemm(Ad, Bd, plan, ws=ws)
+    assert oz.query_status(ws) == oz.OZ_ERR_NONFINITE
+    A[4, 5] = 1.0
+    oz.dgemm(_dev(A), Bd, plan, ws=ws)
+    assert oz.query_status(ws) == oz.OZ_OK
+
+
+def test_full_size_8192_sampled_entries_and_error():
+    """m = n = k = 8192, Q = 16 (the headline size): sampled entries equal the
+    oracle's bit for bit, and the error against the exact product is within
+    2u (|A||B|)_ij at phi = 0.5."""
+    n = 8192
+    plan = oz.Plan(16, 0, n, oz.OZ_ENGINE_IMMA)
+    assert plan.bits == 55
+    A, B = synth.phi_pair(n, n, n, 0.5, seed=0)
+    C = _dgemm(plan, A, B)
+    rows, cols = synth.sample_entries(n, n, 2048, seed=5)
+    ref = oracle.dgemm_entries(A, B, plan.moduli, plan.bits, rows, cols)
+    assert np.array_equal(_bits(C[rows, cols]), _bits(ref))
+    err, ab = oracle.exact_error(A, B, C, rows, cols)
+    assert np.max(err / (2.0**-53 * ab)) <= 2.0
