@@ -1,0 +1,389 @@
+"""Benchmark: emulated FP64 GEMM (Ozaki-II, INT8 residue path) on GB300.
+
+One step = one full emulated product C = A B at m = n = k = 8192 (Scale,
+Reduce, the Q residue GEMMs with their epilogue, Reconstruct), inputs resident
+in HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n 8192] [--q 16] [--bits 0] [--phi 0.5] [--engine auto|imma|tc]
+
+--impl reference times the CPU oracle (the plain restatement of the method)
+on the host cores, on a bounded sample of the same workload.
+
+Under torchrun (N > 1) every rank runs its own independent product (weak
+scaling, no collective on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "emulated-FP64 GEMM TFLOP/s at m=n=k=8192 vs cuBLAS DGEMM, at err ≤2u|A||B|"
+UNIT = "TFLOP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--q", type=int, default=16)
+    ap.add_argument("--bits", type=int, default=0)
+    ap.add_argument("--phi", type=float, default=0.5)
+    ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc"])
+    ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def workload_name(n, phi, q, bits):
+    return (f"emulated dgemm m=n=k={n}, entries U(-0.5,0.5)*exp({phi}*N(0,1)) seed 0 (rank r: seed r), "
+            f"INT8 residue path Q={q} moduli<=239, beta={bits}")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only place bench.py runs the oracle)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(A, B, n, q, bits, seconds):
+    """Time the oracle on a bounded sample of entries of the same product;
+    returns (TFLOP/s of the emulated product, entries, seconds, threads)."""
+    import oracle
+    oracle.build()
+    mods = oracle.max_product_moduli(q, 239)
+    rng = np.random.default_rng(123)
+    count = 64
+    done, elapsed = 0, 0.0
+    while elapsed < seconds:
+        r = rng.integers(0, n, size=count)
+        c = rng.integers(0, n, size=count)
+        t0 = time.perf_counter()
+        oracle.dgemm_entries(A, B, mods, bits, r, c)
+        dt = time.perf_counter() - t0
+        done += count
+        elapsed += dt
+        if dt < seconds / 8:
+            count *= 2
+    flops = 2.0 * n * done          # each entry stands for 2k flops of the emulated product
+    return flops / elapsed / 1e12, done, elapsed, oracle.threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import synth
+    n = args.n
+    A, B = synth.phi_pair(n, n, n, args.phi, seed=0)
+    import oracle
+    bits = args.bits or oracle.beta_max(oracle.max_product_moduli(args.q, 239), n)
+    per_step = max(1.0, min(args.cpu_sample_s, 20.0) / max(args.steps, 1))
+    for _ in range(args.warmup):
+        oracle_rate(A, B, n, args.q, bits, per_step / 4)
+    vals, ents, secs = [], 0, 0.0
+    threads = oracle.threads()
+    for _ in range(args.steps):
+        v, e, s, threads = oracle_rate(A, B, n, args.q, bits, per_step)
+        vals.append(v)
+        ents += e
+        secs += s
+    value = 2.0 * n * ents / secs / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": workload_name(n, args.phi, args.q, bits),
+                   "m": n, "n": n, "k": n, "q": args.q, "bits": bits, "phi": args.phi},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{ents} entries of C ({n}x{n}), each a full k={n} oracle evaluation "
+                                   f"(scale, residues, {args.q} int64 dot products, CRT, rounding)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our path
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2609_37693_gb300 as oz
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    engine = {"auto": oz.OZ_ENGINE_AUTO, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC}[args.engine]
+    plan = oz.Plan(args.q, args.bits, n, engine)
+    A_h, B_h = synth.phi_pair(n, n, n, args.phi, seed=rank)
+    A = torch.from_numpy(A_h).to(dev)
+    B = torch.from_numpy(B_h).to(dev)
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ws = oz.workspace(plan, n, n, n, dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = oz._stream_handle(stream)
+
+    def step():
+        st = oz.oz_dgemm(plan.handle, 0, 0, n, n, n, A.data_ptr(), n, B.data_ptr(), n, C.data_ptr(), n,
+                         ws.data_ptr(), ws.numel(), sh)
+        if st != oz.OZ_OK:
+            raise RuntimeError(f"oz_dgemm: {oz.oz_status_str(st)}")
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    st = oz.query_status(ws, stream)
+    if st != oz.OZ_OK:
+        raise RuntimeError(f"status after warm-up: {oz.oz_status_str(st)}")
+
+    # The paper's gate for a timed call (Table tab:setup): relative Frobenius
+    # difference from native DGEMM below 1e-12. Native DGEMM is also the
+    # throughput comparison.
+    dgemm_tflops = None
+    rel_frob = None
+    if not args.no_dgemm:
+        Cn = A @ B
+        torch.cuda.synchronize()
+        rel_frob = (torch.linalg.norm(C - Cn) / torch.linalg.norm(Cn)).item()
+        ts = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.matmul(A, B, out=Cn)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        dgemm_tflops = 2.0 * n**3 / (min(ts) * 1e-3) / 1e12
+        del Cn
+        if rel_frob > 1e-12:
+            raise RuntimeError(f"result differs from native DGEMM by {rel_frob:.3e} (relative Frobenius)")
+
+    # ---- timed region: K steps of oz_dgemm, inputs (1 GiB) larger than L2 ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = t.item()
+    ms_per_step = elapsed_ms / args.steps
+    flops = 2.0 * n**3
+    value = world * flops * args.steps / (elapsed_ms * 1e-3) / 1e12
+
+    # ---- per-phase times through the phase entry points (same kernels) ----
+    m_pad, n_pad, k_pad = oz.round_up(n, 256), oz.round_up(n, 256), oz.round_up(n, 128)
+    _, lay = oz.oz_workspace_layout(plan.handle, n, n, n)
+    base = ws.data_ptr()
+    phase_ms = {"split_a": 0.0, "split_b": 0.0, "gemm": 0.0, "reconstruct": 0.0}
+    reps = max(3, min(args.steps, 10))
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        oz.oz_split(plan.handle, 1, n, n, A.data_ptr(), n, m_pad, k_pad, base + lay["s"], base + lay["u"],
+                    base + lay["flag"], None, sh)
+        ev[1].record(stream)
+        oz.oz_split(plan.handle, 0, n, n, B.data_ptr(), n, n_pad, k_pad, base + lay["t"], base + lay["v"],
+                    base + lay["flag"], base + lay["colmax"], sh)
+        ev[2].record(stream)
+        oz.oz_residue_gemm(plan.handle, n, n, m_pad, n_pad, k_pad, base + lay["u"], base + lay["v"],
+                           base + lay["y"], 0, sh)
+        ev[3].record(stream)
+        oz.oz_reconstruct(plan.handle, n, n, base + lay["y"], base + lay["s"], base + lay["t"], C.data_ptr(), n,
+                          sh)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for i, key in enumerate(phase_ms):
+            phase_ms[key] += ev[i].elapsed_time(ev[i + 1]) / reps
+    phase_sum = sum(phase_ms.values())
+
+    # ---- e2e: host buffers through the public call, copies inside the timed region ----
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        A.copy_(A_pin, non_blocking=True)
+        B.copy_(B_pin, non_blocking=True)
+        step()
+        C_pin.copy_(C, non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_value = world * flops / (e2e_ms * 1e-3) / 1e12
+
+    # ---- roofline of the dominant kernel (the residue GEMMs) ----
+    peaks = load_peaks()
+    gemm_ops = 2.0 * plan.q * n**3                       # algorithmic low-precision ops per launch
+    gemm_s = phase_ms["gemm"] * 1e-3
+    achieved = gemm_ops / gemm_s / 1e12
+    if plan.engine == oz.OZ_ENGINE_TC:
+        peak = peaks.get("bf16_tflops", 1900.0)
+        peak_src = "bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    else:
+        peak = 167.0
+        peak_src = "INT8 dense on B300 as stated in the paper (Sec. 'Speedup'); no measured INT8 peak exists"
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "residue GEMM (+fused epilogue)",
+                "peak_source": peak_src}
+    hbm = peaks.get("hbm_gbs", 6768.8)
+    bytes_split = 8.0 * 2 * n * n + plan.q * 2.0 * n * n * (2 if plan.engine == oz.OZ_ENGINE_TC else 1)
+    bytes_rec = plan.q * n * n + 8.0 * n * n
+    gemm_peak_s = gemm_ops / (peak * 1e12)
+    t_roof = gemm_peak_s + (bytes_split + bytes_rec + plan.q * n * n) / (hbm * 1e9)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1:
+            v, ents, secs, thr = oracle_rate(A_h, B_h, n, plan.q, plan.bits, args.cpu_sample_s)
+            cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                   "sample": f"{ents} sampled entries of the same {n}^3 product, each a full oracle evaluation "
+                             f"({secs:.1f} s on the host cores)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8" if plan.engine != oz.OZ_ENGINE_TC else "bf16",
+            "data": "synthetic",
+            "config": {"workload": workload_name(n, args.phi, plan.q, plan.bits),
+                       "m": n, "n": n, "k": n, "q": plan.q, "bits": plan.bits, "phi": args.phi,
+                       "engine": {1: "imma", 2: "tc"}[plan.engine], "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (A and B 512 MiB each); no flush",
+                       "cublas_dgemm_tflops": dgemm_tflops, "speedup_vs_cublas_dgemm":
+                           (value / world / dgemm_tflops) if dgemm_tflops else None,
+                       "rel_frobenius_vs_dgemm": rel_frob,
+                       "phase_ms": phase_ms, "phase_share": {k: v / phase_sum for k, v in phase_ms.items()},
+                       "roofline_time_ms": t_roof * 1e3, "roofline_step_frac": t_roof * 1e3 / ms_per_step},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
+                    "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms},
+            "gpu_launches": oz.launches_per_dgemm(False, False) * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,6 +109,15 @@ OZ_API void oz_plan_destroy(oz_plan plan);
 OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
 
 /*
+ * oz_workspace_layout -- where oz_dgemm puts each part of its workspace, so
+ * that the phase entry points below can run the same product step by step.
+ * out[0..9] receives byte offsets of: flag (int32[4]), s (int32[m]),
+ * t (int32[n]), colmax (uint64[max(m, n)]), U planes, V planes, Y residues
+ * (uint8 Q x m x n), then m_pad, n_pad, k_pad (entries, not bytes).
+ */
+OZ_API oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t* out);
+
+/*
  * oz_dgemm -- C = op(A) op(B) (Sec. "Emulation Problem"; five phases of
  * Sec. "Structure"). No alpha/beta: C is overwritten.
  *   m, n, k >= 0 (an empty product writes nothing; k = 0 writes zeros).

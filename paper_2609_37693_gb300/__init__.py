@@ -34,7 +34,8 @@ OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
 OZ_MAX_BITS = 64
 
-EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_dgemm",
+EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
+            "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str")
 
 
@@ -46,8 +47,11 @@ class OzError(RuntimeError):
 
 def _load_library():
     path = _build.LIB
-    if not os.path.exists(path):
-        path = _build.build()
+    try:
+        path = _build.build()          # no-op unless a source is newer than the library
+    except RuntimeError:
+        if not os.path.exists(path):
+            raise
     lib = ctypes.CDLL(path)
     P, I64, I32, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
     sig = {
@@ -56,6 +60,7 @@ def _load_library():
                                ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_uint32)]),
         "oz_plan_destroy": (None, [P]),
         "oz_workspace_bytes": (SZ, [P, I64, I64, I64]),
+        "oz_workspace_layout": (I32, [P, I64, I64, I64, ctypes.POINTER(I64)]),
         "oz_dgemm": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
         "oz_query_status": (I32, [P, P]),
         "oz_split": (I32, [P, I32, I64, I64, P, I64, I64, I64, P, P, P, P, P]),
@@ -107,6 +112,16 @@ def oz_plan_destroy(plan) -> None:
 
 def oz_workspace_bytes(plan, m: int, n: int, k: int) -> int:
     return int(_lib.oz_workspace_bytes(plan, int(m), int(n), int(k)))
+
+
+def oz_workspace_layout(plan, m: int, n: int, k: int):
+    """Returns (status, dict of byte offsets flag/s/t/colmax/u/v/y and m_pad/n_pad/k_pad)."""
+    out = (ctypes.c_int64 * 10)()
+    st = _lib.oz_workspace_layout(plan, int(m), int(n), int(k), out)
+    if st != OZ_OK:
+        return st, None
+    keys = ("flag", "s", "t", "colmax", "u", "v", "y", "m_pad", "n_pad", "k_pad")
+    return st, {key: int(v) for key, v in zip(keys, out)}
 
 
 def oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream) -> int:
@@ -203,6 +218,14 @@ def dgemm(A, B, plan: Plan | None = None, trans_a: bool = False, trans_b: bool =
                   ws.numel(), _stream_handle(stream))
     _check(st, "oz_dgemm")
     return C
+
+
+def launches_per_dgemm(trans_a: bool = False, trans_b: bool = False) -> int:
+    """Kernels one oz_dgemm launches: a row split is one kernel, a column split
+    three (column maxima, shifts, split), then the GEMM and the reconstruct."""
+    a = 3 if trans_a else 1
+    b = 1 if trans_b else 3
+    return a + b + 2
 
 
 def query_status(ws, stream=None) -> int:

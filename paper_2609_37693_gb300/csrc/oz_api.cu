@@ -49,6 +49,17 @@ extern "C" size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t
   return L.total;
 }
 
+extern "C" oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t* out) {
+  Layout L;
+  if (!out || !make_layout(plan, m, n, k, &L)) return OZ_ERR_INVALID_ARG;
+  const size_t v[7] = {L.flag, L.s, L.t, L.colmax, L.u, L.v, L.y};
+  for (int i = 0; i < 7; ++i) out[i] = (int64_t)v[i];
+  out[7] = L.m_pad;
+  out[8] = L.n_pad;
+  out[9] = L.k_pad;
+  return OZ_OK;
+}
+
 extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
                               const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
                               void* workspace, size_t workspace_bytes, void* stream) {
