@@ -182,6 +182,40 @@ OZ_API oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_p
 OZ_API oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                          const int32_t* t, double* C, int64_t ldc, void* stream);
 
+/* ---- Allocation-free variant. ---- */
+
+/* Bytes of the device scratch array built into the library (per GPU). */
+#define OZ_STATIC_SCRATCH_BYTES (32ull << 20)
+
+/*
+ * oz_dgemm_static -- the product of oz_dgemm for callers that cannot allocate
+ * device memory, so cannot pass a workspace. The paper has no counterpart;
+ * this exists for callers such as a BLAS-style dgemm front end, whose
+ * signature has no workspace argument, or code running under a host program
+ * that owns every device allocation through its own pool and forbids
+ * cudaMalloc from libraries. Arguments and result are those of oz_dgemm
+ * without the workspace pair.
+ *   Scratch: a file-scope __device__ array of OZ_STATIC_SCRATCH_BYTES bytes
+ *   inside liboz.so. Every GPU that loads the library holds that memory until
+ *   the process exits. A product fits when oz_workspace_bytes(plan, m, n, k)
+ *   <= OZ_STATIC_SCRATCH_BYTES (about 800^3 at Q = 16); larger sizes return
+ *   OZ_ERR_WORKSPACE before any launch.
+ *   Allocation: none. No cudaMalloc, cudaFree or allocating library routine
+ *   is called, here or in the phases it runs.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   with cudaGetSymbolAddress, with that device current, and caches it; make
+ *   that first call before any stream capture on that device.
+ *   Sharing: every call on a device uses the same array and leaves its
+ *   contents behind; each call clears what must start at zero. Two calls that
+ *   overlap on the GPU (other streams, other host threads) race on the array
+ *   and give undefined results: serialise them.
+ *   Non-finite input is not reported (oz_query_status needs a workspace
+ *   pointer); C is then unspecified.
+ */
+OZ_API oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                                 const double* A, int64_t lda, const double* B, int64_t ldb,
+                                 double* C, int64_t ldc, void* stream);
+
 /* Short English description of a status code (static string). */
 OZ_API const char* oz_status_str(oz_status status);
 

@@ -33,10 +33,12 @@ OZ_ENGINE_TC = 2
 OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
 OZ_MAX_BITS = 64
+OZ_STATIC_SCRATCH_BYTES = 32 << 20
 
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
             "oz_dgemm",
-            "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str")
+            "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
+            "oz_dgemm_static")
 
 
 class OzError(RuntimeError):
@@ -67,6 +69,7 @@ def _load_library():
         "oz_residue_gemm": (I32, [P, I64, I64, I64, I64, I64, P, P, P, I32, P]),
         "oz_reconstruct": (I32, [P, I64, I64, P, P, P, P, I64, P]),
         "oz_status_str": (ctypes.c_char_p, [I32]),
+        "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -127,6 +130,14 @@ def oz_workspace_layout(plan, m: int, n: int, k: int):
 def oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream) -> int:
     return _lib.oz_dgemm(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb), C,
                          int(ldc), workspace, int(workspace_bytes), stream)
+
+
+def oz_dgemm_static(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
+    """oz_dgemm without a workspace argument: the library's built-in device
+    scratch array (OZ_STATIC_SCRATCH_BYTES per GPU) serves as the workspace, for
+    callers that cannot allocate device memory. Calls overlapping on the GPU race."""
+    return _lib.oz_dgemm_static(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb),
+                                C, int(ldc), stream)
 
 
 def oz_query_status(workspace, stream) -> int:

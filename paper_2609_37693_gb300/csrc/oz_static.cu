@@ -1,0 +1,58 @@
+// oz_static.cu -- oz_dgemm_static: oz_dgemm with its workspace in a scratch
+// array built into the library, for callers that cannot allocate device
+// memory (a BLAS-style dgemm interface has no workspace argument; some host
+// programs own every device allocation themselves). The paper has no
+// counterpart to this entry point.
+#include <stdint.h>
+
+#include <atomic>
+
+#include "oz_internal.h"
+
+namespace {
+
+// One array per GPU that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_oz_scratch[OZ_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
+
+// In host code g_oz_scratch names a host-side stand-in, not device memory:
+// the device address comes from cudaGetSymbolAddress, looked up once per
+// device with that device current.
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices) {
+    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (p) {
+      *out = p;
+      return cudaSuccess;
+    }
+  }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_oz_scratch);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices) g_scratch_ptr[dev].store(p, std::memory_order_release);
+  *out = p;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                                     const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                                     int64_t ldc, void* stream) {
+  if (!plan || m < 0 || n < 0 || k < 0) return OZ_ERR_INVALID_ARG;
+  const size_t need = oz_workspace_bytes(plan, m, n, k);
+  if (need == 0) return OZ_ERR_INVALID_ARG;
+  if (need > (size_t)OZ_STATIC_SCRATCH_BYTES) return OZ_ERR_WORKSPACE;
+  if (m == 0 || n == 0) return oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, nullptr, 0, stream);
+  void* ws = nullptr;
+  if (scratch_address(&ws) != cudaSuccess || !ws) return OZ_ERR_CUDA;
+  // oz_dgemm clears the status flag and the column-maximum words it reuses;
+  // every plane and residue it reads was written earlier in the same call.
+  return oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, ws, (size_t)OZ_STATIC_SCRATCH_BYTES,
+                  stream);
+}
