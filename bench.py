@@ -288,7 +288,7 @@ def run_ours(args, rank, world, local):
                     base + lay["flag"], base + lay["colmax"], sh)
         ev[2].record(stream)
         oz.oz_residue_gemm(plan.handle, n, n, m_pad, n_pad, k_pad, base + lay["u"], base + lay["v"],
-                           base + lay["y"], 0, sh)
+                           base + lay["y"], 0, base + lay["flag"], sh)
         ev[3].record(stream)
         oz.oz_reconstruct(plan.handle, n, n, base + lay["y"], base + lay["s"], base + lay["t"], C.data_ptr(), n,
                           sh)

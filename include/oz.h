@@ -135,7 +135,7 @@ OZ_API oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int
 /*
  * oz_query_status -- wait for the stream, then report OZ_ERR_NONFINITE if the
  * last oz_dgemm on this workspace met a NaN or Inf, OZ_ERR_CUDA if the stream
- * has a CUDA error, else OZ_OK.
+ * has a CUDA error or a bounded device wait of that call ran out, else OZ_OK.
  */
 OZ_API oz_status oz_query_status(void* workspace, void* stream);
 
@@ -169,9 +169,12 @@ OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t le
  *   raw != 0: Y[q][i][j] = W mod m_q in [0, m_q) (the paper's epilogue value).
  * U, V: planes from oz_split (m_pad x k_pad and n_pad x k_pad per modulus),
  * Y: uint8, Q planes of m x n (row pitch n). Device pointers.
+ * flag (may be NULL): device int32; the TC engine sets bit 1 if one of its
+ * bounded waits ran out (the kernel then stops early and Y is unspecified).
+ * The TC engine needs U and V 128-byte aligned.
  */
 OZ_API oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                          const void* U, const void* V, uint8_t* Y, int raw, void* stream);
+                          const void* U, const void* V, uint8_t* Y, int raw, int32_t* flag, void* stream);
 
 /*
  * oz_reconstruct -- phase 5 (Sec. "Around the GEMMs", Reconstruct): from the

@@ -66,7 +66,7 @@ def _load_library():
         "oz_dgemm": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
         "oz_query_status": (I32, [P, P]),
         "oz_split": (I32, [P, I32, I64, I64, P, I64, I64, I64, P, P, P, P, P]),
-        "oz_residue_gemm": (I32, [P, I64, I64, I64, I64, I64, P, P, P, I32, P]),
+        "oz_residue_gemm": (I32, [P, I64, I64, I64, I64, I64, P, P, P, I32, P, P]),
         "oz_reconstruct": (I32, [P, I64, I64, P, P, P, P, I64, P]),
         "oz_status_str": (ctypes.c_char_p, [I32]),
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
@@ -149,9 +149,9 @@ def oz_split(plan, contiguous, nvec, length, X, ld, nvec_pad, k_pad, shifts, pla
                          shifts, planes, flag, colmax, stream)
 
 
-def oz_residue_gemm(plan, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, stream) -> int:
+def oz_residue_gemm(plan, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, flag, stream) -> int:
     return _lib.oz_residue_gemm(plan, int(m), int(n), int(m_pad), int(n_pad), int(k_pad), U, V, Y, int(raw),
-                                stream)
+                                flag, stream)
 
 
 def oz_reconstruct(plan, m, n, Y, s, t, C, ldc, stream) -> int:

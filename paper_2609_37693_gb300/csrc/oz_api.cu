@@ -100,9 +100,9 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
               : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // GEMMs + epilogue
-  if (bf16) return OZ_ERR_UNSUPPORTED;
-  e = oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
-                           static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, st);
+  e = bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
+           : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
+                                  static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // Reconstruct
   e = oz::launch_reconstruct(T, m, n, Y, s, t, C, ldc, st);
@@ -115,6 +115,7 @@ extern "C" oz_status oz_query_status(void* workspace, void* stream) {
   if (cudaStreamSynchronize(st) != cudaSuccess) return OZ_ERR_CUDA;
   int32_t flag = 0;
   if (cudaMemcpy(&flag, workspace, sizeof flag, cudaMemcpyDeviceToHost) != cudaSuccess) return OZ_ERR_CUDA;
+  if (flag & 2) return OZ_ERR_CUDA;   // a bounded device wait ran out
   return (flag & 1) ? OZ_ERR_NONFINITE : OZ_OK;
 }
 
@@ -141,7 +142,7 @@ extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_
 
 extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad,
                                      int64_t k_pad, const void* U, const void* V, uint8_t* Y, int raw,
-                                     void* stream) {
+                                     int32_t* flag, void* stream) {
   if (!plan || m < 0 || n < 0) return OZ_ERR_INVALID_ARG;
   if (m_pad < m || n_pad < n || m_pad % oz::kPadRows || n_pad % oz::kPadRows || k_pad <= 0 || k_pad % oz::kPadK)
     return OZ_ERR_INVALID_ARG;
@@ -149,7 +150,8 @@ extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t
   if (m == 0 || n == 0) return OZ_OK;
   if (!U || !V || !Y || !aligned(U, 16) || !aligned(V, 16)) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (plan->engine == OZ_ENGINE_TC) return OZ_ERR_UNSUPPORTED;
+  if (plan->engine == OZ_ENGINE_TC)
+    return cuda_status(oz::launch_gemm_tc(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
   return cuda_status(oz::launch_gemm_imma(plan->tab, m, n, k_pad, static_cast<const int8_t*>(U), m_pad * k_pad,
                                           static_cast<const int8_t*>(V), n_pad * k_pad, Y, raw ? 1 : 0, st));
 }

@@ -1,0 +1,467 @@
+// oz_gemm_tc.cu -- phases 3 (GEMMs) and 4 (Epilogue) of Sec. "Structure" on
+// the 5th-generation tensor cores: W_q = U_q V_q^T with the residues held
+// exactly in BF16 (integers of magnitude <= 119 need 7 significand bits), one
+// tcgen05.mma.kind::f16 stream into FP32 accumulators in tensor memory.
+//
+// Exactness (Sec. "Exactness Constraints and K_max", eq. ov-accgen with the
+// FP32 bound Lambda = 2^24): one FP32 accumulator may sum K_t products of
+// magnitude <= 119^2 only while K_t 119^2 <= 2^24, i.e. K_t <= 1184. The inner
+// dimension is therefore cut into slabs of 1024 terms (Sec. "Slabs"); each
+// slab's accumulator is drained and reduced modulo m into a running residue
+// (order R>C, eq. ov-comrtc: the running residue and the slab sum stay below
+// 2^24). Whether the tensor core adds such integers without rounding is the
+// undocumented behaviour of Sec. "Exactness May Rely on Undocumented
+// Accumulation"; the parity tests drive every accumulator to 1024 * 119^2 and
+// compare bit for bit with exact integer products.
+//
+// Kernel: persistent, one CTA per SM, 10 warps.
+//   warp 0      TMA producer: 128 x 64 (A) and 256 x 64 (B) bf16 tiles, 128-byte
+//               swizzle, 4-stage ring of mbarrier-tracked shared-memory stages;
+//   warp 1      allocates all 512 TMEM columns (two 128 x 256 FP32
+//               accumulators) and, from one thread, issues tcgen05.mma
+//               (M = 128, N = 256, K = 16) and tcgen05.commit;
+//   warps 2..9  epilogue: drain an accumulator with tcgen05.ld while the MMAs
+//               fill the other, reduce each slab sum into a running residue
+//               kept as one byte per entry in registers, and at the end of a
+//               tile write the CRT digit (or W mod m) of each entry.
+// Every wait is bounded (about 2 s of %globaltimer); a wait that runs out sets
+// bit 1 of the status word, makes every role stop issuing work, waits (again
+// bounded) for the copies and products already in flight, frees the tensor
+// memory and returns.
+#include <cuda.h>
+#include <stdint.h>
+
+#include "oz_internal.h"
+
+namespace oz {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;        // BK in bf16 entries = 128 bytes
+constexpr int STAGES = 4;
+constexpr int kSlabBlocks = 16;                    // k-blocks per FP32 slab: 1024 terms
+constexpr int kBand = 8;                           // n-tiles per band of the tile order
+constexpr int A_BYTES = BM * BK * 2;               // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;               // 32 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;     // 48 KiB
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr int kTmemCols = 512;
+constexpr int kBarBytes = 256;
+constexpr int kSmemBytes = STAGES * STAGE_BYTES + kBarBytes + 1024;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+// Instruction descriptor of tcgen05.mma.kind::f16: D = F32 (bits 4-5 = 1),
+// A = B = BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- mbarrier ----
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity. Returns false if the CTA
+// is aborting or the wait ran out (then it records the failure).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        if (status) atomicOr(status, 2);
+        return false;
+      }
+    }
+  }
+}
+
+// Wait used on the way out: bounded, ignores the abort flag.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_timer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer() - t0 > kTimeoutNs) return;
+  }
+}
+
+// ---- TMA ----
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// ---- tcgen05 ----
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit words: thread i gets row (lane base + i),
+// columns taddr.col .. +31.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
+// leading offset 16 B (unused for this layout), stride 1024 B between groups of
+// eight 128-byte rows, descriptor version 1 (bit 46), swizzle mode 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct Coord {
+  int q, tm, tn;
+};
+
+// Tile order: modulus by modulus; within a modulus, bands of kBand n-tiles;
+// within a band, row-major over (tm, tn), so a wave of CTAs shares the B strip
+// of its band and each A panel across kBand neighbours (Sec. "Tile order").
+__device__ __forceinline__ Coord tile_coord(int t, int tiles_m, int tiles_n) {
+  const int per_q = tiles_m * tiles_n;
+  Coord c;
+  c.q = t / per_q;
+  const int r = t - c.q * per_q;
+  const int band = r / (tiles_m * kBand);
+  const int rb = r - band * tiles_m * kBand;
+  const int bw = min(kBand, tiles_n - band * kBand);
+  c.tm = rb / bw;
+  c.tn = band * kBand + (rb - c.tm * bw);
+  return c;
+}
+
+struct Params {
+  int m, n, tiles_m, tiles_n, num_tiles, kblocks, m_pad, n_pad, raw;
+  uint8_t* Y;
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ OzTables T, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_base = smem_u32(smem_raw);
+  const uint32_t base = (raw_base + 1023u) & ~1023u;                  // 1024-aligned stages
+  uint8_t* gbase = smem_raw + (base - raw_base);
+  const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+  // barriers: full[STAGES], empty[STAGES], tfull[2], tempty[2]
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), kEpiWarps * 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  const int nslabs = (p.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[STAGES];
+      bool outstanding[STAGES];
+      for (int i = 0; i < STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+        const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+        const int ya = c.q * p.m_pad + c.tm * BM;
+        const int yb = c.q * p.n_pad + c.tn * BN;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          outstanding[s] = false;
+          const uint32_t sa = base + s * STAGE_BYTES;
+          mbar_expect_tx(full_bar(s), STAGE_BYTES);
+          tma_load_2d(sa, &tmA, full_bar(s), kb * BK, ya);
+          tma_load_2d(sa + A_BYTES, &tmB, full_bar(s), kb * BK, yb);
+          outstanding[s] = true;
+          issued_parity[s] = ph;
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (!ok) {  // wait for our own copies in flight before the CTA exits
+        for (int i = 0; i < STAGES; ++i)
+          if (outstanding[i]) mbar_drain(full_bar(i), issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t g = 0;  // slab counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+        for (int sl = 0; sl < nslabs && ok; ++sl, ++g) {
+          const uint32_t b = g & 1u, use = g >> 1;
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + b * BN;
+          const int kb0 = sl * kSlabBlocks;
+          const int kb1 = min(p.kblocks, kb0 + kSlabBlocks);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (kb > kb0 || kk > 0) ? 1u : 0u);
+            umma_commit(empty_bar(s));  // frees the stage once these products have read it
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(tfull_bar(b));    // accumulator b holds the slab's sums
+        }
+      }
+      if (!ok) {                        // wait for every product this thread issued
+        umma_commit(drain_bar);
+        mbar_drain(drain_bar, 0);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int e = warp - 2;                  // 0..7
+    const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+    const int half = e >> 2;                 // columns 128*half .. +127
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+      const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+      const float mf = (float)T.m[c.q];
+      const float invm = T.invm[c.q];
+      uint32_t acc8[32];                     // running residue + 128, one byte per column
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int sl = 0; sl < nslabs; ++sl, ++g) {
+        const uint32_t b = g & 1u, use = g >> 1;
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + lane_addr + b * BN + half * 128 + ch * 32, v);
+          tmem_ld_wait();
+          if (ch == 3) {                     // all four loads done: hand the accumulator back
+            tc_fence_before();
+            mbar_arrive(tempty_bar(b));
+          }
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            uint32_t out[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              // previous residue r in [-120, 120] from its byte r + 128
+              const float prev = __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) -
+                                 8388736.0f;
+              const float tsum = __uint_as_float(v[4 * w + j]) + prev;          // exact: |t| < 2^24
+              const float qf = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;     // nearest quotient (+-1)
+              const float r = fmaf(-qf, mf, tsum);                              // exact, |r| <= 120
+              out[j] = __float_as_uint(r + 8388736.0f);                         // low byte = r + 128
+            }
+            acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u),
+                                           0x5410u);
+          }
+        }
+      }
+      if (!ok) break;
+      // ---- tile done: residues -> W mod m or CRT digits, one byte per entry ----
+      const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
+      const int row = c.tm * BM + quarter * 32 + lane;
+      const int col0 = c.tn * BN + half * 128;
+      if (row < p.m && col0 < p.n) {
+        uint32_t outw[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          uint32_t w = acc8[i], o = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
+            uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);    // W mod m in [0, m)
+            uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
+            o |= y << (8 * j);
+          }
+          outw[i] = o;
+        }
+        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
+        if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t k_pad, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(planes), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
+      m_pad % BM || n_pad % BN)
+    return cudaErrorInvalidValue;
+  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+  const int64_t num_tiles = tiles_m * tiles_n * t.Q;
+  if (num_tiles > INT32_MAX || (int64_t)t.Q * m_pad > INT32_MAX || (int64_t)t.Q * n_pad > INT32_MAX)
+    return cudaErrorInvalidValue;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, U, (int64_t)t.Q * m_pad, k_pad, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, V, (int64_t)t.Q * n_pad, k_pad, BN)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  Params p;
+  p.m = (int)m;
+  p.n = (int)n;
+  p.tiles_m = (int)tiles_m;
+  p.tiles_n = (int)tiles_n;
+  p.num_tiles = (int)num_tiles;
+  p.kblocks = (int)(k_pad / BK);
+  p.m_pad = (int)m_pad;
+  p.n_pad = (int)n_pad;
+  p.raw = raw;
+  p.Y = Y;
+  p.status = status;
+  const int grid = (int)(num_tiles < sms ? num_tiles : sms);
+  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, t, p);
+  return cudaGetLastError();
+}
+
+}  // namespace oz

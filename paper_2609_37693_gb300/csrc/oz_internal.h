@@ -63,6 +63,8 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
 cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_pad, const int8_t* U,
                              int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int raw,
                              cudaStream_t st);
+cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                                const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
 

@@ -142,8 +142,7 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   } else if (!window_holds(P, k_hint, beta)) {
     return OZ_ERR_K_TOO_LARGE;
   }
-  int resolved = engine == OZ_ENGINE_AUTO ? OZ_ENGINE_IMMA : engine;
-  if (resolved == OZ_ENGINE_TC) return OZ_ERR_UNSUPPORTED;
+  int resolved = engine == OZ_ENGINE_AUTO ? OZ_ENGINE_TC : engine;
 
   oz_plan p = new (std::nothrow) oz_plan_s;
   if (!p) return OZ_ERR_INVALID_ARG;
@@ -151,11 +150,13 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   p->Q = Q;
   p->bits = beta;
   p->engine = resolved;
-  // eq. caps: K_max = min(kappa_rec, kappa_acc); the INT32 accumulator of one
-  // GEMM sums K products of two residues of magnitude <= r (eq. ov-acc).
+  // eq. caps: K_max = min(kappa_rec, kappa_acc). On the IMMA engine one INT32
+  // accumulator sums K products of two residues of magnitude <= r (eq. ov-acc).
+  // The TC engine accumulates in FP32 slabs of 1024 terms and reduces each slab
+  // modulo m (Sec. "Slabs"), so only kappa_rec limits K there.
   uint32_t r = 0;
   for (int i = 0; i < Q; ++i) r = kModuli[i] / 2 > r ? kModuli[i] / 2 : r;
-  int64_t k_acc = (int64_t)2147483647 / ((int64_t)r * r);
+  int64_t k_acc = resolved == OZ_ENGINE_TC ? (int64_t)INT32_MAX : (int64_t)2147483647 / ((int64_t)r * r);
   int64_t k_rec = kappa_rec(P, beta);
   p->k_max = k_acc < k_rec ? k_acc : k_rec;
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }

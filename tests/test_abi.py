@@ -100,7 +100,7 @@ def test_argument_errors_are_caught_on_the_host():
     assert oz.oz_dgemm(h, 0, 0, 0, 8, 8, None, 8, None, 8, None, 8, None, 0, None) == oz.OZ_OK
     assert oz.oz_split(h, 1, 4, 4, fake, 4, 100, 128, fake, fake, None, None, None) == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_split(h, 0, 4, 4, fake, 4, 256, 128, fake, fake, None, None, None) == oz.OZ_ERR_INVALID_ARG
-    assert oz.oz_residue_gemm(h, 4, 4, 256, 256, 100, fake, fake, fake, 0, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_residue_gemm(h, 4, 4, 256, 256, 100, fake, fake, fake, 0, None, None) == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_reconstruct(h, 4, 4, fake, fake, fake, fake, 3, None) == oz.OZ_ERR_INVALID_ARG
 
 

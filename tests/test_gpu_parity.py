@@ -21,6 +21,7 @@ if not torch.cuda.is_available():  # collected on CPU hosts but never run there
 import paper_2609_37693_gb300 as oz  # noqa: E402
 
 DEV = torch.device("cuda:0")
+ENGINES = [oz.OZ_ENGINE_IMMA, oz.OZ_ENGINE_TC]
 
 
 def _bits(x):
@@ -50,7 +51,7 @@ def _split(plan, X, contiguous, nvec, length, ld):
     return shifts.cpu().numpy()[:nvec], planes.float().cpu().numpy().astype(np.int16), flag.cpu().numpy()
 
 
-@pytest.mark.parametrize("engine", [oz.OZ_ENGINE_IMMA])
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("m,k,phi", [(256, 256, 0.5), (300, 1000, 2.0), (1, 1, 1.0), (777, 129, 4.0)])
 def test_split_rows_and_cols_match_oracle(engine, m, k, phi):
     plan = oz.Plan(16, 0, max(k, 1), engine)
@@ -93,13 +94,18 @@ def test_split_flags_nonfinite():
     assert flag[0] & 1
 
 
+def _plane_dtype(plan):
+    return torch.bfloat16 if plan.engine == oz.OZ_ENGINE_TC else torch.int8
+
+
 def _residues(plan, A, B):
     """GPU W mod m (raw epilogue) through oz_split + oz_residue_gemm."""
     m, k = A.shape
     n = B.shape[1]
     m_pad, n_pad, k_pad = oz.round_up(m, 256), oz.round_up(n, 256), oz.round_up(k, 128)
-    U = torch.zeros((plan.q, m_pad, k_pad), dtype=torch.int8, device=DEV)
-    V = torch.zeros((plan.q, n_pad, k_pad), dtype=torch.int8, device=DEV)
+    U = torch.zeros((plan.q, m_pad, k_pad), dtype=_plane_dtype(plan), device=DEV)
+    V = torch.zeros((plan.q, n_pad, k_pad), dtype=_plane_dtype(plan), device=DEV)
+    flag = torch.zeros(4, dtype=torch.int32, device=DEV)
     s = torch.zeros(m, dtype=torch.int32, device=DEV)
     t = torch.zeros(n, dtype=torch.int32, device=DEV)
     cm = torch.zeros(max(m, n), dtype=torch.int64, device=DEV)
@@ -112,20 +118,22 @@ def _residues(plan, A, B):
     Y = torch.zeros((plan.q, m, n), dtype=torch.uint8, device=DEV)
     Yd = torch.zeros((plan.q, m, n), dtype=torch.uint8, device=DEV)
     assert oz.oz_residue_gemm(plan.handle, m, n, m_pad, n_pad, k_pad, U.data_ptr(), V.data_ptr(), Y.data_ptr(), 1,
-                              st) == oz.OZ_OK
+                              flag.data_ptr(), st) == oz.OZ_OK
     assert oz.oz_residue_gemm(plan.handle, m, n, m_pad, n_pad, k_pad, U.data_ptr(), V.data_ptr(), Yd.data_ptr(), 0,
-                              st) == oz.OZ_OK
+                              flag.data_ptr(), st) == oz.OZ_OK
     C = torch.zeros((m, n), dtype=torch.float64, device=DEV)
     assert oz.oz_reconstruct(plan.handle, m, n, Yd.data_ptr(), s.data_ptr(), t.data_ptr(), C.data_ptr(), n,
                              st) == oz.OZ_OK
     torch.cuda.synchronize()
+    assert int(flag[0].item()) == 0
     return Y.cpu().numpy(), Yd.cpu().numpy(), C.cpu().numpy()
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("m,n,k,q,bits", [(256, 256, 256, 14, 50), (300, 200, 1000, 16, 0), (129, 513, 700, 16, 53),
-                                          (64, 300, 2048, 20, 0)])
-def test_residue_products_and_reconstruct_match_oracle(m, n, k, q, bits):
-    plan = oz.Plan(q, bits, k, oz.OZ_ENGINE_IMMA)
+                                          (64, 300, 2048, 20, 0), (200, 520, 3000, 16, 0)])
+def test_residue_products_and_reconstruct_match_oracle(engine, m, n, k, q, bits):
+    plan = oz.Plan(q, bits, k, engine)
     A, B = synth.phi_pair(m, n, k, 1.0, seed=q + k)
     Y, Yd, C = _residues(plan, A, B)
     C_ref, W_ref, _, _ = oracle.dgemm(A, B, plan.moduli, plan.bits, want_residues=True)
@@ -182,21 +190,23 @@ def _dgemm(plan, A, B, trans_a=False, trans_b=False):
     return C.cpu().numpy()
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("m,n,k,q,bits,phi", [(256, 256, 256, 14, 50, 0.5), (1000, 777, 300, 16, 53, 1.0),
                                               (300, 1000, 4096, 16, 0, 2.0), (33, 17, 5000, 16, 0, 4.0),
                                               (1, 1, 1, 16, 53, 1.0), (513, 129, 1, 9, 0, 1.0)])
-def test_dgemm_matches_oracle(m, n, k, q, bits, phi):
-    plan = oz.Plan(q, bits, k, oz.OZ_ENGINE_IMMA)
+def test_dgemm_matches_oracle(engine, m, n, k, q, bits, phi):
+    plan = oz.Plan(q, bits, k, engine)
     A, B = synth.phi_pair(m, n, k, phi, seed=m * 7 + k)
     C = _dgemm(plan, A, B)
     C_ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
     assert np.array_equal(_bits(C), _bits(C_ref))
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("ta,tb", [(0, 1), (1, 0), (1, 1)])
-def test_dgemm_transposed_operands(ta, tb):
+def test_dgemm_transposed_operands(engine, ta, tb):
     m, n, k = 200, 300, 500
-    plan = oz.Plan(16, 0, k, oz.OZ_ENGINE_IMMA)
+    plan = oz.Plan(16, 0, k, engine)
     A, B = synth.phi_pair(m, n, k, 1.0, seed=3)
     C_ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
     Ain = np.ascontiguousarray(A.T) if ta else A
@@ -205,8 +215,9 @@ def test_dgemm_transposed_operands(ta, tb):
     assert np.array_equal(_bits(C), _bits(C_ref))
 
 
-def test_dgemm_special_operands():
-    plan = oz.Plan(16, 53, 64, oz.OZ_ENGINE_IMMA)
+@pytest.mark.parametrize("engine", ENGINES)
+def test_dgemm_special_operands(engine):
+    plan = oz.Plan(16, 53, 64, engine)
     A, B = synth.phi_pair(40, 30, 64, 1.0, seed=11)
     A[3, :] = 0.0
     B[:, 7] = 0.0
@@ -261,12 +272,13 @@ def test_dgemm_reports_nonfinite():
     assert oz.query_status(ws) == oz.OZ_OK
 
 
-def test_full_size_8192_sampled_entries_and_error():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_full_size_8192_sampled_entries_and_error(engine):
     """m = n = k = 8192, Q = 16 (the headline size): sampled entries equal the
     oracle's bit for bit, and the error against the exact product is within
     2u (|A||B|)_ij at phi = 0.5."""
     n = 8192
-    plan = oz.Plan(16, 0, n, oz.OZ_ENGINE_IMMA)
+    plan = oz.Plan(16, 0, n, engine)
     assert plan.bits == 55
     A, B = synth.phi_pair(n, n, n, 0.5, seed=0)
     C = _dgemm(plan, A, B)
@@ -275,3 +287,40 @@ def test_full_size_8192_sampled_entries_and_error():
     assert np.array_equal(_bits(C[rows, cols]), _bits(ref))
     err, ab = oracle.exact_error(A, B, C, rows, cols)
     assert np.max(err / (2.0**-53 * ab)) <= 2.0
+
+
+@pytest.mark.parametrize("pattern", ["all_max", "random_sign", "mixed"])
+def test_tc_fp32_accumulation_is_exact(pattern):
+    """The FP32 accumulators of tcgen05.mma must add integer products without
+    rounding while every partial sum stays within 2^24 (Sec. 'Exactness May
+    Rely on Undocumented Accumulation'). Planes at the largest residue
+    magnitude drive each 1024-term slab to 1024 * 119^2 = 14 500 864; the
+    residues of the product must equal those of the exact integer product."""
+    plan = oz.Plan(16, 0, 4096, oz.OZ_ENGINE_TC)
+    m, n, k = 256, 256, 4096
+    rng = np.random.default_rng(17)
+    if pattern == "all_max":
+        Ui = np.full((m, k), 119, dtype=np.int64)
+        Vi = np.where(np.arange(n)[:, None] % 2 == 0, 119, -119) * np.ones((n, k), dtype=np.int64)
+    elif pattern == "random_sign":
+        Ui = rng.choice([-119, 119], size=(m, k)).astype(np.int64)
+        Vi = rng.choice([-119, 119], size=(n, k)).astype(np.int64)
+    else:
+        Ui = rng.integers(-119, 120, size=(m, k)).astype(np.int64)
+        Ui[: m // 2] = 119
+        Vi = rng.integers(-119, 120, size=(n, k)).astype(np.int64)
+        Vi[: n // 2] = 119
+    W = Ui @ Vi.T
+    U = torch.zeros((plan.q, m, k), dtype=torch.bfloat16, device=DEV)
+    V = torch.zeros((plan.q, n, k), dtype=torch.bfloat16, device=DEV)
+    U[:] = torch.from_numpy(Ui.astype(np.float32)).to(DEV).to(torch.bfloat16)
+    V[:] = torch.from_numpy(Vi.astype(np.float32)).to(DEV).to(torch.bfloat16)
+    Y = torch.zeros((plan.q, m, n), dtype=torch.uint8, device=DEV)
+    flag = torch.zeros(4, dtype=torch.int32, device=DEV)
+    assert oz.oz_residue_gemm(plan.handle, m, n, m, n, k, U.data_ptr(), V.data_ptr(), Y.data_ptr(), 1,
+                              flag.data_ptr(), _stream()) == oz.OZ_OK
+    torch.cuda.synchronize()
+    assert int(flag[0].item()) == 0
+    Yh = Y.cpu().numpy()
+    for q, mq in enumerate(plan.moduli):
+        assert np.array_equal(Yh[q].astype(np.int64), W % mq), f"modulus {mq}"
