@@ -24,8 +24,22 @@ struct OzTables {
   uint32_t c54[OZ_MAX_MODULI];            // 2^54 mod m
   uint32_t inv[OZ_MAX_MODULI];            // (P/m)^-1 mod m: CRT coefficient
   float invm[OZ_MAX_MODULI];              // 1/m rounded to fp32: quotient estimate
+  float mf[OZ_MAX_MODULI];                // m as fp32
+  float hif[OZ_MAX_MODULI];               // ceil(m/2): a residue >= this maps to r - m
+  float lof[OZ_MAX_MODULI];               // -floor(m/2): a residue below this maps to r + m
+  float c15f[OZ_MAX_MODULI];              // 2^15 mod m, 2^30, 2^45, 2^60 mod m, each as the
+  float c30f[OZ_MAX_MODULI];              // representative nearest zero (|c| <= 119)
+  float c45f[OZ_MAX_MODULI];
+  float c60f[OZ_MAX_MODULI];
   uint32_t Mk[OZ_MAX_MODULI][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
+  // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd
+  // Q ends with a pair whose second modulus is 1 (digit 0).
+  int npairs;
+  uint32_t pa[(OZ_MAX_MODULI + 1) / 2];   // m_a
+  uint32_t pb[(OZ_MAX_MODULI + 1) / 2];   // m_b (1 for a lone last modulus)
+  float pinv[(OZ_MAX_MODULI + 1) / 2];    // 1 / (m_a m_b) rounded to fp32
+  uint32_t Np[(OZ_MAX_MODULI + 1) / 2][OZ_MAX_LIMBS];  // P / (m_a m_b), 32-bit limbs
 };
 
 struct oz_plan_s {

@@ -185,7 +185,25 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
     uint32_t mk_mod_m = Mk.divmod(m, &dummy);
     t.inv[q] = inverse_mod(mk_mod_m, m);
     t.invm[q] = 1.0f / (float)m;
+    t.mf[q] = (float)m;
+    t.hif[q] = (float)((m + 1) / 2);
+    t.lof[q] = -(float)(m / 2);
+    auto centred = [m](uint32_t c) { return (float)(c >= (m + 1) / 2 ? (int)c - (int)m : (int)c); };
+    t.c15f[q] = centred(pow2_mod(15, m));
+    t.c30f[q] = centred(pow2_mod(30, m));
+    t.c45f[q] = centred(pow2_mod(45, m));
+    t.c60f[q] = centred(pow2_mod(60, m));
     for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
+  }
+  t.npairs = (Q + 1) / 2;
+  for (int pi = 0; pi < t.npairs; ++pi) {
+    uint32_t ma = kModuli[2 * pi], mb = 2 * pi + 1 < Q ? kModuli[2 * pi + 1] : 1u;
+    t.pa[pi] = ma;
+    t.pb[pi] = mb;
+    t.pinv[pi] = (float)(1.0 / ((double)ma * (double)mb));
+    Big Np;
+    P.divmod(ma * mb, &Np);
+    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Np[pi][i] = Np.w[i];
   }
   *out = p;
   return OZ_OK;

@@ -5,10 +5,12 @@
 //
 // Input per entry: the CRT digits y_q = (W_q mod m_q) (P/m_q)^-1 mod m_q in
 // [0, m_q), written by the GEMM epilogue. Then
-//   S = sum_q y_q (P/m_q) == X (mod P),  0 <= S < Q P,
-// formed in 32-bit limbs with 64-bit accumulators (each y_q (P/m_q)_limb is
-// below 2^40; twenty of them stay below 2^45). The quotient estimate is
-// round(sum_q y_q / m_q) in fp32 (error far below 1/2); X = S - qP is formed
+//   S = sum_q y_q (P/m_q) == X (mod P),  0 <= S < Q P.
+// The moduli are taken in pairs, z = y_a m_b + y_b m_a < 2^17, so that
+// S = sum_pairs z P/(m_a m_b): half as many wide products, formed in 32-bit
+// limbs with 64-bit accumulators (each z limb product is below 2^49; ten of
+// them stay below 2^53). The quotient estimate is round(sum z / (m_a m_b)) in
+// fp32 (error far below 1/2); X = S - qP is formed
 // modulo 2^(32 L) in two's complement and corrected once by +-P into
 // [-P/2, P/2). The window (eq. ov-crtgen) makes that X the exact integer
 // product (A'B')_ij.
@@ -176,14 +178,18 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
                                                           const int32_t* __restrict__ s,
                                                           const int32_t* __restrict__ t, double* __restrict__ C,
                                                           int64_t ldc) {
+  constexpr int kMaxPairs = (OZ_MAX_MODULI + 1) / 2;
   const int64_t i = blockIdx.x;
   const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
+  const int npairs = T.npairs;
   const int64_t plane = m * n;
   const uint8_t* yp = Y + i * n + j0;
   const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
                    ((plane & 3) == 0);
+  // S = sum over pairs (a, b) of z (P / (m_a m_b)), z = y_a m_b + y_b m_a < 2^17,
+  // since y_a (P/m_a) + y_b (P/m_b) = (P / (m_a m_b)) (y_a m_b + y_b m_a).
   uint64_t acc[EPT][L];
   float f[EPT];
 #pragma unroll
@@ -192,29 +198,41 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
 #pragma unroll
     for (int l = 0; l < L; ++l) acc[e][l] = 0;
   }
-  for (int q = 0; q < Q; ++q) {
-    uint32_t d[EPT];
-    if (vec) {
-      uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(yp + q * plane));
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) d[e] = (w >> (8 * e)) & 0xff;
-    } else {
+  for (int pi = 0; pi < kMaxPairs; ++pi) {
+    if (pi < npairs) {
+      const int qa = 2 * pi, qb = 2 * pi + 1;
+      uint32_t da[EPT], db[EPT];
+      if (vec) {
+        const uint32_t wa = __ldg(reinterpret_cast<const uint32_t*>(yp + qa * plane));
+        const uint32_t wb = qb < Q ? __ldg(reinterpret_cast<const uint32_t*>(yp + qb * plane)) : 0u;
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) d[e] = (j0 + e < n) ? __ldg(yp + q * plane + e) : 0u;
-    }
-    const float im = T.invm[q];
+        for (int e = 0; e < EPT; ++e) {
+          da[e] = (wa >> (8 * e)) & 0xffu;
+          db[e] = (wb >> (8 * e)) & 0xffu;
+        }
+      } else {
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      f[e] = fmaf((float)d[e], im, f[e]);
+        for (int e = 0; e < EPT; ++e) {
+          da[e] = (j0 + e < n) ? __ldg(yp + qa * plane + e) : 0u;
+          db[e] = (j0 + e < n && qb < Q) ? __ldg(yp + qb * plane + e) : 0u;
+        }
+      }
+      const uint32_t ma = T.pa[pi], mb = T.pb[pi];
+      const float pinv = T.pinv[pi];
 #pragma unroll
-      for (int l = 0; l < L; ++l) acc[e][l] += (uint64_t)d[e] * T.Mk[q][l];
+      for (int e = 0; e < EPT; ++e) {
+        const uint32_t z = da[e] * mb + db[e] * ma;
+        f[e] = fmaf(__int_as_float(0x4B000000 | z) - 8388608.0f, pinv, f[e]);
+#pragma unroll
+        for (int l = 0; l < L; ++l) acc[e][l] += (uint64_t)z * T.Np[pi][l];
+      }
     }
   }
   const int32_t si = s[i];
+  double out[EPT];
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
-    const int64_t j = j0 + e;
-    if (j >= n) break;
     Limbs<L> X;
     uint64_t carry = 0;
 #pragma unroll
@@ -237,9 +255,146 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
         c = v >> 32;
       }
     }
-    const int ex = -(si + t[j]);
-    const uint64_t bits = round_to_binary64(X, neg, ex);
-    C[i * ldc + j] = __longlong_as_double((long long)bits);
+    const int64_t j = j0 + e;
+    const int ex = j < n ? -(si + t[j]) : 0;
+    out[e] = __longlong_as_double((long long)round_to_binary64(X, neg, ex));
+  }
+  double* cp = C + i * ldc + j0;
+  if (EPT == 4 && j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+    reinterpret_cast<double2*>(cp)[0] = make_double2(out[0], out[1]);
+    reinterpret_cast<double2*>(cp)[1] = make_double2(out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (j0 + e < n) cp[e] = out[e];
+  }
+}
+
+typedef unsigned __int128 u128;
+
+// binary64 bits of (-1)^neg mag 2^e for a 128-bit magnitude, nearest even
+__device__ __forceinline__ uint64_t round128(u128 mag, uint32_t neg, int e) {
+  const uint64_t sign = (uint64_t)neg << 63;
+  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+  const int nb = hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 0);
+  if (nb == 0) return 0ull;
+  const int E = nb - 1 + e;
+  if (E > 1023) return sign | 0x7ff0000000000000ull;
+  const int lsb = E >= -1022 ? E - 52 : -1074;
+  const int sh = lsb - e;
+  uint64_t q;
+  if (sh <= 0) {
+    q = lo << (-sh);                                   // at most 53 bits: exact
+  } else if (sh > nb) {
+    q = 0;                                             // below half of the last place
+  } else if (sh == nb) {                               // the round bit is the leading bit
+    const bool sticky = (mag & ~((u128)1 << (nb - 1))) != 0;
+    q = sticky ? 1 : 0;                                // a tie goes to the even 0
+  } else {                                             // 0 < sh < nb <= 128
+    q = (uint64_t)(mag >> sh);
+    const bool half = (mag >> (sh - 1)) & 1;
+    const bool sticky = (mag & (((u128)1 << (sh - 1)) - 1)) != 0;
+    if (half && (sticky || (q & 1ull))) q += 1ull;
+  }
+  uint64_t b = E >= -1022 ? ((uint64_t)(E + 1022) << 52) + q : q;
+  if (b >= 0x7ff0000000000000ull) b = 0x7ff0000000000000ull;
+  return sign | b;
+}
+
+// The same product for P < 2^125 (Q <= 16): X held in 128-bit integers, and
+// the exact +-P correction only when the quotient estimate is within 1e-3 of
+// a tie (X correct makes |f - q| = |X/P| + fp32 error < 1/2, so an estimate
+// farther than 1e-3 from a tie cannot pick the wrong quotient).
+template <int EPT>
+__global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_constant__ OzTables T, int64_t m,
+                                                             int64_t n, const uint8_t* __restrict__ Y,
+                                                             const int32_t* __restrict__ s,
+                                                             const int32_t* __restrict__ t,
+                                                             double* __restrict__ C, int64_t ldc) {
+  constexpr int kMaxPairs = (OZ_MAX_MODULI + 1) / 2;
+  const int64_t i = blockIdx.x;
+  const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
+  if (i >= m || j0 >= n) return;
+  const int Q = T.Q;
+  const int npairs = T.npairs;
+  const int64_t plane = m * n;
+  const uint8_t* yp = Y + i * n + j0;
+  const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
+                   ((plane & 3) == 0);
+  uint64_t acc[EPT][4];
+  float f[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    f[e] = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[e][l] = 0;
+  }
+#pragma unroll
+  for (int pi = 0; pi < kMaxPairs; ++pi) {
+    if (pi < npairs) {
+      const int qa = 2 * pi, qb = 2 * pi + 1;
+      uint32_t da[EPT], db[EPT];
+      if (vec) {
+        const uint32_t wa = __ldg(reinterpret_cast<const uint32_t*>(yp + qa * plane));
+        const uint32_t wb = qb < Q ? __ldg(reinterpret_cast<const uint32_t*>(yp + qb * plane)) : 0u;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          da[e] = (wa >> (8 * e)) & 0xffu;
+          db[e] = (wb >> (8 * e)) & 0xffu;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          da[e] = (j0 + e < n) ? __ldg(yp + qa * plane + e) : 0u;
+          db[e] = (j0 + e < n && qb < Q) ? __ldg(yp + qb * plane + e) : 0u;
+        }
+      }
+      const uint32_t ma = T.pa[pi], mb = T.pb[pi];
+      const float pinv = T.pinv[pi];
+      const uint32_t n0 = T.Np[pi][0], n1 = T.Np[pi][1], n2 = T.Np[pi][2], n3 = T.Np[pi][3];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const uint32_t z = da[e] * mb + db[e] * ma;
+        f[e] = fmaf(__int_as_float(0x4B000000 | z) - 8388608.0f, pinv, f[e]);
+        acc[e][0] += (uint64_t)z * n0;
+        acc[e][1] += (uint64_t)z * n1;
+        acc[e][2] += (uint64_t)z * n2;
+        acc[e][3] += (uint64_t)z * n3;
+      }
+    }
+  }
+  const u128 P = ((u128)(((uint64_t)T.P[3] << 32) | T.P[2]) << 64) | (((uint64_t)T.P[1] << 32) | T.P[0]);
+  const int32_t si = s[i];
+  double out[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    // S modulo 2^128 from the limb accumulators
+    uint64_t c0 = acc[e][0];
+    uint64_t c1 = acc[e][1] + (c0 >> 32);
+    uint64_t c2 = acc[e][2] + (c1 >> 32);
+    uint64_t c3 = acc[e][3] + (c2 >> 32);
+    const uint64_t lo = (c0 & 0xffffffffull) | (c1 << 32);
+    const uint64_t hi = (c2 & 0xffffffffull) | (c3 << 32);
+    const float qf = rintf(f[e]);
+    __int128 X = (__int128)((((u128)hi) << 64 | lo) - (u128)(uint32_t)qf * P);
+    if (fabsf(f[e] - qf) > 0.499f) {               // near a tie: exact check of [-P/2, P/2)
+      if (2 * X >= (__int128)P) X -= (__int128)P;
+      else if (2 * X < -(__int128)P) X += (__int128)P;
+    }
+    const uint32_t neg = X < 0;
+    const u128 mag = neg ? (u128)(-X) : (u128)X;
+    const int64_t j = j0 + e;
+    const int ex = j < n ? -(si + t[j]) : 0;
+    out[e] = __longlong_as_double((long long)round128(mag, neg, ex));
+  }
+  double* cp = C + i * ldc + j0;
+  if (EPT == 4 && j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+    reinterpret_cast<double2*>(cp)[0] = make_double2(out[0], out[1]);
+    reinterpret_cast<double2*>(cp)[1] = make_double2(out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (j0 + e < n) cp[e] = out[e];
   }
 }
 
@@ -257,9 +412,13 @@ cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, 
 cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                                const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (T.limbs <= 4) {
+    constexpr int EPT = 4;
+    dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
+    reconstruct128_kernel<EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+    return cudaGetLastError();
+  }
   switch (T.limbs) {
-    case 3: return launch_L<3>(T, m, n, Y, s, t, C, ldc, st);
-    case 4: return launch_L<4>(T, m, n, Y, s, t, C, ldc, st);
     case 5: return launch_L<5>(T, m, n, Y, s, t, C, ldc, st);
     case 6: return launch_L<6>(T, m, n, Y, s, t, C, ldc, st);
     default: return cudaErrorInvalidValue;

@@ -8,12 +8,16 @@
 // Reduce: a' = trunc(x 2^s) taken straight from the IEEE fields: with the
 // 53-bit significand f and exponent E, x 2^s = f 2^(E - 1075 + s), so a'
 // is f shifted left or right (the right shift truncates toward zero). The
-// residue of |a'| modulo m uses only 32-bit integer work: |a'| < 2^64 is cut
-// into 18-bit pieces p0..p3, y = p0 + p1 (2^18 mod m) + p2 (2^36 mod m) +
-// p3 (2^54 mod m) < 2^32 is congruent to |a'|, and one Barrett step reduces y
-// (Sec. "Around the GEMMs": a one-byte modulus reduces in 32-bit Barrett
-// steps). The sign is applied modulo m and the result mapped to the
-// representative nearest zero, [-floor(m/2), ceil(m/2) - 1].
+// residue modulo m is formed in exact fp32 arithmetic (twice the integer
+// issue rate): a' (|a'| < 2^64) is cut once per entry into signed 15-bit pieces
+// P0..P4, and for each modulus
+//   y = P0 + P1 c15 + P2 c30 + P3 c45 + P4 c60,   c_k = 2^k mod m, |c_k| <= 119,
+// is congruent to a' with |y| < 2^24, so every step is exact. One quotient
+// q = rint(y / m) (an fp32 estimate, off by at most one near a tie) gives
+// r = y - q m exactly, and two compares map r to the representative nearest
+// zero, [-floor(m/2), ceil(m/2) - 1] (the paper reduces a one-byte modulus
+// in two 32-bit Barrett steps, Sec. "Around the GEMMs"; this is the same
+// reduction in the fp32 pipe).
 //
 // Planes are written K-major, Q planes of nvec_pad x k_pad entries, int8
 // (two's complement, IMMA engine) or bf16 (TC engine; integers below 2^8 are
@@ -26,7 +30,6 @@ namespace oz {
 namespace {
 
 constexpr uint64_t kAbsMask = 0x7fffffffffffffffull;
-constexpr uint32_t kM18 = (1u << 18) - 1;
 
 // Shift s from the largest |x| bit pattern.
 __device__ __forceinline__ int32_t shift_from_maxbits(uint64_t mb, int beta) {
@@ -54,23 +57,64 @@ __device__ __forceinline__ Trunc truncate(uint64_t bits, int32_t s) {
   return t;
 }
 
-// Balanced residue of (+-mag) modulo table entry q.
-__device__ __forceinline__ int32_t residue(const OzTables& T, int q, uint32_t p0, uint32_t p1, uint32_t p2,
-                                           uint32_t p3, uint32_t neg) {
-  uint32_t m = T.m[q];
-  uint32_t y = p0 + p1 * T.c18[q] + p2 * T.c36[q] + p3 * T.c54[q];
-  uint32_t r = mod_barrett(y, m, T.magic[q]);
-  r = neg ? m - r : r;                      // in (0, m]; m maps to 0 below
-  return (int32_t)r - (r >= T.half[q] ? (int32_t)m : 0);
+// Signed 15-bit pieces of a' as exact floats: a' = sum_i P_i 2^(15 i).
+struct Pieces {
+  float p[5];
+};
+
+__device__ __forceinline__ Pieces pieces_of(uint64_t bits, int32_t s) {
+  const Trunc t = truncate(bits, s);
+  const float sg = t.neg ? -1.0f : 1.0f;
+  const float off = t.neg ? 8388608.0f : -8388608.0f;
+  Pieces P;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint32_t v = (uint32_t)(t.mag >> (15 * i)) & 0x7FFFu;
+    P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
+  }
+  return P;
 }
 
-// Exact bf16 bit pattern of an integer |r| < 2^22 (magic-number conversion:
-// the float 1.5*2^23 + r has r in its low significand bits; subtracting
-// 1.5*2^23 leaves r exactly, and an integer below 2^8 needs no more than
-// bf16's 8 significand bits, so the high half of the float is exact).
-__device__ __forceinline__ uint32_t bf16_bits(int32_t r) {
-  float f = __int_as_float(0x4B400000 + r) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
+// The constants of one modulus, held in registers while a tile is reduced.
+struct ModConst {
+  float c15, c30, c45, c60, invm, m, hi, lo;
+};
+
+__device__ __forceinline__ ModConst mod_const(const OzTables& T, int q) {
+  ModConst c;
+  c.c15 = T.c15f[q];
+  c.c30 = T.c30f[q];
+  c.c45 = T.c45f[q];
+  c.c60 = T.c60f[q];
+  c.invm = T.invm[q];
+  c.m = T.mf[q];
+  c.hi = T.hif[q];
+  c.lo = T.lof[q];
+  return c;
+}
+
+// Representative nearest zero of a' modulo one modulus, as an exact float.
+__device__ __forceinline__ float residue_f(const ModConst& c, const Pieces& P) {
+  const float y = fmaf(P.p[4], c.c60, fmaf(P.p[3], c.c45, fmaf(P.p[2], c.c30, fmaf(P.p[1], c.c15, P.p[0]))));
+  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;
+  float r = fmaf(-qf, c.m, y);
+  r = r >= c.hi ? r - c.m : r;
+  r = r < c.lo ? r + c.m : r;
+  return r;
+}
+
+// bf16 bit pattern of an exact small integer held in a float (|r| < 2^8 needs
+// at most 8 significand bits, so the upper half of the float is exact).
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+
+// two's-complement byte of an exact small integer held in a float
+__device__ __forceinline__ uint32_t int8_bits(float r) { return __float_as_uint(r + 12582912.0f); }
+
+__device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d) {
+  return __byte_perm(__byte_perm(int8_bits(a), int8_bits(b), 0x0040u), __byte_perm(int8_bits(c), int8_bits(d), 0x0040u),
+                     0x5410u);
 }
 
 // 64-bit max across a warp.
@@ -131,39 +175,47 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__
 
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
+  const bool vec = live && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
   for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
-    uint32_t p0[8], p1[8], p2[8], p3[8], ng[8];
+    uint64_t b[8];
+    if (vec && h0 + 8 <= len) {
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(row + h0 + e));
+        b[e] = w.x;
+        b[e + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+    }
+    Pieces P[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      int64_t h = h0 + e;
-      uint64_t b = (live && h < len) ? __ldg(row + h) : 0ull;
-      if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;  // non-finite: flagged above
-      Trunc t = truncate(b, s);
-      p0[e] = (uint32_t)t.mag & kM18;
-      p1[e] = (uint32_t)(t.mag >> 18) & kM18;
-      p2[e] = (uint32_t)(t.mag >> 36) & kM18;
-      p3[e] = (uint32_t)(t.mag >> 54);
-      ng[e] = t.neg;
+      if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;  // non-finite: flagged above
+      P[e] = pieces_of(b[e], s);
     }
-    for (int q = 0; q < Q; ++q) {
-      int32_t r[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) r[e] = residue(T, q, p0[e], p1[e], p2[e], p3[e], ng[e]);
-      const int64_t off = (int64_t)q * plane + v * k_pad + h0;
-      if (kBF16) {
-        uint4 o;
-        o.x = bf16_bits(r[0]) | (bf16_bits(r[1]) << 16);
-        o.y = bf16_bits(r[2]) | (bf16_bits(r[3]) << 16);
-        o.z = bf16_bits(r[4]) | (bf16_bits(r[5]) << 16);
-        o.w = bf16_bits(r[6]) | (bf16_bits(r[7]) << 16);
-        *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
-      } else {
-        uint2 o;
-        o.x = (uint32_t)(r[0] & 0xff) | ((uint32_t)(r[1] & 0xff) << 8) | ((uint32_t)(r[2] & 0xff) << 16) |
-              ((uint32_t)(r[3] & 0xff) << 24);
-        o.y = (uint32_t)(r[4] & 0xff) | ((uint32_t)(r[5] & 0xff) << 8) | ((uint32_t)(r[6] & 0xff) << 16) |
-              ((uint32_t)(r[7] & 0xff) << 24);
-        *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
+    for (int q = 0; q < OZ_MAX_MODULI; ++q) {
+      if (q < Q) {
+        const ModConst mc = mod_const(T, q);
+        float r[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = residue_f(mc, P[e]);
+        const int64_t off = (int64_t)q * plane + v * k_pad + h0;
+        if (kBF16) {
+          uint4 o;
+          o.x = bf16_pair(r[0], r[1]);
+          o.y = bf16_pair(r[2], r[3]);
+          o.z = bf16_pair(r[4], r[5]);
+          o.w = bf16_pair(r[6], r[7]);
+          *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
+        } else {
+          uint2 o;
+          o.x = int8_quad(r[0], r[1], r[2], r[3]);
+          o.y = int8_quad(r[4], r[5], r[6], r[7]);
+          *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
+        }
       }
     }
   }
@@ -229,37 +281,31 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__
   const bool live = j < nvec;
   const int32_t s = live ? shifts[j] : 0;
 
-  uint32_t p0[16], p1[16], p2[16], p3[16], ng[16];
+  Pieces P[16];
   const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     int64_t h = hbase + hg * 16 + e;
     uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
     if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
-    Trunc t = truncate(b, s);
-    p0[e] = (uint32_t)t.mag & kM18;
-    p1[e] = (uint32_t)(t.mag >> 18) & kM18;
-    p2[e] = (uint32_t)(t.mag >> 36) & kM18;
-    p3[e] = (uint32_t)(t.mag >> 54);
-    ng[e] = t.neg;
+    P[e] = pieces_of(b, s);
   }
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
+#pragma unroll 1
   for (int q = 0; q < Q; ++q) {
     uint32_t* tb = tile[q & 1];
-    int32_t r[16];
+    const ModConst mc = mod_const(T, q);
+    float r[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = residue(T, q, p0[e], p1[e], p2[e], p3[e], ng[e]);
+    for (int e = 0; e < 16; ++e) r[e] = residue_f(mc, P[e]);
     if (kBF16) {
 #pragma unroll
-      for (int w = 0; w < 8; ++w)
-        tb[jl * kPitchWords + hg * 8 + w] = bf16_bits(r[2 * w]) | (bf16_bits(r[2 * w + 1]) << 16);
+      for (int w = 0; w < 8; ++w) tb[jl * kPitchWords + hg * 8 + w] = bf16_pair(r[2 * w], r[2 * w + 1]);
     } else {
 #pragma unroll
       for (int w = 0; w < 4; ++w)
-        tb[jl * kPitchWords + hg * 4 + w] = (uint32_t)(r[4 * w] & 0xff) | ((uint32_t)(r[4 * w + 1] & 0xff) << 8) |
-                                            ((uint32_t)(r[4 * w + 2] & 0xff) << 16) |
-                                            ((uint32_t)(r[4 * w + 3] & 0xff) << 24);
+        tb[jl * kPitchWords + hg * 4 + w] = int8_quad(r[4 * w], r[4 * w + 1], r[4 * w + 2], r[4 * w + 3]);
     }
     __syncthreads();
     // write 64 rows of 64 entries: int8 -> 4 words of 16 B per row, bf16 -> 8
