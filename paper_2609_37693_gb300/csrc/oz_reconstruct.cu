@@ -304,23 +304,45 @@ __device__ __forceinline__ uint64_t round128(u128 mag, uint32_t neg, int e) {
 // The same product for P < 2^125 (Q <= 16): X held in 128-bit integers, and
 // the exact +-P correction only when the quotient estimate is within 1e-3 of
 // a tie (X correct makes |f - q| = |X/P| + fp32 error < 1/2, so an estimate
-// farther than 1e-3 from a tie cannot pick the wrong quotient).
-template <int EPT>
+// farther than 1e-3 from a tie cannot pick the wrong quotient). The pair
+// count is a template parameter so that every digit load is issued before
+// any arithmetic.
+template <int NP, int EPT>
 __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_constant__ OzTables T, int64_t m,
                                                              int64_t n, const uint8_t* __restrict__ Y,
                                                              const int32_t* __restrict__ s,
                                                              const int32_t* __restrict__ t,
                                                              double* __restrict__ C, int64_t ldc) {
-  constexpr int kMaxPairs = (OZ_MAX_MODULI + 1) / 2;
+  static_assert(EPT == 4, "one 32-bit digit word per plane");
   const int64_t i = blockIdx.x;
   const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
-  const int npairs = T.npairs;
   const int64_t plane = m * n;
   const uint8_t* yp = Y + i * n + j0;
-  const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
-                   ((plane & 3) == 0);
+  const bool vec = (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) && ((plane & 3) == 0);
+  uint32_t wa[NP], wb[NP];
+  if (vec) {
+#pragma unroll
+    for (int pi = 0; pi < NP; ++pi) {
+      wa[pi] = __ldg(reinterpret_cast<const uint32_t*>(yp + (2 * pi) * plane));
+      wb[pi] = (2 * pi + 1 < Q) ? __ldg(reinterpret_cast<const uint32_t*>(yp + (2 * pi + 1) * plane)) : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int pi = 0; pi < NP; ++pi) {
+      uint32_t a = 0, b = 0;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        if (j0 + e < n) {
+          a |= (uint32_t)__ldg(yp + (2 * pi) * plane + e) << (8 * e);
+          if (2 * pi + 1 < Q) b |= (uint32_t)__ldg(yp + (2 * pi + 1) * plane + e) << (8 * e);
+        }
+      }
+      wa[pi] = a;
+      wb[pi] = b;
+    }
+  }
   uint64_t acc[EPT][4];
   float f[EPT];
 #pragma unroll
@@ -330,37 +352,18 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
     for (int l = 0; l < 4; ++l) acc[e][l] = 0;
   }
 #pragma unroll
-  for (int pi = 0; pi < kMaxPairs; ++pi) {
-    if (pi < npairs) {
-      const int qa = 2 * pi, qb = 2 * pi + 1;
-      uint32_t da[EPT], db[EPT];
-      if (vec) {
-        const uint32_t wa = __ldg(reinterpret_cast<const uint32_t*>(yp + qa * plane));
-        const uint32_t wb = qb < Q ? __ldg(reinterpret_cast<const uint32_t*>(yp + qb * plane)) : 0u;
+  for (int pi = 0; pi < NP; ++pi) {
+    const uint32_t ma = T.pa[pi], mb = T.pb[pi];
+    const float pinv = T.pinv[pi];
+    const uint32_t n0 = T.Np[pi][0], n1 = T.Np[pi][1], n2 = T.Np[pi][2], n3 = T.Np[pi][3];
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-          da[e] = (wa >> (8 * e)) & 0xffu;
-          db[e] = (wb >> (8 * e)) & 0xffu;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-          da[e] = (j0 + e < n) ? __ldg(yp + qa * plane + e) : 0u;
-          db[e] = (j0 + e < n && qb < Q) ? __ldg(yp + qb * plane + e) : 0u;
-        }
-      }
-      const uint32_t ma = T.pa[pi], mb = T.pb[pi];
-      const float pinv = T.pinv[pi];
-      const uint32_t n0 = T.Np[pi][0], n1 = T.Np[pi][1], n2 = T.Np[pi][2], n3 = T.Np[pi][3];
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const uint32_t z = da[e] * mb + db[e] * ma;
-        f[e] = fmaf(__int_as_float(0x4B000000 | z) - 8388608.0f, pinv, f[e]);
-        acc[e][0] += (uint64_t)z * n0;
-        acc[e][1] += (uint64_t)z * n1;
-        acc[e][2] += (uint64_t)z * n2;
-        acc[e][3] += (uint64_t)z * n3;
-      }
+    for (int e = 0; e < EPT; ++e) {
+      const uint32_t z = __byte_perm(wa[pi], 0, 0x4440 + e) * mb + __byte_perm(wb[pi], 0, 0x4440 + e) * ma;
+      f[e] = fmaf(__int_as_float(0x4B000000 | z) - 8388608.0f, pinv, f[e]);
+      acc[e][0] += (uint64_t)z * n0;
+      acc[e][1] += (uint64_t)z * n1;
+      acc[e][2] += (uint64_t)z * n2;
+      acc[e][3] += (uint64_t)z * n3;
     }
   }
   const u128 P = ((u128)(((uint64_t)T.P[3] << 32) | T.P[2]) << 64) | (((uint64_t)T.P[1] << 32) | T.P[0]);
@@ -369,10 +372,10 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
 #pragma unroll
   for (int e = 0; e < EPT; ++e) {
     // S modulo 2^128 from the limb accumulators
-    uint64_t c0 = acc[e][0];
-    uint64_t c1 = acc[e][1] + (c0 >> 32);
-    uint64_t c2 = acc[e][2] + (c1 >> 32);
-    uint64_t c3 = acc[e][3] + (c2 >> 32);
+    const uint64_t c0 = acc[e][0];
+    const uint64_t c1 = acc[e][1] + (c0 >> 32);
+    const uint64_t c2 = acc[e][2] + (c1 >> 32);
+    const uint64_t c3 = acc[e][3] + (c2 >> 32);
     const uint64_t lo = (c0 & 0xffffffffull) | (c1 << 32);
     const uint64_t hi = (c2 & 0xffffffffull) | (c3 << 32);
     const float qf = rintf(f[e]);
@@ -385,10 +388,31 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
     const u128 mag = neg ? (u128)(-X) : (u128)X;
     const int64_t j = j0 + e;
     const int ex = j < n ? -(si + t[j]) : 0;
-    out[e] = __longlong_as_double((long long)round128(mag, neg, ex));
+    // normalise the magnitude so that its leading bit is bit 63 of h
+    const uint64_t mh = (uint64_t)(mag >> 64), ml = (uint64_t)mag;
+    const int lz = mh ? __clzll((long long)mh) : 64 + (ml ? __clzll((long long)ml) : 64);
+    const int nb = 128 - lz;
+    const int E = nb - 1 + ex;
+    uint64_t bits;
+    if (nb == 0) {
+      bits = 0;
+    } else if (E >= -1022 && E <= 1023) {            // normal result: 53 bits, round, sticky
+      const u128 nm = mag << lz;
+      const uint64_t h = (uint64_t)(nm >> 64), l = (uint64_t)nm;
+      const uint64_t m53 = h >> 11;
+      const uint64_t half = (h >> 10) & 1ull;
+      const uint64_t sticky = ((h & 0x3ffull) | l) != 0;
+      const uint64_t q = m53 + (half & (sticky | (m53 & 1ull)));
+      uint64_t b = ((uint64_t)(E + 1022) << 52) + q;
+      if (b >= 0x7ff0000000000000ull) b = 0x7ff0000000000000ull;
+      bits = ((uint64_t)neg << 63) | b;
+    } else {
+      bits = round128(mag, neg, ex);                 // subnormal or overflowing result
+    }
+    out[e] = __longlong_as_double((long long)bits);
   }
   double* cp = C + i * ldc + j0;
-  if (EPT == 4 && j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+  if (j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
     reinterpret_cast<double2*>(cp)[0] = make_double2(out[0], out[1]);
     reinterpret_cast<double2*>(cp)[1] = make_double2(out[2], out[3]);
   } else {
@@ -396,6 +420,15 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
     for (int e = 0; e < EPT; ++e)
       if (j0 + e < n) cp[e] = out[e];
   }
+}
+
+template <int NP>
+cudaError_t launch128(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+                      const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int EPT = 4;
+  dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
+  reconstruct128_kernel<NP, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  return cudaGetLastError();
 }
 
 template <int L>
@@ -413,10 +446,13 @@ cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const ui
                                const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
   if (T.limbs <= 4) {
-    constexpr int EPT = 4;
-    dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
-    reconstruct128_kernel<EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
-    return cudaGetLastError();
+    switch (T.npairs) {
+      case 5: return launch128<5>(T, m, n, Y, s, t, C, ldc, st);
+      case 6: return launch128<6>(T, m, n, Y, s, t, C, ldc, st);
+      case 7: return launch128<7>(T, m, n, Y, s, t, C, ldc, st);
+      case 8: return launch128<8>(T, m, n, Y, s, t, C, ldc, st);
+      default: break;
+    }
   }
   switch (T.limbs) {
     case 5: return launch_L<5>(T, m, n, Y, s, t, C, ldc, st);
