@@ -119,6 +119,23 @@ def workload_name(n, phi, q, bits):
             f"INT8 residue path Q={q} moduli<=239, beta={bits}")
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of one float per rank (the step time every rank reports);
+    x itself without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput_tflops(flops_per_step: float, steps: int, elapsed_ms: float, world: int) -> float:
+    """Whole-job rate: every rank runs its own product of flops_per_step per
+    step (weak scaling), timed by the slowest rank."""
+    return world * flops_per_step * steps / (elapsed_ms * 1e-3) / 1e12
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -264,13 +281,10 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     elapsed_ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = t.item()
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     ms_per_step = elapsed_ms / args.steps
     flops = 2.0 * n**3
-    value = world * flops * args.steps / (elapsed_ms * 1e-3) / 1e12
+    value = throughput_tflops(flops, args.steps, elapsed_ms, world)
 
     # ---- per-phase times through the phase entry points (same kernels) ----
     m_pad, n_pad, k_pad = oz.round_up(n, 256), oz.round_up(n, 256), oz.round_up(n, 128)
@@ -314,12 +328,8 @@ def run_ours(args, rank, world, local):
         C_pin.copy_(C, non_blocking=True)
     t1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = t0.elapsed_time(t1) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e_value = world * flops / (e2e_ms * 1e-3) / 1e12
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
+    e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----
     peaks = load_peaks()

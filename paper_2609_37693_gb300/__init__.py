@@ -241,3 +241,75 @@ def launches_per_dgemm(trans_a: bool = False, trans_b: bool = False) -> int:
 
 def query_status(ws, stream=None) -> int:
     return oz_query_status(ws.data_ptr(), _stream_handle(stream))
+
+
+# ---------------------------------------------------------------------------
+# Differentiable emulated FP64 matmul
+# ---------------------------------------------------------------------------
+
+_plan_cache: dict = {}
+
+
+def plan_for(k: int, q: int = 16, engine: int = OZ_ENGINE_AUTO) -> Plan:
+    """A cached plan for inner dimension k (bits chosen as the largest the
+    window allows at that k)."""
+    key = (int(q), int(max(k, 1)), int(engine))
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(q, 0, max(k, 1), engine)
+        _plan_cache[key] = p
+    return p
+
+
+def _matmul_op(A, B, trans_a: bool, trans_b: bool, q: int, engine: int):
+    k = A.shape[0] if trans_a else A.shape[1]
+    return dgemm(A, B, plan_for(k, q, engine), trans_a=trans_a, trans_b=trans_b)
+
+
+def _import_torch():
+    import torch
+    return torch
+
+
+class EmuMatmul:
+    """C = A @ B for float64 CUDA matrices through the emulated product, with
+    dA = dC B^T and dB = A^T dC computed by the same kernels (the transposed
+    operand modes of oz_dgemm). Use ``EmuMatmul.apply(A, B, q=16)``."""
+
+    _fn = None
+
+    @classmethod
+    def _function(cls):
+        if cls._fn is None:
+            torch = _import_torch()
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, A, B, q=16, engine=OZ_ENGINE_AUTO):
+                    A_ = A.contiguous()
+                    B_ = B.contiguous()
+                    ctx.save_for_backward(A_, B_)
+                    ctx.q, ctx.engine = q, engine
+                    return _matmul_op(A_, B_, False, False, q, engine)
+
+                @staticmethod
+                def backward(ctx, dC):
+                    A, B = ctx.saved_tensors
+                    dC = dC.contiguous()
+                    dA = dB = None
+                    if ctx.needs_input_grad[0]:
+                        dA = _matmul_op(dC, B, False, True, ctx.q, ctx.engine)      # dC (m x n) B^T (n x k)
+                    if ctx.needs_input_grad[1]:
+                        dB = _matmul_op(A, dC, True, False, ctx.q, ctx.engine)      # A^T (k x m) dC (m x n)
+                    return dA, dB, None, None
+
+            cls._fn = _F
+        return cls._fn
+
+    @classmethod
+    def apply(cls, A, B, q: int = 16, engine: int = OZ_ENGINE_AUTO):
+        return cls._function().apply(A, B, q, engine)
+
+
+def emu_matmul(A, B, q: int = 16, engine: int = OZ_ENGINE_AUTO):
+    return EmuMatmul.apply(A, B, q, engine)
