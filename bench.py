@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc"])
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
+    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch"],
+                    help="dgemm: one m=n=k product (the headline); batch: 256 uneven products")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -386,11 +389,83 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world, local):
+    """256 products with m, n, k log-uniform on [64, 4096] (phi = 1), through one
+    autotuned oz_dgemm_batched captured into a CUDA graph, next to a loop of
+    cuBLAS DGEMM calls on the same operands."""
+    import torch
+    import paper_2609_37693_gb300 as oz
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shapes = [tuple(int(x) for x in s) for s in synth.batch_shapes(args.batch_count, 64, 4096, seed=0)]
+    As, Bs, Cs = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B = synth.phi_pair(m, n, k, 1.0, seed=i)
+        As.append(torch.from_numpy(A).to(dev))
+        Bs.append(torch.from_numpy(B).to(dev))
+        Cs.append(torch.empty((m, n), dtype=torch.float64, device=dev))
+    flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
+    bg, tune = oz.autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16))
+    for _ in range(max(args.warmup, 1)):
+        bg.replay()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0.record(s0)
+    for _ in range(args.steps):
+        bg.replay()
+    e1.record(s0)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same products through cuBLAS DGEMM, one call each
+    ref = [torch.empty_like(c) for c in Cs]
+    for A, B, R in zip(As, Bs, ref):
+        torch.matmul(A, B, out=R)
+    torch.cuda.synchronize()
+    e0.record(s0)
+    reps = 2
+    for _ in range(reps):
+        for A, B, R in zip(As, Bs, ref):
+            torch.matmul(A, B, out=R)
+    e1.record(s0)
+    torch.cuda.synchronize()
+    ms_dgemm = e0.elapsed_time(e1) / reps
+    num = sum(float(torch.linalg.norm(C - R) ** 2) for C, R in zip(Cs, ref))
+    den = sum(float(torch.linalg.norm(R) ** 2) for R in ref)
+    launches = sum(oz.launches_per_dgemm() for _ in shapes)
+    if rank == 0:
+        line = {
+            "metric": "batched emulated-FP64 GEMM TFLOP/s, 256 products m,n,k log-uniform on [64,4096]",
+            "value": flops / (ms * 1e-3) / 1e12, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"{len(shapes)} uneven products, m,n,k log-uniform [64,4096] seed 0, "
+                                   f"phi=1, least Q at 53 bits per product, one CUDA graph",
+                       "total_flops": flops, "nstreams": bg.nstreams, "autotune_ms": tune,
+                       "q_histogram": {str(q): sum(1 for p in bg.plans if p.q == q) for q in sorted({p.q for p in bg.plans})},
+                       "cublas_dgemm_loop_tflops": flops / (ms_dgemm * 1e-3) / 1e12,
+                       "speedup_vs_cublas_dgemm_loop": ms_dgemm / ms,
+                       "rel_frobenius_vs_dgemm": (num / den) ** 0.5},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

@@ -139,6 +139,33 @@ OZ_API oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int
  */
 OZ_API oz_status oz_query_status(void* workspace, void* stream);
 
+/* ---- Many products of uneven shapes in one call. ---- */
+
+/*
+ * oz_batched_workspace_bytes / oz_dgemm_batched -- count independent products
+ * C_i = op(A_i) op(B_i) (the problem of Sec. "Emulation Problem" for each i),
+ * each with its own plan (plans[i]; one plan may serve several problems) and
+ * its own sizes mnk[3i..3i+2] = (m_i, n_i, k_i).
+ * Scheduling: the problems go to the nstreams caller-owned streams (streams[0]
+ * is the origin; the others join it through events, so the whole batch can be
+ * captured into one CUDA graph on streams[0]), each problem to the stream with
+ * the least estimated work so far, largest problems first. The problems of one
+ * stream run one after another and share that stream's slice of the
+ * workspace, so the workspace is nstreams times the largest single-problem
+ * workspace of any stream's problems. oz_batched_workspace_bytes reports it
+ * (0 for invalid arguments).
+ * Arrays (plans, mnk, trans, pointer and leading-dimension arrays, streams)
+ * are host arrays of length count (streams: nstreams); the matrices and the
+ * workspace are device memory. trans may be NULL (no transposes), else
+ * trans[2i], trans[2i+1] = trans_a, trans_b of problem i.
+ * Errors: as oz_dgemm, checked for every problem before anything launches.
+ */
+OZ_API size_t oz_batched_workspace_bytes(int count, const oz_plan* plans, const int64_t* mnk, int nstreams);
+OZ_API oz_status oz_dgemm_batched(int count, const oz_plan* plans, const int64_t* mnk, const int* trans,
+                                  const double* const* A, const int64_t* lda, const double* const* B,
+                                  const int64_t* ldb, double* const* C, const int64_t* ldc, void* workspace,
+                                  size_t workspace_bytes, void* const* streams, int nstreams);
+
 /* ---- The phases on their own, for parity checks and profiling. ---- */
 
 /*

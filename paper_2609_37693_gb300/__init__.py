@@ -38,7 +38,7 @@ OZ_STATIC_SCRATCH_BYTES = 32 << 20
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
             "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
-            "oz_dgemm_static")
+            "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched")
 
 
 class OzError(RuntimeError):
@@ -70,6 +70,8 @@ def _load_library():
         "oz_reconstruct": (I32, [P, I64, I64, P, P, P, P, I64, P]),
         "oz_status_str": (ctypes.c_char_p, [I32]),
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
+        "oz_batched_workspace_bytes": (SZ, [I32, P, P, I32]),
+        "oz_dgemm_batched": (I32, [I32, P, P, P, P, P, P, P, P, P, P, SZ, P, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -138,6 +140,18 @@ def oz_dgemm_static(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, str
     callers that cannot allocate device memory. Calls overlapping on the GPU race."""
     return _lib.oz_dgemm_static(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb),
                                 C, int(ldc), stream)
+
+
+def oz_batched_workspace_bytes(count, plans, mnk, nstreams) -> int:
+    """plans: ctypes array of plan handles; mnk: ctypes int64 array of 3*count."""
+    return int(_lib.oz_batched_workspace_bytes(int(count), plans, mnk, int(nstreams)))
+
+
+def oz_dgemm_batched(count, plans, mnk, trans, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, streams,
+                     nstreams) -> int:
+    """Array arguments are ctypes arrays (or None for trans); see include/oz.h."""
+    return _lib.oz_dgemm_batched(int(count), plans, mnk, trans, A, lda, B, ldb, C, ldc, workspace,
+                                 int(workspace_bytes), streams, int(nstreams))
 
 
 def oz_query_status(workspace, stream) -> int:
@@ -313,3 +327,130 @@ class EmuMatmul:
 
 def emu_matmul(A, B, q: int = 16, engine: int = OZ_ENGINE_AUTO):
     return EmuMatmul.apply(A, B, q, engine)
+
+
+# ---------------------------------------------------------------------------
+# Batched uneven products, CUDA-graph capture and the autotuner
+# ---------------------------------------------------------------------------
+
+def plan_least_q(k: int, bits: int = 53, engine: int = OZ_ENGINE_AUTO) -> Plan:
+    """The paper's configuration rule for one product: the least Q whose
+    window holds at inner dimension k with `bits` kept (Q = 15 up to k = 836
+    and 16 above at 53 bits). Cached."""
+    key = ("least", int(bits), int(max(k, 1)), int(engine))
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(0, bits, max(k, 1), engine)
+        _plan_cache[key] = p
+    return p
+
+
+class BatchedGemm:
+    """count products C_i = A_i B_i of uneven shapes through one
+    oz_dgemm_batched call (optionally captured into one CUDA graph).
+
+    shapes: list of (m, n, k). plans: one Plan per problem, or None for the
+    least-Q rule at `bits`. nstreams: streams the problems spread over."""
+
+    def __init__(self, shapes, plans=None, nstreams: int = 4, bits: int = 53, engine: int = OZ_ENGINE_AUTO,
+                 device=None):
+        torch = _import_torch()
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        self.count = len(self.shapes)
+        self.plans = list(plans) if plans is not None else [plan_least_q(k, bits, engine) for (_, _, k) in self.shapes]
+        self.nstreams = int(nstreams)
+        self.device = torch.device(device or "cuda")
+        self._plan_arr = (ctypes.c_void_p * max(self.count, 1))(*[p.handle for p in self.plans])
+        flat = [x for s in self.shapes for x in s]
+        self._mnk = (ctypes.c_int64 * max(len(flat), 1))(*flat)
+        nbytes = oz_batched_workspace_bytes(self.count, self._plan_arr, self._mnk, self.nstreams)
+        if self.count and nbytes == 0:
+            raise OzError(OZ_ERR_INVALID_ARG, "oz_batched_workspace_bytes")
+        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        # streams[0] is the batch's origin stream (a side stream, so that the
+        # batch can be captured); run() orders it after the caller's stream
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.nstreams)]
+        self._graph = None
+
+    def _ptrs(self, As, Bs, Cs):
+        n = max(self.count, 1)
+        P = ctypes.c_void_p
+        self._A = (P * n)(*[a.data_ptr() for a in As])
+        self._B = (P * n)(*[b.data_ptr() for b in Bs])
+        self._C = (P * n)(*[c.data_ptr() for c in Cs])
+        self._lda = (ctypes.c_int64 * n)(*[max(a.stride(0), 1) for a in As])
+        self._ldb = (ctypes.c_int64 * n)(*[max(b.stride(0), 1) for b in Bs])
+        self._ldc = (ctypes.c_int64 * n)(*[max(c.stride(0), 1) for c in Cs])
+        self._str = (P * self.nstreams)(*[s.cuda_stream for s in self.streams])
+
+    def run(self, As, Bs, Cs):
+        """Launch the batch after the work queued on the current stream; the
+        current stream then waits for the batch."""
+        torch = _import_torch()
+        self._ptrs(As, Bs, Cs)
+        cur = torch.cuda.current_stream(self.device)
+        self.streams[0].wait_stream(cur)
+        st = oz_dgemm_batched(self.count, self._plan_arr, self._mnk, None, self._A, self._lda, self._B, self._ldb,
+                              self._C, self._ldc, self.ws.data_ptr(), self.ws.numel(), self._str, self.nstreams)
+        cur.wait_stream(self.streams[0])
+        _check(st, "oz_dgemm_batched")
+
+    def capture(self, As, Bs, Cs):
+        """Record the batch into one CUDA graph over these exact tensors;
+        replay() reruns it on whatever they hold then."""
+        torch = _import_torch()
+        self._ptrs(As, Bs, Cs)
+        # the first call on each shape sets kernel attributes outside the capture
+        self.run(As, Bs, Cs)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.streams[0], capture_error_mode="relaxed"):
+            st = oz_dgemm_batched(self.count, self._plan_arr, self._mnk, None, self._A, self._lda, self._B,
+                                  self._ldb, self._C, self._ldc, self.ws.data_ptr(), self.ws.numel(), self._str,
+                                  self.nstreams)
+        _check(st, "oz_dgemm_batched (capture)")
+        self._graph = g
+        return g
+
+    def replay(self):
+        """Replay the captured batch after the work queued on the current stream."""
+        torch = _import_torch()
+        cur = torch.cuda.current_stream(self.device)
+        self.streams[0].wait_stream(cur)
+        with torch.cuda.stream(self.streams[0]):
+            self._graph.replay()
+        cur.wait_stream(self.streams[0])
+
+
+_autotune_cache: dict = {}
+
+
+def autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16), bits: int = 53, reps: int = 3):
+    """Pick the stream count for a batch of shapes by timing captured-graph
+    replays of each candidate; returns (best BatchedGemm with its graph
+    captured over As/Bs/Cs, {nstreams: ms}). Results are cached per shape list."""
+    torch = _import_torch()
+    key = (tuple(tuple(int(x) for x in s) for s in shapes), int(bits))
+    timings = {}
+    best = None
+    choices = [_autotune_cache[key]] if key in _autotune_cache else list(candidates)
+    for ns in choices:
+        bg = BatchedGemm(shapes, nstreams=ns, bits=bits)
+        bg.capture(As, Bs, Cs)
+        bg.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(bg.streams[0])
+            bg.replay()
+            e1.record(bg.streams[0])
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        timings[ns] = min(ts)
+        if best is None or timings[ns] < timings[best[0]]:
+            best = (ns, bg)
+        else:
+            del bg
+    _autotune_cache[key] = best[0]
+    return best[1], timings

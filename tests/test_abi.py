@@ -107,3 +107,34 @@ def test_argument_errors_are_caught_on_the_host():
 def test_status_strings():
     for s in range(7):
         assert oz.oz_status_str(s) and oz.oz_status_str(s) != "unknown status"
+
+
+def test_batched_workspace_and_argument_checks():
+    plans = [oz.Plan(16, 0, 1000, oz.OZ_ENGINE_IMMA), oz.Plan(15, 53, 500, oz.OZ_ENGINE_IMMA)]
+    shapes = [(300, 200, 1000), (64, 64, 500), (1000, 10, 100)]
+    parr = (ctypes.c_void_p * 3)(plans[0].handle, plans[1].handle, plans[1].handle)
+    mnk = (ctypes.c_int64 * 9)(*[x for s in shapes for x in s])
+    one = oz.oz_batched_workspace_bytes(3, parr, mnk, 1)
+    assert one >= max(p.workspace_bytes(*s) for p, s in zip([plans[0], plans[1], plans[1]], shapes))
+    two = oz.oz_batched_workspace_bytes(3, parr, mnk, 2)
+    assert two % 2 == 0 and two >= one
+    assert oz.oz_batched_workspace_bytes(3, parr, mnk, 0) == 0
+    fake = 1 << 20
+    P = ctypes.c_void_p
+    ptrs = (P * 3)(fake, fake, fake)
+    lds = (ctypes.c_int64 * 3)(1000, 500, 100)
+    ldb = (ctypes.c_int64 * 3)(200, 64, 10)
+    ldc = (ctypes.c_int64 * 3)(200, 64, 10)
+    streams = (P * 1)(None)
+    # short workspace, bad leading dimension, K above a plan's K_max: refused before any launch
+    assert oz.oz_dgemm_batched(3, parr, mnk, None, ptrs, lds, ptrs, ldb, ptrs, ldc, fake, one - 256, streams,
+                               1) == oz.OZ_ERR_WORKSPACE
+    bad = (ctypes.c_int64 * 3)(1000, 499, 100)
+    assert oz.oz_dgemm_batched(3, parr, mnk, None, ptrs, bad, ptrs, ldb, ptrs, ldc, fake, one, streams,
+                               1) == oz.OZ_ERR_INVALID_ARG
+    mnk_big = (ctypes.c_int64 * 9)(300, 200, 1000, 64, 64, 5000, 1000, 10, 100)
+    big = oz.oz_batched_workspace_bytes(3, parr, mnk_big, 1)
+    lda_big = (ctypes.c_int64 * 3)(1000, 5000, 100)
+    assert oz.oz_dgemm_batched(3, parr, mnk_big, None, ptrs, lda_big, ptrs, ldb, ptrs, ldc, fake, big, streams,
+                               1) == oz.OZ_ERR_K_TOO_LARGE
+    assert oz.oz_dgemm_batched(0, parr, mnk, None, ptrs, lds, ptrs, ldb, ptrs, ldc, None, 0, streams, 1) == oz.OZ_OK
