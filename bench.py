@@ -315,24 +315,26 @@ def run_ours(args, rank, world, local):
             phase_ms[key] += ev[i].elapsed_time(ev[i + 1]) / reps
     phase_sum = sum(phase_ms.values())
 
-    # ---- e2e: host buffers through the public call, copies inside the timed region ----
+    # ---- e2e: host buffers through the public host-I/O call (oz_dgemm_host),
+    # every step copying A and B in and C out inside the timed region ----
     A_pin = torch.from_numpy(A_h).pin_memory()
     B_pin = torch.from_numpy(B_h).pin_memory()
     C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
+    hg = oz.HostGemm(plan, n, n, n, 0, dev)
+    hg(A_pin, B_pin, C_pin, stream)
     torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 5))
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(e2e_steps):
-        A.copy_(A_pin, non_blocking=True)
-        B.copy_(B_pin, non_blocking=True)
-        step()
-        C_pin.copy_(C, non_blocking=True)
+        hg(A_pin, B_pin, C_pin, stream)
     t1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
     e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
+    e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
+    del hg
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----
     peaks = load_peaks()
@@ -379,7 +381,9 @@ def run_ours(args, rank, world, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
-                    "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms,
+                    "api": "oz_dgemm_host (pinned host A, B, C; row chunks overlap copies and phases)",
+                    "equals_device_result": e2e_exact},
             "gpu_launches": oz.launches_per_dgemm(False, False) * args.steps,
             "clocks": clk,
         }

@@ -38,7 +38,8 @@ OZ_STATIC_SCRATCH_BYTES = 32 << 20
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
             "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
-            "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched")
+            "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
+            "oz_dgemm_host")
 
 
 class OzError(RuntimeError):
@@ -71,6 +72,8 @@ def _load_library():
         "oz_status_str": (ctypes.c_char_p, [I32]),
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
         "oz_batched_workspace_bytes": (SZ, [I32, P, P, I32]),
+        "oz_host_workspace_bytes": (SZ, [P, I64, I64, I64, I64]),
+        "oz_dgemm_host": (I32, [P, I64, I64, I64, P, I64, P, I64, P, I64, I64, P, SZ, P, P, P]),
         "oz_dgemm_batched": (I32, [I32, P, P, P, P, P, P, P, P, P, P, SZ, P, I32]),
     }
     for name, (res, args) in sig.items():
@@ -154,6 +157,17 @@ def oz_dgemm_batched(count, plans, mnk, trans, A, lda, B, ldb, C, ldc, workspace
                                  int(workspace_bytes), streams, int(nstreams))
 
 
+def oz_host_workspace_bytes(plan, m, n, k, rows_per_chunk=0) -> int:
+    return int(_lib.oz_host_workspace_bytes(plan, int(m), int(n), int(k), int(rows_per_chunk)))
+
+
+def oz_dgemm_host(plan, m, n, k, A, lda, B, ldb, C, ldc, rows_per_chunk, workspace, workspace_bytes, stream,
+                  stream_h2d, stream_d2h) -> int:
+    """A, B, C are HOST pointers (pinned memory overlaps the copies)."""
+    return _lib.oz_dgemm_host(plan, int(m), int(n), int(k), A, int(lda), B, int(ldb), C, int(ldc),
+                              int(rows_per_chunk), workspace, int(workspace_bytes), stream, stream_h2d, stream_d2h)
+
+
 def oz_query_status(workspace, stream) -> int:
     return _lib.oz_query_status(workspace, stream)
 
@@ -179,6 +193,12 @@ def oz_reconstruct(plan, m, n, Y, s, t, C, ldc, stream) -> int:
 def _check(st: int, what: str):
     if st != OZ_OK:
         raise OzError(st, what)
+
+
+def _ld(t) -> int:
+    """Leading dimension of a row-major 2-D tensor; for an empty tensor, its
+    column count (the strides of empty tensors carry no layout)."""
+    return max(t.stride(0), 1) if t.numel() else max(t.shape[1], 1)
 
 
 def round_up(x: int, r: int) -> int:
@@ -227,7 +247,7 @@ def dgemm(A, B, plan: Plan | None = None, trans_a: bool = False, trans_b: bool =
     import torch
     if A.dtype != torch.float64 or B.dtype != torch.float64 or not A.is_cuda or not B.is_cuda:
         raise TypeError("dgemm takes float64 CUDA tensors")
-    if A.dim() != 2 or B.dim() != 2 or A.stride(1) != 1 or B.stride(1) != 1:
+    if A.dim() != 2 or B.dim() != 2 or (A.numel() and A.stride(1) != 1) or (B.numel() and B.stride(1) != 1):
         raise ValueError("dgemm takes 2-D tensors with unit inner stride")
     m, k = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
     k2, n = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
@@ -238,8 +258,8 @@ def dgemm(A, B, plan: Plan | None = None, trans_a: bool = False, trans_b: bool =
     C = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A.device)
     if ws is None:
         ws = workspace(plan, m, n, k, A.device)
-    st = oz_dgemm(plan.handle, int(trans_a), int(trans_b), m, n, k, A.data_ptr(), max(A.stride(0), 1),
-                  B.data_ptr(), max(B.stride(0), 1), C.data_ptr(), max(C.stride(0), 1), ws.data_ptr(),
+    st = oz_dgemm(plan.handle, int(trans_a), int(trans_b), m, n, k, A.data_ptr(), _ld(A),
+                  B.data_ptr(), _ld(B), C.data_ptr(), _ld(C), ws.data_ptr(),
                   ws.numel(), _stream_handle(stream))
     _check(st, "oz_dgemm")
     return C
@@ -378,9 +398,9 @@ class BatchedGemm:
         self._A = (P * n)(*[a.data_ptr() for a in As])
         self._B = (P * n)(*[b.data_ptr() for b in Bs])
         self._C = (P * n)(*[c.data_ptr() for c in Cs])
-        self._lda = (ctypes.c_int64 * n)(*[max(a.stride(0), 1) for a in As])
-        self._ldb = (ctypes.c_int64 * n)(*[max(b.stride(0), 1) for b in Bs])
-        self._ldc = (ctypes.c_int64 * n)(*[max(c.stride(0), 1) for c in Cs])
+        self._lda = (ctypes.c_int64 * n)(*[_ld(a) for a in As])
+        self._ldb = (ctypes.c_int64 * n)(*[_ld(b) for b in Bs])
+        self._ldc = (ctypes.c_int64 * n)(*[_ld(c) for c in Cs])
         self._str = (P * self.nstreams)(*[s.cuda_stream for s in self.streams])
 
     def run(self, As, Bs, Cs):
@@ -454,3 +474,30 @@ def autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16), bits: int 
             del bg
     _autotune_cache[key] = best[0]
     return best[1], timings
+
+
+class HostGemm:
+    """C = A B for host (CPU) float64 tensors through oz_dgemm_host: the copies
+    to and from the device overlap the phases of neighbouring row chunks. Pin
+    the host tensors (tensor.pin_memory()) for the overlap to happen."""
+
+    def __init__(self, plan: Plan, m: int, n: int, k: int, rows_per_chunk: int = 0, device=None):
+        torch = _import_torch()
+        self.plan, self.m, self.n, self.k, self.rows = plan, m, n, k, rows_per_chunk
+        self.device = torch.device(device or "cuda")
+        nbytes = oz_host_workspace_bytes(plan.handle, m, n, k, rows_per_chunk)
+        if nbytes == 0:
+            raise OzError(OZ_ERR_INVALID_ARG, "oz_host_workspace_bytes")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.h2d = torch.cuda.Stream(self.device)
+        self.d2h = torch.cuda.Stream(self.device)
+
+    def __call__(self, A, B, C, stream=None):
+        torch = _import_torch()
+        s = torch.cuda.current_stream(self.device) if stream is None else stream
+        st = oz_dgemm_host(self.plan.handle, self.m, self.n, self.k, A.data_ptr(), _ld(A), B.data_ptr(),
+                           _ld(B), C.data_ptr(), _ld(C), self.rows, self.ws.data_ptr(),
+                           self.ws.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.c_void_p(self.h2d.cuda_stream),
+                           ctypes.c_void_p(self.d2h.cuda_stream))
+        _check(st, "oz_dgemm_host")
+        return C

@@ -1,0 +1,30 @@
+"""oz_dgemm_host (host-resident operands, copies overlapped with the phases of
+neighbouring row chunks) gives the product oz_dgemm gives, bit for bit."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2609_37693_gb300 as oz  # noqa: E402
+
+
+@pytest.mark.parametrize("m,n,k,rows", [(1000, 700, 900, 256), (513, 300, 2000, 0), (64, 64, 64, 0),
+                                        (2048, 1024, 1500, 512), (700, 129, 0, 300)])
+def test_host_path_equals_device_path(m, n, k, rows):
+    plan = oz.Plan(16, 0, max(k, 1))
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=m + n)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
+    hg = oz.HostGemm(plan, m, n, k, rows)
+    hg(Ah, Bh, Ch)
+    torch.cuda.synchronize()
+    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
+    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
+    assert oz.query_status(hg.ws) == oz.OZ_OK
