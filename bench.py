@@ -139,6 +139,25 @@ def throughput_tflops(flops_per_step: float, steps: int, elapsed_ms: float, worl
     return world * flops_per_step * steps / (elapsed_ms * 1e-3) / 1e12
 
 
+def gemm_traffic(plan, n, oz):
+    """DRAM bytes per launch of the TC GEMM from its last ncu capture, scaled to
+    this size by n^2; None for another engine, modulus count, or once the
+    kernel source differs from the one the counters were taken on."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if plan.engine != oz.OZ_ENGINE_TC or plan.q != rec["q"]:
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+        return None
+    per = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * (n / rec["captured_n"]) ** 2
+    return {"bytes": per, "captured_n": rec["captured_n"], "scaled_by": "n^2",
+            "algorithmic_bytes": 2.0 * plan.q * 2 * n * n + plan.q * n * n}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -350,6 +369,10 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "residue GEMM (+fused epilogue)",
                 "peak_source": peak_src}
+    tr = gemm_traffic(plan, n, oz)
+    if tr is not None:
+        roofline["traffic"] = tr.pop("bytes")
+        roofline["traffic_source"] = dict(tr, unit="bytes per launch")
     hbm = peaks.get("hbm_gbs", 6768.8)
     bytes_split = 8.0 * 2 * n * n + plan.q * 2.0 * n * n * (2 if plan.engine == oz.OZ_ENGINE_TC else 1)
     bytes_rec = plan.q * n * n + 8.0 * n * n
