@@ -64,8 +64,18 @@ typedef enum {
 typedef enum {
   OZ_ENGINE_AUTO = 0,  /* the fastest engine available for the plan */
   OZ_ENGINE_IMMA = 1,  /* INT8 residue planes, warp-level mma.sync s8 -> s32 */
-  OZ_ENGINE_TC = 2     /* BF16-held residue planes, tcgen05.mma into TMEM */
+  OZ_ENGINE_TC = 2,    /* BF16-held residue planes, tcgen05.mma into TMEM */
+  OZ_ENGINE_FP = 3     /* float-format planes (oz_plan_create_fp), tcgen05.mma kind::f8f6f4 */
 } oz_engine;
+
+/* Low-precision float formats (OCP): FP8 E4M3 and E5M2, FP6 E2M3 and E3M2, FP4 E2M1. */
+typedef enum {
+  OZ_FMT_E4M3 = 1,
+  OZ_FMT_E2M3 = 2,
+  OZ_FMT_E3M2 = 3,
+  OZ_FMT_E2M1 = 4,
+  OZ_FMT_E5M2 = 5
+} oz_format;
 
 typedef struct oz_plan_s* oz_plan;
 
@@ -96,6 +106,40 @@ OZ_API oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int64_t 
  * Any output pointer may be NULL. moduli, if given, must hold OZ_MAX_MODULI.
  */
 OZ_API oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, int* engine, uint32_t* moduli);
+
+/*
+ * oz_plan_create_fp -- a configuration over a low-precision float alphabet
+ * (Sec. "Forms and Channels", Sec. "Instantiation"): pairwise-coprime channels,
+ * each a modulus with a one-limb, schoolbook or Toom (Karatsuba) form whose
+ * tables take values in the format's alphabet S (its finite values scaled to
+ * integers), found by an exact least-GEMM-count search and frozen in the
+ * library for inner dimensions K_cfg = 8192 and 16384; the plan takes the
+ * least K_cfg >= k_hint. Every plane value is at most floor(sqrt(2^24/K_cfg)),
+ * so each GEMM's FP32 accumulator is exact (eq. ov-accgen).
+ *   format   an oz_format value.
+ *   k_hint   the largest inner dimension the caller intends to use.
+ *   bits     as for oz_plan_create (0: the largest beta <= 64 the window allows).
+ * The plan owns a small device table of codes (allocated here on the current
+ * device, freed by oz_plan_destroy). Without a CUDA device the plan is still
+ * made and describes the configuration (oz_plan_info_fp), but products on it
+ * return OZ_ERR_CUDA. Products run through oz_dgemm, oz_dgemm_batched and the
+ * phase entry points as for INT8 plans (oz_dgemm_host does not take float
+ * plans); their residues Y are uint16, one per entry and channel.
+ */
+OZ_API oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint, int bits);
+
+/*
+ * oz_plan_info_fp -- describe a float-format plan: channel count, GEMM count
+ * (the paper's Q), K_cfg, per channel its modulus, form (1 one limb,
+ * 2 schoolbook with m | b^2, 3 Toom at {0, 1, inf}, 4 schoolbook) and base, the
+ * plane count, and (if plane_values is given, values_len entries long) the
+ * plane value tables: plane p (channels in order, planes of a channel in the
+ * order a0 | a0, a1 | a0, a0 + a1, a1) holds m_c scaled alphabet values, one
+ * per class. Any output pointer may be NULL.
+ */
+OZ_API oz_status oz_plan_info_fp(oz_plan plan, int* channels, int* gemms, int64_t* k_cfg, uint32_t* moduli,
+                                 int* forms, int* bases, int* plane_count, int16_t* plane_values,
+                                 size_t values_len);
 
 /* Release a plan (NULL is accepted). */
 OZ_API void oz_plan_destroy(oz_plan plan);

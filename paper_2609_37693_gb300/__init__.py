@@ -29,6 +29,15 @@ OZ_ERR_CUDA = 6
 OZ_ENGINE_AUTO = 0
 OZ_ENGINE_IMMA = 1
 OZ_ENGINE_TC = 2
+OZ_ENGINE_FP = 3
+
+OZ_FMT_E4M3 = 1
+OZ_FMT_E2M3 = 2
+OZ_FMT_E3M2 = 3
+OZ_FMT_E2M1 = 4
+OZ_FMT_E5M2 = 5
+FORMATS = {"E4M3": OZ_FMT_E4M3, "E2M3": OZ_FMT_E2M3, "E3M2": OZ_FMT_E3M2, "E2M1": OZ_FMT_E2M1,
+           "E5M2": OZ_FMT_E5M2}
 
 OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
@@ -39,7 +48,7 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
-            "oz_dgemm_host")
+            "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp")
 
 
 class OzError(RuntimeError):
@@ -73,6 +82,9 @@ def _load_library():
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
         "oz_batched_workspace_bytes": (SZ, [I32, P, P, I32]),
         "oz_host_workspace_bytes": (SZ, [P, I64, I64, I64, I64]),
+        "oz_plan_create_fp": (I32, [ctypes.POINTER(P), I32, I64, I32]),
+        "oz_plan_info_fp": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I64), P, P, P,
+                                  ctypes.POINTER(I32), P, SZ]),
         "oz_dgemm_host": (I32, [P, I64, I64, I64, P, I64, P, I64, P, I64, I64, P, SZ, P, P, P]),
         "oz_dgemm_batched": (I32, [I32, P, P, P, P, P, P, P, P, P, P, SZ, P, I32]),
     }
@@ -100,6 +112,38 @@ def oz_plan_create(num_moduli: int = 16, bits: int = 0, k_hint: int = 8192, engi
     h = ctypes.c_void_p()
     st = _lib.oz_plan_create(ctypes.byref(h), int(num_moduli), int(bits), int(k_hint), int(engine))
     return st, (h.value if st == OZ_OK else None)
+
+
+def oz_plan_create_fp(fmt: int, k_hint: int = 8192, bits: int = 0):
+    """Returns (status, plan handle or None) for a float-format configuration."""
+    h = ctypes.c_void_p()
+    st = _lib.oz_plan_create_fp(ctypes.byref(h), int(fmt), int(k_hint), int(bits))
+    return st, (h.value if st == OZ_OK else None)
+
+
+def oz_plan_info_fp(plan, want_values: bool = False):
+    """Returns (status, dict(channels, gemms, k_cfg, moduli, forms, bases, planes[, values]))."""
+    ch, gm, npl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    kc = ctypes.c_int64()
+    mods = (ctypes.c_uint32 * 32)()
+    forms = (ctypes.c_int * 32)()
+    bases = (ctypes.c_int * 32)()
+    st = _lib.oz_plan_info_fp(plan, ctypes.byref(ch), ctypes.byref(gm), ctypes.byref(kc), mods, forms, bases,
+                              ctypes.byref(npl), None, 0)
+    if st != OZ_OK:
+        return st, None
+    info = {"channels": ch.value, "gemms": gm.value, "k_cfg": kc.value, "moduli": list(mods[: ch.value]),
+            "forms": list(forms[: ch.value]), "bases": list(bases[: ch.value]), "planes": npl.value}
+    if want_values:
+        total = 0
+        for m, f in zip(info["moduli"], info["forms"]):
+            total += m * (1 if f == 1 else 3 if f == 3 else 2)
+        vals = (ctypes.c_int16 * total)()
+        st = _lib.oz_plan_info_fp(plan, None, None, None, None, None, None, None, vals, total)
+        if st != OZ_OK:
+            return st, None
+        info["values"] = list(vals)
+    return st, info
 
 
 def oz_plan_info(plan):
@@ -227,6 +271,37 @@ class Plan:
 
     def __repr__(self):
         return f"Plan(q={self.q}, bits={self.bits}, k_max={self.k_max}, engine={self.engine})"
+
+
+class PlanFP(Plan):
+    """A float-format configuration (oz_plan_create_fp): ``PlanFP("E4M3", k_hint=8192)``.
+    q is the number of low-precision GEMMs; moduli, forms and bases describe
+    the channels."""
+
+    def __init__(self, fmt, k_hint: int = 8192, bits: int = 0):
+        code = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        st, h = oz_plan_create_fp(code, k_hint, bits)
+        _check(st, "oz_plan_create_fp")
+        self.handle = h
+        _, info = oz_plan_info(h)
+        _, fi = oz_plan_info_fp(h)
+        self.format = code
+        self.bits, self.k_max, self.engine = info["bits"], info["k_max"], info["engine"]
+        self.channels, self.q, self.k_cfg = fi["channels"], fi["gemms"], fi["k_cfg"]
+        self.moduli, self.forms, self.bases, self.planes = fi["moduli"], fi["forms"], fi["bases"], fi["planes"]
+
+    def plane_values(self):
+        """[plane][class] scaled alphabet values of every plane's table."""
+        _, fi = oz_plan_info_fp(self.handle, want_values=True)
+        out, off = [], 0
+        for m, f in zip(self.moduli, self.forms):
+            for _ in range(1 if f == 1 else 3 if f == 3 else 2):
+                out.append(fi["values"][off: off + m])
+                off += m
+        return out
+
+    def __repr__(self):
+        return f"PlanFP(format={self.format}, q={self.q}, channels={self.channels}, bits={self.bits})"
 
 
 def _stream_handle(stream=None):

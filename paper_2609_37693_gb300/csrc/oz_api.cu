@@ -21,7 +21,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   if (!p || m < 0 || n < 0 || k < 0) return false;
-  const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;
+  const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;     // bf16 planes; int8 residues or float codes
+  const int64_t nplanes = p->is_fp ? p->fp.nplanes : p->Q;
+  const int64_t ybytes = p->is_fp ? 2 : 1;                    // 16-bit digits for moduli above 255
   L->m_pad = round_up(m > 0 ? m : 1, oz::kPadRows);
   L->n_pad = round_up(n > 0 ? n : 1, oz::kPadRows);
   L->k_pad = round_up(k > 0 ? k : 1, oz::kPadK);
@@ -30,9 +32,9 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   L->s = off; off = align256(off + 4 * (size_t)m);
   L->t = off; off = align256(off + 4 * (size_t)n);
   L->colmax = off; off = align256(off + 8 * (size_t)(m > n ? m : n));
-  L->u = off; off = align256(off + (size_t)p->Q * L->m_pad * L->k_pad * elem);
-  L->v = off; off = align256(off + (size_t)p->Q * L->n_pad * L->k_pad * elem);
-  L->y = off; off = align256(off + (size_t)p->Q * m * n);
+  L->u = off; off = align256(off + (size_t)nplanes * L->m_pad * L->k_pad * elem);
+  L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * L->k_pad * elem);
+  L->y = off; off = align256(off + (size_t)p->Q * m * n * ybytes);
   L->total = off;
   return true;
 }
@@ -91,6 +93,20 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
   void* V = ws + L.v;
   uint8_t* Y = reinterpret_cast<uint8_t*>(ws + L.y);
 
+  if (plan->is_fp) {
+    if (!plan->d_codes) return OZ_ERR_CUDA;
+    const OzFpTables& F = plan->fp;
+    uint8_t* U8 = static_cast<uint8_t*>(U);
+    uint8_t* V8 = static_cast<uint8_t*>(V);
+    uint16_t* Y16 = reinterpret_cast<uint16_t*>(Y);
+    e = oz::launch_split_fp(T, F, !trans_a, m, k, A, lda, L.m_pad, L.k_pad, s, U8, flag, colmax, st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+    e = oz::launch_split_fp(T, F, trans_b, n, k, B, ldb, L.n_pad, L.k_pad, t, V8, flag, colmax, st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+    e = oz::launch_gemm_fp(F, m, n, L.m_pad, L.n_pad, L.k_pad, U8, V8, Y16, 0, flag, st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+    return cuda_status(oz::launch_reconstruct16(T, m, n, Y16, s, t, C, ldc, st));
+  }
   // Scale + Reduce, A side: vectors are the rows of op(A).
   e = trans_a ? oz::launch_split_cols(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, colmax, st)
               : oz::launch_split_rows(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, st);
@@ -132,6 +148,10 @@ extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_
   if (!contiguous && nvec > 0 && !colmax) return OZ_ERR_INVALID_ARG;
   const int bf16 = plan->engine == OZ_ENGINE_TC;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->is_fp && !plan->d_codes) return OZ_ERR_CUDA;
+  if (plan->is_fp)
+    return cuda_status(oz::launch_split_fp(plan->tab, plan->fp, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts,
+                                           static_cast<uint8_t*>(planes), flag, colmax, st));
   cudaError_t e = contiguous
                       ? oz::launch_split_rows(plan->tab, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, bf16,
                                               flag, st)
@@ -150,6 +170,10 @@ extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t
   if (m == 0 || n == 0) return OZ_OK;
   if (!U || !V || !Y || !aligned(U, 16) || !aligned(V, 16)) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->is_fp)
+    return cuda_status(oz::launch_gemm_fp(plan->fp, m, n, m_pad, n_pad, k_pad, static_cast<const uint8_t*>(U),
+                                          static_cast<const uint8_t*>(V), reinterpret_cast<uint16_t*>(Y), raw ? 1 : 0,
+                                          flag, st));
   if (plan->engine == OZ_ENGINE_TC)
     return cuda_status(oz::launch_gemm_tc(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
   return cuda_status(oz::launch_gemm_imma(plan->tab, m, n, k_pad, static_cast<const int8_t*>(U), m_pad * k_pad,
@@ -162,5 +186,7 @@ extern "C" oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const ui
   if (m == 0 || n == 0) return OZ_OK;
   if (!Y || !s || !t || !C || !aligned(C, 8)) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->is_fp)
+    return cuda_status(oz::launch_reconstruct16(plan->tab, m, n, reinterpret_cast<const uint16_t*>(Y), s, t, C, ldc, st));
   return cuda_status(oz::launch_reconstruct(plan->tab, m, n, Y, s, t, C, ldc, st));
 }

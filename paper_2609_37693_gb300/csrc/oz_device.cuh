@@ -1,0 +1,47 @@
+// oz_device.cuh -- device helpers shared by the split kernels (INT8 and
+// float-format planes): the IEEE-field view of eq. convert.
+#pragma once
+
+#include <stdint.h>
+
+namespace oz {
+
+constexpr uint64_t kAbsMask = 0x7fffffffffffffffull;
+
+// Shift s from the largest |x| bit pattern.
+static __device__ __forceinline__ int32_t shift_from_maxbits(uint64_t mb, int beta) {
+  if (mb == 0) return 0;
+  int eb = (int)(mb >> 52);
+  int e = eb ? eb - 1022 : (64 - __clzll((long long)mb)) - 1074;  // frexp exponent
+  return beta - e;
+}
+
+// Decoded truncated integer of one entry: |a'| and its sign.
+struct Trunc {
+  uint64_t mag;
+  uint32_t neg;
+};
+
+static __device__ __forceinline__ Trunc truncate(uint64_t bits, int32_t s) {
+  Trunc t;
+  t.neg = (uint32_t)(bits >> 63);
+  int eb = (int)((bits >> 52) & 0x7ff);
+  uint64_t f = bits & ((1ull << 52) - 1);
+  uint64_t mant = eb ? (f | (1ull << 52)) : f;
+  int sh = (eb ? eb - 1075 : -1074) + s;   // a' = mant * 2^sh, |a'| < 2^beta <= 2^64
+  if (sh >= 0) t.mag = mant << sh;         // sh <= 11 when beta <= 64
+  else t.mag = (-sh) >= 64 ? 0ull : (mant >> (-sh));
+  return t;
+}
+
+// 64-bit max across a warp.
+static __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+}  // namespace oz

@@ -1,0 +1,797 @@
+// oz_fp.cu -- the five phases on a low-precision float configuration
+// (Sec. "Forms and Channels"; oz_plan_fp.cpp builds the configuration).
+//
+// Reduce: for every entry and channel, the class c = a' mod m in [0, m)
+// (a' = trunc(x 2^s) from the IEEE fields, cut into 16-bit pieces, one 32-bit
+// Barrett step), then for each plane of the channel's form the code of the
+// plane value the form assigns to c, read from the plan's code tables.
+//
+// GEMMs and epilogue: tcgen05.mma.kind::f8f6f4 on the codes (E4M3, E5M2, E2M3,
+// E3M2 or E2M1) into FP32 accumulators in tensor memory. The work unit is a
+// (channel, 128 x 256 tile); its GEMMs run one after another, each over the
+// whole inner dimension in one accumulator (every plane value is at most
+// floor(sqrt(2^24 / K)), eq. ov-accgen), and the epilogue folds GEMM k as
+//   r <- r + lambda_k (W_k mod m)  (mod m)                 (order R>C)
+// in exact fp32 arithmetic, keeping r (|r| < 0.51 m) as a 16-bit field per
+// entry in registers; at the end of the unit it writes the CRT digit
+// (W mod m) (P/m)^-1 mod m, or W mod m, as uint16.
+//
+// Reconstruct: the CRT of Sec. "Around the GEMMs" on 16-bit digits, moduli
+// taken in pairs as in oz_reconstruct.cu.
+#include <cuda.h>
+#include <stdint.h>
+
+#include "oz_device.cuh"
+#include "oz_internal.h"
+
+namespace oz {
+namespace {
+
+// =========================================================================
+// Reduce
+// =========================================================================
+
+struct ChConst {
+  uint32_t m, magic, c16, c32, c48;
+};
+
+__device__ __forceinline__ ChConst ch_const(const OzFpTables& F, int c) {
+  ChConst k;
+  k.m = F.m[c];
+  k.magic = F.magic[c];
+  k.c16 = F.c16[c];
+  k.c32 = F.c32[c];
+  k.c48 = F.c48[c];
+  return k;
+}
+
+struct Pieces16 {
+  uint32_t p0, p1, p2, p3, neg;
+};
+
+__device__ __forceinline__ Pieces16 pieces16(uint64_t bits, int32_t s) {
+  const Trunc t = truncate(bits, s);
+  Pieces16 P;
+  P.p0 = (uint32_t)t.mag & 0xffffu;
+  P.p1 = (uint32_t)(t.mag >> 16) & 0xffffu;
+  P.p2 = (uint32_t)(t.mag >> 32) & 0xffffu;
+  P.p3 = (uint32_t)(t.mag >> 48);
+  P.neg = t.neg;
+  return P;
+}
+
+// class of +-|a'| modulo m, in [0, m); y < 2^16 (1 + 3 * 4095) < 2^32
+__device__ __forceinline__ uint32_t class_of(const ChConst& k, const Pieces16& P) {
+  const uint32_t y = P.p0 + P.p1 * k.c16 + P.p2 * k.c32 + P.p3 * k.c48;
+  const uint32_t r = mod_barrett(y, k.m, k.magic);
+  return P.neg ? (r ? k.m - r : 0u) : r;
+}
+
+// Contiguous vectors: one CTA of 256 threads per vector, 8 entries per thread
+// and pass; planes of uint8 codes [nplanes][nvec_pad][k_pad].
+__global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constant__ OzFpTables F, int bits,
+                                                            int64_t nvec, int64_t len, const double* __restrict__ X,
+                                                            int64_t ld, int64_t nvec_pad, int64_t k_pad,
+                                                            int32_t* __restrict__ shifts, uint8_t* __restrict__ planes,
+                                                            int32_t* __restrict__ flag) {
+  __shared__ uint64_t red[8];
+  __shared__ int32_t s_sh;
+  const int64_t v = blockIdx.x;
+  const int tid = threadIdx.x;
+  const bool live = v < nvec;
+  const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
+  uint64_t mx = 0;
+  uint32_t bad = 0;
+  if (live) {
+    for (int64_t h = tid; h < len; h += 256) {
+      uint64_t b = __ldg(row + h) & kAbsMask;
+      bad |= (uint32_t)((b >> 52) == 0x7ff);
+      mx = b > mx ? b : mx;
+    }
+  }
+  mx = warp_max_u64(mx);
+  bad = __any_sync(0xffffffffu, bad);
+  if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t m = 0, anybad = 0;
+    for (int w = 0; w < 8; ++w) {
+      anybad |= red[w] >> 63;
+      uint64_t x = red[w] & kAbsMask;
+      m = x > m ? x : m;
+    }
+    if (anybad && flag) atomicOr(flag, 1);
+    int32_t s = live ? shift_from_maxbits(anybad ? 0 : m, bits) : 0;
+    s_sh = s;
+    if (live) shifts[v] = s;
+  }
+  __syncthreads();
+  const int32_t s = s_sh;
+  const int64_t plane = nvec_pad * k_pad;
+  for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
+    Pieces16 P[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      uint64_t b = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+      if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
+      P[e] = pieces16(b, s);
+    }
+    for (int c = 0; c < F.nch; ++c) {
+      const ChConst k = ch_const(F, c);
+      uint32_t cls[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) cls[e] = class_of(k, P[e]);
+      const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
+      for (int q = 0; q < np; ++q) {
+        const uint8_t* tab = F.codes + F.plane_off[p0 + q];
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) lo |= (uint32_t)__ldg(tab + cls[e]) << (8 * e);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) hi |= (uint32_t)__ldg(tab + cls[4 + e]) << (8 * e);
+        *reinterpret_cast<uint2*>(planes + (int64_t)(p0 + q) * plane + v * k_pad + h0) = make_uint2(lo, hi);
+      }
+    }
+  }
+}
+
+// Strided vectors (columns of B, or of A^T): 64 (h) x 64 (vector) tiles through
+// shared memory so that the planes, K-major per vector, are written along h.
+__global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constant__ OzFpTables F, int64_t nvec,
+                                                            int64_t len, const double* __restrict__ X, int64_t ld,
+                                                            int64_t nvec_pad, int64_t k_pad,
+                                                            const int32_t* __restrict__ shifts,
+                                                            uint8_t* __restrict__ planes) {
+  constexpr int kPitchWords = 17;
+  __shared__ uint32_t tile[2][64 * kPitchWords];
+  const int tid = threadIdx.x;
+  const int jl = tid & 63;
+  const int hg = tid >> 6;
+  const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int64_t hbase = (int64_t)blockIdx.y * 64;
+  const int64_t j = j0 + jl;
+  const bool live = j < nvec;
+  const int32_t s = live ? shifts[j] : 0;
+  Pieces16 P[16];
+  const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    int64_t h = hbase + hg * 16 + e;
+    uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
+    if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
+    P[e] = pieces16(b, s);
+  }
+  const int64_t plane = nvec_pad * k_pad;
+  int pg = 0;  // planes written so far: picks the shared buffer
+  for (int c = 0; c < F.nch; ++c) {
+    const ChConst k = ch_const(F, c);
+    uint32_t cls[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) cls[e] = class_of(k, P[e]);
+    const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
+    for (int q = 0; q < np; ++q, ++pg) {
+      uint32_t* tb = tile[pg & 1];
+      const uint8_t* tab = F.codes + F.plane_off[p0 + q];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) word |= (uint32_t)__ldg(tab + cls[4 * w + e]) << (8 * e);
+        tb[jl * kPitchWords + hg * 4 + w] = word;
+      }
+      __syncthreads();
+      for (int cidx = tid; cidx < 64 * 4; cidx += 256) {
+        const int rowi = cidx >> 2, ch = cidx & 3;
+        uint4 o;
+        o.x = tb[rowi * kPitchWords + ch * 4 + 0];
+        o.y = tb[rowi * kPitchWords + ch * 4 + 1];
+        o.z = tb[rowi * kPitchWords + ch * 4 + 2];
+        o.w = tb[rowi * kPitchWords + ch * 4 + 3];
+        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * k_pad + hbase + ch * 16) = o;
+      }
+    }
+  }
+}
+
+// =========================================================================
+// GEMMs + epilogue (tcgen05, kind::f8f6f4)
+// =========================================================================
+
+constexpr int BM = 128, BN = 256, BK = 128;        // BK in 8-bit entries = 128 bytes
+constexpr int STAGES = 4;
+constexpr int kBand = 8;
+constexpr int A_BYTES = BM * BK;                   // 16 KiB
+constexpr int B_BYTES = BN * BK;                   // 32 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr int kTmemCols = 512;
+constexpr int kSmemBytes = STAGES * STAGE_BYTES + 256 + 1024;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer() - t0 > kTimeoutNs) {
+        *abort_flag = 1;
+        if (status) atomicOr(status, 2);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_timer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer() - t0 > kTimeoutNs) return;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major 128-byte-swizzled operand (rows of 128 bytes, groups of 8 rows 1024 B apart)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct Unit {
+  int c, tm, tn;
+};
+
+__device__ __forceinline__ Unit unit_coord(int t, int tiles_m, int tiles_n) {
+  const int per_c = tiles_m * tiles_n;
+  Unit u;
+  u.c = t / per_c;
+  const int r = t - u.c * per_c;
+  const int band = r / (tiles_m * kBand);
+  const int rb = r - band * tiles_m * kBand;
+  const int bw = min(kBand, tiles_n - band * kBand);
+  u.tm = rb / bw;
+  u.tn = band * kBand + (rb - u.tm * bw);
+  return u;
+}
+
+struct FpParams {
+  int m, n, tiles_m, tiles_n, num_units, kblocks, m_pad, n_pad, raw;
+  uint32_t idesc;
+  uint16_t* Y;
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ OzFpTables F, const FpParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_base = smem_u32(smem_raw);
+  const uint32_t base = (raw_base + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw_base);
+  const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), kEpiWarps * 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[STAGES];
+      bool outstanding[STAGES];
+      for (int i = 0; i < STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_units && ok; t += gridDim.x) {
+        const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+        const int g0 = F.ch_gemm0[u.c], ng = F.ch_ngemm[u.c];
+        for (int g = g0; g < g0 + ng && ok; ++g) {
+          const int ya = (int)F.g_pa[g] * p.m_pad + u.tm * BM;
+          const int yb = (int)F.g_pb[g] * p.n_pad + u.tn * BN;
+          for (int kb = 0; kb < p.kblocks; ++kb) {
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
+            outstanding[s] = false;
+            const uint32_t sa = base + s * STAGE_BYTES;
+            mbar_expect_tx(full_bar(s), STAGE_BYTES);
+            tma_load_2d(sa, &tmA, full_bar(s), kb * BK, ya);
+            tma_load_2d(sa + A_BYTES, &tmB, full_bar(s), kb * BK, yb);
+            outstanding[s] = true;
+            issued_parity[s] = ph;
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+        }
+      }
+      if (!ok) {
+        for (int i = 0; i < STAGES; ++i)
+          if (outstanding[i]) mbar_drain(full_bar(i), issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t g_ctr = 0;  // accumulations issued (one per GEMM of a unit)
+      bool ok = true;
+      for (int t = blockIdx.x; t < p.num_units && ok; t += gridDim.x) {
+        const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+        const int ng = F.ch_ngemm[u.c];
+        for (int gi = 0; gi < ng && ok; ++gi, ++g_ctr) {
+          const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + b * BN;
+          for (int kb = 0; kb < p.kblocks; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 32; ++kk)
+              umma_f8f6f4(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(empty_bar(s));
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(tfull_bar(b));
+        }
+      }
+      if (!ok) {
+        umma_commit(drain_bar);
+        mbar_drain(drain_bar, 0);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int e = warp - 2;
+    const int quarter = warp & 3;
+    const int half = e >> 2;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    const float wscale = __int_as_float((127 + F.e2) << 23);      // 2^e2: accumulator -> W
+    uint32_t g_ctr = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < p.num_units && ok; t += gridDim.x) {
+      const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+      const int g0 = F.ch_gemm0[u.c], ng = F.ch_ngemm[u.c];
+      const float mf = F.mf[u.c], invm = F.invm[u.c];
+      uint32_t acc16[64];                    // running residue + 2048, 16 bits per column
+#pragma unroll
+      for (int i = 0; i < 64; ++i) acc16[i] = 0x08000800u;
+      for (int gi = 0; gi < ng; ++gi, ++g_ctr) {
+        const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+        const float lam = F.g_lam[g0 + gi];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + lane_addr + b * BN + half * 128 + ch * 32, v);
+          tmem_ld_wait();
+          if (ch == 3) {
+            tc_fence_before();
+            mbar_arrive(tempty_bar(b));
+          }
+#pragma unroll
+          for (int w = 0; w < 16; ++w) {
+            uint32_t out[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              // previous residue r from its 16-bit field r + 2048
+              const float prev =
+                  __int_as_float(0x4B000000u | ((acc16[ch * 16 + w] >> (16 * j)) & 0xffffu)) - 8390656.0f;
+              const float W = __uint_as_float(v[2 * w + j]) * wscale;               // exact integer, |W| <= 2^24
+              const float wq = fmaf(W, invm, 12582912.0f) - 12582912.0f;
+              const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.51 m
+              const float tsum = fmaf(lam, wm, prev);                              // exact: < 2^24
+              const float q2 = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
+              const float r = fmaf(-q2, mf, tsum);                                 // |r| < 0.51 m
+              out[j] = __float_as_uint(r + 8390656.0f) & 0xffffu;                  // r + 2048
+            }
+            acc16[ch * 16 + w] = out[0] | (out[1] << 16);
+          }
+        }
+      }
+      if (!ok) break;
+      // ---- unit done: W mod m or the CRT digit, 16 bits per entry ----
+      const int row = u.tm * BM + quarter * 32 + lane;
+      const int col0 = u.tn * BN + half * 128;
+      if (row < p.m && col0 < p.n) {
+        const float inv = (float)F.inv[u.c];
+        uint16_t* dst = p.Y + (size_t)u.c * p.m * p.n + (size_t)row * p.n + col0;
+        const bool vec = col0 + 128 <= p.n && (p.n & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+#pragma unroll
+        for (int i4 = 0; i4 < 16; ++i4) {
+          uint32_t o4[4];
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            uint32_t o = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              float r = __int_as_float(0x4B000000u | ((acc16[4 * i4 + ii] >> (16 * j)) & 0xffffu)) - 8390656.0f;
+              r = r < 0.f ? r + mf : r;                                            // W mod m in [0, m)
+              float y = r;
+              if (!p.raw) {
+                const float tt = r * inv;                                          // < m^2 < 2^24: exact
+                const float q = fmaf(tt, invm, 12582912.0f) - 12582912.0f;
+                y = fmaf(-q, mf, tt);
+                y = y < 0.f ? y + mf : y;
+              }
+              o |= (__float_as_uint(y + 8388608.0f) & 0xffffu) << (16 * j);
+            }
+            o4[ii] = o;
+          }
+          if (vec) {
+            reinterpret_cast<uint4*>(dst)[i4] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+          } else {
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int j = 0; j < 2; ++j)
+                if (col0 + 8 * i4 + 2 * ii + j < p.n) dst[8 * i4 + 2 * ii + j] = (uint16_t)(o4[ii] >> (16 * j));
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+bool make_map8(CUtensorMap* map, const void* planes, int64_t rows, int64_t k_pad, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)k_pad};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(planes), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// kind::f8f6f4 operand type codes of the instruction descriptor
+uint32_t f8f6f4_code(int fmt) {
+  switch (fmt) {
+    case OZ_FMT_E4M3: return 0;
+    case OZ_FMT_E5M2: return 1;
+    case OZ_FMT_E2M3: return 3;
+    case OZ_FMT_E3M2: return 4;
+    case OZ_FMT_E2M1: return 5;
+    default: return 0xffffffffu;
+  }
+}
+
+// =========================================================================
+// Reconstruct on 16-bit digits
+// =========================================================================
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ uint64_t round128b(u128 mag, uint32_t neg, int e) {
+  const uint64_t sign = (uint64_t)neg << 63;
+  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+  const int nb = hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 0);
+  if (nb == 0) return 0ull;
+  const int E = nb - 1 + e;
+  if (E > 1023) return sign | 0x7ff0000000000000ull;
+  const int lsb = E >= -1022 ? E - 52 : -1074;
+  const int sh = lsb - e;
+  uint64_t q;
+  if (sh <= 0) {
+    q = lo << (-sh);
+  } else if (sh > nb) {
+    q = 0;
+  } else if (sh == nb) {
+    q = (mag & ~((u128)1 << (nb - 1))) != 0 ? 1 : 0;
+  } else {
+    q = (uint64_t)(mag >> sh);
+    const bool half = (mag >> (sh - 1)) & 1;
+    const bool sticky = (mag & (((u128)1 << (sh - 1)) - 1)) != 0;
+    if (half && (sticky || (q & 1ull))) q += 1ull;
+  }
+  uint64_t b = E >= -1022 ? ((uint64_t)(E + 1022) << 52) + q : q;
+  if (b >= 0x7ff0000000000000ull) b = 0x7ff0000000000000ull;
+  return sign | b;
+}
+
+// P < 2^125; digits y_c < m_c < 2^12; pairs z = y_a m_b + y_b m_a < 2^25.
+template <int NP>
+__global__ void __launch_bounds__(256) reconstruct16_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n,
+                                                            const uint16_t* __restrict__ Y,
+                                                            const int32_t* __restrict__ s,
+                                                            const int32_t* __restrict__ t,
+                                                            double* __restrict__ C, int64_t ldc) {
+  constexpr int EPT = 4;
+  const int64_t i = blockIdx.x;
+  const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
+  if (i >= m || j0 >= n) return;
+  const int Q = T.Q;
+  const int64_t plane = m * n;
+  const uint16_t* yp = Y + i * n + j0;
+  const bool vec = (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 7) == 0) && ((plane & 3) == 0);
+  uint64_t wa[NP], wb[NP];
+#pragma unroll
+  for (int pi = 0; pi < NP; ++pi) {
+    if (vec) {
+      wa[pi] = __ldg(reinterpret_cast<const unsigned long long*>(yp + (2 * pi) * plane));
+      wb[pi] = (2 * pi + 1 < Q) ? __ldg(reinterpret_cast<const unsigned long long*>(yp + (2 * pi + 1) * plane)) : 0ull;
+    } else {
+      uint64_t a = 0, b = 0;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (j0 + e < n) {
+          a |= (uint64_t)__ldg(yp + (2 * pi) * plane + e) << (16 * e);
+          if (2 * pi + 1 < Q) b |= (uint64_t)__ldg(yp + (2 * pi + 1) * plane + e) << (16 * e);
+        }
+      wa[pi] = a;
+      wb[pi] = b;
+    }
+  }
+  uint64_t acc[EPT][4];
+  float f[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    f[e] = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) acc[e][l] = 0;
+  }
+#pragma unroll
+  for (int pi = 0; pi < NP; ++pi) {
+    const uint32_t ma = T.pa[pi], mb = T.pb[pi];
+    const float pinv = T.pinv[pi];
+    const uint32_t n0 = T.Np[pi][0], n1 = T.Np[pi][1], n2 = T.Np[pi][2], n3 = T.Np[pi][3];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const uint32_t ya = (uint32_t)(wa[pi] >> (16 * e)) & 0xffffu, yb = (uint32_t)(wb[pi] >> (16 * e)) & 0xffffu;
+      const uint32_t z = ya * mb + yb * ma;
+      f[e] = fmaf(__uint2float_rn(z), pinv, f[e]);
+      acc[e][0] += (uint64_t)z * n0;
+      acc[e][1] += (uint64_t)z * n1;
+      acc[e][2] += (uint64_t)z * n2;
+      acc[e][3] += (uint64_t)z * n3;
+    }
+  }
+  const u128 P = ((u128)(((uint64_t)T.P[3] << 32) | T.P[2]) << 64) | (((uint64_t)T.P[1] << 32) | T.P[0]);
+  const int32_t si = s[i];
+  double out[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const uint64_t c0 = acc[e][0];
+    const uint64_t c1 = acc[e][1] + (c0 >> 32);
+    const uint64_t c2 = acc[e][2] + (c1 >> 32);
+    const uint64_t c3 = acc[e][3] + (c2 >> 32);
+    const uint64_t lo = (c0 & 0xffffffffull) | (c1 << 32);
+    const uint64_t hi = (c2 & 0xffffffffull) | (c3 << 32);
+    const float qf = rintf(f[e]);
+    __int128 X = (__int128)((((u128)hi) << 64 | lo) - (u128)(uint32_t)qf * P);
+    if (fabsf(f[e] - qf) > 0.499f) {
+      if (2 * X >= (__int128)P) X -= (__int128)P;
+      else if (2 * X < -(__int128)P) X += (__int128)P;
+    }
+    const uint32_t neg = X < 0;
+    const u128 mag = neg ? (u128)(-X) : (u128)X;
+    const int64_t j = j0 + e;
+    const int ex = j < n ? -(si + t[j]) : 0;
+    out[e] = __longlong_as_double((long long)round128b(mag, neg, ex));
+  }
+  double* cp = C + i * ldc + j0;
+  if (j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+    reinterpret_cast<double2*>(cp)[0] = make_double2(out[0], out[1]);
+    reinterpret_cast<double2*>(cp)[1] = make_double2(out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (j0 + e < n) cp[e] = out[e];
+  }
+}
+
+template <int NP>
+cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s, const int32_t* t,
+                     double* C, int64_t ldc, cudaStream_t st) {
+  dim3 grid((unsigned)m, (unsigned)((n + 1023) / 1024));
+  reconstruct16_kernel<NP><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
+                            const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
+                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+  if (nvec_pad == 0) return cudaSuccess;
+  if (contiguous) {
+    split_fp_rows_kernel<<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad, k_pad, shifts,
+                                                             planes, flag);
+    return cudaGetLastError();
+  }
+  cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
+  if (e != cudaSuccess) return e;
+  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+  split_fp_cols_kernel<<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status,
+                           cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  const uint32_t code = f8f6f4_code(f.fmt);
+  if (code == 0xffffffffu) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
+      m_pad % BM || n_pad % BN)
+    return cudaErrorInvalidValue;
+  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+  const int64_t units = tiles_m * tiles_n * f.nch;
+  if (units > INT32_MAX || (int64_t)f.nplanes * m_pad > INT32_MAX || (int64_t)f.nplanes * n_pad > INT32_MAX)
+    return cudaErrorInvalidValue;
+  CUtensorMap mapA, mapB;
+  if (!make_map8(&mapA, U, (int64_t)f.nplanes * m_pad, k_pad, BM)) return cudaErrorInvalidValue;
+  if (!make_map8(&mapB, V, (int64_t)f.nplanes * n_pad, k_pad, BN)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_fp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  FpParams p;
+  p.m = (int)m;
+  p.n = (int)n;
+  p.tiles_m = (int)tiles_m;
+  p.tiles_n = (int)tiles_n;
+  p.num_units = (int)units;
+  p.kblocks = (int)(k_pad / BK);
+  p.m_pad = (int)m_pad;
+  p.n_pad = (int)n_pad;
+  p.raw = raw;
+  // D = F32, A and B of the format, both K-major, N >> 3, M >> 4
+  p.idesc = (1u << 4) | (code << 7) | (code << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  p.Y = Y;
+  p.status = status;
+  const int grid = (int)(units < sms ? units : sms);
+  gemm_fp_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, f, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s,
+                                 const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  if (T.limbs > 4) return cudaErrorInvalidValue;
+  switch (T.npairs) {
+    case 5: return launch16<5>(T, m, n, Y, s, t, C, ldc, st);
+    case 6: return launch16<6>(T, m, n, Y, s, t, C, ldc, st);
+    case 7: return launch16<7>(T, m, n, Y, s, t, C, ldc, st);
+    case 8: return launch16<8>(T, m, n, Y, s, t, C, ldc, st);
+    case 9: return launch16<9>(T, m, n, Y, s, t, C, ldc, st);
+    case 10: return launch16<10>(T, m, n, Y, s, t, C, ldc, st);
+    case 11: return launch16<11>(T, m, n, Y, s, t, C, ldc, st);
+    case 12: return launch16<12>(T, m, n, Y, s, t, C, ldc, st);
+    case 13: return launch16<13>(T, m, n, Y, s, t, C, ldc, st);
+    case 14: return launch16<14>(T, m, n, Y, s, t, C, ldc, st);
+    case 15: return launch16<15>(T, m, n, Y, s, t, C, ldc, st);
+    case 16: return launch16<16>(T, m, n, Y, s, t, C, ldc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace oz

@@ -63,6 +63,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
                                    void* workspace, size_t workspace_bytes, void* stream, void* stream_h2d,
                                    void* stream_d2h) {
   if (!plan || m < 0 || n < 0 || k < 0 || rows < 0) return OZ_ERR_INVALID_ARG;
+  if (plan->is_fp) return OZ_ERR_UNSUPPORTED;
   if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1)) return OZ_ERR_INVALID_ARG;
   if (k > plan->k_max) return OZ_ERR_K_TOO_LARGE;
   if (stream == stream_h2d || stream == stream_d2h || stream_h2d == stream_d2h) return OZ_ERR_INVALID_ARG;

@@ -7,6 +7,7 @@
 #include "../../include/oz.h"
 
 #define OZ_MAX_LIMBS 6     // 32-bit limbs of the CRT sum: Q P < 2^192 for Q <= 20
+#define OZ_TABLE_CAP 32    // moduli a constant table can hold (INT8 plans use at most 20)
 
 // Everything a kernel needs about a configuration. Passed by value as a kernel
 // parameter, so it lives in the constant bank and every access indexed by a
@@ -16,38 +17,72 @@ struct OzTables {
   int bits;                               // beta: |A'| < 2^beta
   int limbs;                              // 32-bit limbs for X in the reconstruct phase
   int pad_;
-  uint32_t m[OZ_MAX_MODULI];              // moduli, decreasing
-  uint32_t half[OZ_MAX_MODULI];           // ceil(m/2): residues >= half map to r - m
-  uint32_t magic[OZ_MAX_MODULI];          // floor(2^32 / m), Barrett constant
-  uint32_t c18[OZ_MAX_MODULI];            // 2^18 mod m
-  uint32_t c36[OZ_MAX_MODULI];            // 2^36 mod m
-  uint32_t c54[OZ_MAX_MODULI];            // 2^54 mod m
-  uint32_t inv[OZ_MAX_MODULI];            // (P/m)^-1 mod m: CRT coefficient
-  float invm[OZ_MAX_MODULI];              // 1/m rounded to fp32: quotient estimate
-  float mf[OZ_MAX_MODULI];                // m as fp32
-  float hif[OZ_MAX_MODULI];               // ceil(m/2): a residue >= this maps to r - m
-  float lof[OZ_MAX_MODULI];               // -floor(m/2): a residue below this maps to r + m
-  float c15f[OZ_MAX_MODULI];              // 2^15 mod m, 2^30, 2^45, 2^60 mod m, each as the
-  float c30f[OZ_MAX_MODULI];              // representative nearest zero (|c| <= 119)
-  float c45f[OZ_MAX_MODULI];
-  float c60f[OZ_MAX_MODULI];
-  uint32_t Mk[OZ_MAX_MODULI][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
+  uint32_t m[OZ_TABLE_CAP];              // moduli, decreasing
+  uint32_t half[OZ_TABLE_CAP];           // ceil(m/2): residues >= half map to r - m
+  uint32_t magic[OZ_TABLE_CAP];          // floor(2^32 / m), Barrett constant
+  uint32_t c18[OZ_TABLE_CAP];            // 2^18 mod m
+  uint32_t c36[OZ_TABLE_CAP];            // 2^36 mod m
+  uint32_t c54[OZ_TABLE_CAP];            // 2^54 mod m
+  uint32_t inv[OZ_TABLE_CAP];            // (P/m)^-1 mod m: CRT coefficient
+  float invm[OZ_TABLE_CAP];              // 1/m rounded to fp32: quotient estimate
+  float mf[OZ_TABLE_CAP];                // m as fp32
+  float hif[OZ_TABLE_CAP];               // ceil(m/2): a residue >= this maps to r - m
+  float lof[OZ_TABLE_CAP];               // -floor(m/2): a residue below this maps to r + m
+  float c15f[OZ_TABLE_CAP];              // 2^15 mod m, 2^30, 2^45, 2^60 mod m, each as the
+  float c30f[OZ_TABLE_CAP];              // representative nearest zero (|c| <= 119)
+  float c45f[OZ_TABLE_CAP];
+  float c60f[OZ_TABLE_CAP];
+  uint32_t Mk[OZ_TABLE_CAP][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
   // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd
   // Q ends with a pair whose second modulus is 1 (digit 0).
   int npairs;
-  uint32_t pa[(OZ_MAX_MODULI + 1) / 2];   // m_a
-  uint32_t pb[(OZ_MAX_MODULI + 1) / 2];   // m_b (1 for a lone last modulus)
-  float pinv[(OZ_MAX_MODULI + 1) / 2];    // 1 / (m_a m_b) rounded to fp32
-  uint32_t Np[(OZ_MAX_MODULI + 1) / 2][OZ_MAX_LIMBS];  // P / (m_a m_b), 32-bit limbs
+  uint32_t pa[(OZ_TABLE_CAP + 1) / 2];   // m_a
+  uint32_t pb[(OZ_TABLE_CAP + 1) / 2];   // m_b (1 for a lone last modulus)
+  float pinv[(OZ_TABLE_CAP + 1) / 2];    // 1 / (m_a m_b) rounded to fp32
+  uint32_t Np[(OZ_TABLE_CAP + 1) / 2][OZ_MAX_LIMBS];  // P / (m_a m_b), 32-bit limbs
+};
+
+// A low-precision float configuration (Sec. "Forms and Channels"): channels
+// (a modulus with a form), their planes and GEMMs. Plane p of an operand
+// holds, for every entry, the code of the format value the form's table
+// assigns to the entry's class modulo its channel's modulus.
+#define OZ_MAX_FP_GEMMS 128
+#define OZ_MAX_FP_PLANES 96
+struct OzFpTables {
+  int fmt;                                // oz_format
+  int e2;                                 // 2 e_S: an accumulator holds W 2^-e2 exactly
+  int shift;                              // position of the code inside its byte
+  int nch, ngemm, nplanes;
+  int ch_gemm0[OZ_TABLE_CAP], ch_ngemm[OZ_TABLE_CAP];
+  int ch_plane0[OZ_TABLE_CAP], ch_nplanes[OZ_TABLE_CAP];
+  uint32_t m[OZ_TABLE_CAP];               // channel moduli (also in OzTables::m)
+  uint32_t magic[OZ_TABLE_CAP];           // floor(2^32 / m)
+  uint32_t c16[OZ_TABLE_CAP], c32[OZ_TABLE_CAP], c48[OZ_TABLE_CAP];  // 2^16k mod m
+  uint32_t inv[OZ_TABLE_CAP];             // (P/m)^-1 mod m
+  float mf[OZ_TABLE_CAP], invm[OZ_TABLE_CAP];
+  uint8_t g_pa[OZ_MAX_FP_GEMMS], g_pb[OZ_MAX_FP_GEMMS];  // planes of GEMM g
+  uint8_t g_ch[OZ_MAX_FP_GEMMS];          // channel of GEMM g
+  float g_lam[OZ_MAX_FP_GEMMS];           // its weight lambda reduced into [0, m)
+  uint32_t plane_off[OZ_MAX_FP_PLANES];   // byte offset of the plane's code table
+  uint32_t plane_ch[OZ_MAX_FP_PLANES];    // channel of plane p
+  const uint8_t* codes;                   // device: every plane's table, m bytes each
 };
 
 struct oz_plan_s {
-  int Q;
+  int Q;             // INT8: moduli = GEMMs; float formats: channels
   int bits;
   int engine;        // resolved engine (never AUTO)
   int64_t k_max;
-  OzTables tab;
+  OzTables tab;      // moduli and CRT constants
+  int is_fp;
+  int gemms;         // low-precision GEMMs per product
+  int fp_form[OZ_TABLE_CAP], fp_base[OZ_TABLE_CAP];
+  int64_t fp_kcfg;   // inner dimension the configuration was built for
+  OzFpTables fp;
+  uint8_t* d_codes;  // device copy of the code tables (owned)
+  int16_t* h_values; // host copy of the plane values, one table per plane (owned)
+  size_t codes_bytes;
 };
 
 namespace oz {
@@ -81,5 +116,16 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
                            const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                                const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+// float-format path: planes of codes, 16-bit digits
+cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
+                            const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
+                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st);
+cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status, cudaStream_t st);
+cudaError_t launch_reconstruct16(const OzTables& t, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s,
+                                 const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+// shared by the split kernels: shifts of strided vectors (colmax must be zeroed)
+cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
+                               int32_t* flag, uint64_t* colmax, cudaStream_t st);
 
 }  // namespace oz

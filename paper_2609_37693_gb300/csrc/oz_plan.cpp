@@ -120,11 +120,70 @@ int64_t kappa_rec(const Big& P, int beta) {
 
 }  // namespace
 
+namespace oz {
+
+// Per-modulus constants and the CRT sum's limbs for moduli m[0..Q-1] (pairwise
+// coprime, each below 2^12): Barrett and reduction constants for the split
+// kernels, (P/m)^-1 mod m for the epilogue, and P, P/m, and the pair products
+// P/(m_a m_b) as 32-bit limbs for the reconstruct kernels.
+bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
+  if (Q < 1 || Q > OZ_TABLE_CAP) return false;
+  OzTables& t = *tp;
+  memset(&t, 0, sizeof t);
+  Big P(1);
+  for (int i = 0; i < Q; ++i) P = P.mul(moduli[i]);
+  t.Q = Q;
+  t.bits = bits;
+  // The reconstruct phase works modulo 2^(32 limbs) in two's complement. Its
+  // candidate X lies in (-1.5P, 1.5P) and it compares 2X with +-P, so 3P must
+  // stay below 2^(32 limbs - 1).
+  t.limbs = (P.bitlen() + 3 + 31) / 32;
+  if (t.limbs > OZ_MAX_LIMBS) return false;
+  for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.P[i] = P.w[i];
+  for (int q = 0; q < Q; ++q) {
+    uint32_t m = moduli[q];
+    t.m[q] = m;
+    t.half[q] = (m + 1) / 2;
+    t.magic[q] = (uint32_t)((((uint64_t)1) << 32) / m);
+    t.c18[q] = pow2_mod(18, m);
+    t.c36[q] = pow2_mod(36, m);
+    t.c54[q] = pow2_mod(54, m);
+    Big Mk;
+    P.divmod(m, &Mk);
+    Big dummy;
+    uint32_t mk_mod_m = Mk.divmod(m, &dummy);
+    t.inv[q] = inverse_mod(mk_mod_m, m);
+    t.invm[q] = 1.0f / (float)m;
+    t.mf[q] = (float)m;
+    t.hif[q] = (float)((m + 1) / 2);
+    t.lof[q] = -(float)(m / 2);
+    auto centred = [m](uint32_t c) { return (float)(c >= (m + 1) / 2 ? (int)c - (int)m : (int)c); };
+    t.c15f[q] = centred(pow2_mod(15, m));
+    t.c30f[q] = centred(pow2_mod(30, m));
+    t.c45f[q] = centred(pow2_mod(45, m));
+    t.c60f[q] = centred(pow2_mod(60, m));
+    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
+  }
+  t.npairs = (Q + 1) / 2;
+  for (int pi = 0; pi < t.npairs; ++pi) {
+    uint32_t ma = moduli[2 * pi], mb = 2 * pi + 1 < Q ? moduli[2 * pi + 1] : 1u;
+    t.pa[pi] = ma;
+    t.pb[pi] = mb;
+    t.pinv[pi] = (float)(1.0 / ((double)ma * (double)mb));
+    Big Np;
+    P.divmod(ma * mb, &Np);
+    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Np[pi][i] = Np.w[i];
+  }
+  return true;
+}
+
+}  // namespace oz
+
 extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int64_t k_hint, int engine) {
   if (!out) return OZ_ERR_INVALID_ARG;
   *out = nullptr;
   if (k_hint < 1 || bits < 0 || bits > OZ_MAX_BITS) return OZ_ERR_INVALID_ARG;
-  if (engine < OZ_ENGINE_AUTO || engine > OZ_ENGINE_TC) return OZ_ERR_INVALID_ARG;
+  if (engine < OZ_ENGINE_AUTO || engine > OZ_ENGINE_TC) return OZ_ERR_INVALID_ARG;   // float formats: oz_plan_create_fp
   if (num_moduli != 0 && (num_moduli < OZ_MIN_MODULI || num_moduli > OZ_MAX_MODULI)) return OZ_ERR_UNSUPPORTED;
 
   int Q = num_moduli;
@@ -161,50 +220,8 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   p->k_max = k_acc < k_rec ? k_acc : k_rec;
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }
 
-  OzTables& t = p->tab;
-  t.Q = Q;
-  t.bits = beta;
-  // The reconstruct phase works modulo 2^(32 limbs) in two's complement. Its
-  // candidate X lies in (-1.5P, 1.5P) and it compares 2X with +-P, so 3P must
-  // stay below 2^(32 limbs - 1).
-  t.limbs = (P.bitlen() + 3 + 31) / 32;
-  if (t.limbs > OZ_MAX_LIMBS) { delete p; return OZ_ERR_UNSUPPORTED; }
-  for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.P[i] = P.w[i];
-  for (int q = 0; q < Q; ++q) {
-    uint32_t m = kModuli[q];
-    t.m[q] = m;
-    t.half[q] = (m + 1) / 2;
-    t.magic[q] = (uint32_t)((((uint64_t)1) << 32) / m);
-    t.c18[q] = pow2_mod(18, m);
-    t.c36[q] = pow2_mod(36, m);
-    t.c54[q] = pow2_mod(54, m);
-    Big Mk;
-    uint32_t rem = P.divmod(m, &Mk);
-    (void)rem;
-    Big dummy;
-    uint32_t mk_mod_m = Mk.divmod(m, &dummy);
-    t.inv[q] = inverse_mod(mk_mod_m, m);
-    t.invm[q] = 1.0f / (float)m;
-    t.mf[q] = (float)m;
-    t.hif[q] = (float)((m + 1) / 2);
-    t.lof[q] = -(float)(m / 2);
-    auto centred = [m](uint32_t c) { return (float)(c >= (m + 1) / 2 ? (int)c - (int)m : (int)c); };
-    t.c15f[q] = centred(pow2_mod(15, m));
-    t.c30f[q] = centred(pow2_mod(30, m));
-    t.c45f[q] = centred(pow2_mod(45, m));
-    t.c60f[q] = centred(pow2_mod(60, m));
-    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
-  }
-  t.npairs = (Q + 1) / 2;
-  for (int pi = 0; pi < t.npairs; ++pi) {
-    uint32_t ma = kModuli[2 * pi], mb = 2 * pi + 1 < Q ? kModuli[2 * pi + 1] : 1u;
-    t.pa[pi] = ma;
-    t.pb[pi] = mb;
-    t.pinv[pi] = (float)(1.0 / ((double)ma * (double)mb));
-    Big Np;
-    P.divmod(ma * mb, &Np);
-    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Np[pi][i] = Np.w[i];
-  }
+  if (!oz::fill_crt_tables(&p->tab, kModuli, Q, beta)) { delete p; return OZ_ERR_UNSUPPORTED; }
+  p->gemms = Q;
   *out = p;
   return OZ_OK;
 }
@@ -221,7 +238,12 @@ extern "C" oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_ma
   return OZ_OK;
 }
 
-extern "C" void oz_plan_destroy(oz_plan plan) { delete plan; }
+extern "C" void oz_plan_destroy(oz_plan plan) {
+  if (!plan) return;
+  if (plan->d_codes) cudaFree(plan->d_codes);
+  delete[] plan->h_values;
+  delete plan;
+}
 
 extern "C" const char* oz_status_str(oz_status s) {
   switch (s) {

@@ -25,37 +25,10 @@
 #include <stdint.h>
 
 #include "oz_internal.h"
+#include "oz_device.cuh"
 
 namespace oz {
 namespace {
-
-constexpr uint64_t kAbsMask = 0x7fffffffffffffffull;
-
-// Shift s from the largest |x| bit pattern.
-__device__ __forceinline__ int32_t shift_from_maxbits(uint64_t mb, int beta) {
-  if (mb == 0) return 0;
-  int eb = (int)(mb >> 52);
-  int e = eb ? eb - 1022 : (64 - __clzll((long long)mb)) - 1074;  // frexp exponent
-  return beta - e;
-}
-
-// Decoded truncated integer of one entry: |a'| and its sign.
-struct Trunc {
-  uint64_t mag;
-  uint32_t neg;
-};
-
-__device__ __forceinline__ Trunc truncate(uint64_t bits, int32_t s) {
-  Trunc t;
-  t.neg = (uint32_t)(bits >> 63);
-  int eb = (int)((bits >> 52) & 0x7ff);
-  uint64_t f = bits & ((1ull << 52) - 1);
-  uint64_t mant = eb ? (f | (1ull << 52)) : f;
-  int sh = (eb ? eb - 1075 : -1074) + s;   // a' = mant * 2^sh, |a'| < 2^beta <= 2^64
-  if (sh >= 0) t.mag = mant << sh;         // sh <= 11 when beta <= 64
-  else t.mag = (-sh) >= 64 ? 0ull : (mant >> (-sh));
-  return t;
-}
 
 // Signed 15-bit pieces of a' as exact floats: a' = sum_i P_i 2^(15 i).
 struct Pieces {
@@ -115,16 +88,6 @@ __device__ __forceinline__ uint32_t int8_bits(float r) { return __float_as_uint(
 __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d) {
   return __byte_perm(__byte_perm(int8_bits(a), int8_bits(b), 0x0040u), __byte_perm(int8_bits(c), int8_bits(d), 0x0040u),
                      0x5410u);
-}
-
-// 64-bit max across a warp.
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -343,19 +306,25 @@ cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
+                               int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+  if (nvec == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * (size_t)nvec, st);
+  if (e != cudaSuccess) return e;
+  if (len > 0) {
+    dim3 g1((unsigned)((nvec + 31) / 32), (unsigned)((len + 255) / 256));
+    colmax_kernel<<<g1, dim3(32, 8), 0, st>>>(nvec, len, X, ld, colmax, flag);
+  }
+  shifts_from_colmax_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, st>>>(nvec, colmax, bits, shifts);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
                               int32_t* flag, uint64_t* colmax, cudaStream_t st) {
   if (nvec_pad == 0) return cudaSuccess;
-  if (nvec > 0) {
-    cudaError_t e = cudaMemsetAsync(colmax, 0, sizeof(uint64_t) * (size_t)nvec, st);
-    if (e != cudaSuccess) return e;
-    if (len > 0) {
-      dim3 g1((unsigned)((nvec + 31) / 32), (unsigned)((len + 255) / 256));
-      colmax_kernel<<<g1, dim3(32, 8), 0, st>>>(nvec, len, X, ld, colmax, flag);
-    }
-    shifts_from_colmax_kernel<<<(unsigned)((nvec + 255) / 256), 256, 0, st>>>(nvec, colmax, t.bits, shifts);
-  }
+  cudaError_t e0 = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
+  if (e0 != cudaSuccess) return e0;
   dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
   if (bf16)
     split_cols_kernel<true><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);

@@ -1,0 +1,66 @@
+"""The library's frozen float-format configurations against the oracle (no
+GPU): valid configurations (pairwise coprime, window, exactness), least GEMM
+counts equal to the oracle's search or the paper's printed values, and plane
+tables equal to the oracle's enumeration."""
+import itertools
+import math
+
+import pytest
+
+import paper_2609_37693_gb300 as oz
+from oracle import forms
+
+KIND = {1: "one", 2: "school3", 3: "toom", 4: "school4"}
+
+
+def _plan(fmt, K):
+    return oz.PlanFP(fmt, K)
+
+
+@pytest.mark.parametrize("fmt", ["E4M3", "E2M3", "E3M2", "E5M2", "E2M1"])
+@pytest.mark.parametrize("K", [8192, 16384])
+def test_configuration_is_valid_and_tables_match_oracle(fmt, K):
+    p = _plan(fmt, K)
+    assert p.k_cfg == K
+    assert all(math.gcd(a, b) == 1 for a, b in itertools.combinations(p.moduli, 2))
+    P = math.prod(p.moduli)
+    assert P > 2 * K * (2**53 - 1) ** 2                        # eq. ov-crtgen at 53 bits
+    assert p.q == sum(len(forms.weights(KIND[f], b)) for f, b in zip(p.forms, p.bases))
+    r = forms.rmax1(K, forms.LAMBDA_FP32)
+    vals = p.plane_values()
+    i = 0
+    S = set(forms.alphabet(fmt)[0])
+    for m, f, b in zip(p.moduli, p.forms, p.bases):
+        ref = forms.tables(fmt, K, m, KIND[f], b)
+        for plane in ref:
+            assert vals[i] == plane, (fmt, m)
+            assert all(v in S and abs(v) <= r for v in plane)     # eq. ov-accgen per GEMM
+            i += 1
+        # the form's identity eq. ov-linear, checked on every pair of classes
+        for c1 in range(0, m, max(1, m // 23)):
+            for c2 in range(0, m, max(1, m // 19)):
+                lhs = sum(lam * ref[pa][c1] * ref[pb][c2] for pa, pb, lam in forms.weights(KIND[f], b))
+                assert (lhs - c1 * c2) % m == 0
+    assert i == len(vals)
+
+
+@pytest.mark.parametrize("K", [8192, 16384])
+def test_e2m1_least_q_equals_oracle(K):
+    p = _plan("E2M1", K)
+    pool = forms.Pools("E2M1", K)
+    assert p.q == forms.least_q(pool.rank, K)[0] == 59
+
+
+def test_fp8_counts_match_the_paper():
+    """Table tab:moduli / Sec. 'FP8 and FP6': E4M3 and E2M3 take 30 GEMMs at
+    K = 2^14, 15 one-limb channels and 5 channels of three GEMMs."""
+    for fmt in ("E4M3", "E2M3"):
+        p = _plan(fmt, 16384)
+        assert p.q == 30
+        assert sorted(len(forms.weights(KIND[f], b)) for f, b in zip(p.forms, p.bases)) == [1] * 15 + [3] * 5
+
+
+def test_plan_refuses_inner_dimension_above_its_configurations():
+    st, h = oz.oz_plan_create_fp(oz.OZ_FMT_E4M3, 20000, 0)
+    assert st == oz.OZ_ERR_K_TOO_LARGE and h is None
+    assert oz.oz_plan_create_fp(99, 1000, 0)[0] == oz.OZ_ERR_UNSUPPORTED
