@@ -257,7 +257,7 @@ def dgemm(A: np.ndarray, B: np.ndarray, moduli, beta: int, want_residues: bool =
     assert K == K2
     mods = _mods(moduli)
     C = np.zeros((M, N), dtype=np.float64)
-    W = np.zeros((len(mods), M, N), dtype=np.uint8) if want_residues else None
+    W = np.zeros((len(mods), M, N), dtype=np.uint16) if want_residues else None
     s = np.zeros(M, dtype=np.int32)
     t = np.zeros(N, dtype=np.int32)
     _check(_load().ozo_dgemm(M, N, K, _ptr(A), K, _ptr(B), N, _ptr(mods), len(mods), beta, _ptr(C), N,

@@ -233,3 +233,27 @@ def weights(kind, b):
     if kind == "toom":
         return [(0, 0, 1 - b), (1, 1, b), (2, 2, b * b - b)]
     return [(0, 0, 1), (0, 1, b), (1, 0, b), (1, 1, b * b)]
+
+
+def code_values(name):
+    """{code: scaled alphabet value} for every finite code of an OCP format:
+    sign bit on top, then the exponent field, then the mantissa field; the
+    value is (-1)^sign 2^(1 - bias) (mantissa / 2^m_bits) for a zero exponent
+    field and (-1)^sign 2^(e - bias) (1 + mantissa / 2^m_bits) otherwise,
+    times 2^e_S."""
+    eb, mb, bias, style = SPECS[name]
+    _, e_s = alphabet(name)
+    out = {}
+    for sign in (0, 1):
+        for e in range(2**eb):
+            for mt in range(2**mb):
+                if style == "ieee" and e == 2**eb - 1:
+                    continue
+                if style == "fn" and e == 2**eb - 1 and mt == 2**mb - 1:
+                    continue
+                mag = Fraction(mt, 2**mb) * Fraction(2) ** (1 - bias) if e == 0 else \
+                    (1 + Fraction(mt, 2**mb)) * Fraction(2) ** (e - bias)
+                v = mag * 2**e_s
+                assert v.denominator == 1
+                out[(sign << (eb + mb)) | (e << mb) | mt] = -int(v) if sign else int(v)
+    return out

@@ -217,7 +217,7 @@ int ozo_residue_planes(const double* X, int64_t nvec, int64_t len, int64_t s_vec
  * s_out[M], t_out[N]. */
 int ozo_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
               const double* B, int64_t ldb, const int32_t* mod, int Q, int beta,
-              double* C, int64_t ldc, uint8_t* w_out, int32_t* s_out, int32_t* t_out) {
+              double* C, int64_t ldc, uint16_t* w_out, int32_t* s_out, int32_t* t_out) {
   if (M < 0 || N < 0 || K < 0 || Q < 1 || Q > OZO_MAXQ || beta < 1 || beta > 120) return -1;
   int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M + 1));
   int32_t* t = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N + 1));
@@ -254,7 +254,7 @@ int ozo_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
       C[i * ldc + j] = round_scaled(&mag, neg, -((int64_t)s[i] + t[j]));
     }
   if (w_out)
-    for (int64_t x = 0; x < (int64_t)Q * M * N; ++x) w_out[x] = (uint8_t)W[x];
+    for (int64_t x = 0; x < (int64_t)Q * M * N; ++x) w_out[x] = (uint16_t)W[x];
   if (s_out) memcpy(s_out, s, sizeof(int32_t) * (size_t)M);
   if (t_out) memcpy(t_out, t, sizeof(int32_t) * (size_t)N);
 done:

@@ -5,6 +5,11 @@
 // (a' = trunc(x 2^s) from the IEEE fields, cut into 16-bit pieces, one 32-bit
 // Barrett step), then for each plane of the channel's form the code of the
 // plane value the form assigns to c, read from the plan's code tables.
+// Planes are K-major rows of 16-byte chunks, one chunk per 16 consecutive
+// entries: 8-bit codes one per byte; 6- and 4-bit codes packed little-endian
+// from bit 0 of the chunk (12 or 8 bytes used), the layout the f8f6f4 MMA
+// reads for those types from shared memory, so that a K = 32 step is 32 bytes
+// for every format.
 //
 // GEMMs and epilogue: tcgen05.mma.kind::f8f6f4 on the codes (E4M3, E5M2, E2M3,
 // E3M2 or E2M1) into FP32 accumulators in tensor memory. The work unit is a
@@ -67,8 +72,40 @@ __device__ __forceinline__ uint32_t class_of(const ChConst& k, const Pieces16& P
   return P.neg ? (r ? k.m - r : 0u) : r;
 }
 
-// Contiguous vectors: one CTA of 256 threads per vector, 8 entries per thread
-// and pass; planes of uint8 codes [nplanes][nvec_pad][k_pad].
+// The 16-byte chunk the kind::f8f6f4 operands read for 16 consecutive entries:
+// 8-bit codes one per byte; 6- and 4-bit codes packed little-endian from bit 0
+// of the chunk (12 or 8 bytes), the rest of the chunk zero.
+template <int CB>
+__device__ __forceinline__ uint4 pack_chunk(const uint32_t (&c)[16]) {
+  uint4 o;
+  if constexpr (CB == 8) {
+    o.x = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
+    o.y = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
+    o.z = c[8] | (c[9] << 8) | (c[10] << 16) | (c[11] << 24);
+    o.w = c[12] | (c[13] << 8) | (c[14] << 16) | (c[15] << 24);
+  } else if constexpr (CB == 6) {
+    uint64_t lo = 0;
+#pragma unroll
+    for (int e = 0; e < 11; ++e) lo |= (uint64_t)c[e] << (6 * e);        // code 10 keeps its low 4 bits
+    uint32_t hi = c[10] >> 4;
+#pragma unroll
+    for (int e = 11; e < 16; ++e) hi |= c[e] << (6 * e - 64);
+    o = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), hi, 0u);
+  } else {
+    uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      w0 |= c[e] << (4 * e);
+      w1 |= c[8 + e] << (4 * e);
+    }
+    o = make_uint4(w0, w1, 0u, 0u);
+  }
+  return o;
+}
+
+// Contiguous vectors: one CTA of 256 threads per vector, 16 entries (one
+// chunk) per thread and pass; planes of chunks [nplanes][nvec_pad][k_pad].
+template <int CB>
 __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constant__ OzFpTables F, int bits,
                                                             int64_t nvec, int64_t len, const double* __restrict__ X,
                                                             int64_t ld, int64_t nvec_pad, int64_t k_pad,
@@ -108,35 +145,35 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
   __syncthreads();
   const int32_t s = s_sh;
   const int64_t plane = nvec_pad * k_pad;
-  for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
-    Pieces16 P[8];
+  for (int64_t h0 = (int64_t)tid * 16; h0 < k_pad; h0 += 256 * 16) {
+    Pieces16 P[16];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 16; ++e) {
       uint64_t b = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
       if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
       P[e] = pieces16(b, s);
     }
     for (int c = 0; c < F.nch; ++c) {
       const ChConst k = ch_const(F, c);
-      uint32_t cls[8];
+      uint32_t cls[16];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) cls[e] = class_of(k, P[e]);
+      for (int e = 0; e < 16; ++e) cls[e] = class_of(k, P[e]);
       const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
       for (int q = 0; q < np; ++q) {
         const uint8_t* tab = F.codes + F.plane_off[p0 + q];
-        uint32_t lo = 0, hi = 0;
+        uint32_t code[16];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) lo |= (uint32_t)__ldg(tab + cls[e]) << (8 * e);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) hi |= (uint32_t)__ldg(tab + cls[4 + e]) << (8 * e);
-        *reinterpret_cast<uint2*>(planes + (int64_t)(p0 + q) * plane + v * k_pad + h0) = make_uint2(lo, hi);
+        for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
+        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + v * k_pad + h0) = pack_chunk<CB>(code);
       }
     }
   }
 }
 
 // Strided vectors (columns of B, or of A^T): 64 (h) x 64 (vector) tiles through
-// shared memory so that the planes, K-major per vector, are written along h.
+// shared memory so that the planes, K-major per vector, are written along h;
+// each thread forms the chunk of 16 entries of one vector.
+template <int CB>
 __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constant__ OzFpTables F, int64_t nvec,
                                                             int64_t len, const double* __restrict__ X, int64_t ld,
                                                             int64_t nvec_pad, int64_t k_pad,
@@ -172,22 +209,23 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
     for (int q = 0; q < np; ++q, ++pg) {
       uint32_t* tb = tile[pg & 1];
       const uint8_t* tab = F.codes + F.plane_off[p0 + q];
+      uint32_t code[16];
 #pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) word |= (uint32_t)__ldg(tab + cls[4 * w + e]) << (8 * e);
-        tb[jl * kPitchWords + hg * 4 + w] = word;
-      }
+      for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
+      const uint4 o = pack_chunk<CB>(code);
+      tb[jl * kPitchWords + hg * 4 + 0] = o.x;
+      tb[jl * kPitchWords + hg * 4 + 1] = o.y;
+      tb[jl * kPitchWords + hg * 4 + 2] = o.z;
+      tb[jl * kPitchWords + hg * 4 + 3] = o.w;
       __syncthreads();
       for (int cidx = tid; cidx < 64 * 4; cidx += 256) {
         const int rowi = cidx >> 2, ch = cidx & 3;
-        uint4 o;
-        o.x = tb[rowi * kPitchWords + ch * 4 + 0];
-        o.y = tb[rowi * kPitchWords + ch * 4 + 1];
-        o.z = tb[rowi * kPitchWords + ch * 4 + 2];
-        o.w = tb[rowi * kPitchWords + ch * 4 + 3];
-        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * k_pad + hbase + ch * 16) = o;
+        uint4 w;
+        w.x = tb[rowi * kPitchWords + ch * 4 + 0];
+        w.y = tb[rowi * kPitchWords + ch * 4 + 1];
+        w.z = tb[rowi * kPitchWords + ch * 4 + 2];
+        w.w = tb[rowi * kPitchWords + ch * 4 + 3];
+        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * k_pad + hbase + ch * 16) = w;
       }
     }
   }
@@ -713,22 +751,35 @@ cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y,
   return cudaGetLastError();
 }
 
+
+template <int CB>
+cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
+                     const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts, uint8_t* planes,
+                     int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+  if (contiguous) {
+    split_fp_rows_kernel<CB><<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad, k_pad,
+                                                                 shifts, planes, flag);
+    return cudaGetLastError();
+  }
+  cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
+  if (e != cudaSuccess) return e;
+  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+  split_fp_cols_kernel<CB><<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
                             uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st) {
   if (nvec_pad == 0) return cudaSuccess;
-  if (contiguous) {
-    split_fp_rows_kernel<<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad, k_pad, shifts,
-                                                             planes, flag);
-    return cudaGetLastError();
+  switch (f.code_bits) {
+    case 8: return split_fp<8>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
+    case 6: return split_fp<6>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
+    case 4: return split_fp<4>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
+    default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
-  if (e != cudaSuccess) return e;
-  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
-  split_fp_cols_kernel<<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,

@@ -52,7 +52,8 @@ struct OzTables {
 struct OzFpTables {
   int fmt;                                // oz_format
   int e2;                                 // 2 e_S: an accumulator holds W 2^-e2 exactly
-  int shift;                              // position of the code inside its byte
+  int code_bits;                          // 8, 6 or 4: width of a code; 6- and 4-bit codes are
+                                          // packed 16 to a 16-byte chunk (bytes 12.. or 8.. unused)
   int nch, ngemm, nplanes;
   int ch_gemm0[OZ_TABLE_CAP], ch_ngemm[OZ_TABLE_CAP];
   int ch_plane0[OZ_TABLE_CAP], ch_nplanes[OZ_TABLE_CAP];

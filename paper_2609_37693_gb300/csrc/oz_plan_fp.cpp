@@ -245,7 +245,7 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   f.e2 = 2 * e_s;
   FormatBits fb;
   format_bits(format, &fb);
-  f.shift = fb.code_bits == 8 ? 0 : 2;     // 4- and 6-bit codes sit in bits [2, 2 + n) of their byte
+  f.code_bits = fb.code_bits;
   f.nch = cfg->nch;
   std::vector<uint32_t> moduli(cfg->nch);
   std::vector<std::vector<int64_t>> planes;      // value tables, one per plane
@@ -337,7 +337,7 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   for (int q = 0; q < f.nplanes; ++q)
     for (size_t c = 0; c < planes[q].size(); ++c) {
       const int64_t v = planes[q][c];
-      codes[f.plane_off[q] + c] = (uint8_t)(code_of.at(v) << f.shift);
+      codes[f.plane_off[q] + c] = (uint8_t)code_of.at(v);
       p->h_values[f.plane_off[q] + c] = (int16_t)v;
     }
   p->codes_bytes = total;
