@@ -158,3 +158,55 @@ def test_inner_dimension_above_k_max_is_refused():
     B = torch.zeros((plan.k_max + 200, 4), dtype=torch.float64, device=DEV)
     with pytest.raises(oz.OzError):
         oz.dgemm(A, B, plan)
+
+
+def _encode(fmt, codes):
+    """Inverse of _decode on codes: [..., k_pad] codes -> plane bytes."""
+    nb = CODE_BITS[fmt]
+    if nb == 8:
+        return codes.astype(np.uint8)
+    ch = codes.reshape(*codes.shape[:-1], -1, 16).astype(np.int64)
+    bits = ((ch[..., None] >> np.arange(nb)) & 1).reshape(*ch.shape[:-1], 16 * nb)
+    pad = np.zeros((*bits.shape[:-1], 128 - 16 * nb), dtype=np.int64)
+    return np.packbits(np.concatenate([bits, pad], -1).astype(np.uint8), axis=-1,
+                       bitorder="little").reshape(codes.shape)
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_fp32_accumulation_is_exact_at_capacity(fmt):
+    """Every product at the largest plane value rho and K = K_max, so the FP32
+    accumulators reach K rho^2 (at most 2^24, eq. ov-accgen): each channel's
+    folded residue must equal sum_g lambda_g W_g mod m exactly. Rows of B
+    alternate in sign so that both signs reach capacity."""
+    plan = oz.PlanFP(fmt, 8192)
+    vals = plan.plane_values()
+    rho = max(abs(v) for tab in vals for v in tab)
+    code_of = {v: c for c, v in forms.code_values(fmt).items() if not (v == 0 and c != 0)}
+    k = plan.k_max
+    assert k * rho * rho <= 2**24
+    m, n = 128, 256
+    k_pad = oz.round_up(k, 128)
+
+    def row(code):
+        r = np.zeros(k_pad, dtype=np.int64)
+        r[:k] = code
+        return _encode(fmt, r)
+
+    Uh = np.zeros((plan.planes, 256, k_pad), dtype=np.uint8)
+    Vh = np.zeros((plan.planes, 256, k_pad), dtype=np.uint8)
+    Uh[:, :m] = row(code_of[rho])
+    Vh[:, 0:n:2] = row(code_of[rho])
+    Vh[:, 1:n:2] = row(code_of[-rho])
+    U, V = _dev(Uh), _dev(Vh)
+    Y = torch.zeros((plan.channels, m, n), dtype=torch.int16, device=DEV)
+    flag = torch.zeros(4, dtype=torch.int32, device=DEV)
+    st = oz.oz_residue_gemm(plan.handle, m, n, 256, 256, k_pad, U.data_ptr(), V.data_ptr(), Y.data_ptr(), 1,
+                            flag.data_ptr(), oz._stream_handle())
+    assert st == oz.OZ_OK
+    torch.cuda.synchronize()
+    y = Y.cpu().numpy().view(np.uint16)
+    for c, (mod, f, b) in enumerate(zip(plan.moduli, plan.forms, plan.bases)):
+        lam = sum(w[2] for w in forms.weights(KIND[f], b))
+        for sign, cols in ((1, slice(0, n, 2)), (-1, slice(1, n, 2))):
+            want = (lam * sign * k * rho * rho) % mod
+            assert (y[c, :, cols] == want).all(), (c, mod, sign)
