@@ -236,6 +236,18 @@ OZ_API oz_status oz_dgemm_batched(int count, const oz_plan* plans, const int64_t
 /* ---- The phases on their own, for parity checks and profiling. ---- */
 
 /*
+ * oz_plane_geometry -- how a plan lays out the residue planes the phase entry
+ * points exchange: k_align = the multiple k_pad must be (128 entries; 256 for
+ * E2M1 plans), row_bytes = bytes of one plane row of k_pad entries: k_pad for
+ * IMMA (int8) and for float formats other than E2M1 (one 8-bit code per entry,
+ * or 6-bit codes packed 16 to a 16-byte chunk whose last 4 bytes are zero),
+ * 2 k_pad for TC (bf16), k_pad / 2 for E2M1 (two 4-bit codes per byte, the
+ * even entry in the low half). A plane of nvec_pad rows is nvec_pad row_bytes
+ * bytes. k_pad must be a multiple of k_align. Outputs may be NULL.
+ */
+OZ_API oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_align, int64_t* row_bytes);
+
+/*
  * oz_split -- phases 1 and 2 for one operand (Sec. "Structure").
  * The operand is viewed as nvec vectors of len entries: vector v, entry h is
  * X[v*ld + h] if contiguous != 0 (rows of a row-major matrix: A, or B^T), else
@@ -245,11 +257,15 @@ OZ_API oz_status oz_dgemm_batched(int count, const oz_plan* plans, const int64_t
  *   planes     = Q planes of nvec_pad x k_pad entries, plane q row v entry h =
  *                the balanced residue of trunc(x 2^shift) modulo m_q in
  *                [-floor(m/2), ceil(m/2) - 1]; int8 for IMMA, bf16 for TC;
- *                padding (v >= nvec or h >= len) is zero.
+ *                padding (v >= nvec or h >= len) is zero. For a float-format
+ *                plan: its plane count (oz_plan_info_fp) of codes of the
+ *                form's plane values of the class of trunc(x 2^shift) modulo
+ *                each channel's modulus, laid out as oz_plane_geometry states.
+ * nvec_pad must be a multiple of 256 and k_pad of oz_plane_geometry's k_align.
  *   flag       (may be NULL) device int32; bit 0 set if an entry is not finite.
  *   colmax     device scratch of nvec uint64 words, used when contiguous == 0
  *              (may be NULL otherwise).
- * nvec_pad and k_pad must be multiples of 256 and 128, >= nvec and len.
+ * nvec_pad >= nvec and k_pad >= len.
  */
 OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t len, const double* X, int64_t ld,
                    int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag,
@@ -262,7 +278,9 @@ OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t le
  *             digit the reconstruct phase consumes;
  *   raw != 0: Y[q][i][j] = W mod m_q in [0, m_q) (the paper's epilogue value).
  * U, V: planes from oz_split (m_pad x k_pad and n_pad x k_pad per modulus),
- * Y: uint8, Q planes of m x n (row pitch n). Device pointers.
+ * Y: uint8, Q planes of m x n (row pitch n); uint16 for float-format plans,
+ * one plane per channel, the residue folded over the channel's GEMMs
+ * (sum_g lambda_g W_g mod m, order R>C). Device pointers.
  * flag (may be NULL): device int32; the TC engine sets bit 1 if one of its
  * bounded waits ran out (the kernel then stops early and Y is unspecified).
  * The TC engine needs U and V 128-byte aligned.

@@ -48,7 +48,7 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
-            "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp")
+            "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry")
 
 
 class OzError(RuntimeError):
@@ -73,6 +73,7 @@ def _load_library():
         "oz_plan_destroy": (None, [P]),
         "oz_workspace_bytes": (SZ, [P, I64, I64, I64]),
         "oz_workspace_layout": (I32, [P, I64, I64, I64, ctypes.POINTER(I64)]),
+        "oz_plane_geometry": (I32, [P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "oz_dgemm": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
         "oz_query_status": (I32, [P, P]),
         "oz_split": (I32, [P, I32, I64, I64, P, I64, I64, I64, P, P, P, P, P]),
@@ -176,6 +177,13 @@ def oz_workspace_layout(plan, m: int, n: int, k: int):
     return st, {key: int(v) for key, v in zip(keys, out)}
 
 
+def oz_plane_geometry(plan, k_pad: int):
+    """Returns (status, k_align, row_bytes)."""
+    a, r = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _lib.oz_plane_geometry(plan, int(k_pad), ctypes.byref(a), ctypes.byref(r))
+    return st, a.value, r.value
+
+
 def oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream) -> int:
     return _lib.oz_dgemm(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb), C,
                          int(ldc), workspace, int(workspace_bytes), stream)
@@ -268,6 +276,13 @@ class Plan:
 
     def workspace_bytes(self, m: int, n: int, k: int) -> int:
         return oz_workspace_bytes(self.handle, m, n, k)
+
+    def plane_geometry(self, k: int):
+        """(k_pad, row_bytes) of the planes for inner dimension k."""
+        _, align, _ = oz_plane_geometry(self.handle, 0)
+        k_pad = round_up(max(int(k), 1), align)
+        _, _, row = oz_plane_geometry(self.handle, k_pad)
+        return k_pad, row
 
     def __repr__(self):
         return f"Plan(q={self.q}, bits={self.bits}, k_max={self.k_max}, engine={self.engine})"

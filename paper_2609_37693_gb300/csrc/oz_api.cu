@@ -26,14 +26,15 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   const int64_t ybytes = p->is_fp ? 2 : 1;                    // 16-bit digits for moduli above 255
   L->m_pad = round_up(m > 0 ? m : 1, oz::kPadRows);
   L->n_pad = round_up(n > 0 ? n : 1, oz::kPadRows);
-  L->k_pad = round_up(k > 0 ? k : 1, oz::kPadK);
+  L->k_pad = round_up(k > 0 ? k : 1, p->is_fp ? oz::fp_k_align(p->fp) : oz::kPadK);
+  const int64_t row = p->is_fp ? oz::fp_row_bytes(p->fp, L->k_pad) : L->k_pad * elem;   // bytes per plane row
   size_t off = 0;
   L->flag = off; off = align256(off + 16);
   L->s = off; off = align256(off + 4 * (size_t)m);
   L->t = off; off = align256(off + 4 * (size_t)n);
   L->colmax = off; off = align256(off + 8 * (size_t)(m > n ? m : n));
-  L->u = off; off = align256(off + (size_t)nplanes * L->m_pad * L->k_pad * elem);
-  L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * L->k_pad * elem);
+  L->u = off; off = align256(off + (size_t)nplanes * L->m_pad * row);
+  L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * row);
   L->y = off; off = align256(off + (size_t)p->Q * m * n * ybytes);
   L->total = off;
   return true;
@@ -59,6 +60,14 @@ extern "C" oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int
   out[7] = L.m_pad;
   out[8] = L.n_pad;
   out[9] = L.k_pad;
+  return OZ_OK;
+}
+
+extern "C" oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_align, int64_t* row_bytes) {
+  if (!plan || k_pad < 0) return OZ_ERR_INVALID_ARG;
+  if (k_align) *k_align = plan->is_fp ? oz::fp_k_align(plan->fp) : oz::kPadK;
+  if (row_bytes)
+    *row_bytes = plan->is_fp ? oz::fp_row_bytes(plan->fp, k_pad) : k_pad * (plan->engine == OZ_ENGINE_TC ? 2 : 1);
   return OZ_OK;
 }
 
@@ -139,7 +148,8 @@ extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag,
                               uint64_t* colmax, void* stream) {
   if (!plan || nvec < 0 || len < 0) return OZ_ERR_INVALID_ARG;
-  if (nvec_pad < nvec || k_pad < len || nvec_pad % oz::kPadRows || k_pad % oz::kPadK || k_pad == 0)
+  const int64_t k_align = plan->is_fp ? oz::fp_k_align(plan->fp) : oz::kPadK;
+  if (nvec_pad < nvec || k_pad < len || nvec_pad % oz::kPadRows || k_pad % k_align || k_pad == 0)
     return OZ_ERR_INVALID_ARG;
   if (len > plan->k_max) return OZ_ERR_K_TOO_LARGE;
   if (nvec > 0 && (!shifts || (len > 0 && (!X || !aligned(X, 8))))) return OZ_ERR_INVALID_ARG;
@@ -164,9 +174,10 @@ extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t
                                      int64_t k_pad, const void* U, const void* V, uint8_t* Y, int raw,
                                      int32_t* flag, void* stream) {
   if (!plan || m < 0 || n < 0) return OZ_ERR_INVALID_ARG;
-  if (m_pad < m || n_pad < n || m_pad % oz::kPadRows || n_pad % oz::kPadRows || k_pad <= 0 || k_pad % oz::kPadK)
+  const int64_t k_align = plan->is_fp ? oz::fp_k_align(plan->fp) : oz::kPadK;
+  if (m_pad < m || n_pad < n || m_pad % oz::kPadRows || n_pad % oz::kPadRows || k_pad <= 0 || k_pad % k_align)
     return OZ_ERR_INVALID_ARG;
-  if (k_pad > oz::round_up(plan->k_max, oz::kPadK)) return OZ_ERR_K_TOO_LARGE;
+  if (k_pad > oz::round_up(plan->k_max, k_align)) return OZ_ERR_K_TOO_LARGE;
   if (m == 0 || n == 0) return OZ_OK;
   if (!U || !V || !Y || !aligned(U, 16) || !aligned(V, 16)) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -72,17 +72,24 @@ __device__ __forceinline__ uint32_t class_of(const ChConst& k, const Pieces16& P
   return P.neg ? (r ? k.m - r : 0u) : r;
 }
 
-// The 16-byte chunk the kind::f8f6f4 operands read for 16 consecutive entries:
-// 8-bit codes one per byte; 6- and 4-bit codes packed little-endian from bit 0
-// of the chunk (12 or 8 bytes), the rest of the chunk zero.
+// The bytes the MMA operands read for 16 consecutive entries: 8-bit codes one
+// per byte (16 bytes); 6-bit codes packed little-endian from bit 0 of a 16-byte
+// chunk whose last 4 bytes are zero (the kind::f8f6f4 shared-memory layout);
+// 4-bit codes two per byte, densely (8 bytes, the block-scaled kind::mxf4
+// layout). Words: 4, 4 and 2.
 template <int CB>
-__device__ __forceinline__ uint4 pack_chunk(const uint32_t (&c)[16]) {
-  uint4 o;
+struct Chunk {
+  static constexpr int kWords = CB == 4 ? 2 : 4;
+  uint32_t w[kWords];
+};
+
+template <int CB>
+__device__ __forceinline__ Chunk<CB> pack_chunk(const uint32_t (&c)[16]) {
+  Chunk<CB> o;
   if constexpr (CB == 8) {
-    o.x = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
-    o.y = c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24);
-    o.z = c[8] | (c[9] << 8) | (c[10] << 16) | (c[11] << 24);
-    o.w = c[12] | (c[13] << 8) | (c[14] << 16) | (c[15] << 24);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      o.w[q] = c[4 * q] | (c[4 * q + 1] << 8) | (c[4 * q + 2] << 16) | (c[4 * q + 3] << 24);
   } else if constexpr (CB == 6) {
     uint64_t lo = 0;
 #pragma unroll
@@ -90,21 +97,32 @@ __device__ __forceinline__ uint4 pack_chunk(const uint32_t (&c)[16]) {
     uint32_t hi = c[10] >> 4;
 #pragma unroll
     for (int e = 11; e < 16; ++e) hi |= c[e] << (6 * e - 64);
-    o = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), hi, 0u);
+    o.w[0] = (uint32_t)lo;
+    o.w[1] = (uint32_t)(lo >> 32);
+    o.w[2] = hi;
+    o.w[3] = 0u;
   } else {
-    uint32_t w0 = 0, w1 = 0;
+    o.w[0] = 0u;
+    o.w[1] = 0u;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      w0 |= c[e] << (4 * e);
-      w1 |= c[8 + e] << (4 * e);
+      o.w[0] |= c[e] << (4 * e);
+      o.w[1] |= c[8 + e] << (4 * e);
     }
-    o = make_uint4(w0, w1, 0u, 0u);
   }
   return o;
 }
 
-// Contiguous vectors: one CTA of 256 threads per vector, 16 entries (one
-// chunk) per thread and pass; planes of chunks [nplanes][nvec_pad][k_pad].
+template <int CB>
+__device__ __forceinline__ void store_chunk(uint8_t* dst, const Chunk<CB>& o) {
+  if constexpr (CB == 4)
+    *reinterpret_cast<uint2*>(dst) = make_uint2(o.w[0], o.w[1]);
+  else
+    *reinterpret_cast<uint4*>(dst) = make_uint4(o.w[0], o.w[1], o.w[2], o.w[3]);
+}
+
+// Contiguous vectors: one CTA of 256 threads per vector, 16 entries per thread
+// and pass; planes [nplanes][nvec_pad][row bytes of k_pad entries].
 template <int CB>
 __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constant__ OzFpTables F, int bits,
                                                             int64_t nvec, int64_t len, const double* __restrict__ X,
@@ -144,7 +162,8 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
   }
   __syncthreads();
   const int32_t s = s_sh;
-  const int64_t plane = nvec_pad * k_pad;
+  const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
+  const int64_t plane = nvec_pad * row_bytes;
   for (int64_t h0 = (int64_t)tid * 16; h0 < k_pad; h0 += 256 * 16) {
     Pieces16 P[16];
 #pragma unroll
@@ -164,7 +183,8 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
         uint32_t code[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
-        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + v * k_pad + h0) = pack_chunk<CB>(code);
+        store_chunk<CB>(planes + (int64_t)(p0 + q) * plane + v * row_bytes + (CB == 4 ? h0 / 2 : h0),
+                        pack_chunk<CB>(code));
       }
     }
   }
@@ -198,7 +218,9 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
     if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
     P[e] = pieces16(b, s);
   }
-  const int64_t plane = nvec_pad * k_pad;
+  constexpr int kWords = Chunk<CB>::kWords;        // words per 16 entries
+  const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
+  const int64_t plane = nvec_pad * row_bytes;
   int pg = 0;  // planes written so far: picks the shared buffer
   for (int c = 0; c < F.nch; ++c) {
     const ChConst k = ch_const(F, c);
@@ -212,20 +234,20 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
       uint32_t code[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
-      const uint4 o = pack_chunk<CB>(code);
-      tb[jl * kPitchWords + hg * 4 + 0] = o.x;
-      tb[jl * kPitchWords + hg * 4 + 1] = o.y;
-      tb[jl * kPitchWords + hg * 4 + 2] = o.z;
-      tb[jl * kPitchWords + hg * 4 + 3] = o.w;
+      const Chunk<CB> o = pack_chunk<CB>(code);
+#pragma unroll
+      for (int w = 0; w < kWords; ++w) tb[jl * kPitchWords + hg * kWords + w] = o.w[w];
       __syncthreads();
-      for (int cidx = tid; cidx < 64 * 4; cidx += 256) {
-        const int rowi = cidx >> 2, ch = cidx & 3;
+      // a vector's 64 entries are kWords 16-byte pieces of its plane row
+      for (int cidx = tid; cidx < 64 * kWords; cidx += 256) {
+        const int rowi = cidx / kWords, ch = cidx % kWords;
         uint4 w;
         w.x = tb[rowi * kPitchWords + ch * 4 + 0];
         w.y = tb[rowi * kPitchWords + ch * 4 + 1];
         w.z = tb[rowi * kPitchWords + ch * 4 + 2];
         w.w = tb[rowi * kPitchWords + ch * 4 + 3];
-        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * k_pad + hbase + ch * 16) = w;
+        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * row_bytes +
+                                  (CB == 4 ? hbase / 2 : hbase) + ch * 16) = w;
       }
     }
   }
@@ -235,16 +257,31 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
 // GEMMs + epilogue (tcgen05, kind::f8f6f4)
 // =========================================================================
 
-constexpr int BM = 128, BN = 256, BK = 128;        // BK in 8-bit entries = 128 bytes
-constexpr int STAGES = 4;
+constexpr int BM = 128, BK = 128;                  // BK = 128 bytes of a plane row per stage
 constexpr int kBand = 8;
 constexpr int A_BYTES = BM * BK;                   // 16 KiB
-constexpr int B_BYTES = BN * BK;                   // 32 KiB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kTmemCols = 512;
-constexpr int kSmemBytes = STAGES * STAGE_BYTES + 256 + 1024;
+constexpr uint32_t kSfaCol = 448, kSfbCol = 480;   // unit block scales (block-scaled FP4 only)
+
+// Two configurations of the GEMM kernel:
+//  * kind::f8f6f4 (E4M3, E5M2, E2M3, E3M2): 128 x 256 tiles, a stage holds 128
+//    entries per row (four K = 32 MMAs), two 256-column accumulators fill TMEM;
+//  * kind::mxf4 block-scaled (E2M1 at the 4-bit rate, every scale 1): codes two
+//    per byte, a stage holds 256 entries per row (four K = 64 MMAs); 128 x 192
+//    tiles so that two accumulators (384 columns) leave room for the scales.
+template <bool MX>
+struct Cfg {
+  static constexpr int BN = MX ? 192 : 256;
+  static constexpr int HC = BN / 2;                 // columns per epilogue warp
+  static constexpr int NCH = HC / 32;               // 32-column TMEM loads per warp
+  static constexpr int STAGES = MX ? 5 : 4;
+  static constexpr int B_BYTES = BN * BK;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int kSmemBytes = STAGES * STAGE_BYTES + 256 + 1024;
+  static constexpr int KSTAGE = MX ? 2 * BK : BK;   // entries per stage row
+};
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -322,6 +359,23 @@ __device__ __forceinline__ void umma_f8f6f4(uint32_t d_tmem, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void umma_mxf4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32_fill(uint32_t taddr, uint32_t u) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+      "r"(u)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -367,9 +421,12 @@ struct FpParams {
   int32_t* status;
 };
 
+template <bool MX>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ OzFpTables F, const FpParams p) {
+  using C = Cfg<MX>;
+  constexpr int BN = C::BN, STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_base = smem_u32(smem_raw);
   const uint32_t base = (raw_base + 1023u) & ~1023u;
@@ -408,6 +465,18 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  if constexpr (MX) {
+    // every byte of columns 448..511 = 0x7F, the UE8M0 scale 2^0, so the block
+    // scales leave every product unchanged whatever scale layout the MMA reads
+    if (warp >= 2) {
+      const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+      tmem_st32_fill(tmem_base + lane_q + kSfaCol + ((warp - 2) >> 2) * 32, 0x7F7F7F7Fu);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -463,8 +532,13 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t sa = base + s * STAGE_BYTES;
             const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 32; ++kk)
-              umma_f8f6f4(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < BK / 32; ++kk) {
+              if constexpr (MX)
+                umma_mxf4(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, tmem_base + kSfaCol,
+                          tmem_base + kSfbCol, (kb > 0 || kk > 0) ? 1u : 0u);
+              else
+                umma_f8f6f4(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
             umma_commit(empty_bar(s));
             if (++s == STAGES) { s = 0; ph ^= 1u; }
           }
@@ -490,20 +564,20 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
       const int g0 = F.ch_gemm0[u.c], ng = F.ch_ngemm[u.c];
       const float mf = F.mf[u.c], invm = F.invm[u.c];
-      uint32_t acc16[64];                    // running residue + 2048, 16 bits per column
+      uint32_t acc16[C::HC / 2];             // running residue + 2048, 16 bits per column
 #pragma unroll
-      for (int i = 0; i < 64; ++i) acc16[i] = 0x08000800u;
+      for (int i = 0; i < C::HC / 2; ++i) acc16[i] = 0x08000800u;
       for (int gi = 0; gi < ng; ++gi, ++g_ctr) {
         const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
         const float lam = F.g_lam[g0 + gi];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < C::NCH; ++ch) {
           uint32_t v[32];
-          tmem_ld32(tmem_base + lane_addr + b * BN + half * 128 + ch * 32, v);
+          tmem_ld32(tmem_base + lane_addr + b * BN + half * C::HC + ch * 32, v);
           tmem_ld_wait();
-          if (ch == 3) {
+          if (ch == C::NCH - 1) {
             tc_fence_before();
             mbar_arrive(tempty_bar(b));
           }
@@ -530,13 +604,13 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) break;
       // ---- unit done: W mod m or the CRT digit, 16 bits per entry ----
       const int row = u.tm * BM + quarter * 32 + lane;
-      const int col0 = u.tn * BN + half * 128;
+      const int col0 = u.tn * BN + half * C::HC;
       if (row < p.m && col0 < p.n) {
         const float inv = (float)F.inv[u.c];
         uint16_t* dst = p.Y + (size_t)u.c * p.m * p.n + (size_t)row * p.n + col0;
-        const bool vec = col0 + 128 <= p.n && (p.n & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+        const bool vec = col0 + C::HC <= p.n && (p.n & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
 #pragma unroll
-        for (int i4 = 0; i4 < 16; ++i4) {
+        for (int i4 = 0; i4 < C::HC / 8; ++i4) {
           uint32_t o4[4];
 #pragma unroll
           for (int ii = 0; ii < 4; ++ii) {
@@ -751,7 +825,6 @@ cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y,
   return cudaGetLastError();
 }
 
-
 template <int CB>
 cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                      const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts, uint8_t* planes,
@@ -782,28 +855,28 @@ cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguo
   }
 }
 
-cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status,
-                           cudaStream_t st) {
-  if (m == 0 || n == 0) return cudaSuccess;
-  const uint32_t code = f8f6f4_code(f.fmt);
-  if (code == 0xffffffffu) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
-      m_pad % BM || n_pad % BN)
-    return cudaErrorInvalidValue;
-  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+namespace {
+
+template <bool MX>
+cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                    const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status, cudaStream_t st) {
+  using C = Cfg<MX>;
+  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + C::BN - 1) / C::BN;
   const int64_t units = tiles_m * tiles_n * f.nch;
   if (units > INT32_MAX || (int64_t)f.nplanes * m_pad > INT32_MAX || (int64_t)f.nplanes * n_pad > INT32_MAX)
     return cudaErrorInvalidValue;
+  const int64_t row_bytes = fp_row_bytes(f, k_pad);
   CUtensorMap mapA, mapB;
-  if (!make_map8(&mapA, U, (int64_t)f.nplanes * m_pad, k_pad, BM)) return cudaErrorInvalidValue;
-  if (!make_map8(&mapB, V, (int64_t)f.nplanes * n_pad, k_pad, BN)) return cudaErrorInvalidValue;
+  // B tiles of the last plane may run past its rows: the map's bound fills zeros;
+  // elsewhere they read the next plane's rows into columns the epilogue drops
+  if (!make_map8(&mapA, U, (int64_t)f.nplanes * m_pad, row_bytes, BM)) return cudaErrorInvalidValue;
+  if (!make_map8(&mapB, V, (int64_t)f.nplanes * n_pad, row_bytes, C::BN)) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gemm_fp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  e = cudaFuncSetAttribute(gemm_fp_kernel<MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
   FpParams p;
   p.m = (int)m;
@@ -811,17 +884,38 @@ cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_
   p.tiles_m = (int)tiles_m;
   p.tiles_n = (int)tiles_n;
   p.num_units = (int)units;
-  p.kblocks = (int)(k_pad / BK);
+  p.kblocks = (int)(k_pad / C::KSTAGE);
   p.m_pad = (int)m_pad;
   p.n_pad = (int)n_pad;
   p.raw = raw;
-  // D = F32, A and B of the format, both K-major, N >> 3, M >> 4
-  p.idesc = (1u << 4) | (code << 7) | (code << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  if (MX) {
+    // block-scaled: scale factor ids 0, A = B = E2M1 (1), both K-major, N >> 3,
+    // UE8M0 scales (bit 23), M >> 4, K = 64 per instruction
+    p.idesc = (1u << 7) | (1u << 10) | ((uint32_t)(C::BN >> 3) << 17) | (1u << 23) | ((uint32_t)(BM >> 4) << 24);
+  } else {
+    // D = F32, A and B of the format, both K-major, N >> 3, M >> 4
+    const uint32_t code = f8f6f4_code(f.fmt);
+    if (code == 0xffffffffu) return cudaErrorInvalidValue;
+    p.idesc = (1u << 4) | (code << 7) | (code << 10) | ((uint32_t)(C::BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  }
   p.Y = Y;
   p.status = status;
   const int grid = (int)(units < sms ? units : sms);
-  gemm_fp_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, f, p);
+  gemm_fp_kernel<MX><<<grid, kThreads, C::kSmemBytes, st>>>(mapA, mapB, f, p);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status,
+                           cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % fp_k_align(f) ||
+      m_pad % BM || n_pad % kPadRows)
+    return cudaErrorInvalidValue;
+  if (f.code_bits == 4) return gemm_fp<true>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, status, st);
+  return gemm_fp<false>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, status, st);
 }
 
 cudaError_t launch_reconstruct16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s,

@@ -52,8 +52,9 @@ struct OzTables {
 struct OzFpTables {
   int fmt;                                // oz_format
   int e2;                                 // 2 e_S: an accumulator holds W 2^-e2 exactly
-  int code_bits;                          // 8, 6 or 4: width of a code; 6- and 4-bit codes are
-                                          // packed 16 to a 16-byte chunk (bytes 12.. or 8.. unused)
+  int code_bits;                          // 8, 6 or 4: width of a code. 6-bit codes are packed 16
+                                          // to a 16-byte chunk (bytes 12..15 unused); 4-bit codes
+                                          // two to a byte, densely (block-scaled FP4 operands)
   int nch, ngemm, nplanes;
   int ch_gemm0[OZ_TABLE_CAP], ch_ngemm[OZ_TABLE_CAP];
   int ch_plane0[OZ_TABLE_CAP], ch_nplanes[OZ_TABLE_CAP];
@@ -100,6 +101,11 @@ __device__ __forceinline__ uint32_t mod_barrett(uint32_t y, uint32_t m, uint32_t
 constexpr int kTileM = 128;       // M tile of the GEMM engines; m_pad is a multiple of kPadRows
 constexpr int kPadRows = 256;     // row padding of the residue planes
 constexpr int kPadK = 128;        // k padding of the residue planes (entries)
+
+// Geometry of a float-format plan's planes: k padding (entries) and bytes per
+// row of k_pad entries.
+inline int64_t fp_k_align(const OzFpTables& f) { return f.code_bits == 4 ? 256 : kPadK; }
+inline int64_t fp_row_bytes(const OzFpTables& f, int64_t k_pad) { return f.code_bits == 4 ? k_pad / 2 : k_pad; }
 
 inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 

@@ -44,18 +44,22 @@ def _expected_values(plan, fmt, X, axis):
 
 
 def _decode(fmt, planes):
-    """Plane bytes -> scaled alphabet values. Each 16-byte chunk holds 16
-    consecutive entries: one 8-bit code per byte, or 6-/4-bit codes packed
-    little-endian from bit 0 with the rest of the chunk zero."""
+    """Plane bytes [..., row_bytes] -> scaled alphabet values [..., k_pad].
+    8-bit codes one per byte; 6-bit codes packed little-endian 16 to a 16-byte
+    chunk whose last 4 bytes are zero; 4-bit codes two per byte (even entry in
+    the low half)."""
     nb = CODE_BITS[fmt]
     if nb == 8:
         codes = planes.astype(np.int64)
-    else:
+    elif nb == 6:
         chunks = planes.reshape(*planes.shape[:-1], -1, 16)
-        assert not chunks[..., 2 * nb:].any(), "padding bytes of a chunk are not zero"
-        bits = np.unpackbits(chunks, axis=-1, bitorder="little")[..., : 16 * nb]
-        bits = bits.reshape(*bits.shape[:-1], 16, nb).astype(np.int64)
-        codes = (bits << np.arange(nb)).sum(axis=-1).reshape(planes.shape)
+        assert not chunks[..., 12:].any(), "padding bytes of a chunk are not zero"
+        bits = np.unpackbits(chunks, axis=-1, bitorder="little")[..., :96]
+        bits = bits.reshape(*bits.shape[:-1], 16, 6).astype(np.int64)
+        codes = (bits << np.arange(6)).sum(axis=-1).reshape(*planes.shape[:-1], -1)
+    else:
+        b = planes.astype(np.int64)
+        codes = np.stack([b & 15, b >> 4], axis=-1).reshape(*planes.shape[:-1], -1)
     lut = np.zeros(256, dtype=np.int64)
     ok = np.zeros(256, dtype=bool)
     for code, v in forms.code_values(fmt).items():
@@ -66,8 +70,8 @@ def _decode(fmt, planes):
 
 def _split(plan, X, contiguous, nvec, length, ld):
     nvec_pad = oz.round_up(max(nvec, 1), 256)
-    k_pad = oz.round_up(max(length, 1), 128)
-    planes = torch.full((plan.planes, nvec_pad, k_pad), 0x55, dtype=torch.uint8, device=DEV)   # poison
+    k_pad, row_bytes = plan.plane_geometry(length)
+    planes = torch.full((plan.planes, nvec_pad, row_bytes), 0x55, dtype=torch.uint8, device=DEV)   # poison
     shifts = torch.zeros(max(nvec, 1), dtype=torch.int32, device=DEV)
     flag = torch.zeros(4, dtype=torch.int32, device=DEV)
     colmax = torch.zeros(max(nvec, 1), dtype=torch.int64, device=DEV)
@@ -109,8 +113,8 @@ def test_residues_match_oracle(fmt):
     _, V, _ = _split(plan, _dev(B), 0, n, k, n)
     Y = torch.zeros((plan.channels, m, n), dtype=torch.int16, device=DEV)
     flag = torch.zeros(4, dtype=torch.int32, device=DEV)
-    st = oz.oz_residue_gemm(plan.handle, m, n, U.shape[1], V.shape[1], U.shape[2], U.data_ptr(), V.data_ptr(),
-                            Y.data_ptr(), 1, flag.data_ptr(), oz._stream_handle())
+    st = oz.oz_residue_gemm(plan.handle, m, n, U.shape[1], V.shape[1], plan.plane_geometry(k)[0], U.data_ptr(),
+                            V.data_ptr(), Y.data_ptr(), 1, flag.data_ptr(), oz._stream_handle())
     assert st == oz.OZ_OK
     torch.cuda.synchronize()
     assert flag.cpu().numpy()[0] & 2 == 0
@@ -161,13 +165,16 @@ def test_inner_dimension_above_k_max_is_refused():
 
 
 def _encode(fmt, codes):
-    """Inverse of _decode on codes: [..., k_pad] codes -> plane bytes."""
+    """Inverse of _decode: [..., k_pad] codes -> plane bytes [..., row_bytes]."""
     nb = CODE_BITS[fmt]
     if nb == 8:
         return codes.astype(np.uint8)
+    if nb == 4:
+        c = codes.reshape(*codes.shape[:-1], -1, 2).astype(np.int64)
+        return (c[..., 0] | (c[..., 1] << 4)).astype(np.uint8)
     ch = codes.reshape(*codes.shape[:-1], -1, 16).astype(np.int64)
-    bits = ((ch[..., None] >> np.arange(nb)) & 1).reshape(*ch.shape[:-1], 16 * nb)
-    pad = np.zeros((*bits.shape[:-1], 128 - 16 * nb), dtype=np.int64)
+    bits = ((ch[..., None] >> np.arange(6)) & 1).reshape(*ch.shape[:-1], 96)
+    pad = np.zeros((*bits.shape[:-1], 32), dtype=np.int64)
     return np.packbits(np.concatenate([bits, pad], -1).astype(np.uint8), axis=-1,
                        bitorder="little").reshape(codes.shape)
 
@@ -185,15 +192,15 @@ def test_fp32_accumulation_is_exact_at_capacity(fmt):
     k = plan.k_max
     assert k * rho * rho <= 2**24
     m, n = 128, 256
-    k_pad = oz.round_up(k, 128)
+    k_pad, row_bytes = plan.plane_geometry(k)
 
     def row(code):
         r = np.zeros(k_pad, dtype=np.int64)
         r[:k] = code
         return _encode(fmt, r)
 
-    Uh = np.zeros((plan.planes, 256, k_pad), dtype=np.uint8)
-    Vh = np.zeros((plan.planes, 256, k_pad), dtype=np.uint8)
+    Uh = np.zeros((plan.planes, 256, row_bytes), dtype=np.uint8)
+    Vh = np.zeros((plan.planes, 256, row_bytes), dtype=np.uint8)
     Uh[:, :m] = row(code_of[rho])
     Vh[:, 0:n:2] = row(code_of[rho])
     Vh[:, 1:n:2] = row(code_of[-rho])
