@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--bits", type=int, default=0)
     ap.add_argument("--phi", type=float, default=0.5)
     ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc"])
+    ap.add_argument("--format", default="int8", choices=["int8", "E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
+                    help="residue alphabet: the INT8 path, or a float-format configuration")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
     ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch"],
@@ -117,9 +119,17 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def workload_name(n, phi, q, bits):
-    return (f"emulated dgemm m=n=k={n}, entries U(-0.5,0.5)*exp({phi}*N(0,1)) seed 0 (rank r: seed r), "
-            f"INT8 residue path Q={q} moduli<=239, beta={bits}")
+def workload_name(n, phi, q, bits, fmt="int8", channels=None):
+    head = (f"emulated dgemm m=n=k={n}, entries U(-0.5,0.5)*exp({phi}*N(0,1)) seed 0 (rank r: seed r), ")
+    if fmt == "int8":
+        return head + f"INT8 residue path Q={q} moduli<=239, beta={bits}"
+    return head + f"{fmt} configuration, {q} low-precision GEMMs over {channels} channels, beta={bits}"
+
+
+def make_plan(oz, args, n, engine=None):
+    if args.format == "int8":
+        return oz.Plan(args.q, args.bits, n, engine if engine is not None else oz.OZ_ENGINE_AUTO)
+    return oz.PlanFP(args.format, n, args.bits)
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -169,12 +179,11 @@ def load_peaks():
 # CPU oracle leg (the only place bench.py runs the oracle)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(A, B, n, q, bits, seconds):
+def oracle_rate(A, B, n, mods, bits, seconds):
     """Time the oracle on a bounded sample of entries of the same product;
     returns (TFLOP/s of the emulated product, entries, seconds, threads)."""
     import oracle
     oracle.build()
-    mods = oracle.max_product_moduli(q, 239)
     rng = np.random.default_rng(123)
     count = 64
     done, elapsed = 0, 0.0
@@ -199,14 +208,21 @@ def run_reference(args, rank, world):
     n = args.n
     A, B = synth.phi_pair(n, n, n, args.phi, seed=0)
     import oracle
-    bits = args.bits or oracle.beta_max(oracle.max_product_moduli(args.q, 239), n)
+    if args.format == "int8":
+        mods = oracle.max_product_moduli(args.q, 239)
+        bits = args.bits or oracle.beta_max(mods, n)
+        q, channels = args.q, args.q
+    else:
+        import paper_2609_37693_gb300 as oz      # the configuration tables only (host side)
+        plan = oz.PlanFP(args.format, n, args.bits)
+        mods, bits, q, channels = plan.moduli, plan.bits, plan.q, plan.channels
     per_step = max(1.0, min(args.cpu_sample_s, 20.0) / max(args.steps, 1))
     for _ in range(args.warmup):
-        oracle_rate(A, B, n, args.q, bits, per_step / 4)
+        oracle_rate(A, B, n, mods, bits, per_step / 4)
     vals, ents, secs = [], 0, 0.0
     threads = oracle.threads()
     for _ in range(args.steps):
-        v, e, s, threads = oracle_rate(A, B, n, args.q, bits, per_step)
+        v, e, s, threads = oracle_rate(A, B, n, mods, bits, per_step)
         vals.append(v)
         ents += e
         secs += s
@@ -215,11 +231,11 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": workload_name(n, args.phi, args.q, bits),
-                   "m": n, "n": n, "k": n, "q": args.q, "bits": bits, "phi": args.phi},
+        "config": {"workload": workload_name(n, args.phi, q, bits, args.format, channels),
+                   "m": n, "n": n, "k": n, "q": q, "bits": bits, "phi": args.phi, "format": args.format},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ents} entries of C ({n}x{n}), each a full k={n} oracle evaluation "
-                                   f"(scale, residues, {args.q} int64 dot products, CRT, rounding)"},
+                                   f"(scale, residues, {len(mods)} int64 dot products, CRT, rounding)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -242,7 +258,8 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     n = args.n
     engine = {"auto": oz.OZ_ENGINE_AUTO, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC}[args.engine]
-    plan = oz.Plan(args.q, args.bits, n, engine)
+    plan = make_plan(oz, args, n, engine)
+    is_fp = args.format != "int8"
     A_h, B_h = synth.phi_pair(n, n, n, args.phi, seed=rank)
     A = torch.from_numpy(A_h).to(dev)
     B = torch.from_numpy(B_h).to(dev)
@@ -309,8 +326,8 @@ def run_ours(args, rank, world, local):
     value = throughput_tflops(flops, args.steps, elapsed_ms, world)
 
     # ---- per-phase times through the phase entry points (same kernels) ----
-    m_pad, n_pad, k_pad = oz.round_up(n, 256), oz.round_up(n, 256), oz.round_up(n, 128)
     _, lay = oz.oz_workspace_layout(plan.handle, n, n, n)
+    m_pad, n_pad, k_pad = lay["m_pad"], lay["n_pad"], lay["k_pad"]
     base = ws.data_ptr()
     phase_ms = {"split_a": 0.0, "split_b": 0.0, "gemm": 0.0, "reconstruct": 0.0}
     reps = max(3, min(args.steps, 10))
@@ -360,7 +377,14 @@ def run_ours(args, rank, world, local):
     gemm_ops = 2.0 * plan.q * n**3                       # algorithmic low-precision ops per launch
     gemm_s = phase_ms["gemm"] * 1e-3
     achieved = gemm_ops / gemm_s / 1e12
-    if plan.engine == oz.OZ_ENGINE_TC:
+    if is_fp:
+        # no measured FP8/FP4 peak: the measured bf16 burst times the nominal dense
+        # ratio (FP8 4.5 / bf16 2.25 PFLOP/s; FP4 13.5 / 2.25)
+        ratio = 6.0 if args.format == "E2M1" else 2.0
+        peak = peaks.get("bf16_tflops", 1900.0) * ratio
+        peak_src = (f"{'FP4' if ratio == 6.0 else 'FP8'} dense = measured bf16 burst (MEASURED_PEAKS.json "
+                    f"bf16_tflops) x {ratio:g}, the nominal dense ratio")
+    elif plan.engine == oz.OZ_ENGINE_TC:
         peak = peaks.get("bf16_tflops", 1900.0)
         peak_src = "bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops, burst)"
     else:
@@ -374,27 +398,33 @@ def run_ours(args, rank, world, local):
         roofline["traffic"] = tr.pop("bytes")
         roofline["traffic_source"] = dict(tr, unit="bytes per launch")
     hbm = peaks.get("hbm_gbs", 6768.8)
-    bytes_split = 8.0 * 2 * n * n + plan.q * 2.0 * n * n * (2 if plan.engine == oz.OZ_ENGINE_TC else 1)
-    bytes_rec = plan.q * n * n + 8.0 * n * n
+    _, row_bytes = plan.plane_geometry(n)
+    nplanes = plan.planes if is_fp else plan.q
+    ybytes = (2 * plan.channels) if is_fp else plan.q       # residue bytes per output entry
+    bytes_split = 8.0 * 2 * n * n + nplanes * 2.0 * n * row_bytes
+    bytes_rec = ybytes * n * n + 8.0 * n * n
     gemm_peak_s = gemm_ops / (peak * 1e12)
-    t_roof = gemm_peak_s + (bytes_split + bytes_rec + plan.q * n * n) / (hbm * 1e9)
+    t_roof = gemm_peak_s + (bytes_split + bytes_rec + ybytes * n * n) / (hbm * 1e9)
 
     line = None
     if rank == 0:
         cpu = None
         if world == 1:
-            v, ents, secs, thr = oracle_rate(A_h, B_h, n, plan.q, plan.bits, args.cpu_sample_s)
+            v, ents, secs, thr = oracle_rate(A_h, B_h, n, plan.moduli, plan.bits, args.cpu_sample_s)
             cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{ents} sampled entries of the same {n}^3 product, each a full oracle evaluation "
                              f"({secs:.1f} s on the host cores)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int8" if plan.engine != oz.OZ_ENGINE_TC else "bf16",
+            "vs_baseline": None,
+            "dtype": args.format.lower() if is_fp else ("int8" if plan.engine != oz.OZ_ENGINE_TC else "bf16"),
             "data": "synthetic",
-            "config": {"workload": workload_name(n, args.phi, plan.q, plan.bits),
+            "config": {"workload": workload_name(n, args.phi, plan.q, plan.bits, args.format,
+                                                 getattr(plan, "channels", plan.q)),
                        "m": n, "n": n, "k": n, "q": plan.q, "bits": plan.bits, "phi": args.phi,
-                       "engine": {1: "imma", 2: "tc"}[plan.engine], "parallelism": f"replicas{world}",
+                       "format": args.format,
+                       "engine": {1: "imma", 2: "tc", 3: "fp"}[plan.engine], "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (A and B 512 MiB each); no flush",
                        "cublas_dgemm_tflops": dgemm_tflops, "speedup_vs_cublas_dgemm":
                            (value / world / dgemm_tflops) if dgemm_tflops else None,

@@ -122,9 +122,9 @@ OZ_API oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, i
  * The plan owns a small device table of codes (allocated here on the current
  * device, freed by oz_plan_destroy). Without a CUDA device the plan is still
  * made and describes the configuration (oz_plan_info_fp), but products on it
- * return OZ_ERR_CUDA. Products run through oz_dgemm, oz_dgemm_batched and the
- * phase entry points as for INT8 plans (oz_dgemm_host does not take float
- * plans); their residues Y are uint16, one per entry and channel.
+ * return OZ_ERR_CUDA. Products run through oz_dgemm, oz_dgemm_batched,
+ * oz_dgemm_host and the phase entry points as for INT8 plans; their residues
+ * Y are uint16, one per entry and channel.
  */
 OZ_API oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint, int bits);
 

@@ -103,7 +103,7 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
   uint8_t* Y = reinterpret_cast<uint8_t*>(ws + L.y);
 
   if (plan->is_fp) {
-    if (!plan->d_codes) return OZ_ERR_CUDA;
+    if (!plan->d_words) return OZ_ERR_CUDA;
     const OzFpTables& F = plan->fp;
     uint8_t* U8 = static_cast<uint8_t*>(U);
     uint8_t* V8 = static_cast<uint8_t*>(V);
@@ -158,7 +158,7 @@ extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_
   if (!contiguous && nvec > 0 && !colmax) return OZ_ERR_INVALID_ARG;
   const int bf16 = plan->engine == OZ_ENGINE_TC;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (plan->is_fp && !plan->d_codes) return OZ_ERR_CUDA;
+  if (plan->is_fp && !plan->d_words) return OZ_ERR_CUDA;
   if (plan->is_fp)
     return cuda_status(oz::launch_split_fp(plan->tab, plan->fp, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts,
                                            static_cast<uint8_t*>(planes), flag, colmax, st));

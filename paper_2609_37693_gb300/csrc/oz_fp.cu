@@ -3,13 +3,15 @@
 //
 // Reduce: for every entry and channel, the class c = a' mod m in [0, m)
 // (a' = trunc(x 2^s) from the IEEE fields, cut into 16-bit pieces, one 32-bit
-// Barrett step), then for each plane of the channel's form the code of the
-// plane value the form assigns to c, read from the plan's code tables.
-// Planes are K-major rows of 16-byte chunks, one chunk per 16 consecutive
-// entries: 8-bit codes one per byte; 6- and 4-bit codes packed little-endian
-// from bit 0 of the chunk (12 or 8 bytes used), the layout the f8f6f4 MMA
-// reads for those types from shared memory, so that a K = 32 step is 32 bytes
-// for every format.
+// Barrett step), then the channel's code word of c from the plan's tables:
+// byte q of the word is the code of the plane value the form assigns to c in
+// plane q (the sign of a' selects the second half of the table, where entry r
+// holds the word of class (m - r) mod m). Planes are K-major rows: 8-bit codes
+// one per byte; 6-bit codes packed little-endian 16 to a 16-byte chunk whose
+// last 4 bytes are zero (the shared-memory layout kind::f8f6f4 reads for 6-bit
+// types, so a K = 32 step is 32 bytes for 8- and 6-bit formats); 4-bit codes
+// two per byte, densely (the block-scaled kind::mxf4 layout, K = 64 per 32
+// bytes).
 //
 // GEMMs and epilogue: tcgen05.mma.kind::f8f6f4 on the codes (E4M3, E5M2, E2M3,
 // E3M2 or E2M1) into FP32 accumulators in tensor memory. The work unit is a
@@ -50,79 +52,71 @@ __device__ __forceinline__ ChConst ch_const(const OzFpTables& F, int c) {
   return k;
 }
 
+// 16-bit pieces of |a'| (the sign is kept apart, one bit per entry)
 struct Pieces16 {
-  uint32_t p0, p1, p2, p3, neg;
+  uint32_t p0, p1, p2, p3;
 };
 
-__device__ __forceinline__ Pieces16 pieces16(uint64_t bits, int32_t s) {
-  const Trunc t = truncate(bits, s);
+__device__ __forceinline__ Pieces16 pieces16(uint64_t mag) {
   Pieces16 P;
-  P.p0 = (uint32_t)t.mag & 0xffffu;
-  P.p1 = (uint32_t)(t.mag >> 16) & 0xffffu;
-  P.p2 = (uint32_t)(t.mag >> 32) & 0xffffu;
-  P.p3 = (uint32_t)(t.mag >> 48);
-  P.neg = t.neg;
+  P.p0 = (uint32_t)mag & 0xffffu;
+  P.p1 = (uint32_t)(mag >> 16) & 0xffffu;
+  P.p2 = (uint32_t)(mag >> 32) & 0xffffu;
+  P.p3 = (uint32_t)(mag >> 48);
   return P;
 }
 
-// class of +-|a'| modulo m, in [0, m); y < 2^16 (1 + 3 * 4095) < 2^32
-__device__ __forceinline__ uint32_t class_of(const ChConst& k, const Pieces16& P) {
+// Index of the code word of a' = +-|a'|: the class r of |a'| (y < 2^16 (1 + 3 * 4095)
+// < 2^32, one Barrett step), plus m for a negative entry, whose class is (m - r) mod m.
+__device__ __forceinline__ uint32_t word_index(const ChConst& k, const Pieces16& P, uint32_t neg) {
   const uint32_t y = P.p0 + P.p1 * k.c16 + P.p2 * k.c32 + P.p3 * k.c48;
-  const uint32_t r = mod_barrett(y, k.m, k.magic);
-  return P.neg ? (r ? k.m - r : 0u) : r;
+  return mod_barrett(y, k.m, k.magic) + (neg ? k.m : 0u);
 }
 
-// The bytes the MMA operands read for 16 consecutive entries: 8-bit codes one
-// per byte (16 bytes); 6-bit codes packed little-endian from bit 0 of a 16-byte
-// chunk whose last 4 bytes are zero (the kind::f8f6f4 shared-memory layout);
-// 4-bit codes two per byte, densely (8 bytes, the block-scaled kind::mxf4
-// layout). Words: 4, 4 and 2.
-template <int CB>
-struct Chunk {
-  static constexpr int kWords = CB == 4 ? 2 : 4;
-  uint32_t w[kWords];
-};
-
-template <int CB>
-__device__ __forceinline__ Chunk<CB> pack_chunk(const uint32_t (&c)[16]) {
-  Chunk<CB> o;
-  if constexpr (CB == 8) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      o.w[q] = c[4 * q] | (c[4 * q + 1] << 8) | (c[4 * q + 2] << 16) | (c[4 * q + 3] << 24);
-  } else if constexpr (CB == 6) {
-    uint64_t lo = 0;
-#pragma unroll
-    for (int e = 0; e < 11; ++e) lo |= (uint64_t)c[e] << (6 * e);        // code 10 keeps its low 4 bits
-    uint32_t hi = c[10] >> 4;
-#pragma unroll
-    for (int e = 11; e < 16; ++e) hi |= c[e] << (6 * e - 64);
-    o.w[0] = (uint32_t)lo;
-    o.w[1] = (uint32_t)(lo >> 32);
-    o.w[2] = hi;
-    o.w[3] = 0u;
-  } else {
-    o.w[0] = 0u;
-    o.w[1] = 0u;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      o.w[0] |= c[e] << (4 * e);
-      o.w[1] |= c[8 + e] << (4 * e);
-    }
-  }
-  return o;
+// byte q of each of w0..w3, as the bytes of one word
+__device__ __forceinline__ uint32_t gather4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, int q) {
+  const uint32_t sel = (uint32_t)q | ((uint32_t)(q + 4) << 4);
+  return __byte_perm(__byte_perm(w0, w1, sel), __byte_perm(w2, w3, sel), 0x5410);
 }
 
-template <int CB>
-__device__ __forceinline__ void store_chunk(uint8_t* dst, const Chunk<CB>& o) {
-  if constexpr (CB == 4)
-    *reinterpret_cast<uint2*>(dst) = make_uint2(o.w[0], o.w[1]);
-  else
-    *reinterpret_cast<uint4*>(dst) = make_uint4(o.w[0], o.w[1], o.w[2], o.w[3]);
+// four codes held one per byte -> 6-bit fields packed little-endian (24 bits)
+__device__ __forceinline__ uint32_t pack6(uint32_t g) {
+  return (g & 0x3Fu) | ((g >> 2) & 0xFC0u) | ((g >> 4) & 0x3F000u) | ((g >> 6) & 0xFC0000u);
+}
+// four codes held one per byte -> 4-bit fields packed little-endian (16 bits)
+__device__ __forceinline__ uint32_t pack4(uint32_t g) {
+  const uint32_t t = (g | (g >> 4)) & 0x00FF00FFu;
+  return (t | (t >> 8)) & 0xFFFFu;
 }
 
-// Contiguous vectors: one CTA of 256 threads per vector, 16 entries per thread
-// and pass; planes [nplanes][nvec_pad][row bytes of k_pad entries].
+// Plane q's bits for 8 consecutive entries whose code words are w[0..7]:
+// 8-bit codes: 64 bits; 6-bit: 48 bits; 4-bit: 32 bits (little-endian).
+template <int CB>
+__device__ __forceinline__ uint64_t plane_bits8(const uint32_t (&w)[8], int q) {
+  const uint32_t g0 = gather4(w[0], w[1], w[2], w[3], q);
+  const uint32_t g1 = gather4(w[4], w[5], w[6], w[7], q);
+  if constexpr (CB == 8) return (uint64_t)g0 | ((uint64_t)g1 << 32);
+  else if constexpr (CB == 6) return (uint64_t)pack6(g0) | ((uint64_t)pack6(g1) << 24);
+  else return (uint64_t)(pack4(g0) | (pack4(g1) << 16));
+}
+
+// The 16-byte chunk of 16 entries of 6-bit codes from the 48-bit fields of
+// entries 0..7 (a) and 8..15 (b); bytes 12..15 zero.
+__device__ __forceinline__ uint4 chunk6(uint64_t a, uint64_t b) {
+  return make_uint4((uint32_t)a, (uint32_t)(a >> 32) | ((uint32_t)b << 16), (uint32_t)(b >> 16), 0u);
+}
+
+// Entry bits: |a'| pieces and sign of x (non-finite entries count as 0).
+__device__ __forceinline__ Pieces16 load_entry(uint64_t b, int32_t s, uint32_t& neg) {
+  if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
+  const Trunc t = truncate(b, s);
+  neg = t.neg && t.mag;
+  return pieces16(t.mag);
+}
+
+// Contiguous vectors: one CTA of 256 threads per vector, 8 entries per thread
+// and pass; planes [nplanes][nvec_pad][row bytes of k_pad entries]. For 6-bit
+// codes the two threads of a 16-entry chunk meet by a shuffle.
 template <int CB>
 __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constant__ OzFpTables F, int bits,
                                                             int64_t nvec, int64_t len, const double* __restrict__ X,
@@ -164,90 +158,95 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
   const int32_t s = s_sh;
   const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
   const int64_t plane = nvec_pad * row_bytes;
-  for (int64_t h0 = (int64_t)tid * 16; h0 < k_pad; h0 += 256 * 16) {
-    Pieces16 P[16];
+  uint8_t* out_row = planes + v * row_bytes;
+  // every thread runs every pass (the shuffle of the 6-bit path needs both lanes)
+  for (int64_t base = 0; base < k_pad; base += 256 * 8) {
+    const int64_t h0 = base + (int64_t)tid * 8;
+    const bool active = h0 < k_pad;
+    Pieces16 P[8];
+    uint32_t negm = 0;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      uint64_t b = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
-      if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
-      P[e] = pieces16(b, s);
+    for (int e = 0; e < 8; ++e) {
+      const uint64_t b = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+      uint32_t ng;
+      P[e] = load_entry(b, s, ng);
+      negm |= ng << e;
     }
     for (int c = 0; c < F.nch; ++c) {
       const ChConst k = ch_const(F, c);
-      uint32_t cls[16];
+      const uint32_t* tw = F.words + F.ch_woff[c];
+      uint32_t w[8];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) cls[e] = class_of(k, P[e]);
+      for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index(k, P[e], (negm >> e) & 1u));
       const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
-      for (int q = 0; q < np; ++q) {
-        const uint8_t* tab = F.codes + F.plane_off[p0 + q];
-        uint32_t code[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
-        store_chunk<CB>(planes + (int64_t)(p0 + q) * plane + v * row_bytes + (CB == 4 ? h0 / 2 : h0),
-                        pack_chunk<CB>(code));
+      for (int q = 0; q < 3; ++q) {
+        if (q >= np) break;
+        uint8_t* dst = out_row + (int64_t)(p0 + q) * plane;
+        const uint64_t pb = plane_bits8<CB>(w, q);
+        if constexpr (CB == 8) {
+          if (active) *reinterpret_cast<uint2*>(dst + h0) = make_uint2((uint32_t)pb, (uint32_t)(pb >> 32));
+        } else if constexpr (CB == 4) {
+          if (active) *reinterpret_cast<uint32_t*>(dst + h0 / 2) = (uint32_t)pb;
+        } else {
+          const uint64_t other = __shfl_xor_sync(0xffffffffu, pb, 1);
+          if (active && (tid & 1) == 0) *reinterpret_cast<uint4*>(dst + h0) = chunk6(pb, other);
+        }
       }
     }
   }
 }
 
-// Strided vectors (columns of B, or of A^T): 64 (h) x 64 (vector) tiles through
-// shared memory so that the planes, K-major per vector, are written along h;
-// each thread forms the chunk of 16 entries of one vector.
+// Strided vectors (columns of B, or of A^T): 64 (vector) x 32 (h) tiles; lane
+// groups of 4 take the 32 entries of one vector, 8 each, so that a vector's
+// plane bits leave the group as one 32-, 24- (two chunks) or 16-byte piece of
+// its plane row; 6-bit pairs meet by a shuffle. No shared memory.
 template <int CB>
 __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constant__ OzFpTables F, int64_t nvec,
                                                             int64_t len, const double* __restrict__ X, int64_t ld,
                                                             int64_t nvec_pad, int64_t k_pad,
                                                             const int32_t* __restrict__ shifts,
                                                             uint8_t* __restrict__ planes) {
-  constexpr int kPitchWords = 17;
-  __shared__ uint32_t tile[2][64 * kPitchWords];
   const int tid = threadIdx.x;
-  const int jl = tid & 63;
-  const int hg = tid >> 6;
-  const int64_t j0 = (int64_t)blockIdx.x * 64;
-  const int64_t hbase = (int64_t)blockIdx.y * 64;
-  const int64_t j = j0 + jl;
+  const int hg = tid & 3;                              // entries hbase + 8 hg .. + 7
+  const int jl = tid >> 2;
+  const int64_t j = (int64_t)blockIdx.x * 64 + jl;
+  const int64_t hbase = (int64_t)blockIdx.y * 32;
   const bool live = j < nvec;
   const int32_t s = live ? shifts[j] : 0;
-  Pieces16 P[16];
+  Pieces16 P[8];
+  uint32_t negm = 0;
   const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
 #pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    int64_t h = hbase + hg * 16 + e;
-    uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
-    if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
-    P[e] = pieces16(b, s);
+  for (int e = 0; e < 8; ++e) {
+    const int64_t h = hbase + hg * 8 + e;
+    const uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
+    uint32_t ng;
+    P[e] = load_entry(b, s, ng);
+    negm |= ng << e;
   }
-  constexpr int kWords = Chunk<CB>::kWords;        // words per 16 entries
   const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
   const int64_t plane = nvec_pad * row_bytes;
-  int pg = 0;  // planes written so far: picks the shared buffer
+  uint8_t* out = planes + j * row_bytes + (CB == 4 ? (hbase + hg * 8) / 2 : hbase + hg * 8);
   for (int c = 0; c < F.nch; ++c) {
     const ChConst k = ch_const(F, c);
-    uint32_t cls[16];
+    const uint32_t* tw = F.words + F.ch_woff[c];
+    uint32_t w[8];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) cls[e] = class_of(k, P[e]);
+    for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index(k, P[e], (negm >> e) & 1u));
     const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
-    for (int q = 0; q < np; ++q, ++pg) {
-      uint32_t* tb = tile[pg & 1];
-      const uint8_t* tab = F.codes + F.plane_off[p0 + q];
-      uint32_t code[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) code[e] = __ldg(tab + cls[e]);
-      const Chunk<CB> o = pack_chunk<CB>(code);
-#pragma unroll
-      for (int w = 0; w < kWords; ++w) tb[jl * kPitchWords + hg * kWords + w] = o.w[w];
-      __syncthreads();
-      // a vector's 64 entries are kWords 16-byte pieces of its plane row
-      for (int cidx = tid; cidx < 64 * kWords; cidx += 256) {
-        const int rowi = cidx / kWords, ch = cidx % kWords;
-        uint4 w;
-        w.x = tb[rowi * kPitchWords + ch * 4 + 0];
-        w.y = tb[rowi * kPitchWords + ch * 4 + 1];
-        w.z = tb[rowi * kPitchWords + ch * 4 + 2];
-        w.w = tb[rowi * kPitchWords + ch * 4 + 3];
-        *reinterpret_cast<uint4*>(planes + (int64_t)(p0 + q) * plane + (j0 + rowi) * row_bytes +
-                                  (CB == 4 ? hbase / 2 : hbase) + ch * 16) = w;
+    for (int q = 0; q < 3; ++q) {
+      if (q >= np) break;
+      uint8_t* dst = out + (int64_t)(p0 + q) * plane;
+      const uint64_t pb = plane_bits8<CB>(w, q);
+      if constexpr (CB == 8) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)pb, (uint32_t)(pb >> 32));
+      } else if constexpr (CB == 4) {
+        *reinterpret_cast<uint32_t*>(dst) = (uint32_t)pb;
+      } else {
+        const uint64_t other = __shfl_xor_sync(0xffffffffu, pb, 1);
+        if ((hg & 1) == 0) *reinterpret_cast<uint4*>(dst) = chunk6(pb, other);
       }
     }
   }
@@ -836,7 +835,7 @@ cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int
   }
   cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
   if (e != cudaSuccess) return e;
-  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 32));
   split_fp_cols_kernel<CB><<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   return cudaGetLastError();
 }

@@ -31,10 +31,13 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   if (rows > m && m > 0) rows = m;
   if (rows < 1) rows = 1;
   const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;
+  const int64_t nplanes = p->is_fp ? p->fp.nplanes : p->Q;
+  const int64_t ybytes = p->is_fp ? 2 : 1;
   L->chunk = rows;
   L->chunk_pad = round_up(rows, oz::kPadRows);
   L->n_pad = round_up(n > 0 ? n : 1, oz::kPadRows);
-  L->k_pad = round_up(k > 0 ? k : 1, oz::kPadK);
+  L->k_pad = round_up(k > 0 ? k : 1, p->is_fp ? oz::fp_k_align(p->fp) : oz::kPadK);
+  const int64_t row = p->is_fp ? oz::fp_row_bytes(p->fp, L->k_pad) : L->k_pad * elem;   // bytes per plane row
   size_t off = 0;
   L->flag = off; off = al(off + 16);
   L->s = off; off = al(off + 4 * (size_t)(m > 0 ? m : 1));
@@ -43,9 +46,9 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   L->b = off; off = al(off + 8 * (size_t)k * n);
   for (int i = 0; i < 2; ++i) { L->a[i] = off; off = al(off + 8 * (size_t)rows * k); }
   for (int i = 0; i < 2; ++i) { L->c[i] = off; off = al(off + 8 * (size_t)rows * n); }
-  L->u = off; off = al(off + (size_t)p->Q * L->chunk_pad * L->k_pad * elem);
-  L->v = off; off = al(off + (size_t)p->Q * L->n_pad * L->k_pad * elem);
-  L->y = off; off = al(off + (size_t)p->Q * rows * n);
+  L->u = off; off = al(off + (size_t)nplanes * L->chunk_pad * row);
+  L->v = off; off = al(off + (size_t)nplanes * L->n_pad * row);
+  L->y = off; off = al(off + (size_t)p->Q * rows * n * ybytes);
   L->total = off;
   return true;
 }
@@ -63,7 +66,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
                                    void* workspace, size_t workspace_bytes, void* stream, void* stream_h2d,
                                    void* stream_d2h) {
   if (!plan || m < 0 || n < 0 || k < 0 || rows < 0) return OZ_ERR_INVALID_ARG;
-  if (plan->is_fp) return OZ_ERR_UNSUPPORTED;
+  if (plan->is_fp && !plan->d_words) return OZ_ERR_CUDA;
   if (lda < (k > 1 ? k : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1)) return OZ_ERR_INVALID_ARG;
   if (k > plan->k_max) return OZ_ERR_K_TOO_LARGE;
   if (stream == stream_h2d || stream == stream_d2h || stream_h2d == stream_d2h) return OZ_ERR_INVALID_ARG;
@@ -88,7 +91,12 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   void* V = ws + L.v;
   uint8_t* Y = reinterpret_cast<uint8_t*>(ws + L.y);
   const OzTables& T = plan->tab;
+  const OzFpTables& F = plan->fp;
+  const bool fp = plan->is_fp != 0;
   const int bf16 = plan->engine == OZ_ENGINE_TC;
+  uint8_t* U8 = static_cast<uint8_t*>(U);
+  uint8_t* V8 = static_cast<uint8_t*>(V);
+  uint16_t* Y16 = reinterpret_cast<uint16_t*>(Y);
   const int64_t nchunks = (m + L.chunk - 1) / L.chunk;
 
   // events: start, B ready, A slot ready/free, C slot ready/free, end of both copy streams
@@ -136,22 +144,27 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
     const int64_t r0 = ci * L.chunk, nr = (m - r0) < L.chunk ? (m - r0) : L.chunk;
     chk(cudaStreamWaitEvent(sc, ev_a_ready[slot], 0));
     if (k > 0) {
-      chk(oz::launch_split_rows(T, nr, k, Ad[slot], k, L.chunk_pad, L.k_pad, s + r0, U, bf16, flag, sc));
+      chk(fp ? oz::launch_split_fp(T, F, 1, nr, k, Ad[slot], k, L.chunk_pad, L.k_pad, s + r0, U8, flag, nullptr, sc)
+             : oz::launch_split_rows(T, nr, k, Ad[slot], k, L.chunk_pad, L.k_pad, s + r0, U, bf16, flag, sc));
       chk(cudaEventRecord(ev_a_free[slot], sc));
       if (ci + 2 < nchunks) copy_a(ci + 2);
       if (ci == 0) {
         chk(cudaStreamWaitEvent(sc, ev_b, 0));
-        chk(oz::launch_split_cols(T, n, k, Bd, n, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, sc));
+        chk(fp ? oz::launch_split_fp(T, F, 0, n, k, Bd, n, L.n_pad, L.k_pad, t, V8, flag, colmax, sc)
+               : oz::launch_split_cols(T, n, k, Bd, n, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, sc));
       }
-      chk(bf16 ? oz::launch_gemm_tc(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
-               : oz::launch_gemm_imma(T, nr, n, L.k_pad, static_cast<const int8_t*>(U), L.chunk_pad * L.k_pad,
-                                      static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, sc));
+      chk(fp     ? oz::launch_gemm_fp(F, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U8, V8, Y16, 0, flag, sc)
+          : bf16 ? oz::launch_gemm_tc(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
+                 : oz::launch_gemm_imma(T, nr, n, L.k_pad, static_cast<const int8_t*>(U), L.chunk_pad * L.k_pad,
+                                        static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, sc));
     } else {
       chk(cudaEventRecord(ev_a_free[slot], sc));
       if (ci + 2 < nchunks) copy_a(ci + 2);
     }
     if (ci >= 2) chk(cudaStreamWaitEvent(sc, ev_c_free[slot], 0));      // copy-back of chunk ci-2 done
-    if (k > 0) chk(oz::launch_reconstruct(T, nr, n, Y, s + r0, t, Cd[slot], n, sc));
+    if (k > 0)
+      chk(fp ? oz::launch_reconstruct16(T, nr, n, Y16, s + r0, t, Cd[slot], n, sc)
+             : oz::launch_reconstruct(T, nr, n, Y, s + r0, t, Cd[slot], n, sc));
     else chk(cudaMemsetAsync(Cd[slot], 0, (size_t)nr * n * 8, sc));
     chk(cudaEventRecord(ev_c_ready[slot], sc));
     chk(cudaStreamWaitEvent(sd, ev_c_ready[slot], 0));

@@ -66,9 +66,13 @@ struct OzFpTables {
   uint8_t g_pa[OZ_MAX_FP_GEMMS], g_pb[OZ_MAX_FP_GEMMS];  // planes of GEMM g
   uint8_t g_ch[OZ_MAX_FP_GEMMS];          // channel of GEMM g
   float g_lam[OZ_MAX_FP_GEMMS];           // its weight lambda reduced into [0, m)
-  uint32_t plane_off[OZ_MAX_FP_PLANES];   // byte offset of the plane's code table
+  uint32_t plane_off[OZ_MAX_FP_PLANES];   // offset of the plane's value table (host copy)
   uint32_t plane_ch[OZ_MAX_FP_PLANES];    // channel of plane p
-  const uint8_t* codes;                   // device: every plane's table, m bytes each
+  uint32_t ch_woff[OZ_TABLE_CAP];         // offset of the channel's code words
+  // device: per channel 2 m words; word i < m is class i, word m + i is class
+  // (m - i) mod m (the class of -x when x has class i); byte q of a word is
+  // the code of the channel's plane q
+  const uint32_t* words;
 };
 
 struct oz_plan_s {
@@ -82,9 +86,9 @@ struct oz_plan_s {
   int fp_form[OZ_TABLE_CAP], fp_base[OZ_TABLE_CAP];
   int64_t fp_kcfg;   // inner dimension the configuration was built for
   OzFpTables fp;
-  uint8_t* d_codes;  // device copy of the code tables (owned)
+  uint32_t* d_words; // device copy of the code words (owned)
   int16_t* h_values; // host copy of the plane values, one table per plane (owned)
-  size_t codes_bytes;
+  size_t values_len;
 };
 
 namespace oz {

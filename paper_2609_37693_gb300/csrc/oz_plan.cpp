@@ -240,7 +240,7 @@ extern "C" oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_ma
 
 extern "C" void oz_plan_destroy(oz_plan plan) {
   if (!plan) return;
-  if (plan->d_codes) cudaFree(plan->d_codes);
+  if (plan->d_words) cudaFree(plan->d_words);
   delete[] plan->h_values;
   delete plan;
 }

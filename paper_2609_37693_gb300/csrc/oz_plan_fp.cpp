@@ -331,22 +331,31 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   }
   for (int c = 0; c < cfg->nch; ++c)
     for (int q = 0; q < f.ch_nplanes[c]; ++q) f.plane_ch[f.ch_plane0[c] + q] = (uint32_t)c;
-  std::vector<uint8_t> codes(total);
   p->h_values = new (std::nothrow) int16_t[total];
   if (!p->h_values) { delete p; return OZ_ERR_INVALID_ARG; }
   for (int q = 0; q < f.nplanes; ++q)
-    for (size_t c = 0; c < planes[q].size(); ++c) {
-      const int64_t v = planes[q][c];
-      codes[f.plane_off[q] + c] = (uint8_t)code_of.at(v);
-      p->h_values[f.plane_off[q] + c] = (int16_t)v;
+    for (size_t c = 0; c < planes[q].size(); ++c) p->h_values[f.plane_off[q] + c] = (int16_t)planes[q][c];
+  p->values_len = total;
+  // code words: per channel 2 m words, class i then the class of its negation
+  std::vector<uint32_t> words;
+  for (int c = 0; c < cfg->nch; ++c) {
+    const uint32_t m = f.m[c];
+    f.ch_woff[c] = (uint32_t)words.size();
+    for (uint32_t i = 0; i < 2 * m; ++i) {
+      const uint32_t cls = i < m ? i : (m - (i - m)) % m;
+      uint32_t w = 0;
+      for (int q = 0; q < f.ch_nplanes[c]; ++q)
+        w |= (uint32_t)code_of.at(planes[f.ch_plane0[c] + q][cls]) << (8 * q);
+      words.push_back(w);
     }
-  p->codes_bytes = total;
+  }
   // Without a CUDA device the plan still describes the configuration
   // (oz_plan_info_fp); products on it then return OZ_ERR_CUDA.
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) {
-    if (cudaMalloc(&p->d_codes, total) != cudaSuccess ||
-        cudaMemcpy(p->d_codes, codes.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    const size_t nb = words.size() * sizeof(uint32_t);
+    if (cudaMalloc(&p->d_words, nb) != cudaSuccess ||
+        cudaMemcpy(p->d_words, words.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       oz_plan_destroy(p);
       return OZ_ERR_CUDA;
@@ -354,7 +363,7 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   } else {
     cudaGetLastError();
   }
-  f.codes = p->d_codes;
+  f.words = p->d_words;
   *out = p;
   return OZ_OK;
 }
@@ -373,8 +382,8 @@ extern "C" oz_status oz_plan_info_fp(oz_plan plan, int* channels, int* gemms, in
     if (bases) bases[c] = plan->fp_base[c];
   }
   if (plane_values) {
-    if (values_len < plan->codes_bytes) return OZ_ERR_INVALID_ARG;
-    memcpy(plane_values, plan->h_values, plan->codes_bytes * sizeof(int16_t));
+    if (values_len < plan->values_len) return OZ_ERR_INVALID_ARG;
+    memcpy(plane_values, plan->h_values, plan->values_len * sizeof(int16_t));
   }
   return OZ_OK;
 }

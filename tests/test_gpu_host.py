@@ -28,3 +28,19 @@ def test_host_path_equals_device_path(m, n, k, rows):
     ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
     assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
     assert oz.query_status(hg.ws) == oz.OZ_OK
+
+
+@pytest.mark.parametrize("fmt", ["E4M3", "E3M2", "E2M1"])
+@pytest.mark.parametrize("m,n,k,rows", [(1000, 700, 900, 256), (300, 257, 1000, 0)])
+def test_host_path_float_formats(fmt, m, n, k, rows):
+    plan = oz.PlanFP(fmt, max(k, 1))
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=m + k)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
+    hg = oz.HostGemm(plan, m, n, k, rows)
+    hg(Ah, Bh, Ch)
+    torch.cuda.synchronize()
+    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
+    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
+    assert oz.query_status(hg.ws) == oz.OZ_OK
