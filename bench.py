@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--q", type=int, default=16)
     ap.add_argument("--bits", type=int, default=0)
     ap.add_argument("--phi", type=float, default=0.5)
-    ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc", "tc1"])
     ap.add_argument("--format", default="int8", choices=["int8", "E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
                     help="residue alphabet: the INT8 path, or a float-format configuration")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
@@ -257,7 +257,8 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     n = args.n
-    engine = {"auto": oz.OZ_ENGINE_AUTO, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC}[args.engine]
+    engine = {"auto": oz.OZ_ENGINE_AUTO, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC,
+              "tc1": oz.OZ_ENGINE_TC1}[args.engine]
     plan = make_plan(oz, args, n, engine)
     is_fp = args.format != "int8"
     A_h, B_h = synth.phi_pair(n, n, n, args.phi, seed=rank)
@@ -384,7 +385,7 @@ def run_ours(args, rank, world, local):
         peak = peaks.get("bf16_tflops", 1900.0) * ratio
         peak_src = (f"{'FP4' if ratio == 6.0 else 'FP8'} dense = measured bf16 burst (MEASURED_PEAKS.json "
                     f"bf16_tflops) x {ratio:g}, the nominal dense ratio")
-    elif plan.engine == oz.OZ_ENGINE_TC:
+    elif plan.engine in (oz.OZ_ENGINE_TC, oz.OZ_ENGINE_TC1):
         peak = peaks.get("bf16_tflops", 1900.0)
         peak_src = "bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops, burst)"
     else:
@@ -418,13 +419,13 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": args.format.lower() if is_fp else ("int8" if plan.engine != oz.OZ_ENGINE_TC else "bf16"),
+            "dtype": args.format.lower() if is_fp else ("int8" if plan.engine == oz.OZ_ENGINE_IMMA else "bf16"),
             "data": "synthetic",
             "config": {"workload": workload_name(n, args.phi, plan.q, plan.bits, args.format,
                                                  getattr(plan, "channels", plan.q)),
                        "m": n, "n": n, "k": n, "q": plan.q, "bits": plan.bits, "phi": args.phi,
                        "format": args.format,
-                       "engine": {1: "imma", 2: "tc", 3: "fp"}[plan.engine], "parallelism": f"replicas{world}",
+                       "engine": {1: "imma", 2: "tc", 3: "fp", 4: "tc1"}[plan.engine], "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (A and B 512 MiB each); no flush",
                        "cublas_dgemm_tflops": dgemm_tflops, "speedup_vs_cublas_dgemm":
                            (value / world / dgemm_tflops) if dgemm_tflops else None,

@@ -64,8 +64,10 @@ typedef enum {
 typedef enum {
   OZ_ENGINE_AUTO = 0,  /* the fastest engine available for the plan */
   OZ_ENGINE_IMMA = 1,  /* INT8 residue planes, warp-level mma.sync s8 -> s32 */
-  OZ_ENGINE_TC = 2,    /* BF16-held residue planes, tcgen05.mma into TMEM */
-  OZ_ENGINE_FP = 3     /* float-format planes (oz_plan_create_fp), tcgen05.mma kind::f8f6f4 */
+  OZ_ENGINE_TC = 2,    /* BF16-held residue planes, tcgen05.mma into TMEM, CTA pairs
+                          (cta_group::2) on 256 x 256 output tiles */
+  OZ_ENGINE_FP = 3,    /* float-format planes (oz_plan_create_fp), tcgen05.mma kind::f8f6f4 */
+  OZ_ENGINE_TC1 = 4    /* as OZ_ENGINE_TC with one CTA per 128 x 256 tile (same bits) */
 } oz_engine;
 
 /* Low-precision float formats (OCP): FP8 E4M3 and E5M2, FP6 E2M3 and E3M2, FP4 E2M1. */

@@ -30,6 +30,7 @@ OZ_ENGINE_AUTO = 0
 OZ_ENGINE_IMMA = 1
 OZ_ENGINE_TC = 2
 OZ_ENGINE_FP = 3
+OZ_ENGINE_TC1 = 4
 
 OZ_FMT_E4M3 = 1
 OZ_FMT_E2M3 = 2

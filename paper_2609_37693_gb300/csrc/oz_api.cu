@@ -21,7 +21,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   if (!p || m < 0 || n < 0 || k < 0) return false;
-  const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;     // bf16 planes; int8 residues or float codes
+  const int64_t elem = oz::engine_bf16(p->engine) ? 2 : 1;     // bf16 planes; int8 residues or float codes
   const int64_t nplanes = p->is_fp ? p->fp.nplanes : p->Q;
   const int64_t ybytes = p->is_fp ? 2 : 1;                    // 16-bit digits for moduli above 255
   L->m_pad = round_up(m > 0 ? m : 1, oz::kPadRows);
@@ -67,7 +67,7 @@ extern "C" oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_a
   if (!plan || k_pad < 0) return OZ_ERR_INVALID_ARG;
   if (k_align) *k_align = plan->is_fp ? oz::fp_k_align(plan->fp) : oz::kPadK;
   if (row_bytes)
-    *row_bytes = plan->is_fp ? oz::fp_row_bytes(plan->fp, k_pad) : k_pad * (plan->engine == OZ_ENGINE_TC ? 2 : 1);
+    *row_bytes = plan->is_fp ? oz::fp_row_bytes(plan->fp, k_pad) : k_pad * (oz::engine_bf16(plan->engine) ? 2 : 1);
   return OZ_OK;
 }
 
@@ -94,7 +94,7 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
   if (k == 0) return cuda_status(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)n * 8, (size_t)m, st));
 
   const OzTables& T = plan->tab;
-  const int bf16 = plan->engine == OZ_ENGINE_TC;
+  const int bf16 = oz::engine_bf16(plan->engine);
   int32_t* s = reinterpret_cast<int32_t*>(ws + L.s);
   int32_t* t = reinterpret_cast<int32_t*>(ws + L.t);
   uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.colmax);
@@ -125,7 +125,8 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
               : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // GEMMs + epilogue
-  e = bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
+  e = plan->engine == OZ_ENGINE_TC1 ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
+    : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
            : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
                                   static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
@@ -156,7 +157,7 @@ extern "C" oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_
   if (!planes || !aligned(planes, 16)) return OZ_ERR_INVALID_ARG;
   if (contiguous ? ld < (len > 1 ? len : 1) : ld < (nvec > 1 ? nvec : 1)) return OZ_ERR_INVALID_ARG;
   if (!contiguous && nvec > 0 && !colmax) return OZ_ERR_INVALID_ARG;
-  const int bf16 = plan->engine == OZ_ENGINE_TC;
+  const int bf16 = oz::engine_bf16(plan->engine);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->is_fp && !plan->d_words) return OZ_ERR_CUDA;
   if (plan->is_fp)
@@ -187,6 +188,9 @@ extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t
                                           flag, st));
   if (plan->engine == OZ_ENGINE_TC)
     return cuda_status(oz::launch_gemm_tc(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
+  if (plan->engine == OZ_ENGINE_TC1)
+    return cuda_status(
+        oz::launch_gemm_tc_single(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
   return cuda_status(oz::launch_gemm_imma(plan->tab, m, n, k_pad, static_cast<const int8_t*>(U), m_pad * k_pad,
                                           static_cast<const int8_t*>(V), n_pad * k_pad, Y, raw ? 1 : 0, st));
 }

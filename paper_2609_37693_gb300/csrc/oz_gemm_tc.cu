@@ -147,6 +147,66 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// ---- the CTA pair (cta_group::2) ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// a load into this CTA's shared memory whose completion is counted on a
+// barrier of the pair's leader
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(dst),
+      "l"(map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// M = 256 across the pair (128 rows of A in each CTA), N = 256 (128 rows of B in each)
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                                ((uint32_t)(256 >> 4) << 24);
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
+      : "memory");
+}
+// arrive on the barrier at this offset in both CTAs of the pair once the
+// products issued so far are done
+__device__ __forceinline__ void umma_commit_pair_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_self(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 // 32 lanes x 32 columns of 32-bit words: thread i gets row (lane base + i),
 // columns taddr.col .. +31.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -395,6 +455,229 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on CTA pairs (cluster of 2, tcgen05 cta_group::2): a pair
+// computes a 256 x 256 output tile; each CTA stages its 128 rows of A and its
+// 128 rows of B (a third less shared-memory and L2 traffic per SM than the
+// 128 x 256 tile of one CTA), the leader (rank 0) issues M = 256 products that
+// read both CTAs' stages and write 128 rows into each CTA's tensor memory.
+//   full[s]   leader only: counts both CTAs' copies of stage s;
+//   empty[s]  each CTA: its stage s may be refilled (multicast commit);
+//   tfull[b]  each CTA: accumulator b holds a slab (multicast commit);
+//   tempty[b] leader only: both CTAs' epilogues have drained accumulator b.
+// ---------------------------------------------------------------------------
+constexpr int P_BM = 128;                          // rows of A per CTA
+constexpr int P_BN = 128;                          // rows of B per CTA (N = 256 per pair)
+constexpr int P_STAGES = 6;
+constexpr int P_A_BYTES = P_BM * BK * 2;           // 16 KiB
+constexpr int P_STAGE_BYTES = P_A_BYTES + P_BN * BK * 2;   // 32 KiB
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + kBarBytes + 1024;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ OzTables T, const Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_base = smem_u32(smem_raw);
+  const uint32_t base = (raw_base + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw_base);
+  const uint32_t bar0 = base + P_STAGES * P_STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (P_STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * P_STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * P_STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * P_STAGES + 4);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + P_STAGES * P_STAGE_BYTES + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + P_STAGES * P_STAGE_BYTES + 136);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 2 * kEpiWarps * 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {                          // one warp of each CTA: the pair's allocation
+    tmem_alloc_pair(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();                           // both CTAs' barriers exist before any remote use
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  const int nslabs = (p.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer (both CTAs) ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[P_STAGES];
+      bool outstanding[P_STAGES];
+      for (int i = 0; i < P_STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
+      bool ok = true;
+      for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+        const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+        const int ya = c.q * p.m_pad + c.tm * 2 * P_BM + (int)rank * P_BM;
+        const int yb = c.q * p.n_pad + c.tn * 2 * P_BN + (int)rank * P_BN;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          outstanding[s] = false;
+          const uint32_t sa = base + s * P_STAGE_BYTES;
+          if (leader) mbar_expect_tx(full_bar(s), 2 * P_STAGE_BYTES);
+          const uint32_t fb = mapa(full_bar(s), 0);
+          tma_load_2d_pair(sa, &tmA, fb, kb * BK, ya);
+          tma_load_2d_pair(sa + P_A_BYTES, &tmB, fb, kb * BK, yb);
+          outstanding[s] = true;
+          issued_parity[s] = ph;
+          if (++s == P_STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+      // both CTAs' copies complete on the leader's barriers: the leader waits
+      // (bounded) for every stage it expected before the pair may exit
+      if (!ok && leader) {
+        for (int i = 0; i < P_STAGES; ++i)
+          if (outstanding[i]) mbar_drain(full_bar(i), issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer (leader) ------------------------------
+    if (lane == 0 && leader) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+        for (int sl = 0; sl < nslabs && ok; ++sl, ++g) {
+          const uint32_t b = g & 1u, use = g >> 1;
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + b * 256;
+          const int kb0 = sl * kSlabBlocks;
+          const int kb1 = min(p.kblocks, kb0 + kSlabBlocks);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = base + s * P_STAGE_BYTES;
+            const uint32_t sb = sa + P_A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16_pair(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (kb > kb0 || kk > 0) ? 1u : 0u);
+            umma_commit_pair_both(empty_bar(s));
+            if (++s == P_STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit_pair_both(tfull_bar(b));
+        }
+      }
+      if (!ok) {
+        umma_commit_pair_self(drain_bar);
+        mbar_drain(drain_bar, 0);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue (both CTAs) ------------------------------
+    const int e = warp - 2;
+    const int quarter = warp & 3;
+    const int half = e >> 2;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+      const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+      const float mf = (float)T.m[c.q];
+      const float invm = T.invm[c.q];
+      uint32_t acc8[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int sl = 0; sl < nslabs; ++sl, ++g) {
+        const uint32_t b = g & 1u, use = g >> 1;
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t v[32];
+          tmem_ld32(tmem_base + lane_addr + b * 256 + half * 128 + ch * 32, v);
+          tmem_ld_wait();
+          if (ch == 3) {
+            tc_fence_before();
+            mbar_arrive_cluster(mapa(tempty_bar(b), 0));
+          }
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            uint32_t out[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float prev = __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) -
+                                 8388736.0f;
+              const float tsum = __uint_as_float(v[4 * w + j]) + prev;
+              const float qf = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
+              const float r = fmaf(-qf, mf, tsum);
+              out[j] = __float_as_uint(r + 8388736.0f);
+            }
+            acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u),
+                                           0x5410u);
+          }
+        }
+      }
+      if (!ok) break;
+      const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
+      const int row = c.tm * 2 * P_BM + (int)rank * P_BM + quarter * 32 + lane;
+      const int col0 = c.tn * 256 + half * 128;
+      if (row < p.m && col0 < p.n) {
+        uint32_t outw[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          uint32_t w = acc8[i], o = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
+            uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);
+            uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
+            o |= y << (8 * j);
+          }
+          outw[i] = o;
+        }
+        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
+        if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();                           // neither CTA leaves while the pair may touch its memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -429,6 +712,46 @@ bool make_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t k_pad,
 
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  // pair tiles: 256 x 256 per CTA pair
+  if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
+      m_pad % (2 * P_BM) || n_pad % (2 * P_BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles_m = (m + 2 * P_BM - 1) / (2 * P_BM), tiles_n = (n + 2 * P_BN - 1) / (2 * P_BN);
+  const int64_t num_tiles = tiles_m * tiles_n * t.Q;
+  if (num_tiles > INT32_MAX || (int64_t)t.Q * m_pad > INT32_MAX || (int64_t)t.Q * n_pad > INT32_MAX)
+    return cudaErrorInvalidValue;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, U, (int64_t)t.Q * m_pad, k_pad, P_BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, V, (int64_t)t.Q * n_pad, k_pad, P_BN)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  Params p;
+  p.m = (int)m;
+  p.n = (int)n;
+  p.tiles_m = (int)tiles_m;
+  p.tiles_n = (int)tiles_n;
+  p.num_tiles = (int)num_tiles;
+  p.kblocks = (int)(k_pad / BK);
+  p.m_pad = (int)m_pad;
+  p.n_pad = (int)n_pad;
+  p.raw = raw;
+  p.Y = Y;
+  p.status = status;
+  const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
+  gemm_tc_pair_kernel<<<(unsigned)(2 * pairs), kThreads, P_SMEM_BYTES, st>>>(mapA, mapB, t, p);
+  return cudaGetLastError();
+}
+
+// The one-CTA kernel (128 x 256 tiles), kept for comparison.
+cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad,
+                                  int64_t k_pad, const void* U, const void* V, uint8_t* Y, int raw, int32_t* status,
+                                  cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
   if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
       m_pad % BM || n_pad % BN)

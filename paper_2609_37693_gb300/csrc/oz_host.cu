@@ -30,7 +30,7 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   if (rows == 0) rows = round_up((m + 3) / 4 > 0 ? (m + 3) / 4 : 1, 256);
   if (rows > m && m > 0) rows = m;
   if (rows < 1) rows = 1;
-  const int64_t elem = p->engine == OZ_ENGINE_TC ? 2 : 1;
+  const int64_t elem = oz::engine_bf16(p->engine) ? 2 : 1;
   const int64_t nplanes = p->is_fp ? p->fp.nplanes : p->Q;
   const int64_t ybytes = p->is_fp ? 2 : 1;
   L->chunk = rows;
@@ -93,7 +93,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   const OzTables& T = plan->tab;
   const OzFpTables& F = plan->fp;
   const bool fp = plan->is_fp != 0;
-  const int bf16 = plan->engine == OZ_ENGINE_TC;
+  const int bf16 = oz::engine_bf16(plan->engine);
   uint8_t* U8 = static_cast<uint8_t*>(U);
   uint8_t* V8 = static_cast<uint8_t*>(V);
   uint16_t* Y16 = reinterpret_cast<uint16_t*>(Y);
@@ -154,6 +154,8 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
                : oz::launch_split_cols(T, n, k, Bd, n, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, sc));
       }
       chk(fp     ? oz::launch_gemm_fp(F, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U8, V8, Y16, 0, flag, sc)
+          : plan->engine == OZ_ENGINE_TC1
+              ? oz::launch_gemm_tc_single(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
           : bf16 ? oz::launch_gemm_tc(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
                  : oz::launch_gemm_imma(T, nr, n, L.k_pad, static_cast<const int8_t*>(U), L.chunk_pad * L.k_pad,
                                         static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, sc));

@@ -106,6 +106,9 @@ constexpr int kTileM = 128;       // M tile of the GEMM engines; m_pad is a mult
 constexpr int kPadRows = 256;     // row padding of the residue planes
 constexpr int kPadK = 128;        // k padding of the residue planes (entries)
 
+// Engines that hold the INT8 residues in BF16 planes.
+inline bool engine_bf16(int e) { return e == OZ_ENGINE_TC || e == OZ_ENGINE_TC1; }
+
 // Geometry of a float-format plan's planes: k padding (entries) and bytes per
 // row of k_pad entries.
 inline int64_t fp_k_align(const OzFpTables& f) { return f.code_bits == 4 ? 256 : kPadK; }
@@ -124,6 +127,8 @@ cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_
                              int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int raw,
                              cudaStream_t st);
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
+cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                                const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);

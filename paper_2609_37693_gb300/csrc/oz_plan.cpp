@@ -183,7 +183,8 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   if (!out) return OZ_ERR_INVALID_ARG;
   *out = nullptr;
   if (k_hint < 1 || bits < 0 || bits > OZ_MAX_BITS) return OZ_ERR_INVALID_ARG;
-  if (engine < OZ_ENGINE_AUTO || engine > OZ_ENGINE_TC) return OZ_ERR_INVALID_ARG;   // float formats: oz_plan_create_fp
+  if (engine < OZ_ENGINE_AUTO || engine > OZ_ENGINE_TC1 || engine == OZ_ENGINE_FP)
+    return OZ_ERR_INVALID_ARG;   // float formats: oz_plan_create_fp
   if (num_moduli != 0 && (num_moduli < OZ_MIN_MODULI || num_moduli > OZ_MAX_MODULI)) return OZ_ERR_UNSUPPORTED;
 
   int Q = num_moduli;
@@ -215,7 +216,7 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   // modulo m (Sec. "Slabs"), so only kappa_rec limits K there.
   uint32_t r = 0;
   for (int i = 0; i < Q; ++i) r = kModuli[i] / 2 > r ? kModuli[i] / 2 : r;
-  int64_t k_acc = resolved == OZ_ENGINE_TC ? (int64_t)INT32_MAX : (int64_t)2147483647 / ((int64_t)r * r);
+  int64_t k_acc = oz::engine_bf16(resolved) ? (int64_t)INT32_MAX : (int64_t)2147483647 / ((int64_t)r * r);
   int64_t k_rec = kappa_rec(P, beta);
   p->k_max = k_acc < k_rec ? k_acc : k_rec;
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }

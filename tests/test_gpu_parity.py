@@ -21,7 +21,8 @@ if not torch.cuda.is_available():  # collected on CPU hosts but never run there
 import paper_2609_37693_gb300 as oz  # noqa: E402
 
 DEV = torch.device("cuda:0")
-ENGINES = [oz.OZ_ENGINE_IMMA, oz.OZ_ENGINE_TC]
+ENGINES = [oz.OZ_ENGINE_IMMA, oz.OZ_ENGINE_TC, oz.OZ_ENGINE_TC1]
+BF16 = (oz.OZ_ENGINE_TC, oz.OZ_ENGINE_TC1)
 
 
 def _bits(x):
@@ -39,7 +40,7 @@ def _stream():
 def _split(plan, X, contiguous, nvec, length, ld):
     nvec_pad = oz.round_up(max(nvec, 1), 256)
     k_pad = oz.round_up(max(length, 1), 128)
-    elem = torch.bfloat16 if plan.engine == oz.OZ_ENGINE_TC else torch.int8
+    elem = torch.bfloat16 if plan.engine in BF16 else torch.int8
     planes = torch.full((plan.q, nvec_pad, k_pad), 7, dtype=elem, device=DEV)  # poison: padding must be zeroed
     shifts = torch.zeros(max(nvec, 1), dtype=torch.int32, device=DEV)
     flag = torch.zeros(4, dtype=torch.int32, device=DEV)
@@ -95,7 +96,7 @@ def test_split_flags_nonfinite():
 
 
 def _plane_dtype(plan):
-    return torch.bfloat16 if plan.engine == oz.OZ_ENGINE_TC else torch.int8
+    return torch.bfloat16 if plan.engine in BF16 else torch.int8
 
 
 def _residues(plan, A, B):
@@ -289,14 +290,15 @@ def test_full_size_8192_sampled_entries_and_error(engine):
     assert np.max(err / (2.0**-53 * ab)) <= 2.0
 
 
+@pytest.mark.parametrize("engine", BF16)
 @pytest.mark.parametrize("pattern", ["all_max", "random_sign", "mixed"])
-def test_tc_fp32_accumulation_is_exact(pattern):
+def test_tc_fp32_accumulation_is_exact(pattern, engine):
     """The FP32 accumulators of tcgen05.mma must add integer products without
     rounding while every partial sum stays within 2^24 (Sec. 'Exactness May
     Rely on Undocumented Accumulation'). Planes at the largest residue
     magnitude drive each 1024-term slab to 1024 * 119^2 = 14 500 864; the
     residues of the product must equal those of the exact integer product."""
-    plan = oz.Plan(16, 0, 4096, oz.OZ_ENGINE_TC)
+    plan = oz.Plan(16, 0, 4096, engine)
     m, n, k = 256, 256, 4096
     rng = np.random.default_rng(17)
     if pattern == "all_max":
