@@ -219,6 +219,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
@@ -577,7 +588,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const uint32_t sb = sa + P_A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              umma_bf16_pair(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (kb > kb0 || kk > 0) ? 1u : 0u);
+              umma_bf16_pair(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (sl >= 2 || kb > kb0 || kk > 0) ? 1u : 0u);
             umma_commit_pair_both(empty_bar(s));
             if (++s == P_STAGES) { s = 0; ph ^= 1u; }
           }
@@ -592,6 +603,12 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
   } else {
     // ------------------------------ epilogue (both CTAs) ------------------------------
+    // Slab sl of a tile lands in accumulator sl & 1 on top of what that
+    // accumulator holds. The epilogue reduces each value t (|t| < 2^24) to
+    // r = t - m rint(t / m), |r| <= 120, and writes r back when slab sl + 2
+    // accumulates on it; the residue of slab nsl - 2 is kept as one byte per
+    // entry and added to that of the last slab (eq. ov-comrtc: every partial
+    // sum stays below 2^24, so the FP32 arithmetic is exact).
     const int e = warp - 2;
     const int quarter = warp & 3;
     const int half = e >> 2;
@@ -602,38 +619,50 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
-      uint32_t acc8[32];
+      uint32_t acc8[32];                     // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
       for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
+        const bool write_back = sl + 2 < nslabs;
+        const bool last = sl + 1 == nslabs;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * 256 + half * 128 + ch * 32;
           uint32_t v[32];
-          tmem_ld32(tmem_base + lane_addr + b * 256 + half * 128 + ch * 32, v);
+          tmem_ld32(taddr, v);
           tmem_ld_wait();
-          if (ch == 3) {
-            tc_fence_before();
-            mbar_arrive_cluster(mapa(tempty_bar(b), 0));
-          }
+          if (write_back) {
 #pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            uint32_t out[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float prev = __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) -
-                                 8388736.0f;
-              const float tsum = __uint_as_float(v[4 * w + j]) + prev;
-              const float qf = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
-              const float r = fmaf(-qf, mf, tsum);
-              out[j] = __float_as_uint(r + 8388736.0f);
+            for (int j = 0; j < 32; ++j) {
+              const float tv = __uint_as_float(v[j]);
+              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
+              v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
             }
-            acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u),
-                                           0x5410u);
+            tmem_st32(taddr, v);
+          } else {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              uint32_t out[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float tv = __uint_as_float(v[4 * w + j]);
+                if (last)                      // plus the residue of the other chain, r + 128 in a byte
+                  tv += __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) - 8388736.0f;
+                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+                const float r = fmaf(-qf, mf, tv);
+                out[j] = __float_as_uint(r + 8388736.0f);                     // low byte = r + 128
+              }
+              acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u),
+                                             __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+            }
           }
         }
+        if (write_back) tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive_cluster(mapa(tempty_bar(b), 0));
       }
       if (!ok) break;
       const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
