@@ -483,10 +483,17 @@ constexpr int P_STAGES = 6;
 constexpr int P_A_BYTES = P_BM * BK * 2;           // 16 KiB
 constexpr int P_STAGE_BYTES = P_A_BYTES + P_BN * BK * 2;   // 32 KiB
 constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + kBarBytes + 1024;
+// epilogue warps of the pair kernel (eight: with four, one warp's drain of a
+// slab outlasts the slab's products)
+constexpr int kPairEpiWarps = 8;
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+// EW epilogue warps (4 or 8): every warp drains the 32 TMEM lanes of its
+// quarter (warp index mod 4), over 256 / (EW / 4) columns.
+template <int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((2 + EW) * 32, 1)
 gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ OzTables T, const Params p) {
+  constexpr int NH = 8 / EW;                // 128-column halves per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_base = smem_u32(smem_raw);
   const uint32_t base = (raw_base + 1023u) & ~1023u;
@@ -513,7 +520,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 2 * kEpiWarps * 32);
+      mbar_init(tempty_bar(b), 2 * EW * 32);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -611,7 +618,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     // sum stays below 2^24, so the FP32 arithmetic is exact).
     const int e = warp - 2;
     const int quarter = warp & 3;
-    const int half = e >> 2;
+    const int half0 = NH == 1 ? (e >> 2) : 0;   // first 128-column half this warp drains
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
@@ -619,9 +626,9 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
-      uint32_t acc8[32];                     // residue + 128 of the chain of slab nsl - 2, one byte per column
+      uint32_t acc8[32 * NH];                // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int i = 0; i < 32 * NH; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
@@ -629,34 +636,37 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          const uint32_t taddr = tmem_base + lane_addr + b * 256 + half * 128 + ch * 32;
-          uint32_t v[32];
-          tmem_ld32(taddr, v);
-          tmem_ld_wait();
-          if (write_back) {
+        for (int hh = 0; hh < NH; ++hh) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float tv = __uint_as_float(v[j]);
-              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
-              v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
-            }
-            tmem_st32(taddr, v);
-          } else {
+          for (int ch = 0; ch < 4; ++ch) {
+            const uint32_t taddr = tmem_base + lane_addr + b * 256 + (half0 + hh) * 128 + ch * 32;
+            uint32_t v[32];
+            tmem_ld32(taddr, v);
+            tmem_ld_wait();
+            if (write_back) {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-              uint32_t out[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float tv = __uint_as_float(v[4 * w + j]);
-                if (last)                      // plus the residue of the other chain, r + 128 in a byte
-                  tv += __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) - 8388736.0f;
-                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                const float r = fmaf(-qf, mf, tv);
-                out[j] = __float_as_uint(r + 8388736.0f);                     // low byte = r + 128
+              for (int j = 0; j < 32; ++j) {
+                const float tv = __uint_as_float(v[j]);
+                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
+                v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
               }
-              acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u),
-                                             __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+              tmem_st32(taddr, v);
+            } else {
+#pragma unroll
+              for (int w = 0; w < 8; ++w) {
+                uint32_t out[4];
+                uint32_t& a8 = acc8[hh * 32 + ch * 8 + w];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  float tv = __uint_as_float(v[4 * w + j]);
+                  if (last)                    // plus the residue of the other chain, r + 128 in a byte
+                    tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
+                  const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+                  const float r = fmaf(-qf, mf, tv);
+                  out[j] = __float_as_uint(r + 8388736.0f);                   // low byte = r + 128
+                }
+                a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+              }
             }
           }
         }
@@ -667,32 +677,36 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       if (!ok) break;
       const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
       const int row = c.tm * 2 * P_BM + (int)rank * P_BM + quarter * 32 + lane;
-      const int col0 = c.tn * 256 + half * 128;
-      if (row < p.m && col0 < p.n) {
-        uint32_t outw[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          uint32_t w = acc8[i], o = 0;
+      for (int hh = 0; hh < NH; ++hh) {
+        const int col0 = c.tn * 256 + (half0 + hh) * 128;
+        if (row < p.m && col0 < p.n) {
+          uint32_t outw[32];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
-            uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);
-            uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
-            o |= y << (8 * j);
+          for (int i = 0; i < 32; ++i) {
+            uint32_t w = acc8[hh * 32 + i], o = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
+              uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);
+              uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
+              o |= y << (8 * j);
+            }
+            outw[i] = o;
           }
-          outw[i] = o;
-        }
-        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
-        if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+          uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
+          if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
-        } else {
+            for (int i = 0; i < 8; ++i)
+              reinterpret_cast<uint4*>(dst)[i] =
+                  make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < 32; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
+              for (int j = 0; j < 4; ++j)
+                if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
+          }
         }
       }
     }
@@ -758,7 +772,8 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gemm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES);
+  e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   Params p;
   p.m = (int)m;
@@ -773,7 +788,8 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   p.Y = Y;
   p.status = status;
   const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
-  gemm_tc_pair_kernel<<<(unsigned)(2 * pairs), kThreads, P_SMEM_BYTES, st>>>(mapA, mapB, t, p);
+  gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, P_SMEM_BYTES, st>>>(
+      mapA, mapB, t, p);
   return cudaGetLastError();
 }
 

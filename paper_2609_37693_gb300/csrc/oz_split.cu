@@ -10,7 +10,7 @@
 // is f shifted left or right (the right shift truncates toward zero). The
 // residue modulo m is formed in exact fp32 arithmetic (twice the integer
 // issue rate): a' (|a'| < 2^64) is cut once per entry into signed 15-bit pieces
-// P0..P4, and for each modulus
+// P0..P4 (P0..P3 when beta <= 60, so that |a'| < 2^60), and for each modulus
 //   y = P0 + P1 c15 + P2 c30 + P3 c45 + P4 c60,   c_k = 2^k mod m, |c_k| <= 119,
 // is congruent to a' with |y| < 2^24, so every step is exact. One quotient
 // q = rint(y / m) (an fp32 estimate, off by at most one near a tie) gives
@@ -30,18 +30,21 @@
 namespace oz {
 namespace {
 
-// Signed 15-bit pieces of a' as exact floats: a' = sum_i P_i 2^(15 i).
+// Signed 15-bit pieces of a' as exact floats: a' = sum_i P_i 2^(15 i), NP of
+// them (NP = 4 covers |a'| < 2^60).
+template <int NP>
 struct Pieces {
-  float p[5];
+  float p[NP];
 };
 
-__device__ __forceinline__ Pieces pieces_of(uint64_t bits, int32_t s) {
+template <int NP>
+__device__ __forceinline__ Pieces<NP> pieces_of(uint64_t bits, int32_t s) {
   const Trunc t = truncate(bits, s);
   const float sg = t.neg ? -1.0f : 1.0f;
   const float off = t.neg ? 8388608.0f : -8388608.0f;
-  Pieces P;
+  Pieces<NP> P;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < NP; ++i) {
     const uint32_t v = (uint32_t)(t.mag >> (15 * i)) & 0x7FFFu;
     P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
   }
@@ -67,8 +70,10 @@ __device__ __forceinline__ ModConst mod_const(const OzTables& T, int q) {
 }
 
 // Representative nearest zero of a' modulo one modulus, as an exact float.
-__device__ __forceinline__ float residue_f(const ModConst& c, const Pieces& P) {
-  const float y = fmaf(P.p[4], c.c60, fmaf(P.p[3], c.c45, fmaf(P.p[2], c.c30, fmaf(P.p[1], c.c15, P.p[0]))));
+template <int NP>
+__device__ __forceinline__ float residue_f(const ModConst& c, const Pieces<NP>& P) {
+  float y = fmaf(P.p[3], c.c45, fmaf(P.p[2], c.c30, fmaf(P.p[1], c.c15, P.p[0])));
+  if constexpr (NP == 5) y = fmaf(P.p[4], c.c60, y);
   const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;
   float r = fmaf(-qf, c.m, y);
   r = r >= c.hi ? r - c.m : r;
@@ -95,7 +100,7 @@ __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d
 // vector. Pass 1 finds the max bits; pass 2 re-reads the row (from L2) and
 // writes 8 consecutive entries per thread per plane.
 // ---------------------------------------------------------------------------
-template <bool kBF16>
+template <bool kBF16, int NP>
 __global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
                                                          const double* __restrict__ X, int64_t ld,
                                                          int64_t nvec_pad, int64_t k_pad,
@@ -152,11 +157,11 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__
 #pragma unroll
       for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
     }
-    Pieces P[8];
+    Pieces<NP> P[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;  // non-finite: flagged above
-      P[e] = pieces_of(b[e], s);
+      P[e] = pieces_of<NP>(b[e], s);
     }
 #pragma unroll
     for (int q = 0; q < OZ_MAX_MODULI; ++q) {
@@ -227,7 +232,7 @@ __global__ void shifts_from_colmax_kernel(int64_t nvec, const uint64_t* __restri
 // Pass 2: 64 (h) x 64 (vector) tiles; residues go through shared memory so
 // that the planes, which are K-major per vector, are written along h.
 // Thread t handles vector j = t % 64 and 16 consecutive h.
-template <bool kBF16>
+template <bool kBF16, int NP>
 __global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
                                                          const double* __restrict__ X, int64_t ld,
                                                          int64_t nvec_pad, int64_t k_pad,
@@ -244,14 +249,14 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__
   const bool live = j < nvec;
   const int32_t s = live ? shifts[j] : 0;
 
-  Pieces P[16];
+  Pieces<NP> P[16];
   const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     int64_t h = hbase + hg * 16 + e;
     uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
     if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
-    P[e] = pieces_of(b, s);
+    P[e] = pieces_of<NP>(b, s);
   }
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
@@ -299,10 +304,15 @@ cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, cons
                               int32_t* flag, cudaStream_t st) {
   if (nvec_pad == 0) return cudaSuccess;
   dim3 grid((unsigned)nvec_pad);
-  if (bf16)
-    split_rows_kernel<true><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  const bool np4 = t.bits <= 60;                 // |a'| < 2^60: four 15-bit pieces
+  if (bf16 && np4)
+    split_rows_kernel<true, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  else if (bf16)
+    split_rows_kernel<true, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  else if (np4)
+    split_rows_kernel<false, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
   else
-    split_rows_kernel<false><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    split_rows_kernel<false, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
   return cudaGetLastError();
 }
 
@@ -326,10 +336,15 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
   cudaError_t e0 = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
   if (e0 != cudaSuccess) return e0;
   dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
-  if (bf16)
-    split_cols_kernel<true><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  const bool np4 = t.bits <= 60;
+  if (bf16 && np4)
+    split_cols_kernel<true, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  else if (bf16)
+    split_cols_kernel<true, 5><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  else if (np4)
+    split_cols_kernel<false, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   else
-    split_cols_kernel<false><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+    split_cols_kernel<false, 5><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   return cudaGetLastError();
 }
 
