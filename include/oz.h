@@ -148,9 +148,11 @@ OZ_API void oz_plan_destroy(oz_plan plan);
 
 /*
  * oz_workspace_bytes -- device workspace a product of this shape needs: the
- * shifts, the residue planes of both operands (Q (m_pad + n_pad) k_pad entries
- * of 1 byte for IMMA, 2 bytes for TC) and the Q m n residues of the product.
- * Returns 0 for an invalid plan or shape.
+ * shifts, the residue planes of both operands (planes x (m_pad + n_pad) rows
+ * of oz_plane_geometry's row bytes) and the residues of the product (Q x m
+ * rows of n entries, each row padded to a multiple of 16 bytes so that the
+ * GEMM epilogue stores whole 16-byte runs; uint8, or uint16 per channel for
+ * float-format plans). Returns 0 for an invalid plan or shape.
  */
 OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
 
@@ -159,7 +161,9 @@ OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
  * that the phase entry points below can run the same product step by step.
  * out[0..9] receives byte offsets of: flag (int32[4]), s (int32[m]),
  * t (int32[n]), colmax (uint64[max(m, n)]), U planes, V planes, Y residues
- * (uint8 Q x m x n), then m_pad, n_pad, k_pad (entries, not bytes).
+ * (Q x m rows, row pitch n rounded up to 16 bytes; the phase entry points
+ * below take and give row pitch n, which fits in the same region), then m_pad,
+ * n_pad, k_pad (entries, not bytes).
  */
 OZ_API oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t* out);
 

@@ -14,6 +14,7 @@ using oz::round_up;
 
 struct Layout {
   int64_t m_pad, n_pad, k_pad;
+  int64_t ldy;       // row pitch of the residue planes Y: n rounded up to 16 bytes
   size_t flag, s, t, colmax, u, v, y, total;
 };
 
@@ -35,7 +36,8 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   L->colmax = off; off = align256(off + 8 * (size_t)(m > n ? m : n));
   L->u = off; off = align256(off + (size_t)nplanes * L->m_pad * row);
   L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * row);
-  L->y = off; off = align256(off + (size_t)p->Q * m * n * ybytes);
+  L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
+  L->y = off; off = align256(off + (size_t)p->Q * m * L->ldy * ybytes);
   L->total = off;
   return true;
 }
@@ -112,9 +114,9 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
     if (e != cudaSuccess) return OZ_ERR_CUDA;
     e = oz::launch_split_fp(T, F, trans_b, n, k, B, ldb, L.n_pad, L.k_pad, t, V8, flag, colmax, st);
     if (e != cudaSuccess) return OZ_ERR_CUDA;
-    e = oz::launch_gemm_fp(F, m, n, L.m_pad, L.n_pad, L.k_pad, U8, V8, Y16, 0, flag, st);
+    e = oz::launch_gemm_fp(F, m, n, L.m_pad, L.n_pad, L.k_pad, U8, V8, Y16, L.ldy, 0, flag, st);
     if (e != cudaSuccess) return OZ_ERR_CUDA;
-    return cuda_status(oz::launch_reconstruct16(T, m, n, Y16, s, t, C, ldc, st));
+    return cuda_status(oz::launch_reconstruct16(T, m, n, Y16, L.ldy, s, t, C, ldc, st));
   }
   // Scale + Reduce, A side: vectors are the rows of op(A).
   e = trans_a ? oz::launch_split_cols(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, colmax, st)
@@ -125,13 +127,14 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
               : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // GEMMs + epilogue
-  e = plan->engine == OZ_ENGINE_TC1 ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
-    : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, st)
-           : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
-                                  static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, st);
+  e = plan->engine == OZ_ENGINE_TC1
+          ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
+      : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
+             : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
+                                    static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, L.ldy, 0, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // Reconstruct
-  e = oz::launch_reconstruct(T, m, n, Y, s, t, C, ldc, st);
+  e = oz::launch_reconstruct(T, m, n, Y, L.ldy, s, t, C, ldc, st);
   return cuda_status(e);
 }
 
@@ -184,15 +187,15 @@ extern "C" oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->is_fp)
     return cuda_status(oz::launch_gemm_fp(plan->fp, m, n, m_pad, n_pad, k_pad, static_cast<const uint8_t*>(U),
-                                          static_cast<const uint8_t*>(V), reinterpret_cast<uint16_t*>(Y), raw ? 1 : 0,
-                                          flag, st));
+                                          static_cast<const uint8_t*>(V), reinterpret_cast<uint16_t*>(Y), n,
+                                          raw ? 1 : 0, flag, st));
   if (plan->engine == OZ_ENGINE_TC)
-    return cuda_status(oz::launch_gemm_tc(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
+    return cuda_status(oz::launch_gemm_tc(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, n, raw ? 1 : 0, flag, st));
   if (plan->engine == OZ_ENGINE_TC1)
     return cuda_status(
-        oz::launch_gemm_tc_single(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, raw ? 1 : 0, flag, st));
+        oz::launch_gemm_tc_single(plan->tab, m, n, m_pad, n_pad, k_pad, U, V, Y, n, raw ? 1 : 0, flag, st));
   return cuda_status(oz::launch_gemm_imma(plan->tab, m, n, k_pad, static_cast<const int8_t*>(U), m_pad * k_pad,
-                                          static_cast<const int8_t*>(V), n_pad * k_pad, Y, raw ? 1 : 0, st));
+                                          static_cast<const int8_t*>(V), n_pad * k_pad, Y, n, raw ? 1 : 0, st));
 }
 
 extern "C" oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
@@ -202,6 +205,7 @@ extern "C" oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const ui
   if (!Y || !s || !t || !C || !aligned(C, 8)) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->is_fp)
-    return cuda_status(oz::launch_reconstruct16(plan->tab, m, n, reinterpret_cast<const uint16_t*>(Y), s, t, C, ldc, st));
-  return cuda_status(oz::launch_reconstruct(plan->tab, m, n, Y, s, t, C, ldc, st));
+    return cuda_status(
+        oz::launch_reconstruct16(plan->tab, m, n, reinterpret_cast<const uint16_t*>(Y), n, s, t, C, ldc, st));
+  return cuda_status(oz::launch_reconstruct(plan->tab, m, n, Y, n, s, t, C, ldc, st));
 }

@@ -417,6 +417,7 @@ struct FpParams {
   int m, n, tiles_m, tiles_n, num_units, kblocks, m_pad, n_pad, raw;
   uint32_t idesc;
   uint16_t* Y;
+  int64_t ldy;       // row pitch of Y (entries)
   int32_t* status;
 };
 
@@ -606,8 +607,8 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int col0 = u.tn * BN + half * C::HC;
       if (row < p.m && col0 < p.n) {
         const float inv = (float)F.inv[u.c];
-        uint16_t* dst = p.Y + (size_t)u.c * p.m * p.n + (size_t)row * p.n + col0;
-        const bool vec = col0 + C::HC <= p.n && (p.n & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+        uint16_t* dst = p.Y + (size_t)u.c * p.m * p.ldy + (size_t)row * p.ldy + col0;
+        const bool vec = col0 + C::HC <= p.n && (p.ldy & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
 #pragma unroll
         for (int i4 = 0; i4 < C::HC / 8; ++i4) {
           uint32_t o4[4];
@@ -728,7 +729,7 @@ __device__ __forceinline__ uint64_t round128b(u128 mag, uint32_t neg, int e) {
 // P < 2^125; digits y_c < m_c < 2^12; pairs z = y_a m_b + y_b m_a < 2^25.
 template <int NP>
 __global__ void __launch_bounds__(256) reconstruct16_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n,
-                                                            const uint16_t* __restrict__ Y,
+                                                            const uint16_t* __restrict__ Y, int64_t ldy,
                                                             const int32_t* __restrict__ s,
                                                             const int32_t* __restrict__ t,
                                                             double* __restrict__ C, int64_t ldc) {
@@ -737,8 +738,8 @@ __global__ void __launch_bounds__(256) reconstruct16_kernel(const __grid_constan
   const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
-  const int64_t plane = m * n;
-  const uint16_t* yp = Y + i * n + j0;
+  const int64_t plane = m * ldy;
+  const uint16_t* yp = Y + i * ldy + j0;
   const bool vec = (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 7) == 0) && ((plane & 3) == 0);
   uint64_t wa[NP], wb[NP];
 #pragma unroll
@@ -817,10 +818,10 @@ __global__ void __launch_bounds__(256) reconstruct16_kernel(const __grid_constan
 }
 
 template <int NP>
-cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s, const int32_t* t,
-                     double* C, int64_t ldc, cudaStream_t st) {
+cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy, const int32_t* s,
+                     const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   dim3 grid((unsigned)m, (unsigned)((n + 1023) / 1024));
-  reconstruct16_kernel<NP><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  reconstruct16_kernel<NP><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc);
   return cudaGetLastError();
 }
 
@@ -858,7 +859,8 @@ namespace {
 
 template <bool MX>
 cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                    const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status, cudaStream_t st) {
+                    const uint8_t* U, const uint8_t* V, uint16_t* Y, int64_t ldy, int raw, int32_t* status,
+                    cudaStream_t st) {
   using C = Cfg<MX>;
   const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + C::BN - 1) / C::BN;
   const int64_t units = tiles_m * tiles_n * f.nch;
@@ -898,6 +900,7 @@ cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, in
     p.idesc = (1u << 4) | (code << 7) | (code << 10) | ((uint32_t)(C::BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   }
   p.Y = Y;
+  p.ldy = ldy;
   p.status = status;
   const int grid = (int)(units < sms ? units : sms);
   gemm_fp_kernel<MX><<<grid, kThreads, C::kSmemBytes, st>>>(mapA, mapB, f, p);
@@ -907,33 +910,35 @@ cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, in
 }  // namespace
 
 cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status,
-                           cudaStream_t st) {
+                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int64_t ldy, int raw,
+                           int32_t* status, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % fp_k_align(f) ||
       m_pad % BM || n_pad % kPadRows)
     return cudaErrorInvalidValue;
-  if (f.code_bits == 4) return gemm_fp<true>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, status, st);
-  return gemm_fp<false>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, raw, status, st);
+  if (f.code_bits == 4) return gemm_fp<true>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, ldy, raw, status, st);
+  return gemm_fp<false>(f, m, n, m_pad, n_pad, k_pad, U, V, Y, ldy, raw, status, st);
 }
 
-cudaError_t launch_reconstruct16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s,
-                                 const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+cudaError_t launch_reconstruct16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy,
+                                 const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   if (T.limbs > 4) return cudaErrorInvalidValue;
   switch (T.npairs) {
-    case 5: return launch16<5>(T, m, n, Y, s, t, C, ldc, st);
-    case 6: return launch16<6>(T, m, n, Y, s, t, C, ldc, st);
-    case 7: return launch16<7>(T, m, n, Y, s, t, C, ldc, st);
-    case 8: return launch16<8>(T, m, n, Y, s, t, C, ldc, st);
-    case 9: return launch16<9>(T, m, n, Y, s, t, C, ldc, st);
-    case 10: return launch16<10>(T, m, n, Y, s, t, C, ldc, st);
-    case 11: return launch16<11>(T, m, n, Y, s, t, C, ldc, st);
-    case 12: return launch16<12>(T, m, n, Y, s, t, C, ldc, st);
-    case 13: return launch16<13>(T, m, n, Y, s, t, C, ldc, st);
-    case 14: return launch16<14>(T, m, n, Y, s, t, C, ldc, st);
-    case 15: return launch16<15>(T, m, n, Y, s, t, C, ldc, st);
-    case 16: return launch16<16>(T, m, n, Y, s, t, C, ldc, st);
+    case 5: return launch16<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 6: return launch16<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 7: return launch16<7>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 8: return launch16<8>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 9: return launch16<9>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 10: return launch16<10>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 11: return launch16<11>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 12: return launch16<12>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 13: return launch16<13>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 14: return launch16<14>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 15: return launch16<15>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 16: return launch16<16>(T, m, n, Y, ldy, s, t, C, ldc, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -67,7 +67,7 @@ __device__ __forceinline__ uint32_t epilogue(int32_t w, uint32_t m, uint32_t mag
 __global__ void __launch_bounds__(256, 1)
 gemm_imma_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n, int64_t k_pad, const int8_t* __restrict__ U,
                  int64_t u_plane, const int8_t* __restrict__ V, int64_t v_plane, uint8_t* __restrict__ Y,
-                 int raw) {
+                 int64_t ldy, int raw) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -163,14 +163,14 @@ gemm_imma_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n, int64
         *reinterpret_cast<uint16_t*>(so + row * kOutPitch + col) = (uint16_t)(y0 | (y1 << 8));
       }
   __syncthreads();
-  uint8_t* Yq = Y + (int64_t)q * m * n;
-  const bool vec_ok = (n % 16) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  uint8_t* Yq = Y + (int64_t)q * m * ldy;
+  const bool vec_ok = (ldy % 16) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
   for (int c = tid; c < BM * (BN / 16); c += 256) {
     int row = c / (BN / 16), cb = (c % (BN / 16)) * 16;
     int64_t gi = m0 + row, gj = n0 + cb;
     if (gi >= m || gj >= n) continue;
     const uint8_t* src = so + row * kOutPitch + cb;
-    uint8_t* dst = Yq + gi * n + gj;
+    uint8_t* dst = Yq + gi * ldy + gj;
     if (vec_ok && gj + 16 <= n) {
       *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
     } else {
@@ -182,13 +182,14 @@ gemm_imma_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n, int64
 }  // namespace
 
 cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_pad, const int8_t* U,
-                             int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int raw,
+                             int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int64_t ldy, int raw,
                              cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(gemm_imma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM), (unsigned)t.Q);
-  gemm_imma_kernel<<<grid, 256, kSmemBytes, st>>>(t, m, n, k_pad, U, u_plane, V, v_plane, Y, raw);
+  gemm_imma_kernel<<<grid, 256, kSmemBytes, st>>>(t, m, n, k_pad, U, u_plane, V, v_plane, Y, ldy, raw);
   return cudaGetLastError();
 }
 

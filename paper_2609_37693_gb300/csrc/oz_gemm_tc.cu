@@ -263,6 +263,7 @@ __device__ __forceinline__ Coord tile_coord(int t, int tiles_m, int tiles_n) {
 struct Params {
   int m, n, tiles_m, tiles_n, num_tiles, kblocks, m_pad, n_pad, raw;
   uint8_t* Y;
+  int64_t ldy;       // row pitch of Y
   int32_t* status;
 };
 
@@ -442,8 +443,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           }
           outw[i] = o;
         }
-        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
-        if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
+        if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
 #pragma unroll
           for (int i = 0; i < 8; ++i)
             reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
@@ -694,8 +695,8 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             }
             outw[i] = o;
           }
-          uint8_t* dst = p.Y + (size_t)c.q * p.m * p.n + (size_t)row * p.n + col0;
-          if (col0 + 128 <= p.n && (p.n & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+          uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
+          if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
               reinterpret_cast<uint4*>(dst)[i] =
@@ -754,8 +755,10 @@ bool make_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t k_pad,
 }  // namespace
 
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st) {
+                           const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
+                           cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   // pair tiles: 256 x 256 per CTA pair
   if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
       m_pad % (2 * P_BM) || n_pad % (2 * P_BN))
@@ -786,6 +789,7 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   p.n_pad = (int)n_pad;
   p.raw = raw;
   p.Y = Y;
+  p.ldy = ldy;
   p.status = status;
   const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
   gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, P_SMEM_BYTES, st>>>(
@@ -795,9 +799,11 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
 
 // The one-CTA kernel (128 x 256 tiles), kept for comparison.
 cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad,
-                                  int64_t k_pad, const void* U, const void* V, uint8_t* Y, int raw, int32_t* status,
+                                  int64_t k_pad, const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw,
+                                  int32_t* status,
                                   cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
       m_pad % BM || n_pad % BN)
     return cudaErrorInvalidValue;
@@ -826,6 +832,7 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
   p.n_pad = (int)n_pad;
   p.raw = raw;
   p.Y = Y;
+  p.ldy = ldy;
   p.status = status;
   const int grid = (int)(num_tiles < sms ? num_tiles : sms);
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, t, p);

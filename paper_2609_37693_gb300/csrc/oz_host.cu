@@ -20,6 +20,7 @@ using oz::round_up;
 
 struct HostLayout {
   int64_t chunk, chunk_pad, n_pad, k_pad;
+  int64_t ldy;       // row pitch of the residue planes: n rounded up to 16 bytes
   size_t flag, s, t, colmax, b, a[2], c[2], u, v, y, total;
 };
 
@@ -48,7 +49,8 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   for (int i = 0; i < 2; ++i) { L->c[i] = off; off = al(off + 8 * (size_t)rows * n); }
   L->u = off; off = al(off + (size_t)nplanes * L->chunk_pad * row);
   L->v = off; off = al(off + (size_t)nplanes * L->n_pad * row);
-  L->y = off; off = al(off + (size_t)p->Q * rows * n * ybytes);
+  L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
+  L->y = off; off = al(off + (size_t)p->Q * rows * L->ldy * ybytes);
   L->total = off;
   return true;
 }
@@ -153,20 +155,20 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
         chk(fp ? oz::launch_split_fp(T, F, 0, n, k, Bd, n, L.n_pad, L.k_pad, t, V8, flag, colmax, sc)
                : oz::launch_split_cols(T, n, k, Bd, n, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, sc));
       }
-      chk(fp     ? oz::launch_gemm_fp(F, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U8, V8, Y16, 0, flag, sc)
+      chk(fp     ? oz::launch_gemm_fp(F, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U8, V8, Y16, L.ldy, 0, flag, sc)
           : plan->engine == OZ_ENGINE_TC1
-              ? oz::launch_gemm_tc_single(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
-          : bf16 ? oz::launch_gemm_tc(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, 0, flag, sc)
+              ? oz::launch_gemm_tc_single(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, sc)
+          : bf16 ? oz::launch_gemm_tc(T, nr, n, L.chunk_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, sc)
                  : oz::launch_gemm_imma(T, nr, n, L.k_pad, static_cast<const int8_t*>(U), L.chunk_pad * L.k_pad,
-                                        static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, 0, sc));
+                                        static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, L.ldy, 0, sc));
     } else {
       chk(cudaEventRecord(ev_a_free[slot], sc));
       if (ci + 2 < nchunks) copy_a(ci + 2);
     }
     if (ci >= 2) chk(cudaStreamWaitEvent(sc, ev_c_free[slot], 0));      // copy-back of chunk ci-2 done
     if (k > 0)
-      chk(fp ? oz::launch_reconstruct16(T, nr, n, Y16, s + r0, t, Cd[slot], n, sc)
-             : oz::launch_reconstruct(T, nr, n, Y, s + r0, t, Cd[slot], n, sc));
+      chk(fp ? oz::launch_reconstruct16(T, nr, n, Y16, L.ldy, s + r0, t, Cd[slot], n, sc)
+             : oz::launch_reconstruct(T, nr, n, Y, L.ldy, s + r0, t, Cd[slot], n, sc));
     else chk(cudaMemsetAsync(Cd[slot], 0, (size_t)nr * n * 8, sc));
     chk(cudaEventRecord(ev_c_ready[slot], sc));
     chk(cudaStreamWaitEvent(sd, ev_c_ready[slot], 0));

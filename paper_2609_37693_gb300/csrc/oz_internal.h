@@ -124,22 +124,26 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
                               int32_t* flag, uint64_t* colmax, cudaStream_t st);
 cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_pad, const int8_t* U,
-                             int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int raw,
+                             int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int64_t ldy, int raw,
                              cudaStream_t st);
+// Y: residue planes [Q][m][ldy] (ldy >= n; a multiple of 16 lets the epilogue store whole 16-byte runs)
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
+                           const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
+                           cudaStream_t st);
 cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const void* U, const void* V, uint8_t* Y, int raw, int32_t* status, cudaStream_t st);
-cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
-                               const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+                           const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
+                           cudaStream_t st);
+cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
+                               const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
 // float-format path: planes of codes, 16-bit digits
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
                             uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st);
 cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
-                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int raw, int32_t* status, cudaStream_t st);
-cudaError_t launch_reconstruct16(const OzTables& t, int64_t m, int64_t n, const uint16_t* Y, const int32_t* s,
-                                 const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+                           const uint8_t* U, const uint8_t* V, uint16_t* Y, int64_t ldy, int raw, int32_t* status,
+                           cudaStream_t st);
+cudaError_t launch_reconstruct16(const OzTables& t, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy,
+                                 const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
 // shared by the split kernels: shifts of strided vectors (colmax must be zeroed)
 cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
                                int32_t* flag, uint64_t* colmax, cudaStream_t st);

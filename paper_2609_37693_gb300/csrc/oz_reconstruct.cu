@@ -174,7 +174,7 @@ __device__ __forceinline__ uint64_t round_to_binary64(const Limbs<L>& mag, uint3
 
 template <int L, int EPT>
 __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n,
-                                                          const uint8_t* __restrict__ Y,
+                                                          const uint8_t* __restrict__ Y, int64_t ldy,
                                                           const int32_t* __restrict__ s,
                                                           const int32_t* __restrict__ t, double* __restrict__ C,
                                                           int64_t ldc) {
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
   const int npairs = T.npairs;
-  const int64_t plane = m * n;
-  const uint8_t* yp = Y + i * n + j0;
+  const int64_t plane = m * ldy;
+  const uint8_t* yp = Y + i * ldy + j0;
   const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
                    ((plane & 3) == 0);
   // S = sum over pairs (a, b) of z (P / (m_a m_b)), z = y_a m_b + y_b m_a < 2^17,
@@ -310,7 +310,7 @@ __device__ __forceinline__ uint64_t round128(u128 mag, uint32_t neg, int e) {
 template <int NP, int EPT>
 __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_constant__ OzTables T, int64_t m,
                                                              int64_t n, const uint8_t* __restrict__ Y,
-                                                             const int32_t* __restrict__ s,
+                                                             int64_t ldy, const int32_t* __restrict__ s,
                                                              const int32_t* __restrict__ t,
                                                              double* __restrict__ C, int64_t ldc) {
   static_assert(EPT == 4, "one 32-bit digit word per plane");
@@ -318,8 +318,8 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
   const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
-  const int64_t plane = m * n;
-  const uint8_t* yp = Y + i * n + j0;
+  const int64_t plane = m * ldy;
+  const uint8_t* yp = Y + i * ldy + j0;
   const bool vec = (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) && ((plane & 3) == 0);
   uint32_t wa[NP], wb[NP];
   if (vec) {
@@ -423,40 +423,41 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
 }
 
 template <int NP>
-cudaError_t launch128(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+cudaError_t launch128(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
                       const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   constexpr int EPT = 4;
   dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
-  reconstruct128_kernel<NP, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  reconstruct128_kernel<NP, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc);
   return cudaGetLastError();
 }
 
 template <int L>
-cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
+cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
                      const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   constexpr int EPT = 4;
   dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
-  reconstruct_kernel<L, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, s, t, C, ldc);
+  reconstruct_kernel<L, EPT><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
-                               const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
+                               const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n) return cudaErrorInvalidValue;
   if (T.limbs <= 4) {
     switch (T.npairs) {
-      case 5: return launch128<5>(T, m, n, Y, s, t, C, ldc, st);
-      case 6: return launch128<6>(T, m, n, Y, s, t, C, ldc, st);
-      case 7: return launch128<7>(T, m, n, Y, s, t, C, ldc, st);
-      case 8: return launch128<8>(T, m, n, Y, s, t, C, ldc, st);
+      case 5: return launch128<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
+      case 6: return launch128<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
+      case 7: return launch128<7>(T, m, n, Y, ldy, s, t, C, ldc, st);
+      case 8: return launch128<8>(T, m, n, Y, ldy, s, t, C, ldc, st);
       default: break;
     }
   }
   switch (T.limbs) {
-    case 5: return launch_L<5>(T, m, n, Y, s, t, C, ldc, st);
-    case 6: return launch_L<6>(T, m, n, Y, s, t, C, ldc, st);
+    case 5: return launch_L<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 6: return launch_L<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
     default: return cudaErrorInvalidValue;
   }
 }
