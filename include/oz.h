@@ -225,8 +225,10 @@ OZ_API oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k, co
  * the least estimated work so far, largest problems first. The problems of one
  * stream run one after another and share that stream's slice of the
  * workspace, so the workspace is nstreams times the largest single-problem
- * workspace of any stream's problems. oz_batched_workspace_bytes reports it
- * (0 for invalid arguments).
+ * workspace of any stream's problems; oz_batched_workspace_bytes reports it
+ * (0 for invalid arguments). With nstreams > 1, OZ_ENGINE_TC plans run their
+ * GEMMs with one CTA per tile (as OZ_ENGINE_TC1): CTA-pair GEMMs of products
+ * running at once on several streams were seen to stall one another.
  * Arrays (plans, mnk, trans, pointer and leading-dimension arrays, streams)
  * are host arrays of length count (streams: nstreams); the matrices and the
  * workspace are device memory. trans may be NULL (no transposes), else

@@ -461,9 +461,11 @@ class BatchedGemm:
     oz_dgemm_batched call (optionally captured into one CUDA graph).
 
     shapes: list of (m, n, k). plans: one Plan per problem, or None for the
-    least-Q rule at `bits`. nstreams: streams the problems spread over."""
+    least-Q rule at `bits` (TC engine with one CTA per tile: over several
+    streams oz_dgemm_batched runs TC GEMMs that way in any case).
+    nstreams: streams the problems spread over."""
 
-    def __init__(self, shapes, plans=None, nstreams: int = 4, bits: int = 53, engine: int = OZ_ENGINE_AUTO,
+    def __init__(self, shapes, plans=None, nstreams: int = 4, bits: int = 53, engine: int = OZ_ENGINE_TC1,
                  device=None):
         torch = _import_torch()
         self.shapes = [tuple(int(x) for x in s) for s in shapes]

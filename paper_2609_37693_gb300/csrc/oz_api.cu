@@ -73,9 +73,14 @@ extern "C" oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_a
   return OZ_OK;
 }
 
-extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
-                              const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
-                              void* workspace, size_t workspace_bytes, void* stream) {
+namespace oz {
+
+// oz_dgemm with one option: single_cta runs the TC engine's GEMM with one CTA
+// per tile (no CTA pairs), for callers that run several products at once on
+// different streams (oz_dgemm_batched).
+oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, void* workspace,
+                    size_t workspace_bytes, void* stream, bool single_cta) {
   if (!plan || m < 0 || n < 0 || k < 0) return OZ_ERR_INVALID_ARG;
   if ((trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1)) return OZ_ERR_INVALID_ARG;
   const int64_t a_cols = trans_a ? m : k, b_cols = trans_b ? k : n;
@@ -127,7 +132,7 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
               : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // GEMMs + epilogue
-  e = plan->engine == OZ_ENGINE_TC1
+  e = (plan->engine == OZ_ENGINE_TC1 || (single_cta && plan->engine == OZ_ENGINE_TC))
           ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
       : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
              : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
@@ -136,6 +141,15 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
   // Reconstruct
   e = oz::launch_reconstruct(T, m, n, Y, L.ldy, s, t, C, ldc, st);
   return cuda_status(e);
+}
+
+}  // namespace oz
+
+extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                              const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  return oz::dgemm_run(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream,
+                       false);
 }
 
 extern "C" oz_status oz_query_status(void* workspace, void* stream) {

@@ -103,8 +103,10 @@ extern "C" oz_status oz_dgemm_batched(int count, const oz_plan* plans, const int
   for (int i = 0; i < count && st == OZ_OK; ++i) {
     const int s = a.stream_of[i];
     const int ta = trans ? trans[2 * i] : 0, tb = trans ? trans[2 * i + 1] : 0;
-    st = oz_dgemm(plans[i], ta, tb, mnk[3 * i], mnk[3 * i + 1], mnk[3 * i + 2], A[i], lda[i], B[i], ldb[i], C[i],
-                  ldc[i], ws + slice * (size_t)s, slice, streams[s]);
+    // several streams: the TC engine's GEMMs run with one CTA per tile, since
+    // CTA-pair GEMMs of concurrent products were seen to stall one another
+    st = oz::dgemm_run(plans[i], ta, tb, mnk[3 * i], mnk[3 * i + 1], mnk[3 * i + 2], A[i], lda[i], B[i], ldb[i],
+                       C[i], ldc[i], ws + slice * (size_t)s, slice, streams[s], nstreams > 1);
   }
   // join: streams[0] waits for every other stream
   if (nstreams > 1) {

@@ -627,6 +627,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
+      const float invf = (float)T.inv[c.q];
       uint32_t acc8[32 * NH];                // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
       for (int i = 0; i < 32 * NH; ++i) acc8[i] = 0x80808080u;
@@ -660,11 +661,24 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                   float tv = __uint_as_float(v[4 * w + j]);
-                  if (last)                    // plus the residue of the other chain, r + 128 in a byte
+                  if (last && nslabs > 1)      // plus the residue of the other chain, r + 128 in a byte
                     tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
                   const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                  const float r = fmaf(-qf, mf, tv);
-                  out[j] = __float_as_uint(r + 8388736.0f);                   // low byte = r + 128
+                  const float r = fmaf(-qf, mf, tv);                          // exact, |r| <= 120
+                  if (last) {
+                    // W mod m in [0, m), then (raw == 0) the CRT digit (W mod m) inv mod m:
+                    // y = rr inv < 239^2 is exact, one rint quotient, one sign correction
+                    float y = r < 0.0f ? r + mf : r;
+                    if (!p.raw) {
+                      y *= invf;
+                      const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
+                      y = fmaf(-q2, mf, y);
+                      y = y < 0.0f ? y + mf : y;
+                    }
+                    out[j] = __float_as_uint(y + 8388608.0f);                 // low byte = y
+                  } else {
+                    out[j] = __float_as_uint(r + 8388736.0f);                 // low byte = r + 128
+                  }
                 }
                 a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
               }
@@ -676,25 +690,13 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         mbar_arrive_cluster(mapa(tempty_bar(b), 0));
       }
       if (!ok) break;
-      const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
+      // ---- tile done: acc8 holds the digits (or W mod m), one byte per entry ----
       const int row = c.tm * 2 * P_BM + (int)rank * P_BM + quarter * 32 + lane;
 #pragma unroll
       for (int hh = 0; hh < NH; ++hh) {
         const int col0 = c.tn * 256 + (half0 + hh) * 128;
         if (row < p.m && col0 < p.n) {
-          uint32_t outw[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            uint32_t w = acc8[hh * 32 + i], o = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
-              uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);
-              uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
-              o |= y << (8 * j);
-            }
-            outw[i] = o;
-          }
+          const uint32_t* outw = acc8 + hh * 32;
           uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
           if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
 #pragma unroll
@@ -775,8 +777,15 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  // A pair's CTA takes all the shared memory a block may have, so that no CTA
+  // of another kernel shares its SM: CTA-pair GEMMs running beside other
+  // kernels' CTAs on several streams were seen to stall.
+  int smem_optin = 0;
+  e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const int smem_bytes = smem_optin > P_SMEM_BYTES ? smem_optin : P_SMEM_BYTES;
   e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         P_SMEM_BYTES);
+                           smem_bytes);
   if (e != cudaSuccess) return e;
   Params p;
   p.m = (int)m;
@@ -792,7 +801,7 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   p.ldy = ldy;
   p.status = status;
   const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
-  gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, P_SMEM_BYTES, st>>>(
+  gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(
       mapA, mapB, t, p);
   return cudaGetLastError();
 }

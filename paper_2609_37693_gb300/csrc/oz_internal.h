@@ -106,6 +106,12 @@ constexpr int kTileM = 128;       // M tile of the GEMM engines; m_pad is a mult
 constexpr int kPadRows = 256;     // row padding of the residue planes
 constexpr int kPadK = 128;        // k padding of the residue planes (entries)
 
+// oz_dgemm with the TC engine's GEMM optionally forced onto one CTA per tile
+// (oz_api.cu): products that run concurrently on several streams use it.
+oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, const double* A,
+                    int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, void* workspace,
+                    size_t workspace_bytes, void* stream, bool single_cta);
+
 // Engines that hold the INT8 residues in BF16 planes.
 inline bool engine_bf16(int e) { return e == OZ_ENGINE_TC || e == OZ_ENGINE_TC1; }
 
