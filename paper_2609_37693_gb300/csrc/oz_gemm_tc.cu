@@ -14,16 +14,20 @@
 // Accumulation"; the parity tests drive every accumulator to 1024 * 119^2 and
 // compare bit for bit with exact integer products.
 //
-// Kernel: persistent, one CTA per SM, 10 warps.
-//   warp 0      TMA producer: 128 x 64 (A) and 256 x 64 (B) bf16 tiles, 128-byte
-//               swizzle, 4-stage ring of mbarrier-tracked shared-memory stages;
-//   warp 1      allocates all 512 TMEM columns (two 128 x 256 FP32
+// Two kernels: gemm_tc_pair_kernel (the default; CTA pairs, cta_group::2,
+// 256 x 256 tiles, described before it) and gemm_tc_kernel (one CTA per
+// 128 x 256 tile). Both are persistent, one CTA per SM, 10 warps:
+//   warp 0      TMA producer: bf16 tiles, 128-byte swizzle, a ring of
+//               mbarrier-tracked shared-memory stages;
+//   warp 1      allocates all 512 TMEM columns (two 256-column FP32
 //               accumulators) and, from one thread, issues tcgen05.mma
-//               (M = 128, N = 256, K = 16) and tcgen05.commit;
+//               (K = 16) and tcgen05.commit;
 //   warps 2..9  epilogue: drain an accumulator with tcgen05.ld while the MMAs
-//               fill the other, reduce each slab sum into a running residue
-//               kept as one byte per entry in registers, and at the end of a
-//               tile write the CRT digit (or W mod m) of each entry.
+//               fill the other; each slab's sums are reduced modulo m and
+//               written back into the accumulator, on which the slab after
+//               next accumulates; the last two slabs of a tile give the CRT
+//               digit (or W mod m) of each entry, one byte, stored in 16-byte
+//               runs.
 // Every wait is bounded (about 2 s of %globaltimer); a wait that runs out sets
 // bit 1 of the status word, makes every role stop issuing work, waits (again
 // bounded) for the copies and products already in flight, frees the tensor
@@ -365,7 +369,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t sb = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-              umma_bf16(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (kb > kb0 || kk > 0) ? 1u : 0u);
+              umma_bf16(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (sl >= 2 || kb > kb0 || kk > 0) ? 1u : 0u);
             umma_commit(empty_bar(s));  // frees the stage once these products have read it
             if (++s == STAGES) { s = 0; ph ^= 1u; }
           }
@@ -380,6 +384,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else {
     // ------------------------------ epilogue ------------------------------
+    // As in the pair kernel: slab sl lands in accumulator sl & 1 on top of what
+    // it holds; the epilogue writes each residue r (|r| <= 120) back while slab
+    // sl + 2 accumulates on it, keeps the residue of slab nsl - 2 as a byte,
+    // and turns the last slab's sum into the digit in fp32.
     const int e = warp - 2;                  // 0..7
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
     const int half = e >> 2;                 // columns 128*half .. +127
@@ -390,59 +398,69 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
-      uint32_t acc8[32];                     // running residue + 128, one byte per column
+      const float invf = (float)T.inv[c.q];
+      uint32_t acc8[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
+        const bool write_back = sl + 2 < nslabs;
+        const bool last = sl + 1 == nslabs;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * BN + half * 128 + ch * 32;
           uint32_t v[32];
-          tmem_ld32(tmem_base + lane_addr + b * BN + half * 128 + ch * 32, v);
+          tmem_ld32(taddr, v);
           tmem_ld_wait();
-          if (ch == 3) {                     // all four loads done: hand the accumulator back
-            tc_fence_before();
-            mbar_arrive(tempty_bar(b));
-          }
+          if (write_back) {
 #pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            uint32_t out[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              // previous residue r in [-120, 120] from its byte r + 128
-              const float prev = __int_as_float(__byte_perm(acc8[ch * 8 + w], 0x4B000000u, 0x7540u + j)) -
-                                 8388736.0f;
-              const float tsum = __uint_as_float(v[4 * w + j]) + prev;          // exact: |t| < 2^24
-              const float qf = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;     // nearest quotient (+-1)
-              const float r = fmaf(-qf, mf, tsum);                              // exact, |r| <= 120
-              out[j] = __float_as_uint(r + 8388736.0f);                         // low byte = r + 128
+            for (int j = 0; j < 32; ++j) {
+              const float tv = __uint_as_float(v[j]);
+              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+              v[j] = __float_as_uint(fmaf(-qf, mf, tv));
             }
-            acc8[ch * 8 + w] = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u),
-                                           0x5410u);
+            tmem_st32(taddr, v);
+          } else {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              uint32_t out[4];
+              uint32_t& a8 = acc8[ch * 8 + w];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float tv = __uint_as_float(v[4 * w + j]);
+                if (last && nslabs > 1)
+                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
+                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+                const float r = fmaf(-qf, mf, tv);
+                if (last) {
+                  float y = r < 0.0f ? r + mf : r;
+                  if (!p.raw) {
+                    y *= invf;
+                    const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
+                    y = fmaf(-q2, mf, y);
+                    y = y < 0.0f ? y + mf : y;
+                  }
+                  out[j] = __float_as_uint(y + 8388608.0f);
+                } else {
+                  out[j] = __float_as_uint(r + 8388736.0f);
+                }
+              }
+              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+            }
           }
         }
+        if (write_back) tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(tempty_bar(b));
       }
       if (!ok) break;
-      // ---- tile done: residues -> W mod m or CRT digits, one byte per entry ----
-      const uint32_t m = T.m[c.q], magic = T.magic[c.q], inv = T.inv[c.q];
+      // ---- tile done: acc8 holds the digits (or W mod m), one byte per entry ----
       const int row = c.tm * BM + quarter * 32 + lane;
       const int col0 = c.tn * BN + half * 128;
       if (row < p.m && col0 < p.n) {
-        uint32_t outw[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          uint32_t w = acc8[i], o = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            int r = (int)((w >> (8 * j)) & 0xFFu) - 128;
-            uint32_t rr = (uint32_t)(r < 0 ? r + (int)m : r);    // W mod m in [0, m)
-            uint32_t y = p.raw ? rr : mod_barrett(rr * inv, m, magic);
-            o |= y << (8 * j);
-          }
-          outw[i] = o;
-        }
+        const uint32_t* outw = acc8;
         uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
         if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
 #pragma unroll
