@@ -305,6 +305,42 @@ OZ_API oz_status oz_residue_gemm(oz_plan plan, int64_t m, int64_t n, int64_t m_p
 OZ_API oz_status oz_reconstruct(oz_plan plan, int64_t m, int64_t n, const uint8_t* Y, const int32_t* s,
                          const int32_t* t, double* C, int64_t ldc, void* stream);
 
+/* ---- Grouped products: one launch per phase for many products. ---- */
+
+typedef struct oz_group_s* oz_group;
+
+/*
+ * oz_grouped_workspace_bytes / oz_group_create / oz_group_run / oz_group_destroy
+ * -- count independent products C_i = A_i B_i (row-major, no transposes; the
+ * problem of Sec. "Emulation Problem" for each i) whose phases run as one
+ * launch per phase over all products whose plans share moduli and bit
+ * budget (plans made separately but alike count as one): every A is split in one
+ * launch, every B in one, the GEMMs of all products run in one persistent
+ * kernel (one CTA per 128 x 256 tile, units of the longest k first), and one
+ * reconstruct writes every C. Plans must be INT8 plans of a BF16 engine
+ * (OZ_ENGINE_TC or OZ_ENGINE_TC1) with Q <= 16; others give
+ * OZ_ERR_UNSUPPORTED.
+ *   oz_grouped_workspace_bytes: the device workspace (every product's planes
+ *     and residues at once, plus a descriptor table), 0 for invalid arguments.
+ *   oz_group_create: checks every problem (as oz_dgemm), lays out the
+ *     workspace, and writes the descriptor table into it with a synchronous
+ *     copy; the matrix pointers are fixed from then on (new values in the same
+ *     buffers need no new group). Arrays are host arrays of length count; the
+ *     matrices and the workspace (256-byte aligned, owned by the caller, which
+ *     must keep it alive while the group is used) are device memory.
+ *   oz_group_run: enqueues the phases on the stream; asynchronous and
+ *     capturable into a CUDA graph. oz_query_status(workspace, stream)
+ *     reports non-finite input and bounded-wait time-outs as for oz_dgemm.
+ *   oz_group_destroy: frees the host-side handle (NULL is accepted).
+ */
+OZ_API size_t oz_grouped_workspace_bytes(int count, const oz_plan* plans, const int64_t* mnk);
+OZ_API oz_status oz_group_create(oz_group* out, int count, const oz_plan* plans, const int64_t* mnk,
+                                 const double* const* A, const int64_t* lda, const double* const* B,
+                                 const int64_t* ldb, double* const* C, const int64_t* ldc, void* workspace,
+                                 size_t workspace_bytes);
+OZ_API oz_status oz_group_run(oz_group group, void* stream);
+OZ_API void oz_group_destroy(oz_group group);
+
 /* ---- Allocation-free variant. ---- */
 
 /* Bytes of the device scratch array built into the library (per GPU). */

@@ -49,7 +49,8 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm",
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
-            "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry")
+            "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry",
+            "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy")
 
 
 class OzError(RuntimeError):
@@ -89,6 +90,10 @@ def _load_library():
                                   ctypes.POINTER(I32), P, SZ]),
         "oz_dgemm_host": (I32, [P, I64, I64, I64, P, I64, P, I64, P, I64, I64, P, SZ, P, P, P]),
         "oz_dgemm_batched": (I32, [I32, P, P, P, P, P, P, P, P, P, P, SZ, P, I32]),
+        "oz_grouped_workspace_bytes": (SZ, [I32, P, P]),
+        "oz_group_create": (I32, [ctypes.POINTER(P), I32, P, P, P, P, P, P, P, P, P, SZ]),
+        "oz_group_run": (I32, [P, P]),
+        "oz_group_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -567,6 +572,65 @@ def autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16), bits: int 
             del bg
     _autotune_cache[key] = best[0]
     return best[1], timings
+
+
+class GroupedGemm:
+    """count products C_i = A_i B_i (float64 CUDA tensors, row-major) through
+    oz_group_create / oz_group_run: one launch per phase over all products of
+    a plan. The tensors are fixed at construction; new values written into
+    them are picked up by the next run or replay. Plans: the least-Q rule at
+    `bits` per product (TC engine) unless given."""
+
+    def __init__(self, As, Bs, Cs, plans=None, bits: int = 53, engine: int = OZ_ENGINE_AUTO, device=None):
+        torch = _import_torch()
+        self.count = len(As)
+        self.shapes = [(int(A.shape[0]), int(B.shape[1]), int(A.shape[1])) for A, B in zip(As, Bs)]
+        self.plans = list(plans) if plans is not None else [plan_least_q(k, bits, engine) for (_, _, k) in self.shapes]
+        self.device = torch.device(device or "cuda")
+        P, I64 = ctypes.c_void_p, ctypes.c_int64
+        n = max(self.count, 1)
+        self._plan_arr = (P * n)(*[p.handle for p in self.plans])
+        self._mnk = (I64 * (3 * n))(*[x for s in self.shapes for x in s])
+        nbytes = _lib.oz_grouped_workspace_bytes(self.count, self._plan_arr, self._mnk)
+        if self.count and not nbytes:
+            raise OzError(OZ_ERR_UNSUPPORTED, "oz_grouped_workspace_bytes")
+        self.ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+        self._keep = (As, Bs, Cs)
+        self._A = (P * n)(*[A.data_ptr() for A in As])
+        self._B = (P * n)(*[B.data_ptr() for B in Bs])
+        self._C = (P * n)(*[C.data_ptr() for C in Cs])
+        self._lda = (I64 * n)(*[_ld(A) for A in As])
+        self._ldb = (I64 * n)(*[_ld(B) for B in Bs])
+        self._ldc = (I64 * n)(*[_ld(C) for C in Cs])
+        h = P()
+        st = _lib.oz_group_create(ctypes.byref(h), self.count, self._plan_arr, self._mnk, self._A, self._lda,
+                                  self._B, self._ldb, self._C, self._ldc, self.ws.data_ptr(), self.ws.numel())
+        _check(st, "oz_group_create")
+        self.handle = h
+        self.graph = None
+
+    def run(self, stream=None):
+        _check(_lib.oz_group_run(self.handle, _stream_handle(stream)), "oz_group_run")
+
+    def capture(self, stream=None):
+        """Record one run into a CUDA graph (replay() runs it)."""
+        torch = _import_torch()
+        s = stream or torch.cuda.Stream(self.device)
+        self.run(s)                       # warm-up outside the capture
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.run(s)
+        self.graph = g
+
+    def replay(self):
+        self.graph.replay()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.oz_group_destroy(h)
+            self.handle = None
 
 
 class HostGemm:

@@ -462,10 +462,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (row < p.m && col0 < p.n) {
         const uint32_t* outw = acc8;
         uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-        if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+        if ((p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+          // whole 16-byte runs up to n rounded up to 16: the row pitch leaves room,
+          // and bytes past n are never read
+          const int chunks = min(8, (p.n - col0 + 15) >> 4);
 #pragma unroll
           for (int i = 0; i < 8; ++i)
-            reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
+            if (i < chunks)
+              reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i)
@@ -716,11 +720,13 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         if (row < p.m && col0 < p.n) {
           const uint32_t* outw = acc8 + hh * 32;
           uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-          if (col0 + 128 <= p.n && (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+          if ((p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
+            const int chunks = min(8, (p.n - col0 + 15) >> 4);   // 16-byte runs up to n rounded up
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-              reinterpret_cast<uint4*>(dst)[i] =
-                  make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
+              if (i < chunks)
+                reinterpret_cast<uint4*>(dst)[i] =
+                    make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
@@ -739,6 +745,235 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped products (oz_group_run): the one-CTA kernel over the units of many
+// products of one plan. Unit t belongs to the problem whose unit range holds
+// it (problems in decreasing order of k, so the longest units go first); that
+// problem's descriptor gives its tensor maps (in global memory), padding, k
+// blocks and output. Roles and barriers as in gemm_tc_kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem* __restrict__ probs, int count,
+                       int64_t total_units, int32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_base = smem_u32(smem_raw);
+  const uint32_t base = (raw_base + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw_base);
+  const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  auto unit_begin = [](const OzGroupProblem& q) { return q.unit_begin; };
+  // a CTA visits its units in increasing order, so each role carries the
+  // index of the current problem forward instead of searching per unit
+  auto advance = [&](int pi, int64_t t) {
+    while (pi + 1 < count && probs[pi + 1].unit_begin <= t) ++pi;
+    return pi;
+  };
+  const int pi0 = group_find(probs, count, (int64_t)blockIdx.x < total_units ? (int64_t)blockIdx.x : 0, unit_begin);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), kEpiWarps * 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[STAGES];
+      bool outstanding[STAGES];
+      for (int i = 0; i < STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
+      bool ok = true;
+      int pi = pi0;
+      for (int64_t t = blockIdx.x; t < total_units && ok; t += gridDim.x) {
+        pi = advance(pi, t);
+        const OzGroupProblem& P = probs[pi];
+        const Coord c = tile_coord((int)(t - P.unit_begin), P.tiles_m, P.tiles_n);
+        const int ya = c.q * (int)P.m_pad + c.tm * BM;
+        const int yb = c.q * (int)P.n_pad + c.tn * BN;
+        for (int kb = 0; kb < P.kblocks; ++kb) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, status)) { ok = false; break; }
+          outstanding[s] = false;
+          const uint32_t sa = base + s * STAGE_BYTES;
+          mbar_expect_tx(full_bar(s), STAGE_BYTES);
+          tma_load_2d(sa, &P.mapA, full_bar(s), kb * BK, ya);
+          tma_load_2d(sa + A_BYTES, &P.mapB, full_bar(s), kb * BK, yb);
+          outstanding[s] = true;
+          issued_parity[s] = ph;
+          if (++s == STAGES) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (!ok) {
+        for (int i = 0; i < STAGES; ++i)
+          if (outstanding[i]) mbar_drain(full_bar(i), issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t g = 0;
+      bool ok = true;
+      int pi = pi0;
+      for (int64_t t = blockIdx.x; t < total_units && ok; t += gridDim.x) {
+        pi = advance(pi, t);
+        const OzGroupProblem& P = probs[pi];
+        const int kblocks = P.kblocks;
+        const int nslabs = (kblocks + kSlabBlocks - 1) / kSlabBlocks;
+        for (int sl = 0; sl < nslabs && ok; ++sl, ++g) {
+          const uint32_t b = g & 1u, use = g >> 1;
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + b * BN;
+          const int kb0 = sl * kSlabBlocks;
+          const int kb1 = min(kblocks, kb0 + kSlabBlocks);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, abort_flag, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_bf16(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), (sl >= 2 || kb > kb0 || kk > 0) ? 1u : 0u);
+            umma_commit(empty_bar(s));
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit(tfull_bar(b));
+        }
+      }
+      if (!ok) {
+        umma_commit(drain_bar);
+        mbar_drain(drain_bar, 0);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    const int e = warp - 2;
+    const int quarter = warp & 3;
+    const int half = e >> 2;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    uint32_t g = 0;
+    bool ok = true;
+    int pi = pi0;
+      for (int64_t t = blockIdx.x; t < total_units && ok; t += gridDim.x) {
+      pi = advance(pi, t);
+        const OzGroupProblem& P = probs[pi];
+      const Coord c = tile_coord((int)(t - P.unit_begin), P.tiles_m, P.tiles_n);
+      const int nslabs = (P.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+      const float mf = (float)T.m[c.q];
+      const float invm = T.invm[c.q];
+      const float invf = (float)T.inv[c.q];
+      uint32_t acc8[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int sl = 0; sl < nslabs; ++sl, ++g) {
+        const uint32_t b = g & 1u, use = g >> 1;
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, status)) { ok = false; break; }
+        tc_fence_after();
+        const bool write_back = sl + 2 < nslabs;
+        const bool last = sl + 1 == nslabs;
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * BN + half * 128 + ch * 32;
+          uint32_t v[32];
+          tmem_ld32(taddr, v);
+          tmem_ld_wait();
+          if (write_back) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float tv = __uint_as_float(v[j]);
+              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+              v[j] = __float_as_uint(fmaf(-qf, mf, tv));
+            }
+            tmem_st32(taddr, v);
+          } else {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              uint32_t out[4];
+              uint32_t& a8 = acc8[ch * 8 + w];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float tv = __uint_as_float(v[4 * w + j]);
+                if (last && nslabs > 1)
+                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
+                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+                const float r = fmaf(-qf, mf, tv);
+                if (last) {
+                  float y = r < 0.0f ? r + mf : r;          // W mod m, then the CRT digit
+                  y *= invf;
+                  const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
+                  y = fmaf(-q2, mf, y);
+                  y = y < 0.0f ? y + mf : y;
+                  out[j] = __float_as_uint(y + 8388608.0f);
+                } else {
+                  out[j] = __float_as_uint(r + 8388736.0f);
+                }
+              }
+              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+            }
+          }
+        }
+        if (write_back) tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(tempty_bar(b));
+      }
+      if (!ok) break;
+      const int row = c.tm * BM + quarter * 32 + lane;
+      const int col0 = c.tn * BN + half * 128;
+      if (row < P.m && col0 < P.n) {
+        uint8_t* dst = P.Y + (size_t)c.q * P.m * P.ldy + (size_t)row * P.ldy + col0;
+        if ((P.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(P.Y) & 15) == 0) {
+          const int chunks = min(8, (int)((P.n - col0 + 15) >> 4));   // 16-byte runs up to n rounded up
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (i < chunks)
+              reinterpret_cast<uint4*>(dst)[i] = make_uint4(acc8[4 * i], acc8[4 * i + 1], acc8[4 * i + 2], acc8[4 * i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (col0 + 4 * i + j < P.n) dst[4 * i + j] = (uint8_t)(acc8[i] >> (8 * j));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
@@ -821,6 +1056,29 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
   gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(
       mapA, mapB, t, p);
+  return cudaGetLastError();
+}
+
+// Tensor maps of one grouped problem's planes (rows of Q planes, 128-row boxes
+// for A and 256-row boxes for B, as the one-CTA kernel stages them).
+bool group_maps_tc(OzGroupProblem* pr, int Q) {
+  return make_map(&pr->mapA, pr->U, (int64_t)Q * pr->m_pad, pr->k_pad, BM) &&
+         make_map(&pr->mapB, pr->V, (int64_t)Q * pr->n_pad, pr->k_pad, BN);
+}
+
+cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
+                                   int32_t* status, cudaStream_t st) {
+  if (count == 0 || total_units == 0) return cudaSuccess;
+  if (total_units > INT32_MAX) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(gemm_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)(total_units < sms ? total_units : sms);
+  gemm_tc_grouped_kernel<<<grid, kThreads, kSmemBytes, st>>>(t, probs, count, total_units, status);
   return cudaGetLastError();
 }
 

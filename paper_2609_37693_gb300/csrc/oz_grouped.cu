@@ -1,0 +1,282 @@
+// oz_grouped.cu -- many products in one launch per phase (oz_group_create /
+// oz_group_run): the five phases of Sec. "Structure" run over all products
+// of a plan at once, the split of every A, then of every B, the GEMMs of
+// every product as one persistent kernel, and one reconstruct. Each block (or
+// GEMM unit) finds its product by a binary search over the products' first
+// block indices in a device table written once, at create time.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "oz_internal.h"
+
+namespace {
+
+using oz::round_up;
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Group {
+  oz_plan plan;
+  int first, count;                     // range of the device table
+  int nlong;                            // its first nlong products have rows longer than 1024
+  int64_t total_rows, total_wrows, total_cm, total_sh, total_sc, total_units, total_rec;
+};
+
+// threads per row chunk of the grouped reconstruct: the least power of two
+// covering n / 4 entries, within [32, 256]
+int rec_tpr(int64_t n) {
+  int tpr = 32;
+  while (tpr < 256 && 4 * (int64_t)tpr < n) tpr *= 2;
+  return tpr;
+}
+
+// Byte sizes of one product's part of the workspace (TC engine planes).
+struct Part {
+  int64_t m_pad, n_pad, k_pad, ldy;
+  size_t s, t, u, v, y, total;
+};
+
+Part part_of(const oz_plan p, int64_t m, int64_t n, int64_t k) {
+  Part P;
+  P.m_pad = round_up(m > 0 ? m : 1, oz::kPadRows);
+  P.n_pad = round_up(n > 0 ? n : 1, oz::kPadRows);
+  P.k_pad = round_up(k > 0 ? k : 1, oz::kPadK);
+  P.ldy = round_up(n > 0 ? n : 1, 16);
+  size_t off = 0;
+  P.s = off; off = al256(off + 4 * (size_t)m);
+  P.t = off; off = al256(off + 4 * (size_t)n);
+  P.u = off; off = al256(off + (size_t)p->Q * P.m_pad * P.k_pad * 2);
+  P.v = off; off = al256(off + (size_t)p->Q * P.n_pad * P.k_pad * 2);
+  P.y = off; off = al256(off + (size_t)p->Q * m * P.ldy);
+  P.total = off;
+  return P;
+}
+
+// Plans with the same moduli and bit budget have the same tables: their
+// products can share every launch.
+bool same_tables(const oz_plan a, const oz_plan b) {
+  if (a == b) return true;
+  if (a->tab.Q != b->tab.Q || a->tab.bits != b->tab.bits) return false;
+  for (int q = 0; q < a->tab.Q; ++q)
+    if (a->tab.m[q] != b->tab.m[q]) return false;
+  return true;
+}
+
+bool plan_ok(const oz_plan p) {
+  return p && !p->is_fp && oz::engine_bf16(p->engine) && p->tab.limbs <= 4 && p->tab.npairs >= 5 &&
+         p->tab.npairs <= 8;
+}
+
+// Layout of the whole workspace: status word, table, column maxima, parts.
+struct Layout {
+  size_t table, colmax, parts, total;
+  std::vector<size_t> part_off;         // per caller index (0 for skipped products)
+  std::vector<size_t> colmax_off;
+};
+
+bool layout(int count, const oz_plan* plans, const int64_t* mnk, Layout* L) {
+  if (count < 0 || (count > 0 && (!plans || !mnk))) return false;
+  size_t off = 256;                                       // status word (oz_query_status reads it)
+  L->table = off;
+  off = al256(off + sizeof(OzGroupProblem) * (size_t)(count > 0 ? count : 1));
+  L->colmax = off;
+  L->colmax_off.assign(count, 0);
+  for (int i = 0; i < count; ++i) {
+    const int64_t n = mnk[3 * i + 1];
+    if (n < 0) return false;
+    L->colmax_off[i] = off;
+    off += 8 * (size_t)n;
+  }
+  off = al256(off);
+  L->parts = off;
+  L->part_off.assign(count, 0);
+  for (int i = 0; i < count; ++i) {
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    if (m < 0 || n < 0 || k < 0 || !plan_ok(plans[i])) return false;
+    if (m == 0 || n == 0 || k == 0) continue;
+    L->part_off[i] = off;
+    off += part_of(plans[i], m, n, k).total;
+  }
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+
+struct oz_group_s {
+  char* ws;
+  size_t table_off, colmax_off, colmax_bytes;
+  std::vector<Group> groups;
+  // products with k == 0: C = 0
+  std::vector<double*> zero_c;
+  std::vector<int64_t> zero_m, zero_n, zero_ldc;
+};
+
+extern "C" size_t oz_grouped_workspace_bytes(int count, const oz_plan* plans, const int64_t* mnk) {
+  Layout L;
+  if (!layout(count, plans, mnk, &L)) return 0;
+  return L.total;
+}
+
+extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* plans, const int64_t* mnk,
+                                     const double* const* A, const int64_t* lda, const double* const* B,
+                                     const int64_t* ldb, double* const* C, const int64_t* ldc, void* workspace,
+                                     size_t workspace_bytes) {
+  if (!out) return OZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 0 || (count > 0 && (!plans || !mnk || !A || !B || !C || !lda || !ldb || !ldc)))
+    return OZ_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!plans[i]) return OZ_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!plan_ok(plans[i])) return OZ_ERR_UNSUPPORTED;
+  Layout L;
+  if (!layout(count, plans, mnk, &L)) return OZ_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    if (lda[i] < (k > 1 ? k : 1) || ldb[i] < (n > 1 ? n : 1) || ldc[i] < (n > 1 ? n : 1)) return OZ_ERR_INVALID_ARG;
+    if (k > plans[i]->k_max) return OZ_ERR_K_TOO_LARGE;
+    if (m > 0 && n > 0 && (!C[i] || (reinterpret_cast<uintptr_t>(C[i]) & 7))) return OZ_ERR_INVALID_ARG;
+    if (m > 0 && n > 0 && k > 0 &&
+        (!A[i] || !B[i] || (reinterpret_cast<uintptr_t>(A[i]) & 7) || (reinterpret_cast<uintptr_t>(B[i]) & 7)))
+      return OZ_ERR_INVALID_ARG;
+  }
+  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return OZ_ERR_WORKSPACE;
+
+  oz_group g = new (std::nothrow) oz_group_s;
+  if (!g) return OZ_ERR_INVALID_ARG;
+  g->ws = static_cast<char*>(workspace);
+  g->table_off = L.table;
+  g->colmax_off = L.colmax;
+  g->colmax_bytes = L.parts - L.colmax;
+
+  // groups by tables (order of first appearance); within a group, longest k first
+  std::vector<oz_plan> distinct;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < count; ++i) {
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    if (m == 0 || n == 0) continue;
+    if (k == 0) {
+      g->zero_c.push_back(C[i]);
+      g->zero_m.push_back(m);
+      g->zero_n.push_back(n);
+      g->zero_ldc.push_back(ldc[i]);
+      continue;
+    }
+    size_t gi = 0;
+    while (gi < distinct.size() && !same_tables(distinct[gi], plans[i])) ++gi;
+    if (gi == distinct.size()) {
+      distinct.push_back(plans[i]);
+      members.emplace_back();
+    }
+    members[gi].push_back(i);
+  }
+  std::vector<OzGroupProblem> table;
+  int32_t* status = reinterpret_cast<int32_t*>(g->ws);
+  for (size_t gi = 0; gi < distinct.size(); ++gi) {
+    std::vector<int>& mem = members[gi];
+    std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) { return mnk[3 * x + 2] > mnk[3 * y + 2]; });
+    const oz_plan p = distinct[gi];
+    Group G = {};
+    G.plan = p;
+    G.first = (int)table.size();
+    G.count = (int)mem.size();
+    for (int i : mem) {
+      const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+      const Part P = part_of(p, m, n, k);
+      char* base = g->ws + L.part_off[i];
+      OzGroupProblem pr;
+      memset(&pr, 0, sizeof pr);
+      pr.A = A[i];
+      pr.B = B[i];
+      pr.C = C[i];
+      pr.lda = lda[i];
+      pr.ldb = ldb[i];
+      pr.ldc = ldc[i];
+      pr.m = m;
+      pr.n = n;
+      pr.k = k;
+      pr.m_pad = P.m_pad;
+      pr.n_pad = P.n_pad;
+      pr.k_pad = P.k_pad;
+      pr.ldy = P.ldy;
+      pr.U = base + P.u;
+      pr.V = base + P.v;
+      pr.Y = reinterpret_cast<uint8_t*>(base + P.y);
+      pr.s = reinterpret_cast<int32_t*>(base + P.s);
+      pr.t = reinterpret_cast<int32_t*>(base + P.t);
+      pr.colmax = reinterpret_cast<uint64_t*>(g->ws + L.colmax_off[i]);
+      pr.flag = status;
+      pr.tiles_m = (int)((m + oz::kTileM - 1) / oz::kTileM);
+      pr.tiles_n = (int)((n + 255) / 256);
+      pr.kblocks = (int)(P.k_pad / 64);
+      if (P.k_pad > 1024) {             // one block per row (the long products come first)
+        pr.rows_begin = G.total_rows;
+        G.total_rows += P.m_pad;
+        ++G.nlong;
+      } else {                          // one warp per row, eight rows per block
+        pr.rows_begin = G.total_wrows;
+        G.total_wrows += P.m_pad / 8;
+      }
+      pr.cm_begin = G.total_cm;
+      G.total_cm += ((n + 31) / 32) * ((k + 255) / 256);
+      pr.sh_begin = G.total_sh;
+      G.total_sh += (n + 255) / 256;
+      pr.sc_begin = G.total_sc;
+      G.total_sc += (P.n_pad / 64) * (P.k_pad / 64);
+      pr.unit_begin = G.total_units;
+      G.total_units += (int64_t)p->Q * pr.tiles_m * pr.tiles_n;
+      pr.rec_tpr = rec_tpr(n);
+      pr.rec_begin = G.total_rec;
+      G.total_rec += ((m + 256 / pr.rec_tpr - 1) / (256 / pr.rec_tpr)) * ((n + 4 * pr.rec_tpr - 1) / (4 * pr.rec_tpr));
+      if (!oz::group_maps_tc(&pr, p->Q)) {
+        delete g;
+        return OZ_ERR_INVALID_ARG;
+      }
+      table.push_back(pr);
+    }
+    g->groups.push_back(G);
+  }
+  if (!table.empty() &&
+      cudaMemcpy(g->ws + L.table, table.data(), sizeof(OzGroupProblem) * table.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return OZ_ERR_CUDA;
+  }
+  *out = g;
+  return OZ_OK;
+}
+
+extern "C" oz_status oz_group_run(oz_group g, void* stream) {
+  if (!g) return OZ_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the status word, and the column maxima of every B (atomicMax targets), start from zero
+  cudaError_t e = cudaMemsetAsync(g->ws, 0, 16, st);
+  if (e == cudaSuccess && g->colmax_bytes) e = cudaMemsetAsync(g->ws + g->colmax_off, 0, g->colmax_bytes, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  const OzGroupProblem* table = reinterpret_cast<const OzGroupProblem*>(g->ws + g->table_off);
+  for (size_t i = 0; i < g->zero_c.size(); ++i) {
+    e = cudaMemset2DAsync(g->zero_c[i], (size_t)g->zero_ldc[i] * 8, 0, (size_t)g->zero_n[i] * 8,
+                          (size_t)g->zero_m[i], st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+  }
+  int32_t* status = reinterpret_cast<int32_t*>(g->ws);
+  for (const Group& G : g->groups) {
+    const OzTables& T = G.plan->tab;
+    const OzGroupProblem* probs = table + G.first;
+    e = oz::launch_split_rows_grouped(T, probs, G.count, G.nlong, G.total_rows, G.total_wrows, st);
+    if (e == cudaSuccess) e = oz::launch_split_cols_grouped(T, probs, G.count, G.total_cm, G.total_sh, G.total_sc, st);
+    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, st);
+    if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.count, G.total_rec, st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+  }
+  return OZ_OK;
+}
+
+extern "C" void oz_group_destroy(oz_group g) { delete g; }

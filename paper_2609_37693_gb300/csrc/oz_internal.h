@@ -2,6 +2,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/oz.h"
@@ -91,6 +92,44 @@ struct oz_plan_s {
   size_t values_len;
 };
 
+// One product of a grouped call (oz_group_create): its operands, its part of
+// the workspace and, per phase, the first block (or unit) of the group's
+// launch that belongs to it. Device memory; 64-byte aligned for the maps.
+struct alignas(64) OzGroupProblem {
+  CUtensorMap mapA, mapB;            // residue planes of A and B (TMA, GEMM phase)
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t lda, ldb, ldc;
+  int64_t m, n, k, m_pad, n_pad, k_pad, ldy;
+  void* U;
+  void* V;
+  uint8_t* Y;
+  int32_t* s;
+  int32_t* t;
+  uint64_t* colmax;
+  int32_t* flag;
+  int64_t rows_begin;   // split of A: one block per row of m_pad
+  int64_t cm_begin;     // column maxima of B: ceil(n/32) * ceil(k/256) blocks
+  int64_t sh_begin;     // shifts of B: ceil(n/256) blocks
+  int64_t sc_begin;     // split of B: (n_pad/64) * (k_pad/64) blocks
+  int64_t unit_begin;   // GEMMs: Q * tiles_m * tiles_n units
+  int64_t rec_begin;    // reconstruct: m * ceil(n/1024) blocks
+  int tiles_m, tiles_n, kblocks;
+  int rec_tpr;          // reconstruct: threads per row chunk (32..256), 256 / rec_tpr rows per block
+};
+
+// the problem whose range [begin, next begin) holds index x (probs sorted by begin)
+template <typename F>
+__device__ __forceinline__ int group_find(const OzGroupProblem* probs, int count, int64_t x, F begin) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin(probs[mid]) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 namespace oz {
 
 // Barrett reduction of y < 2^32 by m (2 <= m < 2^16) with magic = floor(2^32/m).
@@ -141,6 +180,17 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
                            cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
                                const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+// grouped products (oz_grouped.cu): one launch per phase over count problems
+// of one plan; probs is device memory; totals are the launch sizes.
+cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int nlong,
+                                      int64_t total_rows, int64_t total_wrows, cudaStream_t st);
+cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_cm,
+                                      int64_t total_sh, int64_t total_sc, cudaStream_t st);
+cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
+                                   int32_t* status, cudaStream_t st);
+bool group_maps_tc(OzGroupProblem* pr, int Q);   // host: the TMA maps of a grouped problem's planes
+cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_rec,
+                                       cudaStream_t st);
 // float-format path: planes of codes, 16-bit digits
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,

@@ -307,20 +307,19 @@ __device__ __forceinline__ uint64_t round128(u128 mag, uint32_t neg, int e) {
 // farther than 1e-3 from a tie cannot pick the wrong quotient). The pair
 // count is a template parameter so that every digit load is issued before
 // any arithmetic.
+// One thread: entries (i, j0 .. j0 + 3).
 template <int NP, int EPT>
-__global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_constant__ OzTables T, int64_t m,
-                                                             int64_t n, const uint8_t* __restrict__ Y,
-                                                             int64_t ldy, const int32_t* __restrict__ s,
-                                                             const int32_t* __restrict__ t,
-                                                             double* __restrict__ C, int64_t ldc) {
+__device__ __forceinline__ void reconstruct128_entries(const OzTables& T, int64_t i, int64_t j0, int64_t m, int64_t n,
+                                                       const uint8_t* __restrict__ Y, int64_t ldy,
+                                                       const int32_t* __restrict__ s, const int32_t* __restrict__ t,
+                                                       double* __restrict__ C, int64_t ldc) {
   static_assert(EPT == 4, "one 32-bit digit word per plane");
-  const int64_t i = blockIdx.x;
-  const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
   const int64_t plane = m * ldy;
   const uint8_t* yp = Y + i * ldy + j0;
-  const bool vec = (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) && ((plane & 3) == 0);
+  // whole 4-byte words whenever the row pitch has room (bytes past n are unused)
+  const bool vec = (j0 + 4 <= ldy) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) && ((plane & 3) == 0);
   uint32_t wa[NP], wb[NP];
   if (vec) {
 #pragma unroll
@@ -422,6 +421,33 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
   }
 }
 
+template <int NP, int EPT>
+__global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_constant__ OzTables T, int64_t m,
+                                                             int64_t n, const uint8_t* __restrict__ Y,
+                                                             int64_t ldy, const int32_t* __restrict__ s,
+                                                             const int32_t* __restrict__ t,
+                                                             double* __restrict__ C, int64_t ldc) {
+  reconstruct128_entries<NP, EPT>(T, blockIdx.x, ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT, m, n, Y, ldy, s, t,
+                                  C, ldc);
+}
+
+// Grouped: a block covers 256 / tpr rows of one column chunk of 4 tpr entries
+// (tpr = rec_tpr threads per row chunk, so short rows share a block); block b
+// is row group l / nch, chunk l % nch of its problem, l = b - rec_begin.
+template <int NP>
+__global__ void __launch_bounds__(256) reconstruct128_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                     const OzGroupProblem* __restrict__ probs,
+                                                                     int count) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rec_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int tpr = P.rec_tpr, rows = 256 / tpr;
+  const int64_t l = b - P.rec_begin, nch = (P.n + 4 * tpr - 1) / (4 * tpr);
+  const int64_t i = (l / nch) * rows + threadIdx.x / tpr;
+  const int64_t j0 = ((l % nch) * tpr + threadIdx.x % tpr) * 4;
+  reconstruct128_entries<NP, 4>(T, i, j0, P.m, P.n, P.Y, P.ldy, P.s, P.t, P.C, P.ldc);
+}
+
 template <int NP>
 cudaError_t launch128(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
                       const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
@@ -460,6 +486,20 @@ cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const ui
     case 6: return launch_L<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* probs, int count, int64_t total_rec,
+                                       cudaStream_t st) {
+  if (count == 0 || total_rec == 0) return cudaSuccess;
+  if (total_rec > INT32_MAX || T.limbs > 4) return cudaErrorInvalidValue;
+  switch (T.npairs) {
+    case 5: reconstruct128_grouped_kernel<5><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
+    case 6: reconstruct128_grouped_kernel<6><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
+    case 7: reconstruct128_grouped_kernel<7><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
+    case 8: reconstruct128_grouped_kernel<8><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace oz

@@ -101,14 +101,12 @@ __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d
 // writes 8 consecutive entries per thread per plane.
 // ---------------------------------------------------------------------------
 template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
-                                                         const double* __restrict__ X, int64_t ld,
-                                                         int64_t nvec_pad, int64_t k_pad,
-                                                         int32_t* __restrict__ shifts, void* __restrict__ planes,
-                                                         int32_t* __restrict__ flag) {
+__device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
+                                          const double* __restrict__ X, int64_t ld, int64_t nvec_pad, int64_t k_pad,
+                                          int32_t* __restrict__ shifts, void* __restrict__ planes,
+                                          int32_t* __restrict__ flag) {
   __shared__ uint64_t red[8];
   __shared__ int32_t s_sh;
-  const int64_t v = blockIdx.x;
   const int tid = threadIdx.x;
   const bool live = v < nvec;
   const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
@@ -189,18 +187,133 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__
   }
 }
 
+// The same for a short row (k_pad <= 1024): one warp per row, eight rows
+// per block; the row's maximum is a warp reduction.
+template <bool kBF16, int NP>
+__device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
+                                               const double* __restrict__ X, int64_t ld, int64_t nvec_pad,
+                                               int64_t k_pad, int32_t* __restrict__ shifts,
+                                               void* __restrict__ planes, int32_t* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  const bool live = v < nvec;
+  const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
+  uint64_t mx = 0;
+  uint32_t bad = 0;
+  if (live) {
+    for (int64_t h = lane; h < len; h += 32) {
+      uint64_t b = __ldg(row + h) & kAbsMask;
+      bad |= (uint32_t)((b >> 52) == 0x7ff);
+      mx = b > mx ? b : mx;
+    }
+  }
+  mx = warp_max_u64(mx);
+  bad = __any_sync(0xffffffffu, bad);
+  const int32_t s = live ? shift_from_maxbits(bad ? 0 : mx, T.bits) : 0;
+  if (lane == 0) {
+    if (bad && flag) atomicOr(flag, 1);
+    if (live) shifts[v] = s;
+  }
+  const int Q = T.Q;
+  const int64_t plane = nvec_pad * k_pad;
+  const bool vec = live && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
+  for (int64_t h0 = (int64_t)lane * 8; h0 < k_pad; h0 += 32 * 8) {
+    uint64_t b[8];
+    if (vec && h0 + 8 <= len) {
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(row + h0 + e));
+        b[e] = w.x;
+        b[e + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+    }
+    Pieces<NP> P[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;
+      P[e] = pieces_of<NP>(b[e], s);
+    }
+#pragma unroll
+    for (int q = 0; q < OZ_MAX_MODULI; ++q) {
+      if (q < Q) {
+        const ModConst mc = mod_const(T, q);
+        float r[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = residue_f(mc, P[e]);
+        const int64_t off = (int64_t)q * plane + v * k_pad + h0;
+        if (kBF16) {
+          uint4 o;
+          o.x = bf16_pair(r[0], r[1]);
+          o.y = bf16_pair(r[2], r[3]);
+          o.z = bf16_pair(r[4], r[5]);
+          o.w = bf16_pair(r[6], r[7]);
+          *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
+        } else {
+          uint2 o;
+          o.x = int8_quad(r[0], r[1], r[2], r[3]);
+          o.y = int8_quad(r[4], r[5], r[6], r[7]);
+          *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
+        }
+      }
+    }
+  }
+}
+
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_rows_warp_kernel(const __grid_constant__ OzTables T, int64_t nvec,
+                                                              int64_t len, const double* __restrict__ X, int64_t ld,
+                                                              int64_t nvec_pad, int64_t k_pad,
+                                                              int32_t* __restrict__ shifts,
+                                                              void* __restrict__ planes, int32_t* __restrict__ flag) {
+  const int64_t v = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  split_row_warp<kBF16, NP>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+}
+
+// Grouped, short rows: block b holds rows 8 (b - rows_begin) .. + 7 of its problem.
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_rows_warp_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                      const OzGroupProblem* __restrict__ probs,
+                                                                      int count) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int64_t v = (b - P.rows_begin) * 8 + (threadIdx.x >> 5);
+  split_row_warp<kBF16, NP>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag);
+}
+
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
+                                                         const double* __restrict__ X, int64_t ld,
+                                                         int64_t nvec_pad, int64_t k_pad,
+                                                         int32_t* __restrict__ shifts, void* __restrict__ planes,
+                                                         int32_t* __restrict__ flag) {
+  split_row<kBF16, NP>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+}
+
+// Grouped: block b is row b - rows_begin of its problem's A.
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_rows_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                 const OzGroupProblem* __restrict__ probs, int count) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
+  const OzGroupProblem& P = probs[pi];
+  split_row<kBF16, NP>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag);
+}
+
 // ---------------------------------------------------------------------------
 // Strided vectors (columns of B, or of A^T).
 // Pass 1: column maxima by atomicMax into colmax (zeroed by the launcher).
 // Block (32 x 8): 32 consecutive columns, 8 warps over rows; each CTA covers
 // 256 rows.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) colmax_kernel(int64_t nvec, int64_t len, const double* __restrict__ X,
-                                                     int64_t ld, uint64_t* __restrict__ colmax,
-                                                     int32_t* __restrict__ flag) {
+__device__ __forceinline__ void colmax_block(int64_t bx, int64_t by, int64_t nvec, int64_t len,
+                                             const double* __restrict__ X, int64_t ld,
+                                             uint64_t* __restrict__ colmax, int32_t* __restrict__ flag) {
   __shared__ uint64_t red[8][32];
-  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t h0 = (int64_t)blockIdx.y * 256;
+  const int64_t j = bx * 32 + threadIdx.x;
+  const int64_t h0 = by * 256;
   uint64_t mx = 0;
   uint32_t bad = 0;
   if (j < nvec) {
@@ -223,28 +336,51 @@ __global__ void __launch_bounds__(256) colmax_kernel(int64_t nvec, int64_t len, 
   }
 }
 
+__global__ void __launch_bounds__(256) colmax_kernel(int64_t nvec, int64_t len, const double* __restrict__ X,
+                                                     int64_t ld, uint64_t* __restrict__ colmax,
+                                                     int32_t* __restrict__ flag) {
+  colmax_block(blockIdx.x, blockIdx.y, nvec, len, X, ld, colmax, flag);
+}
+
+// Grouped: block b is block b - cm_begin of its problem's (ceil(n/32) x
+// ceil(k/256)) grid, x fastest.
+__global__ void __launch_bounds__(256) colmax_grouped_kernel(const OzGroupProblem* __restrict__ probs, int count) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.cm_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int64_t l = b - P.cm_begin, nbx = (P.n + 31) / 32;
+  colmax_block(l % nbx, l / nbx, P.n, P.k, P.B, P.ldb, P.colmax, P.flag);
+}
+
 __global__ void shifts_from_colmax_kernel(int64_t nvec, const uint64_t* __restrict__ colmax, int beta,
                                           int32_t* __restrict__ shifts) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j < nvec) shifts[j] = shift_from_maxbits(colmax[j], beta);
 }
 
+__global__ void shifts_grouped_kernel(const OzGroupProblem* __restrict__ probs, int count, int beta) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.sh_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int64_t j = (b - P.sh_begin) * blockDim.x + threadIdx.x;
+  if (j < P.n) P.t[j] = shift_from_maxbits(P.colmax[j], beta);
+}
+
 // Pass 2: 64 (h) x 64 (vector) tiles; residues go through shared memory so
 // that the planes, which are K-major per vector, are written along h.
 // Thread t handles vector j = t % 64 and 16 consecutive h.
 template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
-                                                         const double* __restrict__ X, int64_t ld,
-                                                         int64_t nvec_pad, int64_t k_pad,
-                                                         const int32_t* __restrict__ shifts,
-                                                         void* __restrict__ planes) {
+__device__ __forceinline__ void split_cols_block(const OzTables& T, int64_t bx, int64_t by, int64_t nvec,
+                                                 int64_t len, const double* __restrict__ X, int64_t ld,
+                                                 int64_t nvec_pad, int64_t k_pad,
+                                                 const int32_t* __restrict__ shifts, void* __restrict__ planes) {
   constexpr int kPitchWords = kBF16 ? 33 : 17;   // 64 entries + 4 bytes of padding per row
   __shared__ uint32_t tile[2][64 * kPitchWords];
   const int tid = threadIdx.x;
   const int jl = tid & 63;
   const int hg = tid >> 6;                         // 0..3: h = hg*16 .. hg*16+15
-  const int64_t j0 = (int64_t)blockIdx.x * 64;
-  const int64_t hbase = (int64_t)blockIdx.y * 64;
+  const int64_t j0 = bx * 64;
+  const int64_t hbase = by * 64;
   const int64_t j = j0 + jl;
   const bool live = j < nvec;
   const int32_t s = live ? shifts[j] : 0;
@@ -294,6 +430,26 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__
   }
 }
 
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
+                                                         const double* __restrict__ X, int64_t ld,
+                                                         int64_t nvec_pad, int64_t k_pad,
+                                                         const int32_t* __restrict__ shifts,
+                                                         void* __restrict__ planes) {
+  split_cols_block<kBF16, NP>(T, blockIdx.x, blockIdx.y, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+}
+
+// Grouped: block b is block b - sc_begin of its problem's (n_pad/64 x k_pad/64) grid, x fastest.
+template <bool kBF16, int NP>
+__global__ void __launch_bounds__(256) split_cols_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                 const OzGroupProblem* __restrict__ probs, int count) {
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.sc_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int64_t l = b - P.sc_begin, nbx = P.n_pad / 64;
+  split_cols_block<kBF16, NP>(T, l % nbx, l / nbx, P.n, P.k, P.B, P.ldb, P.n_pad, P.k_pad, P.t, P.V);
+}
+
 // Rows v in [nvec, nvec_pad) of the strided layout are covered by the grid
 // (grid.x spans nvec_pad), so no separate padding pass is needed.
 
@@ -303,8 +459,20 @@ cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, cons
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
                               int32_t* flag, cudaStream_t st) {
   if (nvec_pad == 0) return cudaSuccess;
-  dim3 grid((unsigned)nvec_pad);
   const bool np4 = t.bits <= 60;                 // |a'| < 2^60: four 15-bit pieces
+  if (k_pad <= 1024) {                           // short rows: one warp per row
+    const unsigned g = (unsigned)(nvec_pad / 8);
+    if (bf16 && np4)
+      split_rows_warp_kernel<true, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    else if (bf16)
+      split_rows_warp_kernel<true, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    else if (np4)
+      split_rows_warp_kernel<false, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    else
+      split_rows_warp_kernel<false, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    return cudaGetLastError();
+  }
+  dim3 grid((unsigned)nvec_pad);
   if (bf16 && np4)
     split_rows_kernel<true, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
   else if (bf16)
@@ -345,6 +513,45 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
     split_cols_kernel<false, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   else
     split_cols_kernel<false, 5><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  return cudaGetLastError();
+}
+
+// Problems [0, nlong) have long rows (one block per row, total_rows blocks),
+// the rest short rows (eight per block, total_wrows blocks); each range has its
+// own rows_begin numbering.
+cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int nlong,
+                                      int64_t total_rows, int64_t total_wrows, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  if (total_rows > INT32_MAX || total_wrows > INT32_MAX) return cudaErrorInvalidValue;
+  const bool np4 = t.bits <= 60;
+  if (nlong > 0 && total_rows > 0) {
+    if (np4)
+      split_rows_grouped_kernel<true, 4><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
+    else
+      split_rows_grouped_kernel<true, 5><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
+  }
+  if (count > nlong && total_wrows > 0) {
+    if (np4)
+      split_rows_warp_grouped_kernel<true, 4><<<(unsigned)total_wrows, 256, 0, st>>>(t, probs + nlong, count - nlong);
+    else
+      split_rows_warp_grouped_kernel<true, 5><<<(unsigned)total_wrows, 256, 0, st>>>(t, probs + nlong, count - nlong);
+  }
+  return cudaGetLastError();
+}
+
+// column maxima, shifts and split of the B operands (colmax zeroed by the caller)
+cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_cm,
+                                      int64_t total_sh, int64_t total_sc, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  if (total_cm > INT32_MAX || total_sh > INT32_MAX || total_sc > INT32_MAX) return cudaErrorInvalidValue;
+  if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, count);
+  if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, count, t.bits);
+  if (total_sc > 0) {
+    if (t.bits <= 60)
+      split_cols_grouped_kernel<true, 4><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
+    else
+      split_cols_grouped_kernel<true, 5><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
+  }
   return cudaGetLastError();
 }
 

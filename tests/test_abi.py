@@ -138,3 +138,26 @@ def test_batched_workspace_and_argument_checks():
     assert oz.oz_dgemm_batched(3, parr, mnk_big, None, ptrs, lda_big, ptrs, ldb, ptrs, ldc, fake, big, streams,
                                1) == oz.OZ_ERR_K_TOO_LARGE
     assert oz.oz_dgemm_batched(0, parr, mnk, None, ptrs, lds, ptrs, ldb, ptrs, ldc, None, 0, streams, 1) == oz.OZ_OK
+
+
+def test_grouped_refuses_unsupported_plans_before_any_work():
+    """oz_group_create takes INT8 plans of a BF16 engine only; a float-format or
+    IMMA plan is refused on the host, before any pointer is used."""
+    import ctypes
+    fp = oz.PlanFP("E4M3", 1000)
+    imma = oz.Plan(16, 0, 1000, oz.OZ_ENGINE_IMMA)
+    tc = oz.Plan(16, 0, 1000, oz.OZ_ENGINE_TC)
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    mnk = (I64 * 3)(64, 64, 64)
+    for plan, want in ((fp, oz.OZ_ERR_UNSUPPORTED), (imma, oz.OZ_ERR_UNSUPPORTED)):
+        arr = (P * 1)(plan.handle)
+        assert oz._lib.oz_grouped_workspace_bytes(1, arr, mnk) == 0
+        h = P()
+        st = oz._lib.oz_group_create(ctypes.byref(h), 1, arr, mnk, None, None, None, None, None, None, None, 0)
+        assert st == oz.OZ_ERR_INVALID_ARG           # null operand arrays are checked first
+        one = (P * 1)(None)
+        ld = (I64 * 1)(64)
+        st = oz._lib.oz_group_create(ctypes.byref(h), 1, arr, mnk, one, ld, one, ld, one, ld, None, 0)
+        assert st == want and not h.value
+    arr = (P * 1)(tc.handle)
+    assert oz._lib.oz_grouped_workspace_bytes(1, arr, mnk) > 0

@@ -73,3 +73,60 @@ def test_autotuner_picks_a_stream_count():
     ref = _alone(shapes, As, Bs, bg.plans)
     for C, R in zip(Cs, ref):
         assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+
+
+# ---- grouped products: one launch per phase (oz_group_create / oz_group_run) ----
+
+def _edge_problems():
+    """Uneven shapes with the edge cases of the grouped path: 1 x 1 x 1, one
+    row, one column, k = 0, k at a slab boundary, ragged tiles, Q = 14/15/16."""
+    shapes = [(1, 1, 1), (1, 300, 77), (300, 1, 77), (5, 7, 0), (130, 257, 1024), (129, 255, 1025),
+              (64, 64, 3), (700, 513, 900), (256, 256, 5000), (33, 1000, 837)]
+    As, Bs, Cs = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B = synth.phi_pair(m, n, k, 1.5, seed=300 + i)
+        As.append(torch.from_numpy(A).to(DEV))
+        Bs.append(torch.from_numpy(B).to(DEV))
+        Cs.append(torch.full((m, n), np.nan, dtype=torch.float64, device=DEV))
+    return shapes, As, Bs, Cs
+
+
+@pytest.mark.parametrize("which", ["uneven", "edges"])
+def test_grouped_equals_individual_products(which):
+    shapes, As, Bs, Cs = _problems(40, 1, 1500, seed=6) if which == "uneven" else _edge_problems()
+    gg = oz.GroupedGemm(As, Bs, Cs)
+    assert sorted({p.q for p in gg.plans}) == sorted({14 if k <= 4 else 15 if k <= 836 else 16
+                                                        for (_, _, k) in shapes})
+    gg.run()
+    torch.cuda.synchronize()
+    assert oz.query_status(gg.ws) == oz.OZ_OK
+    ref = _alone(shapes, As, Bs, gg.plans)
+    for (m, n, k), C, R in zip(shapes, Cs, ref):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64)), (m, n, k)
+
+
+def test_grouped_graph_replays_on_new_inputs():
+    shapes, As, Bs, Cs = _problems(20, 16, 2000, seed=7)
+    gg = oz.GroupedGemm(As, Bs, Cs)
+    gg.capture()
+    for rnd in range(2):
+        for i, (A, B) in enumerate(zip(As, Bs)):
+            m, k = A.shape
+            n = B.shape[1]
+            a, b = synth.phi_pair(m, n, k, 2.0, seed=2000 * (rnd + 1) + i)
+            A.copy_(torch.from_numpy(a))
+            B.copy_(torch.from_numpy(b))
+        gg.replay()
+        torch.cuda.synchronize()
+        ref = _alone(shapes, As, Bs, gg.plans)
+        for C, R in zip(Cs, ref):
+            assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+
+
+def test_grouped_reports_nonfinite():
+    shapes, As, Bs, Cs = _problems(6, 32, 300, seed=8)
+    As[2][0, 0] = float("nan")
+    Bs[4][-1, -1] = float("inf")
+    gg = oz.GroupedGemm(As, Bs, Cs)
+    gg.run()
+    assert oz.query_status(gg.ws) == oz.OZ_ERR_NONFINITE
