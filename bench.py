@@ -48,9 +48,13 @@ def parse():
                     help="residue alphabet: the INT8 path, or a float-format configuration")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
-    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch"],
+    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch", "blocked"],
                     help="dgemm: one m=n=k product (the headline); batch: 256 uneven products")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-mode", default="grouped", choices=["grouped", "streams"],
+                    help="batch: one launch per phase over grouped products, or products on autotuned streams")
+    ap.add_argument("--k", type=int, default=65536, help="blocked: the inner dimension")
+    ap.add_argument("--k-slab", type=int, default=8192, help="blocked: terms per slab")
     return ap.parse_args()
 
 
@@ -448,9 +452,11 @@ def run_ours(args, rank, world, local):
 
 
 def run_batch(args, rank, world, local):
-    """256 products with m, n, k log-uniform on [64, 4096] (phi = 1), through one
-    autotuned oz_dgemm_batched captured into a CUDA graph, next to a loop of
-    cuBLAS DGEMM calls on the same operands."""
+    """256 products with m, n, k log-uniform on [64, 4096] (phi = 1), captured
+    into one CUDA graph, next to a loop of cuBLAS DGEMM calls on the same
+    operands. --batch-mode grouped: oz_group_run, one launch per phase over
+    the products of alike plans; streams: oz_dgemm_batched over an autotuned
+    number of streams."""
     import torch
     import paper_2609_37693_gb300 as oz
     import synth
@@ -464,7 +470,14 @@ def run_batch(args, rank, world, local):
         Bs.append(torch.from_numpy(B).to(dev))
         Cs.append(torch.empty((m, n), dtype=torch.float64, device=dev))
     flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
-    bg, tune = oz.autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16))
+    if args.batch_mode == "grouped":
+        bg = oz.GroupedGemm(As, Bs, Cs)
+        bg.capture()
+        tune, mode_desc, launches = None, "grouped products, one launch per phase", bg.launches()
+    else:
+        bg, tune = oz.autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16))
+        mode_desc = f"oz_dgemm_batched on {bg.nstreams} streams"
+        launches = sum(oz.launches_per_dgemm() for _ in shapes)
     for _ in range(max(args.warmup, 1)):
         bg.replay()
     torch.cuda.synchronize()
@@ -496,7 +509,6 @@ def run_batch(args, rank, world, local):
     ms_dgemm = e0.elapsed_time(e1) / reps
     num = sum(float(torch.linalg.norm(C - R) ** 2) for C, R in zip(Cs, ref))
     den = sum(float(torch.linalg.norm(R) ** 2) for R in ref)
-    launches = sum(oz.launches_per_dgemm() for _ in shapes)
     if rank == 0:
         line = {
             "metric": "batched emulated-FP64 GEMM TFLOP/s, 256 products m,n,k log-uniform on [64,4096]",
@@ -505,12 +517,81 @@ def run_batch(args, rank, world, local):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"{len(shapes)} uneven products, m,n,k log-uniform [64,4096] seed 0, "
                                    f"phi=1, least Q at 53 bits per product, one CUDA graph",
-                       "total_flops": flops, "nstreams": bg.nstreams, "autotune_ms": tune,
+                       "mode": mode_desc, "total_flops": flops, "autotune_ms": tune,
                        "q_histogram": {str(q): sum(1 for p in bg.plans if p.q == q) for q in sorted({p.q for p in bg.plans})},
                        "cublas_dgemm_loop_tflops": flops / (ms_dgemm * 1e-3) / 1e12,
                        "speedup_vs_cublas_dgemm_loop": ms_dgemm / ms,
                        "rel_frobenius_vs_dgemm": (num / den) ** 0.5},
             "gpu_launches": launches * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_blocked(args, rank, world, local):
+    """One product m = n = --n with inner dimension --k through the blocked
+    call in slabs of --k-slab terms (Sec. "Slabs"), next to the unblocked
+    oz_dgemm of the same product (whose planes for the whole K must fit): the
+    cost of running the epilogue once per slab and of the per-slab launches,
+    and a check that both give the same bits."""
+    import torch
+    import paper_2609_37693_gb300 as oz
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, k, kt = args.n, args.k, args.k_slab
+    A, B = synth.phi_pair(n, n, k, args.phi, seed=rank)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    del A, B
+    plan = oz.Plan(args.q, args.bits, min(k, kt), oz.OZ_ENGINE_TC if args.engine == "auto" else
+                   {"imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC, "tc1": oz.OZ_ENGINE_TC1}[args.engine])
+    Cb = torch.empty((n, n), dtype=torch.float64, device=dev)
+    wsb = torch.empty(oz.oz_blocked_workspace_bytes(plan.handle, n, n, kt), dtype=torch.uint8, device=dev)
+    s0 = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        for _ in range(steps):
+            fn()
+        e1.record(s0)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(lambda: oz.dgemm_blocked(Ad, Bd, plan, kt, out=Cb, ws=wsb), args.steps)
+    clk = clocks.stop()
+    del wsb
+    ms_u, same = None, None
+    if k <= plan.k_max:
+        Cu = torch.empty_like(Cb)
+        wsu = oz.workspace(plan, n, n, k, dev)
+        ms_u = timed(lambda: oz.dgemm(Ad, Bd, plan, out=Cu, ws=wsu), max(args.steps // 2, 1))
+        same = bool(torch.equal(Cb.view(torch.int64), Cu.view(torch.int64)))
+    flops = 2.0 * n * n * k
+    nslabs = -(-k // kt)
+    if rank == 0:
+        line = {
+            "metric": "emulated-FP64 GEMM TFLOP/s, blocked call", "value": flops / (ms * 1e-3) / 1e12,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": f"m=n={n}, k={k} in {nslabs} slabs of {kt}, phi={args.phi}, Q={plan.q}, "
+                                   f"beta={plan.bits}, TC engine",
+                       "unblocked_ms": ms_u,
+                       "unblocked_tflops": flops / (ms_u * 1e-3) / 1e12 if ms_u else None,
+                       "blocked_over_unblocked": ms / ms_u if ms_u else None,
+                       "equals_unblocked_bits": same,
+                       "workspace_gb_blocked": oz.oz_blocked_workspace_bytes(plan.handle, n, n, kt) / 1e9,
+                       "workspace_gb_unblocked": plan.workspace_bytes(n, n, k) / 1e9},
+            # shifts of A's rows (1) and B's columns (2); per slab two splits and the
+            # GEMM; one Reconstruct
+            "gpu_launches": (4 + 3 * nslabs) * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -524,6 +605,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, rank, world, local)
+        return
+    if args.workload == "blocked":
+        run_blocked(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

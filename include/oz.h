@@ -143,6 +143,17 @@ OZ_API oz_status oz_plan_info_fp(oz_plan plan, int* channels, int* gemms, int64_
                                  int* forms, int* bases, int* plane_count, int16_t* plane_values,
                                  size_t values_len);
 
+/*
+ * oz_plan_caps -- the two caps of eq. caps separately: k_acc, the largest
+ * inner dimension one accumulation may take (INT32 accumulators on the IMMA
+ * engine, FP32 accumulators of float-format plans; the TC engine drains its
+ * FP32 slabs itself and has none below 2^31), and k_rec, the largest K the
+ * CRT window admits at the plan's beta (eq. ov-crtgen). K_max of
+ * oz_plan_info is their minimum; a blocked call (oz_dgemm_blocked) takes any
+ * K <= k_rec in slabs of at most k_acc. Either output may be NULL.
+ */
+OZ_API oz_status oz_plan_caps(oz_plan plan, int64_t* k_acc, int64_t* k_rec);
+
 /* Release a plan (NULL is accepted). */
 OZ_API void oz_plan_destroy(oz_plan plan);
 
@@ -188,6 +199,39 @@ OZ_API oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m, int
  * has a CUDA error or a bounded device wait of that call ran out, else OZ_OK.
  */
 OZ_API oz_status oz_query_status(void* workspace, void* stream);
+
+/* ---- Blocked call: the inner dimension in slabs (Sec. "Slabs"). ---- */
+
+/*
+ * oz_blocked_workspace_bytes -- device workspace of a blocked call: the
+ * workspace of one product with inner dimension k_slab (the planes of one
+ * slab of each operand) plus nothing else; the residues Y cover the whole
+ * output as in oz_workspace_bytes. Returns 0 for an invalid plan or shape.
+ */
+OZ_API size_t oz_blocked_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k_slab);
+
+/*
+ * oz_dgemm_blocked -- the product of oz_dgemm, with the inner dimension cut
+ * into slabs of k_slab terms (the last one shorter), each accumulated on its
+ * own and added into a running residue (Sec. "Slabs"):
+ *   1. the shifts s, t are taken over the whole of each row of op(A) and
+ *      column of op(B) (eq. convert), so the truncated operands A', B' are
+ *      those of the unblocked call;
+ *   2. per slab, the residue planes of that slab's columns of op(A) and rows
+ *      of op(B) are formed, and each modulus' GEMM epilogue adds the slab's
+ *      CRT digit into the digits of the earlier slabs, modulo m (digits are
+ *      linear in W, and W is the sum of the slabs' products);
+ *   3. one Reconstruct after the last slab.
+ * The result is therefore bit for bit that of oz_dgemm whenever both apply.
+ * The call serves K above the accumulation cap (k <= k_rec, k_slab <= k_acc
+ * of oz_plan_caps, else OZ_ERR_K_TOO_LARGE) and operands whose planes for the
+ * whole K would not fit in memory: the workspace holds one slab's planes,
+ * oz_blocked_workspace_bytes(plan, m, n, k_slab) bytes, 256-byte aligned.
+ * Other arguments, errors and asynchrony as for oz_dgemm; k_slab >= 1.
+ */
+OZ_API oz_status oz_dgemm_blocked(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                                  int64_t k_slab, const double* A, int64_t lda, const double* B, int64_t ldb,
+                                  double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---- Host-resident operands with the copies overlapped. ---- */
 

@@ -50,7 +50,8 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_query_status", "oz_split", "oz_residue_gemm", "oz_reconstruct", "oz_status_str",
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
             "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry",
-            "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy")
+            "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy",
+            "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked")
 
 
 class OzError(RuntimeError):
@@ -94,6 +95,9 @@ def _load_library():
         "oz_group_create": (I32, [ctypes.POINTER(P), I32, P, P, P, P, P, P, P, P, P, SZ]),
         "oz_group_run": (I32, [P, P]),
         "oz_group_destroy": (None, [P]),
+        "oz_plan_caps": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "oz_blocked_workspace_bytes": (SZ, [P, I64, I64, I64]),
+        "oz_dgemm_blocked": (I32, [P, I32, I32, I64, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -165,6 +169,13 @@ def oz_plan_info(plan):
                 "moduli": [int(x) for x in mods[: q.value]]}
 
 
+def oz_plan_caps(plan):
+    """Returns (status, k_acc, k_rec)."""
+    a, r = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = _lib.oz_plan_caps(plan, ctypes.byref(a), ctypes.byref(r))
+    return st, a.value, r.value
+
+
 def oz_plan_destroy(plan) -> None:
     _lib.oz_plan_destroy(plan)
 
@@ -193,6 +204,16 @@ def oz_plane_geometry(plan, k_pad: int):
 def oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, workspace, workspace_bytes, stream) -> int:
     return _lib.oz_dgemm(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb), C,
                          int(ldc), workspace, int(workspace_bytes), stream)
+
+
+def oz_blocked_workspace_bytes(plan, m: int, n: int, k_slab: int) -> int:
+    return int(_lib.oz_blocked_workspace_bytes(plan, int(m), int(n), int(k_slab)))
+
+
+def oz_dgemm_blocked(plan, trans_a, trans_b, m, n, k, k_slab, A, lda, B, ldb, C, ldc, workspace, workspace_bytes,
+                     stream) -> int:
+    return _lib.oz_dgemm_blocked(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), int(k_slab), A, int(lda),
+                                 B, int(ldb), C, int(ldc), workspace, int(workspace_bytes), stream)
 
 
 def oz_dgemm_static(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
@@ -273,6 +294,7 @@ class Plan:
         _, info = oz_plan_info(h)
         self.q, self.bits, self.k_max = info["q"], info["bits"], info["k_max"]
         self.engine, self.moduli = info["engine"], info["moduli"]
+        _, self.k_acc, self.k_rec = oz_plan_caps(h)
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -308,6 +330,7 @@ class PlanFP(Plan):
         _, fi = oz_plan_info_fp(h)
         self.format = code
         self.bits, self.k_max, self.engine = info["bits"], info["k_max"], info["engine"]
+        _, self.k_acc, self.k_rec = oz_plan_caps(h)
         self.channels, self.q, self.k_cfg = fi["channels"], fi["gemms"], fi["k_cfg"]
         self.moduli, self.forms, self.bases, self.planes = fi["moduli"], fi["forms"], fi["bases"], fi["planes"]
 
@@ -358,6 +381,38 @@ def dgemm(A, B, plan: Plan | None = None, trans_a: bool = False, trans_b: bool =
                   B.data_ptr(), _ld(B), C.data_ptr(), _ld(C), ws.data_ptr(),
                   ws.numel(), _stream_handle(stream))
     _check(st, "oz_dgemm")
+    return C
+
+
+def _operands(A, B, trans_a, trans_b, what):
+    import torch
+    if A.dtype != torch.float64 or B.dtype != torch.float64 or not A.is_cuda or not B.is_cuda:
+        raise TypeError(f"{what} takes float64 CUDA tensors")
+    if A.dim() != 2 or B.dim() != 2 or (A.numel() and A.stride(1) != 1) or (B.numel() and B.stride(1) != 1):
+        raise ValueError(f"{what} takes 2-D tensors with unit inner stride")
+    m, k = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
+    k2, n = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} vs {k2}")
+    return m, n, k
+
+
+def dgemm_blocked(A, B, plan: Plan, k_slab: int, trans_a: bool = False, trans_b: bool = False, out=None, ws=None,
+                  stream=None):
+    """C = op(A) op(B) through oz_dgemm_blocked: the inner dimension in slabs
+    of k_slab terms, each slab's digits added into a running residue (the same
+    bits as ``dgemm`` wherever both apply; K up to ``plan.k_rec``, slabs up to
+    ``plan.k_acc``). The workspace holds one slab's planes."""
+    import torch
+    m, n, k = _operands(A, B, trans_a, trans_b, "dgemm_blocked")
+    C = out if out is not None else torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if ws is None:
+        nbytes = oz_blocked_workspace_bytes(plan.handle, m, n, max(min(int(k_slab), k), 1))
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
+    st = oz_dgemm_blocked(plan.handle, int(trans_a), int(trans_b), m, n, k, int(k_slab), A.data_ptr(), _ld(A),
+                          B.data_ptr(), _ld(B), C.data_ptr(), _ld(C), ws.data_ptr(), ws.numel(),
+                          _stream_handle(stream))
+    _check(st, "oz_dgemm_blocked")
     return C
 
 
@@ -611,6 +666,18 @@ class GroupedGemm:
 
     def run(self, stream=None):
         _check(_lib.oz_group_run(self.handle, _stream_handle(stream)), "oz_group_run")
+
+    def launches(self) -> int:
+        """Kernels one run launches: per group of alike plans, the split of A
+        (one kernel for long rows, one for short rows of at most 1024 padded
+        entries), column maxima, shifts and split of B, the GEMMs and the
+        Reconstruct."""
+        groups = {}
+        for p, (m, n, k) in zip(self.plans, self.shapes):
+            g = groups.setdefault((p.q, p.bits, tuple(p.moduli)), set())
+            if m and n and k:
+                g.add(round_up(k, 128) > 1024)
+        return sum(5 + len(kinds) for kinds in groups.values() if kinds)
 
     def capture(self, stream=None):
         """Record one run into a CUDA graph (replay() runs it)."""

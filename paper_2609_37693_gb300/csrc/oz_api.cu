@@ -152,6 +152,96 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
                        false);
 }
 
+// ---------------------------------------------------------------------------
+// Blocked call (Sec. "Slabs"): the shifts over the whole inner dimension, then
+// per slab of k_slab terms the planes of that slab and the GEMMs, whose
+// epilogues add the slab's digits into Y modulo m; one Reconstruct at the end.
+// ---------------------------------------------------------------------------
+
+extern "C" size_t oz_blocked_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k_slab) {
+  if (k_slab < 1) return 0;
+  return oz_workspace_bytes(plan, m, n, k_slab);
+}
+
+extern "C" oz_status oz_dgemm_blocked(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
+                                      int64_t k_slab, const double* A, int64_t lda, const double* B, int64_t ldb,
+                                      double* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!plan || m < 0 || n < 0 || k < 0 || k_slab < 1) return OZ_ERR_INVALID_ARG;
+  if ((trans_a != 0 && trans_a != 1) || (trans_b != 0 && trans_b != 1)) return OZ_ERR_INVALID_ARG;
+  const int64_t a_cols = trans_a ? m : k, b_cols = trans_b ? k : n;
+  if (lda < (a_cols > 1 ? a_cols : 1) || ldb < (b_cols > 1 ? b_cols : 1) || ldc < (n > 1 ? n : 1))
+    return OZ_ERR_INVALID_ARG;
+  if (k > plan->k_rec || k_slab > plan->k_acc) return OZ_ERR_K_TOO_LARGE;
+  if (m == 0 || n == 0) return OZ_OK;
+  if (!C || !aligned(C, 8)) return OZ_ERR_INVALID_ARG;
+  if (k > 0 && (!A || !B || !aligned(A, 8) || !aligned(B, 8))) return OZ_ERR_INVALID_ARG;
+  const int64_t kt = k_slab < k ? k_slab : (k > 0 ? k : 1);
+  Layout L;
+  make_layout(plan, m, n, kt, &L);
+  if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256)) return OZ_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  int32_t* flag = reinterpret_cast<int32_t*>(ws + L.flag);
+  cudaError_t e = cudaMemsetAsync(flag, 0, 16, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  if (k == 0) return cuda_status(cudaMemset2DAsync(C, (size_t)ldc * 8, 0, (size_t)n * 8, (size_t)m, st));
+
+  const OzTables& T = plan->tab;
+  const int bf16 = oz::engine_bf16(plan->engine);
+  int32_t* s = reinterpret_cast<int32_t*>(ws + L.s);
+  int32_t* t = reinterpret_cast<int32_t*>(ws + L.t);
+  uint64_t* colmax = reinterpret_cast<uint64_t*>(ws + L.colmax);
+  void* U = ws + L.u;
+  void* V = ws + L.v;
+  uint8_t* Y = reinterpret_cast<uint8_t*>(ws + L.y);
+  if (plan->is_fp && !plan->d_words) return OZ_ERR_CUDA;
+
+  // Scale over the whole inner dimension: rows of op(A), columns of op(B).
+  e = trans_a ? oz::launch_shifts_cols(T.bits, m, k, A, lda, s, flag, colmax, st)
+              : oz::launch_shifts_rows(T.bits, m, k, A, lda, s, flag, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+  e = trans_b ? oz::launch_shifts_rows(T.bits, n, k, B, ldb, t, flag, st)
+              : oz::launch_shifts_cols(T.bits, n, k, B, ldb, t, flag, colmax, st);
+  if (e != cudaSuccess) return OZ_ERR_CUDA;
+
+  const int64_t k_align = plan->is_fp ? oz::fp_k_align(plan->fp) : oz::kPadK;
+  for (int64_t h0 = 0; h0 < k; h0 += kt) {
+    const int64_t len = k - h0 < kt ? k - h0 : kt;
+    const int64_t k_pad = round_up(len, k_align);
+    // the slab: columns h0 .. h0 + len of op(A), rows of op(B)
+    const double* As = trans_a ? A + h0 * lda : A + h0;
+    const double* Bs = trans_b ? B + h0 : B + h0 * ldb;
+    const int mode = h0 > 0 ? oz::kEpiAccumulate : 0;
+    if (plan->is_fp) {
+      const OzFpTables& F = plan->fp;
+      uint8_t* U8 = static_cast<uint8_t*>(U);
+      uint8_t* V8 = static_cast<uint8_t*>(V);
+      e = oz::launch_split_fp(T, F, !trans_a, m, len, As, lda, L.m_pad, k_pad, s, U8, flag, colmax, st, true);
+      if (e == cudaSuccess)
+        e = oz::launch_split_fp(T, F, trans_b, n, len, Bs, ldb, L.n_pad, k_pad, t, V8, flag, colmax, st, true);
+      if (e == cudaSuccess)
+        e = oz::launch_gemm_fp(F, m, n, L.m_pad, L.n_pad, k_pad, U8, V8, reinterpret_cast<uint16_t*>(Y), L.ldy, mode,
+                               flag, st);
+    } else {
+      e = trans_a ? oz::launch_split_cols(T, m, len, As, lda, L.m_pad, k_pad, s, U, bf16, flag, colmax, st, true)
+                  : oz::launch_split_rows(T, m, len, As, lda, L.m_pad, k_pad, s, U, bf16, flag, st, true);
+      if (e == cudaSuccess)
+        e = trans_b ? oz::launch_split_rows(T, n, len, Bs, ldb, L.n_pad, k_pad, t, V, bf16, flag, st, true)
+                    : oz::launch_split_cols(T, n, len, Bs, ldb, L.n_pad, k_pad, t, V, bf16, flag, colmax, st, true);
+      if (e == cudaSuccess)
+        e = plan->engine == OZ_ENGINE_TC1
+                ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, k_pad, U, V, Y, L.ldy, mode, flag, st)
+            : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, k_pad, U, V, Y, L.ldy, mode, flag, st)
+                   : oz::launch_gemm_imma(T, m, n, k_pad, static_cast<const int8_t*>(U), L.m_pad * k_pad,
+                                          static_cast<const int8_t*>(V), L.n_pad * k_pad, Y, L.ldy, mode, st);
+    }
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+  }
+  e = plan->is_fp ? oz::launch_reconstruct16(T, m, n, reinterpret_cast<const uint16_t*>(Y), L.ldy, s, t, C, ldc, st)
+                  : oz::launch_reconstruct(T, m, n, Y, L.ldy, s, t, C, ldc, st);
+  return cuda_status(e);
+}
+
 extern "C" oz_status oz_query_status(void* workspace, void* stream) {
   if (!workspace) return OZ_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

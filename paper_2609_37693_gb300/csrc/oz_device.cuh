@@ -1,5 +1,6 @@
-// oz_device.cuh -- device helpers shared by the split kernels (INT8 and
-// float-format planes): the IEEE-field view of eq. convert.
+// oz_device.cuh -- device helpers shared by the kernels: the IEEE-field view
+// of eq. convert (split kernels, INT8 and float-format planes) and the
+// modular byte sum of the blocked call's epilogues.
 #pragma once
 
 #include <stdint.h>
@@ -42,6 +43,16 @@ static __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
     v = w > v ? w : v;
   }
   return v;
+}
+
+// (a + b) mod m in each byte, for bytes a, b in [0, m) and m < 256 given as
+// mm = m * 0x01010101: a - (m - b), plus m in the bytes where that borrows.
+// The GEMM epilogues of a blocked call add a slab's digits into the earlier
+// slabs' this way.
+static __device__ __forceinline__ uint32_t addmod_bytes(uint32_t a, uint32_t b, uint32_t mm) {
+  const uint32_t c = __vsub4(mm, b);
+  const uint32_t lt = __vcmpltu4(a, c);
+  return __vadd4(__vsub4(a, c), lt & mm);
 }
 
 }  // namespace oz

@@ -122,40 +122,45 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
                                                             int64_t nvec, int64_t len, const double* __restrict__ X,
                                                             int64_t ld, int64_t nvec_pad, int64_t k_pad,
                                                             int32_t* __restrict__ shifts, uint8_t* __restrict__ planes,
-                                                            int32_t* __restrict__ flag) {
+                                                            int32_t* __restrict__ flag, bool given) {
   __shared__ uint64_t red[8];
   __shared__ int32_t s_sh;
   const int64_t v = blockIdx.x;
   const int tid = threadIdx.x;
   const bool live = v < nvec;
   const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
-  uint64_t mx = 0;
-  uint32_t bad = 0;
-  if (live) {
-    for (int64_t h = tid; h < len; h += 256) {
-      uint64_t b = __ldg(row + h) & kAbsMask;
-      bad |= (uint32_t)((b >> 52) == 0x7ff);
-      mx = b > mx ? b : mx;
+  int32_t s;
+  if (given) {                      // the shift of the whole row is known (blocked call)
+    s = live ? shifts[v] : 0;
+  } else {
+    uint64_t mx = 0;
+    uint32_t bad = 0;
+    if (live) {
+      for (int64_t h = tid; h < len; h += 256) {
+        uint64_t b = __ldg(row + h) & kAbsMask;
+        bad |= (uint32_t)((b >> 52) == 0x7ff);
+        mx = b > mx ? b : mx;
+      }
     }
-  }
-  mx = warp_max_u64(mx);
-  bad = __any_sync(0xffffffffu, bad);
-  if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
-  __syncthreads();
-  if (tid == 0) {
-    uint64_t m = 0, anybad = 0;
-    for (int w = 0; w < 8; ++w) {
-      anybad |= red[w] >> 63;
-      uint64_t x = red[w] & kAbsMask;
-      m = x > m ? x : m;
+    mx = warp_max_u64(mx);
+    bad = __any_sync(0xffffffffu, bad);
+    if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t m = 0, anybad = 0;
+      for (int w = 0; w < 8; ++w) {
+        anybad |= red[w] >> 63;
+        uint64_t x = red[w] & kAbsMask;
+        m = x > m ? x : m;
+      }
+      if (anybad && flag) atomicOr(flag, 1);
+      int32_t s0 = live ? shift_from_maxbits(anybad ? 0 : m, bits) : 0;
+      s_sh = s0;
+      if (live) shifts[v] = s0;
     }
-    if (anybad && flag) atomicOr(flag, 1);
-    int32_t s = live ? shift_from_maxbits(anybad ? 0 : m, bits) : 0;
-    s_sh = s;
-    if (live) shifts[v] = s;
+    __syncthreads();
+    s = s_sh;
   }
-  __syncthreads();
-  const int32_t s = s_sh;
   const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
   const int64_t plane = nvec_pad * row_bytes;
   uint8_t* out_row = planes + v * row_bytes;
@@ -415,6 +420,7 @@ __device__ __forceinline__ Unit unit_coord(int t, int tiles_m, int tiles_n) {
 
 struct FpParams {
   int m, n, tiles_m, tiles_n, num_units, kblocks, m_pad, n_pad, raw;
+  int acc;           // add into the digits already in Y, modulo the channel's m (blocked call)
   uint32_t idesc;
   uint16_t* Y;
   int64_t ldy;       // row pitch of Y (entries)
@@ -612,6 +618,22 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
         for (int i4 = 0; i4 < C::HC / 8; ++i4) {
           uint32_t o4[4];
+          uint32_t prev[4] = {0u, 0u, 0u, 0u};
+          if (p.acc) {                       // the digits of the earlier slabs
+            if (vec) {
+              const uint4 w = reinterpret_cast<const uint4*>(dst)[i4];
+              prev[0] = w.x;
+              prev[1] = w.y;
+              prev[2] = w.z;
+              prev[3] = w.w;
+            } else {
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                  if (col0 + 8 * i4 + 2 * ii + j < p.n) prev[ii] |= (uint32_t)dst[8 * i4 + 2 * ii + j] << (16 * j);
+            }
+          }
 #pragma unroll
           for (int ii = 0; ii < 4; ++ii) {
             uint32_t o = 0;
@@ -625,6 +647,10 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const float q = fmaf(tt, invm, 12582912.0f) - 12582912.0f;
                 y = fmaf(-q, mf, tt);
                 y = y < 0.f ? y + mf : y;
+              }
+              if (p.acc) {
+                y += (float)((prev[ii] >> (16 * j)) & 0xffffu);
+                y = y >= mf ? y - mf : y;
               }
               o |= (__float_as_uint(y + 8388608.0f) & 0xffffu) << (16 * j);
             }
@@ -828,14 +854,16 @@ cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y,
 template <int CB>
 cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                      const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts, uint8_t* planes,
-                     int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+                     int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
   if (contiguous) {
     split_fp_rows_kernel<CB><<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad, k_pad,
-                                                                 shifts, planes, flag);
+                                                                 shifts, planes, flag, given);
     return cudaGetLastError();
   }
-  cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
-  if (e != cudaSuccess) return e;
+  if (!given) {
+    cudaError_t e = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
+    if (e != cudaSuccess) return e;
+  }
   dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 32));
   split_fp_cols_kernel<CB><<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   return cudaGetLastError();
@@ -845,12 +873,15 @@ cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int
 
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
-                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
   if (nvec_pad == 0) return cudaSuccess;
   switch (f.code_bits) {
-    case 8: return split_fp<8>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
-    case 6: return split_fp<6>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
-    case 4: return split_fp<4>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st);
+    case 8:
+      return split_fp<8>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st, given);
+    case 6:
+      return split_fp<6>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st, given);
+    case 4:
+      return split_fp<4>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax, st, given);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -888,7 +919,8 @@ cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, in
   p.kblocks = (int)(k_pad / C::KSTAGE);
   p.m_pad = (int)m_pad;
   p.n_pad = (int)n_pad;
-  p.raw = raw;
+  p.raw = raw & kEpiRaw;
+  p.acc = (raw & kEpiAccumulate) != 0;
   if (MX) {
     // block-scaled: scale factor ids 0, A = B = E2M1 (1), both K-major, N >> 3,
     // UE8M0 scales (bit 23), M >> 4, K = 64 per instruction

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "oz_internal.h"
+#include "oz_device.cuh"
 
 namespace oz {
 namespace {
@@ -67,7 +68,9 @@ __device__ __forceinline__ uint32_t epilogue(int32_t w, uint32_t m, uint32_t mag
 __global__ void __launch_bounds__(256, 1)
 gemm_imma_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n, int64_t k_pad, const int8_t* __restrict__ U,
                  int64_t u_plane, const int8_t* __restrict__ V, int64_t v_plane, uint8_t* __restrict__ Y,
-                 int64_t ldy, int raw) {
+                 int64_t ldy, int mode) {
+  const int raw = mode & kEpiRaw;
+  const bool accum = (mode & kEpiAccumulate) != 0;   // blocked call: add into Y modulo m
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -172,9 +175,25 @@ gemm_imma_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n, int64
     const uint8_t* src = so + row * kOutPitch + cb;
     uint8_t* dst = Yq + gi * ldy + gj;
     if (vec_ok && gj + 16 <= n) {
-      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+      uint4 o = *reinterpret_cast<const uint4*>(src);
+      if (accum) {
+        const uint32_t mm = mq * 0x01010101u;
+        const uint4 old = *reinterpret_cast<const uint4*>(dst);
+        o.x = addmod_bytes(o.x, old.x, mm);
+        o.y = addmod_bytes(o.y, old.y, mm);
+        o.z = addmod_bytes(o.z, old.z, mm);
+        o.w = addmod_bytes(o.w, old.w, mm);
+      }
+      *reinterpret_cast<uint4*>(dst) = o;
     } else {
-      for (int e = 0; e < 16 && gj + e < n; ++e) dst[e] = src[e];
+      for (int e = 0; e < 16 && gj + e < n; ++e) {
+        uint32_t y = src[e];
+        if (accum) {
+          y += dst[e];
+          y = y >= mq ? y - mq : y;
+        }
+        dst[e] = (uint8_t)y;
+      }
     }
   }
 }

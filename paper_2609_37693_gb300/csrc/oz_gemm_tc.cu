@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "oz_internal.h"
+#include "oz_device.cuh"
 
 namespace oz {
 namespace {
@@ -264,8 +265,48 @@ __device__ __forceinline__ Coord tile_coord(int t, int tiles_m, int tiles_n) {
   return c;
 }
 
+// One thread's 128 digits of a tile row (one byte each, packed in words) to
+// Y: whole 16-byte runs up to `left` (the columns of the row from here to n)
+// rounded up to 16 when the row pitch is a multiple of 16 (bytes past n are
+// never read), byte stores otherwise. acc: add into the digits in Y modulo m.
+__device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, int left, bool runs, int acc,
+                                             uint32_t m) {
+  if (runs) {
+    const int chunks = min(8, (left + 15) >> 4);
+    const uint32_t mm = m * 0x01010101u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i < chunks) {
+        uint4 o = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+        if (acc) {
+          const uint4 old = reinterpret_cast<const uint4*>(dst)[i];
+          o.x = addmod_bytes(o.x, old.x, mm);
+          o.y = addmod_bytes(o.y, old.y, mm);
+          o.z = addmod_bytes(o.z, old.z, mm);
+          o.w = addmod_bytes(o.w, old.w, mm);
+        }
+        reinterpret_cast<uint4*>(dst)[i] = o;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (4 * i + j < left) {
+          uint32_t y = (w[i] >> (8 * j)) & 0xffu;
+          if (acc) {
+            y += dst[4 * i + j];
+            y = y >= m ? y - m : y;
+          }
+          dst[4 * i + j] = (uint8_t)y;
+        }
+  }
+}
+
 struct Params {
   int m, n, tiles_m, tiles_n, num_tiles, kblocks, m_pad, n_pad, raw;
+  int acc;           // add into the digits already in Y, modulo m (blocked call)
   uint8_t* Y;
   int64_t ldy;       // row pitch of Y
   int32_t* status;
@@ -462,21 +503,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (row < p.m && col0 < p.n) {
         const uint32_t* outw = acc8;
         uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-        if ((p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
-          // whole 16-byte runs up to n rounded up to 16: the row pitch leaves room,
-          // and bytes past n are never read
-          const int chunks = min(8, (p.n - col0 + 15) >> 4);
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (i < chunks)
-              reinterpret_cast<uint4*>(dst)[i] = make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
-        }
+        store_digits(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
+                     p.acc, T.m[c.q]);
       }
     }
   }
@@ -720,20 +748,8 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         if (row < p.m && col0 < p.n) {
           const uint32_t* outw = acc8 + hh * 32;
           uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-          if ((p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0) {
-            const int chunks = min(8, (p.n - col0 + 15) >> 4);   // 16-byte runs up to n rounded up
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (i < chunks)
-                reinterpret_cast<uint4*>(dst)[i] =
-                    make_uint4(outw[4 * i], outw[4 * i + 1], outw[4 * i + 2], outw[4 * i + 3]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (col0 + 4 * i + j < p.n) dst[4 * i + j] = (uint8_t)(outw[i] >> (8 * j));
-          }
+          store_digits(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
+                       p.acc, T.m[c.q]);
         }
       }
     }
@@ -1049,7 +1065,8 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   p.kblocks = (int)(k_pad / BK);
   p.m_pad = (int)m_pad;
   p.n_pad = (int)n_pad;
-  p.raw = raw;
+  p.raw = raw & kEpiRaw;
+  p.acc = (raw & kEpiAccumulate) != 0;
   p.Y = Y;
   p.ldy = ldy;
   p.status = status;
@@ -1115,7 +1132,8 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
   p.kblocks = (int)(k_pad / BK);
   p.m_pad = (int)m_pad;
   p.n_pad = (int)n_pad;
-  p.raw = raw;
+  p.raw = raw & kEpiRaw;
+  p.acc = (raw & kEpiAccumulate) != 0;
   p.Y = Y;
   p.ldy = ldy;
   p.status = status;

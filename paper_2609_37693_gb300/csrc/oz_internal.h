@@ -80,7 +80,9 @@ struct oz_plan_s {
   int Q;             // INT8: moduli = GEMMs; float formats: channels
   int bits;
   int engine;        // resolved engine (never AUTO)
-  int64_t k_max;
+  int64_t k_max;     // min(k_acc, k_rec): the largest K of one accumulation (eq. caps)
+  int64_t k_acc;     // accumulation cap: the largest slab a blocked call may take
+  int64_t k_rec;     // window cap (eq. ov-crtgen): the largest K of a blocked call
   OzTables tab;      // moduli and CRT constants
   int is_fp;
   int gemms;         // low-precision GEMMs per product
@@ -94,8 +96,9 @@ struct oz_plan_s {
 
 // One product of a grouped call (oz_group_create): its operands, its part of
 // the workspace and, per phase, the first block (or unit) of the group's
-// launch that belongs to it. Device memory; 64-byte aligned for the maps.
-struct alignas(64) OzGroupProblem {
+// launch that belongs to it. Device memory, aligned as its tensor maps
+// require (128 bytes; the table starts on a 256-byte boundary).
+struct OzGroupProblem {
   CUtensorMap mapA, mapB;            // residue planes of A and B (TMA, GEMM phase)
   const double* A;
   const double* B;
@@ -145,6 +148,10 @@ constexpr int kTileM = 128;       // M tile of the GEMM engines; m_pad is a mult
 constexpr int kPadRows = 256;     // row padding of the residue planes
 constexpr int kPadK = 128;        // k padding of the residue planes (entries)
 
+// Epilogue modes of the GEMM launchers (their `raw` argument, a bit set).
+constexpr int kEpiRaw = 1;         // store W mod m in [0, m) instead of the CRT digit
+constexpr int kEpiAccumulate = 2;  // add the slab's value into the one already in Y, modulo m
+
 // oz_dgemm with the TC engine's GEMM optionally forced onto one CTA per tile
 // (oz_api.cu): products that run concurrently on several streams use it.
 oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, const double* A,
@@ -162,12 +169,14 @@ inline int64_t fp_row_bytes(const OzFpTables& f, int64_t k_pad) { return f.code_
 inline int64_t round_up(int64_t x, int64_t r) { return (x + r - 1) / r * r; }
 
 // Launchers (defined in the .cu files). Each returns cudaGetLastError().
+// given: the shifts are already in `shifts` (taken over a longer vector, as
+// in a blocked call); the split then neither scans for the maximum nor flags.
 cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
-                              int32_t* flag, cudaStream_t st);
+                              int32_t* flag, cudaStream_t st, bool given = false);
 cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
-                              int32_t* flag, uint64_t* colmax, cudaStream_t st);
+                              int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given = false);
 cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_pad, const int8_t* U,
                              int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int64_t ldy, int raw,
                              cudaStream_t st);
@@ -194,7 +203,7 @@ cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* 
 // float-format path: planes of codes, 16-bit digits
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
-                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st);
+                            uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given = false);
 cudaError_t launch_gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const uint8_t* U, const uint8_t* V, uint16_t* Y, int64_t ldy, int raw, int32_t* status,
                            cudaStream_t st);
@@ -203,5 +212,8 @@ cudaError_t launch_reconstruct16(const OzTables& t, int64_t m, int64_t n, const 
 // shared by the split kernels: shifts of strided vectors (colmax must be zeroed)
 cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
                                int32_t* flag, uint64_t* colmax, cudaStream_t st);
+// shifts of contiguous vectors (rows), one warp per row; flags non-finite entries
+cudaError_t launch_shifts_rows(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
+                               int32_t* flag, cudaStream_t st);
 
 }  // namespace oz

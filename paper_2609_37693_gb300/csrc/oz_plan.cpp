@@ -219,6 +219,8 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   int64_t k_acc = oz::engine_bf16(resolved) ? (int64_t)INT32_MAX : (int64_t)2147483647 / ((int64_t)r * r);
   int64_t k_rec = kappa_rec(P, beta);
   p->k_max = k_acc < k_rec ? k_acc : k_rec;
+  p->k_acc = k_acc;
+  p->k_rec = k_rec;
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }
 
   if (!oz::fill_crt_tables(&p->tab, kModuli, Q, beta)) { delete p; return OZ_ERR_UNSUPPORTED; }
@@ -236,6 +238,13 @@ extern "C" oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_ma
   if (moduli) {
     for (int i = 0; i < OZ_MAX_MODULI; ++i) moduli[i] = i < plan->Q ? plan->tab.m[i] : 0;
   }
+  return OZ_OK;
+}
+
+extern "C" oz_status oz_plan_caps(oz_plan plan, int64_t* k_acc, int64_t* k_rec) {
+  if (!plan) return OZ_ERR_INVALID_ARG;
+  if (k_acc) *k_acc = plan->k_acc;
+  if (k_rec) *k_rec = plan->k_rec;
   return OZ_OK;
 }
 

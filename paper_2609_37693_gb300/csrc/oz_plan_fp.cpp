@@ -321,6 +321,8 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   }
   const int64_t k_acc = rho > 0 ? (1ll << 24) / (rho * rho) : (int64_t)1 << 40;
   p->k_max = std::min(lo, k_acc);
+  p->k_acc = k_acc;
+  p->k_rec = lo;
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }
   // codes: host values and device code tables (plane p, class c at plane_off[p] + c)
   size_t total = 0;

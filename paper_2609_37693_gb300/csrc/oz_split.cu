@@ -104,40 +104,45 @@ template <bool kBF16, int NP>
 __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                           const double* __restrict__ X, int64_t ld, int64_t nvec_pad, int64_t k_pad,
                                           int32_t* __restrict__ shifts, void* __restrict__ planes,
-                                          int32_t* __restrict__ flag) {
+                                          int32_t* __restrict__ flag, bool given) {
   __shared__ uint64_t red[8];
   __shared__ int32_t s_sh;
   const int tid = threadIdx.x;
   const bool live = v < nvec;
   const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
 
-  uint64_t mx = 0;
-  uint32_t bad = 0;
-  if (live) {
-    for (int64_t h = tid; h < len; h += 256) {
-      uint64_t b = __ldg(row + h) & kAbsMask;
-      bad |= (uint32_t)((b >> 52) == 0x7ff);
-      mx = b > mx ? b : mx;
+  int32_t s;
+  if (given) {                      // block-uniform: the shift of the whole row is known
+    s = live ? shifts[v] : 0;
+  } else {
+    uint64_t mx = 0;
+    uint32_t bad = 0;
+    if (live) {
+      for (int64_t h = tid; h < len; h += 256) {
+        uint64_t b = __ldg(row + h) & kAbsMask;
+        bad |= (uint32_t)((b >> 52) == 0x7ff);
+        mx = b > mx ? b : mx;
+      }
     }
-  }
-  mx = warp_max_u64(mx);
-  bad = __any_sync(0xffffffffu, bad);
-  if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
-  __syncthreads();
-  if (tid == 0) {
-    uint64_t m = 0, anybad = 0;
-    for (int w = 0; w < 8; ++w) {
-      anybad |= red[w] >> 63;
-      uint64_t x = red[w] & kAbsMask;
-      m = x > m ? x : m;
+    mx = warp_max_u64(mx);
+    bad = __any_sync(0xffffffffu, bad);
+    if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t m = 0, anybad = 0;
+      for (int w = 0; w < 8; ++w) {
+        anybad |= red[w] >> 63;
+        uint64_t x = red[w] & kAbsMask;
+        m = x > m ? x : m;
+      }
+      if (anybad && flag) atomicOr(flag, 1);
+      int32_t s0 = live ? shift_from_maxbits(anybad ? 0 : m, T.bits) : 0;
+      s_sh = s0;
+      if (live) shifts[v] = s0;
     }
-    if (anybad && flag) atomicOr(flag, 1);
-    int32_t s = live ? shift_from_maxbits(anybad ? 0 : m, T.bits) : 0;
-    s_sh = s;
-    if (live) shifts[v] = s;
+    __syncthreads();
+    s = s_sh;
   }
-  __syncthreads();
-  const int32_t s = s_sh;
 
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
@@ -193,25 +198,30 @@ template <bool kBF16, int NP>
 __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                                const double* __restrict__ X, int64_t ld, int64_t nvec_pad,
                                                int64_t k_pad, int32_t* __restrict__ shifts,
-                                               void* __restrict__ planes, int32_t* __restrict__ flag) {
+                                               void* __restrict__ planes, int32_t* __restrict__ flag, bool given) {
   const int lane = threadIdx.x & 31;
   const bool live = v < nvec;
   const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + (live ? v * ld : 0);
-  uint64_t mx = 0;
-  uint32_t bad = 0;
-  if (live) {
-    for (int64_t h = lane; h < len; h += 32) {
-      uint64_t b = __ldg(row + h) & kAbsMask;
-      bad |= (uint32_t)((b >> 52) == 0x7ff);
-      mx = b > mx ? b : mx;
+  int32_t s;
+  if (given) {
+    s = live ? shifts[v] : 0;
+  } else {
+    uint64_t mx = 0;
+    uint32_t bad = 0;
+    if (live) {
+      for (int64_t h = lane; h < len; h += 32) {
+        uint64_t b = __ldg(row + h) & kAbsMask;
+        bad |= (uint32_t)((b >> 52) == 0x7ff);
+        mx = b > mx ? b : mx;
+      }
     }
-  }
-  mx = warp_max_u64(mx);
-  bad = __any_sync(0xffffffffu, bad);
-  const int32_t s = live ? shift_from_maxbits(bad ? 0 : mx, T.bits) : 0;
-  if (lane == 0) {
-    if (bad && flag) atomicOr(flag, 1);
-    if (live) shifts[v] = s;
+    mx = warp_max_u64(mx);
+    bad = __any_sync(0xffffffffu, bad);
+    s = live ? shift_from_maxbits(bad ? 0 : mx, T.bits) : 0;
+    if (lane == 0) {
+      if (bad && flag) atomicOr(flag, 1);
+      if (live) shifts[v] = s;
+    }
   }
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
@@ -266,9 +276,10 @@ __global__ void __launch_bounds__(256) split_rows_warp_kernel(const __grid_const
                                                               int64_t len, const double* __restrict__ X, int64_t ld,
                                                               int64_t nvec_pad, int64_t k_pad,
                                                               int32_t* __restrict__ shifts,
-                                                              void* __restrict__ planes, int32_t* __restrict__ flag) {
+                                                              void* __restrict__ planes, int32_t* __restrict__ flag,
+                                                              bool given) {
   const int64_t v = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  split_row_warp<kBF16, NP>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+  split_row_warp<kBF16, NP>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
 // Grouped, short rows: block b holds rows 8 (b - rows_begin) .. + 7 of its problem.
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(256) split_rows_warp_grouped_kernel(const __gr
   const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
   const OzGroupProblem& P = probs[pi];
   const int64_t v = (b - P.rows_begin) * 8 + (threadIdx.x >> 5);
-  split_row_warp<kBF16, NP>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag);
+  split_row_warp<kBF16, NP>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
 template <bool kBF16, int NP>
@@ -288,8 +299,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__
                                                          const double* __restrict__ X, int64_t ld,
                                                          int64_t nvec_pad, int64_t k_pad,
                                                          int32_t* __restrict__ shifts, void* __restrict__ planes,
-                                                         int32_t* __restrict__ flag) {
-  split_row<kBF16, NP>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+                                                         int32_t* __restrict__ flag, bool given) {
+  split_row<kBF16, NP>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
 // Grouped: block b is row b - rows_begin of its problem's A.
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(256) split_rows_grouped_kernel(const __grid_co
   const int64_t b = blockIdx.x;
   const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
   const OzGroupProblem& P = probs[pi];
-  split_row<kBF16, NP>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag);
+  split_row<kBF16, NP>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,6 +375,31 @@ __global__ void shifts_grouped_kernel(const OzGroupProblem* __restrict__ probs, 
   const OzGroupProblem& P = probs[pi];
   const int64_t j = (b - P.sh_begin) * blockDim.x + threadIdx.x;
   if (j < P.n) P.t[j] = shift_from_maxbits(P.colmax[j], beta);
+}
+
+// Shifts of contiguous vectors without a split (a blocked call takes them over
+// the whole row before splitting it slab by slab): one warp per row.
+__global__ void __launch_bounds__(256) shifts_rows_kernel(int64_t nvec, int64_t len, const double* __restrict__ X,
+                                                          int64_t ld, int beta, int32_t* __restrict__ shifts,
+                                                          int32_t* __restrict__ flag) {
+  const int64_t v = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= nvec) return;                 // the whole warp shares v
+  const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + v * ld;
+  uint64_t mx = 0;
+  uint32_t bad = 0;
+#pragma unroll 4
+  for (int64_t h = lane; h < len; h += 32) {
+    const uint64_t b = __ldg(row + h) & kAbsMask;
+    bad |= (uint32_t)((b >> 52) == 0x7ff);
+    mx = b > mx ? b : mx;
+  }
+  mx = warp_max_u64(mx);
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (bad && flag) atomicOr(flag, 1);
+    shifts[v] = shift_from_maxbits(bad ? 0 : mx, beta);
+  }
 }
 
 // Pass 2: 64 (h) x 64 (vector) tiles; residues go through shared memory so
@@ -457,30 +493,38 @@ __global__ void __launch_bounds__(256) split_cols_grouped_kernel(const __grid_co
 
 cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
-                              int32_t* flag, cudaStream_t st) {
+                              int32_t* flag, cudaStream_t st, bool given) {
   if (nvec_pad == 0) return cudaSuccess;
   const bool np4 = t.bits <= 60;                 // |a'| < 2^60: four 15-bit pieces
   if (k_pad <= 1024) {                           // short rows: one warp per row
     const unsigned g = (unsigned)(nvec_pad / 8);
     if (bf16 && np4)
-      split_rows_warp_kernel<true, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+      split_rows_warp_kernel<true, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                         given);
     else if (bf16)
-      split_rows_warp_kernel<true, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+      split_rows_warp_kernel<true, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                         given);
     else if (np4)
-      split_rows_warp_kernel<false, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+      split_rows_warp_kernel<false, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                         given);
     else
-      split_rows_warp_kernel<false, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+      split_rows_warp_kernel<false, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                         given);
     return cudaGetLastError();
   }
   dim3 grid((unsigned)nvec_pad);
   if (bf16 && np4)
-    split_rows_kernel<true, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    split_rows_kernel<true, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                      given);
   else if (bf16)
-    split_rows_kernel<true, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    split_rows_kernel<true, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                      given);
   else if (np4)
-    split_rows_kernel<false, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    split_rows_kernel<false, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                      given);
   else
-    split_rows_kernel<false, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag);
+    split_rows_kernel<false, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
+                                                      given);
   return cudaGetLastError();
 }
 
@@ -497,12 +541,21 @@ cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double
   return cudaGetLastError();
 }
 
+cudaError_t launch_shifts_rows(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
+                               int32_t* flag, cudaStream_t st) {
+  if (nvec == 0) return cudaSuccess;
+  shifts_rows_kernel<<<(unsigned)((nvec + 7) / 8), 256, 0, st>>>(nvec, len, X, ld, bits, shifts, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
-                              int32_t* flag, uint64_t* colmax, cudaStream_t st) {
+                              int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
   if (nvec_pad == 0) return cudaSuccess;
-  cudaError_t e0 = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
-  if (e0 != cudaSuccess) return e0;
+  if (!given) {
+    cudaError_t e0 = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
+    if (e0 != cudaSuccess) return e0;
+  }
   dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
   const bool np4 = t.bits <= 60;
   if (bf16 && np4)

@@ -161,3 +161,45 @@ def test_grouped_refuses_unsupported_plans_before_any_work():
         assert st == want and not h.value
     arr = (P * 1)(tc.handle)
     assert oz._lib.oz_grouped_workspace_bytes(1, arr, mnk) > 0
+
+
+@pytest.mark.parametrize("q", range(14, 21))
+def test_plan_caps_match_the_oracle(q):
+    """oz_plan_caps reports the two caps of eq. caps separately: on the IMMA
+    engine k_acc is the INT32 accumulation cap and k_rec the window of eq.
+    ov-crtgen, as the oracle computes them; the TC engine drains its FP32 slabs
+    and has no accumulation cap below 2^31."""
+    mods = oracle.max_product_moduli(q, 239)
+    k_rec, k_acc, _ = oracle.caps(mods, 53)
+    p = oz.Plan(q, 53, 1, oz.OZ_ENGINE_IMMA)
+    assert (p.k_acc, p.k_rec) == (k_acc, k_rec)
+    t = oz.Plan(q, 53, 1, oz.OZ_ENGINE_TC)
+    assert (t.k_acc, t.k_rec) == (2**31 - 1, k_rec)
+
+
+def test_paper_int8_caps():
+    """Sec. "INT4 and INT8": K_max = 151 647 at Q = 16 comes from the INT32
+    accumulator; the window alone admits 159 819 at beta = 53."""
+    p = oz.Plan(16, 53, 8192, oz.OZ_ENGINE_IMMA)
+    assert (p.k_acc, p.k_rec, p.k_max) == (151647, 159819, 151647)
+
+
+def test_blocked_argument_errors_are_caught_on_the_host():
+    p = oz.Plan(16, 53, 100000, oz.OZ_ENGINE_IMMA)
+    h = p.handle
+    fake = 1 << 20  # never dereferenced: every case fails its checks before a launch
+    ws = oz.oz_blocked_workspace_bytes(h, 8, 8, 64)
+    assert ws == p.workspace_bytes(8, 8, 64)
+    assert oz.oz_blocked_workspace_bytes(h, 8, 8, 0) == 0
+
+    def call(k, k_slab, lda=None, wsb=ws, A=fake):
+        return oz.oz_dgemm_blocked(h, 0, 0, 8, 8, k, k_slab, A, lda or k, fake, 8, fake, 8, fake, wsb, None)
+
+    assert call(159820, 64) == oz.OZ_ERR_K_TOO_LARGE        # above the window at beta = 53
+    assert call(152000, 151648) == oz.OZ_ERR_K_TOO_LARGE    # a slab above the INT32 cap
+    assert call(152000, 0) == oz.OZ_ERR_INVALID_ARG
+    assert call(1000, 64, lda=999) == oz.OZ_ERR_INVALID_ARG
+    assert call(1000, 64, wsb=ws - 1) == oz.OZ_ERR_WORKSPACE
+    assert call(1000, 64, A=fake + 4) == oz.OZ_ERR_INVALID_ARG
+    assert call(1000, 256) == oz.OZ_ERR_WORKSPACE            # workspace sized for slabs of k_pad 128
+    assert oz.oz_dgemm_blocked(h, 0, 0, 0, 8, 8, 8, None, 8, None, 8, None, 8, None, 0, None) == oz.OZ_OK
