@@ -543,8 +543,12 @@ def run_blocked(args, rank, world, local):
     A, B = synth.phi_pair(n, n, k, args.phi, seed=rank)
     Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
     del A, B
-    plan = oz.Plan(args.q, args.bits, min(k, kt), oz.OZ_ENGINE_TC if args.engine == "auto" else
-                   {"imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC, "tc1": oz.OZ_ENGINE_TC1}[args.engine])
+    engine = {"auto": oz.OZ_ENGINE_TC, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC,
+              "tc1": oz.OZ_ENGINE_TC1}[args.engine]
+    # the window must admit the whole K; an IMMA plan is made for one slab (its
+    # INT32 cap), at 53 bits unless given, and the call checks K against k_rec
+    plan = oz.Plan(args.q, args.bits or (53 if engine == oz.OZ_ENGINE_IMMA else 0),
+                   min(k, kt) if engine == oz.OZ_ENGINE_IMMA else k, engine)
     Cb = torch.empty((n, n), dtype=torch.float64, device=dev)
     wsb = torch.empty(oz.oz_blocked_workspace_bytes(plan.handle, n, n, kt), dtype=torch.uint8, device=dev)
     s0 = torch.cuda.current_stream(dev)
@@ -582,7 +586,7 @@ def run_blocked(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
             "config": {"workload": f"m=n={n}, k={k} in {nslabs} slabs of {kt}, phi={args.phi}, Q={plan.q}, "
-                                   f"beta={plan.bits}, TC engine",
+                                   f"beta={plan.bits}, engine {args.engine}",
                        "unblocked_ms": ms_u,
                        "unblocked_tflops": flops / (ms_u * 1e-3) / 1e12 if ms_u else None,
                        "blocked_over_unblocked": ms / ms_u if ms_u else None,

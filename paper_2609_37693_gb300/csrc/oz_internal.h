@@ -27,12 +27,10 @@ struct OzTables {
   uint32_t inv[OZ_TABLE_CAP];            // (P/m)^-1 mod m: CRT coefficient
   float invm[OZ_TABLE_CAP];              // 1/m rounded to fp32: quotient estimate
   float mf[OZ_TABLE_CAP];                // m as fp32
-  float hif[OZ_TABLE_CAP];               // ceil(m/2): a residue >= this maps to r - m
-  float lof[OZ_TABLE_CAP];               // -floor(m/2): a residue below this maps to r + m
-  float c15f[OZ_TABLE_CAP];              // 2^15 mod m, 2^30, 2^45, 2^60 mod m, each as the
-  float c30f[OZ_TABLE_CAP];              // representative nearest zero (|c| <= 119)
-  float c45f[OZ_TABLE_CAP];
-  float c60f[OZ_TABLE_CAP];
+  float c13f[OZ_TABLE_CAP];              // 2^13 mod m, 2^26, 2^39, 2^52 mod m, each as the
+  float c26f[OZ_TABLE_CAP];              // representative nearest zero (|c| <= 119)
+  float c39f[OZ_TABLE_CAP];
+  float c52f[OZ_TABLE_CAP];
   uint32_t Mk[OZ_TABLE_CAP][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
   // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd

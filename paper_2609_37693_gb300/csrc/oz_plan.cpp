@@ -155,13 +155,11 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
     t.inv[q] = inverse_mod(mk_mod_m, m);
     t.invm[q] = 1.0f / (float)m;
     t.mf[q] = (float)m;
-    t.hif[q] = (float)((m + 1) / 2);
-    t.lof[q] = -(float)(m / 2);
     auto centred = [m](uint32_t c) { return (float)(c >= (m + 1) / 2 ? (int)c - (int)m : (int)c); };
-    t.c15f[q] = centred(pow2_mod(15, m));
-    t.c30f[q] = centred(pow2_mod(30, m));
-    t.c45f[q] = centred(pow2_mod(45, m));
-    t.c60f[q] = centred(pow2_mod(60, m));
+    t.c13f[q] = centred(pow2_mod(13, m));
+    t.c26f[q] = centred(pow2_mod(26, m));
+    t.c39f[q] = centred(pow2_mod(39, m));
+    t.c52f[q] = centred(pow2_mod(52, m));
     for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
   }
   t.npairs = (Q + 1) / 2;

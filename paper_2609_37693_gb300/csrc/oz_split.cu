@@ -8,16 +8,21 @@
 // Reduce: a' = trunc(x 2^s) taken straight from the IEEE fields: with the
 // 53-bit significand f and exponent E, x 2^s = f 2^(E - 1075 + s), so a'
 // is f shifted left or right (the right shift truncates toward zero). The
-// residue modulo m is formed in exact fp32 arithmetic (twice the integer
-// issue rate): a' (|a'| < 2^64) is cut once per entry into signed 15-bit pieces
-// P0..P4 (P0..P3 when beta <= 60, so that |a'| < 2^60), and for each modulus
-//   y = P0 + P1 c15 + P2 c30 + P3 c45 + P4 c60,   c_k = 2^k mod m, |c_k| <= 119,
-// is congruent to a' with |y| < 2^24, so every step is exact. One quotient
-// q = rint(y / m) (an fp32 estimate, off by at most one near a tie) gives
-// r = y - q m exactly, and two compares map r to the representative nearest
-// zero, [-floor(m/2), ceil(m/2) - 1] (the paper reduces a one-byte modulus
+// residue modulo m (m <= 239) is formed in exact fp32 arithmetic (twice the
+// integer issue rate): |a'| < 2^64 is cut once per entry into signed 13-bit
+// pieces P0..P4 (P0..P3 when beta <= 52), P0 biased by 1/4, and per modulus
+//   y' = P0 + 1/4 + P1 c13 + P2 c26 + P3 c39 + P4 c52,   c_k = 2^k mod m, |c_k| <= 119,
+// a multiple of 1/4 congruent to a' + 1/4 with |y'| < 8191 * 477 + 1 < 2^22,
+// so every partial sum is exact. One quotient q = rint(y' * fl(1/m)) (an
+// fma against the 1.5 * 2^23 rounding constant) is the integer nearest to
+// y'/m: the estimate is off by at most |y'/m| 2^-24 < 1/(4m), and y'/m is at
+// least 1/(4m) away from every half-integer (2y' - (2k+1)m is an odd
+// multiple of 1/2 for odd m, and 1/2 away from an even integer for even m).
+// So r = y' - q m - 1/4 is exactly the representative nearest zero,
+// [-floor(m/2), ceil(m/2) - 1]: the bias sends the tie of an even modulus
+// to -m/2, and no compare is needed. (The paper reduces a one-byte modulus
 // in two 32-bit Barrett steps, Sec. "Around the GEMMs"; this is the same
-// reduction in the fp32 pipe).
+// reduction in the fp32 pipe.)
 //
 // Planes are written K-major, Q planes of nvec_pad x k_pad entries, int8
 // (two's complement, IMMA engine) or bf16 (TC engine; integers below 2^8 are
@@ -30,8 +35,9 @@
 namespace oz {
 namespace {
 
-// Signed 15-bit pieces of a' as exact floats: a' = sum_i P_i 2^(15 i), NP of
-// them (NP = 4 covers |a'| < 2^60).
+// Signed 13-bit pieces of a' as exact floats: a' = sum_i P_i 2^(13 i), NP of
+// them (NP = 4 covers |a'| < 2^52, NP = 5 every |a'| < 2^64); P_0 carries the
+// bias of 1/4.
 template <int NP>
 struct Pieces {
   float p[NP];
@@ -45,50 +51,49 @@ __device__ __forceinline__ Pieces<NP> pieces_of(uint64_t bits, int32_t s) {
   Pieces<NP> P;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
-    const uint32_t v = (uint32_t)(t.mag >> (15 * i)) & 0x7FFFu;
+    const uint32_t v = (uint32_t)(t.mag >> (13 * i)) & 0x1FFFu;
     P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
   }
+  P.p[0] += 0.25f;
   return P;
 }
 
 // The constants of one modulus, held in registers while a tile is reduced.
 struct ModConst {
-  float c15, c30, c45, c60, invm, m, hi, lo;
+  float c13, c26, c39, c52, invm, m;
 };
 
 __device__ __forceinline__ ModConst mod_const(const OzTables& T, int q) {
   ModConst c;
-  c.c15 = T.c15f[q];
-  c.c30 = T.c30f[q];
-  c.c45 = T.c45f[q];
-  c.c60 = T.c60f[q];
+  c.c13 = T.c13f[q];
+  c.c26 = T.c26f[q];
+  c.c39 = T.c39f[q];
+  c.c52 = T.c52f[q];
   c.invm = T.invm[q];
   c.m = T.mf[q];
-  c.hi = T.hif[q];
-  c.lo = T.lof[q];
   return c;
 }
 
-// Representative nearest zero of a' modulo one modulus, as an exact float.
+// Representative nearest zero of a' modulo one modulus plus 1/4, as an exact
+// float (r + 1/4; see the header).
 template <int NP>
-__device__ __forceinline__ float residue_f(const ModConst& c, const Pieces<NP>& P) {
-  float y = fmaf(P.p[3], c.c45, fmaf(P.p[2], c.c30, fmaf(P.p[1], c.c15, P.p[0])));
-  if constexpr (NP == 5) y = fmaf(P.p[4], c.c60, y);
-  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;
-  float r = fmaf(-qf, c.m, y);
-  r = r >= c.hi ? r - c.m : r;
-  r = r < c.lo ? r + c.m : r;
-  return r;
+__device__ __forceinline__ float residue_q(const ModConst& c, const Pieces<NP>& P) {
+  float y = fmaf(P.p[1], c.c13, P.p[0]);
+  y = fmaf(P.p[2], c.c26, y);
+  y = fmaf(P.p[3], c.c39, y);
+  if constexpr (NP == 5) y = fmaf(P.p[4], c.c52, y);
+  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;   // rint(y' / m), exact
+  return fmaf(-qf, c.m, y);
 }
 
-// bf16 bit pattern of an exact small integer held in a float (|r| < 2^8 needs
-// at most 8 significand bits, so the upper half of the float is exact).
-__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
-  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+// bf16 bit pattern of the integers r = rq - 1/4 (rq from residue_q): |r| < 2^8
+// needs at most 8 significand bits, so the upper half of the float is exact.
+__device__ __forceinline__ uint32_t bf16_pair(float rq_lo, float rq_hi) {
+  return __byte_perm(__float_as_uint(rq_lo - 0.25f), __float_as_uint(rq_hi - 0.25f), 0x7632u);
 }
 
-// two's-complement byte of an exact small integer held in a float
-__device__ __forceinline__ uint32_t int8_bits(float r) { return __float_as_uint(r + 12582912.0f); }
+// two's-complement byte of r = rq - 1/4: rq + 1.5 * 2^23 rounds to r + 1.5 * 2^23
+__device__ __forceinline__ uint32_t int8_bits(float rq) { return __float_as_uint(rq + 12582912.0f); }
 
 __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d) {
   return __byte_perm(__byte_perm(int8_bits(a), int8_bits(b), 0x0040u), __byte_perm(int8_bits(c), int8_bits(d), 0x0040u),
@@ -172,7 +177,7 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
         const ModConst mc = mod_const(T, q);
         float r[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = residue_f(mc, P[e]);
+        for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
         const int64_t off = (int64_t)q * plane + v * k_pad + h0;
         if (kBF16) {
           uint4 o;
@@ -251,7 +256,7 @@ __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int
         const ModConst mc = mod_const(T, q);
         float r[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = residue_f(mc, P[e]);
+        for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
         const int64_t off = (int64_t)q * plane + v * k_pad + h0;
         if (kBF16) {
           uint4 o;
@@ -438,7 +443,7 @@ __device__ __forceinline__ void split_cols_block(const OzTables& T, int64_t bx, 
     const ModConst mc = mod_const(T, q);
     float r[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = residue_f(mc, P[e]);
+    for (int e = 0; e < 16; ++e) r[e] = residue_q(mc, P[e]);
     if (kBF16) {
 #pragma unroll
       for (int w = 0; w < 8; ++w) tb[jl * kPitchWords + hg * 8 + w] = bf16_pair(r[2 * w], r[2 * w + 1]);
@@ -495,7 +500,7 @@ cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, cons
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
                               int32_t* flag, cudaStream_t st, bool given) {
   if (nvec_pad == 0) return cudaSuccess;
-  const bool np4 = t.bits <= 60;                 // |a'| < 2^60: four 15-bit pieces
+  const bool np4 = t.bits <= 52;                 // |a'| < 2^52: four 13-bit pieces
   if (k_pad <= 1024) {                           // short rows: one warp per row
     const unsigned g = (unsigned)(nvec_pad / 8);
     if (bf16 && np4)
@@ -557,7 +562,7 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
     if (e0 != cudaSuccess) return e0;
   }
   dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
-  const bool np4 = t.bits <= 60;
+  const bool np4 = t.bits <= 52;   // four 13-bit pieces
   if (bf16 && np4)
     split_cols_kernel<true, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   else if (bf16)
@@ -576,7 +581,7 @@ cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* p
                                       int64_t total_rows, int64_t total_wrows, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   if (total_rows > INT32_MAX || total_wrows > INT32_MAX) return cudaErrorInvalidValue;
-  const bool np4 = t.bits <= 60;
+  const bool np4 = t.bits <= 52;   // four 13-bit pieces
   if (nlong > 0 && total_rows > 0) {
     if (np4)
       split_rows_grouped_kernel<true, 4><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
@@ -600,7 +605,7 @@ cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* p
   if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, count);
   if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, count, t.bits);
   if (total_sc > 0) {
-    if (t.bits <= 60)
+    if (t.bits <= 52)
       split_cols_grouped_kernel<true, 4><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
     else
       split_cols_grouped_kernel<true, 5><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);

@@ -79,7 +79,7 @@ def test_blocked_float_formats(fmt):
     """Float-format plans: slabs within the FP32 accumulation cap, the 16-bit
     digits added modulo each channel's modulus; bit for bit the unblocked
     product and the oracle's."""
-    plan = oz.PlanFP(fmt, 1000)
+    plan = oz.PlanFP(fmt, 3000, 53)
     m, n, k = 200, 300, 3000
     A, B = synth.phi_pair(m, n, k, 1.0, seed=11)
     Ad, Bd = _dev(A), _dev(B)
