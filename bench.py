@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-mode", default="grouped", choices=["grouped", "streams"],
                     help="batch: one launch per phase over grouped products, or products on autotuned streams")
+    ap.add_argument("--e2e-rows", type=int, default=0, help="e2e: rows of a block of C (0: about n/4)")
+    ap.add_argument("--e2e-cols", type=int, default=0, help="e2e: columns of a block of C (0: about n/4)")
     ap.add_argument("--k", type=int, default=65536, help="blocked: the inner dimension")
     ap.add_argument("--k-slab", type=int, default=8192, help="blocked: terms per slab")
     return ap.parse_args()
@@ -361,7 +363,7 @@ def run_ours(args, rank, world, local):
     A_pin = torch.from_numpy(A_h).pin_memory()
     B_pin = torch.from_numpy(B_h).pin_memory()
     C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    hg = oz.HostGemm(plan, n, n, n, 0, dev)
+    hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
     hg(A_pin, B_pin, C_pin, stream)
     torch.cuda.synchronize()
     e2e_steps = max(2, min(args.steps, 5))
@@ -375,6 +377,7 @@ def run_ours(args, rank, world, local):
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
     e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
     e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
+    hg_rows, hg_cols = hg.rows, hg.cols
     del hg
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----
@@ -440,7 +443,8 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
                     "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms,
-                    "api": "oz_dgemm_host (pinned host A, B, C; row chunks overlap copies and phases)",
+                    "api": "oz_dgemm_host (pinned host A, B, C; blocks of C overlap copies and phases)",
+                    "block": [hg_rows, hg_cols],
                     "equals_device_result": e2e_exact},
             "gpu_launches": oz.launches_per_dgemm(False, False) * args.steps,
             "clocks": clk,

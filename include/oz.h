@@ -239,22 +239,26 @@ OZ_API oz_status oz_dgemm_blocked(oz_plan plan, int trans_a, int trans_b, int64_
  * oz_host_workspace_bytes / oz_dgemm_host -- C = A B (row-major, no
  * transposes) with A, B and C in HOST memory (pinned memory lets the copies
  * overlap; pageable memory works but serialises them). The product is the one
- * oz_dgemm computes. The rows of A and C are processed in chunks of
- * rows_per_chunk rows (0 picks about m/4, a multiple of 256): B is copied to
- * the device and split once; then, for each chunk, the copy of the next A
- * chunk (stream_h2d) and the copy back of the previous C chunk (stream_d2h)
- * run under the current chunk's split, GEMMs and reconstruct (stream). When
- * the call returns the work is queued; once `stream` has finished, C holds
- * the result (the copy streams join it through events). The three streams
- * must be distinct; the workspace (device, 256-byte aligned) holds B, two A
- * and two C chunks, the planes and the residues of one chunk. Non-finite
- * input is reported by oz_query_status on this workspace.
+ * oz_dgemm computes. C is cut into blocks of rows_per_chunk rows by
+ * cols_per_chunk columns (0 picks about a quarter of m or n, a multiple of
+ * 256). The copy stream brings the first row chunk of A, then B column chunk
+ * by column chunk, then the other row chunks of A; each column chunk of B is
+ * split once, when it has arrived, and each row chunk of A when its block row
+ * starts; each block's GEMMs and reconstruct run on `stream` and its copy back
+ * on stream_d2h, under the next block's work. The first GEMMs thus wait for
+ * one chunk of each operand only. When the call returns the work is queued;
+ * once `stream` has finished, C holds the result (the copy streams join it
+ * through events). The three streams must be distinct; the workspace (device,
+ * 256-byte aligned) holds B, two A chunks, two C blocks, the planes of one A
+ * chunk and of all of B, and the residues of one block row. Non-finite input
+ * is reported by oz_query_status on this workspace.
  */
-OZ_API size_t oz_host_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t rows_per_chunk);
+OZ_API size_t oz_host_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t rows_per_chunk,
+                                      int64_t cols_per_chunk);
 OZ_API oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                                const double* B, int64_t ldb, double* C, int64_t ldc, int64_t rows_per_chunk,
-                               void* workspace, size_t workspace_bytes, void* stream, void* stream_h2d,
-                               void* stream_d2h);
+                               int64_t cols_per_chunk, void* workspace, size_t workspace_bytes, void* stream,
+                               void* stream_h2d, void* stream_d2h);
 
 /* ---- Many products of uneven shapes in one call. ---- */
 

@@ -85,11 +85,11 @@ def _load_library():
         "oz_status_str": (ctypes.c_char_p, [I32]),
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
         "oz_batched_workspace_bytes": (SZ, [I32, P, P, I32]),
-        "oz_host_workspace_bytes": (SZ, [P, I64, I64, I64, I64]),
+        "oz_host_workspace_bytes": (SZ, [P, I64, I64, I64, I64, I64]),
         "oz_plan_create_fp": (I32, [ctypes.POINTER(P), I32, I64, I32]),
         "oz_plan_info_fp": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I64), P, P, P,
                                   ctypes.POINTER(I32), P, SZ]),
-        "oz_dgemm_host": (I32, [P, I64, I64, I64, P, I64, P, I64, P, I64, I64, P, SZ, P, P, P]),
+        "oz_dgemm_host": (I32, [P, I64, I64, I64, P, I64, P, I64, P, I64, I64, I64, P, SZ, P, P, P]),
         "oz_dgemm_batched": (I32, [I32, P, P, P, P, P, P, P, P, P, P, SZ, P, I32]),
         "oz_grouped_workspace_bytes": (SZ, [I32, P, P]),
         "oz_group_create": (I32, [ctypes.POINTER(P), I32, P, P, P, P, P, P, P, P, P, SZ]),
@@ -236,15 +236,16 @@ def oz_dgemm_batched(count, plans, mnk, trans, A, lda, B, ldb, C, ldc, workspace
                                  int(workspace_bytes), streams, int(nstreams))
 
 
-def oz_host_workspace_bytes(plan, m, n, k, rows_per_chunk=0) -> int:
-    return int(_lib.oz_host_workspace_bytes(plan, int(m), int(n), int(k), int(rows_per_chunk)))
+def oz_host_workspace_bytes(plan, m, n, k, rows_per_chunk=0, cols_per_chunk=0) -> int:
+    return int(_lib.oz_host_workspace_bytes(plan, int(m), int(n), int(k), int(rows_per_chunk), int(cols_per_chunk)))
 
 
-def oz_dgemm_host(plan, m, n, k, A, lda, B, ldb, C, ldc, rows_per_chunk, workspace, workspace_bytes, stream,
-                  stream_h2d, stream_d2h) -> int:
+def oz_dgemm_host(plan, m, n, k, A, lda, B, ldb, C, ldc, rows_per_chunk, cols_per_chunk, workspace, workspace_bytes,
+                  stream, stream_h2d, stream_d2h) -> int:
     """A, B, C are HOST pointers (pinned memory overlaps the copies)."""
     return _lib.oz_dgemm_host(plan, int(m), int(n), int(k), A, int(lda), B, int(ldb), C, int(ldc),
-                              int(rows_per_chunk), workspace, int(workspace_bytes), stream, stream_h2d, stream_d2h)
+                              int(rows_per_chunk), int(cols_per_chunk), workspace, int(workspace_bytes), stream,
+                              stream_h2d, stream_d2h)
 
 
 def oz_query_status(workspace, stream) -> int:
@@ -701,15 +702,18 @@ class GroupedGemm:
 
 
 class HostGemm:
-    """C = A B for host (CPU) float64 tensors through oz_dgemm_host: the copies
-    to and from the device overlap the phases of neighbouring row chunks. Pin
-    the host tensors (tensor.pin_memory()) for the overlap to happen."""
+    """C = A B for host (CPU) float64 tensors through oz_dgemm_host: C in blocks
+    of rows_per_chunk x cols_per_chunk, the copies to and from the device
+    overlapping the phases of neighbouring blocks. Pin the host tensors
+    (tensor.pin_memory()) for the overlap to happen."""
 
-    def __init__(self, plan: Plan, m: int, n: int, k: int, rows_per_chunk: int = 0, device=None):
+    def __init__(self, plan: Plan, m: int, n: int, k: int, rows_per_chunk: int = 0, device=None,
+                 cols_per_chunk: int = 0):
         torch = _import_torch()
-        self.plan, self.m, self.n, self.k, self.rows = plan, m, n, k, rows_per_chunk
+        self.plan, self.m, self.n, self.k = plan, m, n, k
+        self.rows, self.cols = rows_per_chunk, cols_per_chunk
         self.device = torch.device(device or "cuda")
-        nbytes = oz_host_workspace_bytes(plan.handle, m, n, k, rows_per_chunk)
+        nbytes = oz_host_workspace_bytes(plan.handle, m, n, k, rows_per_chunk, cols_per_chunk)
         if nbytes == 0:
             raise OzError(OZ_ERR_INVALID_ARG, "oz_host_workspace_bytes")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -720,7 +724,7 @@ class HostGemm:
         torch = _import_torch()
         s = torch.cuda.current_stream(self.device) if stream is None else stream
         st = oz_dgemm_host(self.plan.handle, self.m, self.n, self.k, A.data_ptr(), _ld(A), B.data_ptr(),
-                           _ld(B), C.data_ptr(), _ld(C), self.rows, self.ws.data_ptr(),
+                           _ld(B), C.data_ptr(), _ld(C), self.rows, self.cols, self.ws.data_ptr(),
                            self.ws.numel(), ctypes.c_void_p(s.cuda_stream), ctypes.c_void_p(self.h2d.cuda_stream),
                            ctypes.c_void_p(self.d2h.cuda_stream))
         _check(st, "oz_dgemm_host")

@@ -1,5 +1,7 @@
-"""oz_dgemm_host (host-resident operands, copies overlapped with the phases of
-neighbouring row chunks) gives the product oz_dgemm gives, bit for bit."""
+"""oz_dgemm_host (host-resident operands, C in blocks, copies overlapped with
+the phases of neighbouring blocks) gives the product oz_dgemm gives, bit for
+bit, whatever the block shape (ragged last blocks, edges not multiples of 16,
+one block, k = 0)."""
 import numpy as np
 import pytest
 
@@ -14,15 +16,17 @@ if not torch.cuda.is_available():
 import paper_2609_37693_gb300 as oz  # noqa: E402
 
 
-@pytest.mark.parametrize("m,n,k,rows", [(1000, 700, 900, 256), (513, 300, 2000, 0), (64, 64, 64, 0),
-                                        (2048, 1024, 1500, 512), (700, 129, 0, 300)])
-def test_host_path_equals_device_path(m, n, k, rows):
-    plan = oz.Plan(16, 0, max(k, 1))
+@pytest.mark.parametrize("engine", [oz.OZ_ENGINE_TC, oz.OZ_ENGINE_TC1, oz.OZ_ENGINE_IMMA])
+@pytest.mark.parametrize("m,n,k,rows,cols", [(1000, 700, 900, 256, 0), (513, 300, 2000, 0, 0), (64, 64, 64, 0, 0),
+                                             (2048, 1024, 1500, 512, 256), (700, 129, 0, 300, 50),
+                                             (777, 1000, 700, 300, 333), (300, 520, 1024, 4096, 4096)])
+def test_host_path_equals_device_path(engine, m, n, k, rows, cols):
+    plan = oz.Plan(16, 0, max(k, 1), engine)
     A, B = synth.phi_pair(m, n, k, 1.0, seed=m + n)
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
     Ch = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
-    hg = oz.HostGemm(plan, m, n, k, rows)
+    hg = oz.HostGemm(plan, m, n, k, rows, cols_per_chunk=cols)
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
     ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
@@ -31,14 +35,14 @@ def test_host_path_equals_device_path(m, n, k, rows):
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E3M2", "E2M1"])
-@pytest.mark.parametrize("m,n,k,rows", [(1000, 700, 900, 256), (300, 257, 1000, 0)])
-def test_host_path_float_formats(fmt, m, n, k, rows):
+@pytest.mark.parametrize("m,n,k,rows,cols", [(1000, 700, 900, 256, 0), (300, 257, 1000, 0, 100)])
+def test_host_path_float_formats(fmt, m, n, k, rows, cols):
     plan = oz.PlanFP(fmt, max(k, 1))
     A, B = synth.phi_pair(m, n, k, 1.0, seed=m + k)
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
     Ch = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
-    hg = oz.HostGemm(plan, m, n, k, rows)
+    hg = oz.HostGemm(plan, m, n, k, rows, cols_per_chunk=cols)
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
     ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
