@@ -375,11 +375,18 @@ typedef struct oz_group_s* oz_group;
  *     copy; the matrix pointers are fixed from then on (new values in the same
  *     buffers need no new group). Arrays are host arrays of length count; the
  *     matrices and the workspace (256-byte aligned, owned by the caller, which
- *     must keep it alive while the group is used) are device memory.
- *   oz_group_run: enqueues the phases on the stream; asynchronous and
- *     capturable into a CUDA graph. oz_query_status(workspace, stream)
- *     reports non-finite input and bounded-wait time-outs as for oz_dgemm.
- *   oz_group_destroy: frees the host-side handle (NULL is accepted).
+ *     must keep it alive while the group is used) are device memory. The
+ *     group also creates two CUDA streams and a few events per set of alike
+ *     plans, on the current device.
+ *   oz_group_run: enqueues the phases; asynchronous and capturable into a
+ *     CUDA graph. The sets of alike plans run side by side, and within a set
+ *     the splits of A and of B, on the group's streams, which start after the
+ *     work already queued on `stream` and which `stream` waits for at the
+ *     end. oz_query_status(workspace, stream) reports non-finite input and
+ *     bounded-wait time-outs as for oz_dgemm. Runs of one group must not
+ *     overlap (they share the workspace and streams).
+ *   oz_group_destroy: frees the handle, its streams and events (NULL is
+ *     accepted).
  */
 OZ_API size_t oz_grouped_workspace_bytes(int count, const oz_plan* plans, const int64_t* mnk);
 OZ_API oz_status oz_group_create(oz_group* out, int count, const oz_plan* plans, const int64_t* mnk,

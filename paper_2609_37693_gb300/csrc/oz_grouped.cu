@@ -4,6 +4,12 @@
 // every product as one persistent kernel, and one reconstruct. Each block (or
 // GEMM unit) finds its product by a binary search over the products' first
 // block indices in a device table written once, at create time.
+//
+// Products of different tables form separate groups, and the groups run side
+// by side on streams the group object owns (forked from and joined back to
+// the caller's stream, so a run can be captured into a CUDA graph); within a
+// group the splits of A and of B run side by side too. The GEMMs are the
+// one-CTA-per-tile kind, which may share SMs with other kernels.
 #include <stdint.h>
 #include <string.h>
 
@@ -114,6 +120,14 @@ struct oz_group_s {
   // products with k == 0: C = 0
   std::vector<double*> zero_c;
   std::vector<int64_t> zero_m, zero_n, zero_ldc;
+  // per group: a stream for the A side (then GEMMs and reconstruct) and one
+  // for the B side; events: fork, per group the B side done and the group done
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  ~oz_group_s() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaStream_t st : streams) cudaStreamDestroy(st);
+  }
 };
 
 extern "C" size_t oz_grouped_workspace_bytes(int count, const oz_plan* plans, const int64_t* mnk) {
@@ -249,6 +263,25 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
     delete g;
     return OZ_ERR_CUDA;
   }
+  const size_t ng = g->groups.size();
+  for (size_t i = 0; i < 2 * ng; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete g;
+      return OZ_ERR_CUDA;
+    }
+    g->streams.push_back(st);
+  }
+  for (size_t i = 0; i < 1 + 2 * ng; ++i) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      delete g;
+      return OZ_ERR_CUDA;
+    }
+    g->events.push_back(ev);
+  }
   *out = g;
   return OZ_OK;
 }
@@ -267,16 +300,27 @@ extern "C" oz_status oz_group_run(oz_group g, void* stream) {
     if (e != cudaSuccess) return OZ_ERR_CUDA;
   }
   int32_t* status = reinterpret_cast<int32_t*>(g->ws);
-  for (const Group& G : g->groups) {
+  cudaEvent_t fork = g->events[0];
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess && r != cudaSuccess) e = r; };
+  chk(cudaEventRecord(fork, st));
+  for (size_t gi = 0; gi < g->groups.size(); ++gi) {
+    const Group& G = g->groups[gi];
     const OzTables& T = G.plan->tab;
     const OzGroupProblem* probs = table + G.first;
-    e = oz::launch_split_rows_grouped(T, probs, G.count, G.nlong, G.total_rows, G.total_wrows, st);
-    if (e == cudaSuccess) e = oz::launch_split_cols_grouped(T, probs, G.count, G.total_cm, G.total_sh, G.total_sc, st);
-    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, st);
-    if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.count, G.total_rec, st);
-    if (e != cudaSuccess) return OZ_ERR_CUDA;
+    cudaStream_t sa = g->streams[2 * gi], sb = g->streams[2 * gi + 1];
+    cudaEvent_t b_done = g->events[1 + 2 * gi], done = g->events[2 + 2 * gi];
+    chk(cudaStreamWaitEvent(sa, fork, 0));
+    chk(cudaStreamWaitEvent(sb, fork, 0));
+    if (e == cudaSuccess) e = oz::launch_split_rows_grouped(T, probs, G.count, G.nlong, G.total_rows, G.total_wrows, sa);
+    if (e == cudaSuccess) e = oz::launch_split_cols_grouped(T, probs, G.count, G.total_cm, G.total_sh, G.total_sc, sb);
+    chk(cudaEventRecord(b_done, sb));
+    chk(cudaStreamWaitEvent(sa, b_done, 0));
+    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, sa);
+    if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.count, G.total_rec, sa);
+    chk(cudaEventRecord(done, sa));
+    chk(cudaStreamWaitEvent(st, done, 0));
   }
-  return OZ_OK;
+  return e == cudaSuccess ? OZ_OK : OZ_ERR_CUDA;
 }
 
 extern "C" void oz_group_destroy(oz_group g) { delete g; }
