@@ -630,6 +630,68 @@ def autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4, 8, 16), bits: int 
     return best[1], timings
 
 
+def blocked_candidates(k: int, bits: int = 53, formats=("E4M3", "E2M1"), slabs=(8192, 16384, 32768)):
+    """Configurations that can run a product with inner dimension k through
+    the blocked call at `bits` kept bits, as (label, plan, k_slab): the INT8
+    plan of the least Q on the TC engine (whole K, and the given slab lengths
+    below K), and each float format's plan for its largest frozen K_cfg whose
+    window admits k, in slabs of its accumulation cap. Every candidate keeps
+    the same bits, so every one returns the same C."""
+    out = []
+    try:
+        p = Plan(0, bits, max(k, 1), OZ_ENGINE_TC)
+    except OzError:
+        p = None
+    if p is not None:
+        out.append(("int8 q=%d" % p.q, p, max(k, 1)))
+        for s in slabs:
+            if s < k:
+                out.append(("int8 q=%d slab=%d" % (p.q, s), p, s))
+    for f in formats:
+        for kcfg in (16384, 8192):
+            try:
+                q = PlanFP(f, kcfg, bits)
+            except OzError:
+                continue
+            if k <= q.k_rec:
+                out.append(("%s (%d GEMMs) slab=%d" % (f, q.q, min(q.k_acc, max(k, 1))), q, min(q.k_acc, max(k, 1))))
+                break
+    return out
+
+
+def autotune_blocked(A, B, candidates=None, bits: int = 53, reps: int = 2, stream=None):
+    """The configuration trade-off of a blocked product (plane format, the
+    GEMM count it implies, slab length): time C = A B through
+    oz_dgemm_blocked for each candidate (label, plan, k_slab) -- by default
+    blocked_candidates(K, bits) -- and return (label, plan, k_slab) of the
+    fastest with {label: ms}."""
+    torch = _import_torch()
+    m, n, k = _operands(A, B, False, False, "autotune_blocked")
+    cands = candidates if candidates is not None else blocked_candidates(k, bits)
+    if not cands:
+        raise OzError(OZ_ERR_K_TOO_LARGE, "autotune_blocked")
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    s = torch.cuda.current_stream(A.device) if stream is None else stream
+    timings, best = {}, None
+    for label, plan, k_slab in cands:
+        nbytes = oz_blocked_workspace_bytes(plan.handle, m, n, max(min(int(k_slab), k), 1))
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
+        dgemm_blocked(A, B, plan, k_slab, out=C, ws=ws, stream=s)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            dgemm_blocked(A, B, plan, k_slab, out=C, ws=ws, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize(A.device)
+            ts.append(e0.elapsed_time(e1))
+        timings[label] = min(ts)
+        if best is None or timings[label] < timings[best[0]]:
+            best = (label, plan, k_slab)
+        del ws
+    return best, timings
+
+
 class GroupedGemm:
     """count products C_i = A_i B_i (float64 CUDA tensors, row-major) through
     oz_group_create / oz_group_run: one launch per phase over all products of

@@ -127,3 +127,22 @@ def test_blocked_edges_and_nonfinite():
     A[4, 650] = 1.0
     oz.dgemm_blocked(_dev(A), _dev(B), plan, 256, ws=ws)
     assert oz.query_status(ws) == oz.OZ_OK
+
+
+def test_autotuned_configurations_agree():
+    """The configuration trade-off (plane format and its GEMM count, slab
+    length): every candidate keeps beta = 53 bits, so every one returns the
+    oracle's bits, and the autotuner returns one of them with its timing."""
+    m, n, k = 160, 96, 3000
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=21)
+    Ad, Bd = _dev(A), _dev(B)
+    cands = oz.blocked_candidates(k, 53, slabs=(1024,))
+    labels = [c[0] for c in cands]
+    assert any(l.startswith("int8") for l in labels) and any(l.startswith("E4M3") for l in labels)
+    ref = _bits(oracle.dgemm(A, B, cands[0][1].moduli, 53))
+    for label, plan, k_slab in cands:
+        C = oz.dgemm_blocked(Ad, Bd, plan, k_slab)
+        torch.cuda.synchronize()
+        assert np.array_equal(_bits(C.cpu().numpy()), ref), label
+    (label, plan, k_slab), times = oz.autotune_blocked(Ad, Bd, cands, reps=1)
+    assert label in times and set(times) == set(labels)
