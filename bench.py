@@ -364,9 +364,10 @@ def run_ours(args, rank, world, local):
     B_pin = torch.from_numpy(B_h).pin_memory()
     C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
     hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
-    hg(A_pin, B_pin, C_pin, stream)
+    for _ in range(2):
+        hg(A_pin, B_pin, C_pin, stream)
     torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args.steps, 10))
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)

@@ -49,7 +49,8 @@ extern "C" {
 
 #define OZ_MAX_MODULI 20   /* largest Q the library accepts */
 #define OZ_MIN_MODULI 9    /* smallest Q the library accepts */
-#define OZ_MAX_BITS 64     /* largest bit budget beta (|A'| < 2^beta) */
+#define OZ_MAX_BITS 80     /* largest bit budget beta (|A'| < 2^beta) of an INT8 plan */
+#define OZ_MAX_BITS_FP 64  /* largest bit budget of a float-format plan */
 
 typedef enum {
   OZ_OK = 0,
@@ -92,7 +93,11 @@ typedef struct oz_plan_s* oz_plan;
  *                largest product (for Q >= 9 these are prefixes of one list).
  *   bits         beta, the bits kept per row/column maximum (eq. convert uses
  *                53). 0 picks the largest beta <= OZ_MAX_BITS with
- *                2 k_hint (2^beta - 1)^2 < P.
+ *                2 k_hint (2^beta - 1)^2 < P. Above 53 the operands are
+ *                widened (Sec. "Not True Emulation of DGEMM", Example
+ *                widened): rows and columns whose entries span at most
+ *                2^(beta - 53) convert without loss, and the product is then
+ *                fl(AB) exactly.
  *   k_hint       the largest inner dimension the caller intends to use (>= 1).
  *                The plan is refused with OZ_ERR_K_TOO_LARGE if the window
  *                does not hold at k_hint.
@@ -120,7 +125,8 @@ OZ_API oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, i
  * so each GEMM's FP32 accumulator is exact (eq. ov-accgen).
  *   format   an oz_format value.
  *   k_hint   the largest inner dimension the caller intends to use.
- *   bits     as for oz_plan_create (0: the largest beta <= 64 the window allows).
+ *   bits     as for oz_plan_create, up to OZ_MAX_BITS_FP (0: the largest beta
+ *            <= OZ_MAX_BITS_FP the window allows).
  * The plan owns a small device table of codes (allocated here on the current
  * device, freed by oz_plan_destroy). Without a CUDA device the plan is still
  * made and describes the configuration (oz_plan_info_fp), but products on it

@@ -42,7 +42,8 @@ FORMATS = {"E4M3": OZ_FMT_E4M3, "E2M3": OZ_FMT_E2M3, "E3M2": OZ_FMT_E3M2, "E2M1"
 
 OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
-OZ_MAX_BITS = 64
+OZ_MAX_BITS = 80
+OZ_MAX_BITS_FP = 64
 OZ_STATIC_SCRATCH_BYTES = 32 << 20
 
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",

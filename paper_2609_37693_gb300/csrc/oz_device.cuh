@@ -30,8 +30,26 @@ static __device__ __forceinline__ Trunc truncate(uint64_t bits, int32_t s) {
   uint64_t f = bits & ((1ull << 52) - 1);
   uint64_t mant = eb ? (f | (1ull << 52)) : f;
   int sh = (eb ? eb - 1075 : -1074) + s;   // a' = mant * 2^sh, |a'| < 2^beta <= 2^64
-  if (sh >= 0) t.mag = mant << sh;         // sh <= 11 when beta <= 64
+  if (sh >= 0) t.mag = mant << sh;         // sh <= 11 when beta <= 64 (wider: truncate_wide)
   else t.mag = (-sh) >= 64 ? 0ull : (mant >> (-sh));
+  return t;
+}
+
+// The same for a widened budget (beta up to 84): |a'| < 2^84 needs 128 bits.
+struct TruncWide {
+  unsigned __int128 mag;
+  uint32_t neg;
+};
+
+static __device__ __forceinline__ TruncWide truncate_wide(uint64_t bits, int32_t s) {
+  TruncWide t;
+  t.neg = (uint32_t)(bits >> 63);
+  int eb = (int)((bits >> 52) & 0x7ff);
+  uint64_t f = bits & ((1ull << 52) - 1);
+  uint64_t mant = eb ? (f | (1ull << 52)) : f;
+  int sh = (eb ? eb - 1075 : -1074) + s;   // a' = mant * 2^sh, |a'| < 2^beta <= 2^84
+  if (sh >= 0) t.mag = (unsigned __int128)mant << sh;   // sh <= 31
+  else t.mag = (-sh) >= 64 ? 0 : (unsigned __int128)(mant >> (-sh));
   return t;
 }
 

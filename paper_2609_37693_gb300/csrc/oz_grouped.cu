@@ -74,7 +74,7 @@ bool same_tables(const oz_plan a, const oz_plan b) {
 
 bool plan_ok(const oz_plan p) {
   return p && !p->is_fp && oz::engine_bf16(p->engine) && p->tab.limbs <= 4 && p->tab.npairs >= 5 &&
-         p->tab.npairs <= 8;
+         p->tab.npairs <= 8 && p->tab.bits <= 64;
 }
 
 // Layout of the whole workspace: status word, table, column maxima, parts.

@@ -31,6 +31,8 @@ struct OzTables {
   float c26f[OZ_TABLE_CAP];              // representative nearest zero (|c| <= 119)
   float c39f[OZ_TABLE_CAP];
   float c52f[OZ_TABLE_CAP];
+  float c12f[6][OZ_TABLE_CAP];           // 2^(12 i) mod m, i = 1..6, nearest zero: the
+                                          // 12-bit pieces of widened operands (beta > 64)
   uint32_t Mk[OZ_TABLE_CAP][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
   // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd

@@ -160,6 +160,7 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
     t.c26f[q] = centred(pow2_mod(26, m));
     t.c39f[q] = centred(pow2_mod(39, m));
     t.c52f[q] = centred(pow2_mod(52, m));
+    for (int i = 0; i < 6; ++i) t.c12f[i][q] = centred(pow2_mod(12 * (i + 1), m));
     for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
   }
   t.npairs = (Q + 1) / 2;

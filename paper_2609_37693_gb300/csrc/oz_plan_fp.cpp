@@ -216,7 +216,7 @@ bool fill_crt_tables(OzTables* t, const uint32_t* moduli, int Q, int bits);
 extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint, int bits) {
   if (!out) return OZ_ERR_INVALID_ARG;
   *out = nullptr;
-  if (k_hint < 1 || bits < 0 || bits > OZ_MAX_BITS) return OZ_ERR_INVALID_ARG;
+  if (k_hint < 1 || bits < 0 || bits > OZ_MAX_BITS_FP) return OZ_ERR_INVALID_ARG;
   std::map<int64_t, int> code_of;
   int e_s = 0;
   if (!alphabet(format, &code_of, &e_s)) return OZ_ERR_UNSUPPORTED;
@@ -303,7 +303,7 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   for (uint32_t m : moduli) u_mul(&P, m);
   int beta = bits;
   if (beta == 0) {
-    for (beta = OZ_MAX_BITS; beta >= 1; --beta)
+    for (beta = OZ_MAX_BITS_FP; beta >= 1; --beta)
       if (u_cmp(u_window(k_hint, beta), P) < 0) break;
     if (beta < 1) { delete p; return OZ_ERR_K_TOO_LARGE; }
   } else if (u_cmp(u_window(k_hint, beta), P) >= 0) {

@@ -13,7 +13,9 @@
 // pieces P0..P4 (P0..P3 when beta <= 52), P0 biased by 1/4, and per modulus
 //   y' = P0 + 1/4 + P1 c13 + P2 c26 + P3 c39 + P4 c52,   c_k = 2^k mod m, |c_k| <= 119,
 // a multiple of 1/4 congruent to a' + 1/4 with |y'| < 8191 * 477 + 1 < 2^22,
-// so every partial sum is exact. One quotient q = rint(y' * fl(1/m)) (an
+// so every partial sum is exact. Widened operands (beta up to 84, Sec. "Not
+// True Emulation of DGEMM") take seven 12-bit pieces of a 128-bit a', with
+// |y'| < 4095 * 715 + 1 < 2^22 as well. One quotient q = rint(y' * fl(1/m)) (an
 // fma against the 1.5 * 2^23 rounding constant) is the integer nearest to
 // y'/m: the estimate is off by at most |y'/m| 2^-24 < 1/(4m), and y'/m is at
 // least 1/(4m) away from every half-integer (2y' - (2k+1)m is an odd
@@ -35,40 +37,63 @@
 namespace oz {
 namespace {
 
-// Signed 13-bit pieces of a' as exact floats: a' = sum_i P_i 2^(13 i), NP of
-// them (NP = 4 covers |a'| < 2^52, NP = 5 every |a'| < 2^64); P_0 carries the
-// bias of 1/4.
+// Signed pieces of a' as exact floats, NP of them: 13-bit pieces when NP <= 5
+// (NP = 4 covers |a'| < 2^52, NP = 5 every |a'| < 2^64), 12-bit pieces when
+// NP = 7 (widened operands, |a'| < 2^84). P_0 carries the bias of 1/4. With
+// 12-bit pieces |y'| <= 4095 (1 + 6 * 119) + 1/4 < 2^22 as well.
 template <int NP>
 struct Pieces {
+  static constexpr int kBits = NP > 5 ? 12 : 13;
   float p[NP];
 };
 
 template <int NP>
 __device__ __forceinline__ Pieces<NP> pieces_of(uint64_t bits, int32_t s) {
-  const Trunc t = truncate(bits, s);
-  const float sg = t.neg ? -1.0f : 1.0f;
-  const float off = t.neg ? 8388608.0f : -8388608.0f;
   Pieces<NP> P;
+  constexpr int PB = Pieces<NP>::kBits;
+  constexpr uint32_t mask = (1u << PB) - 1u;
+  if constexpr (NP > 5) {
+    const TruncWide t = truncate_wide(bits, s);
+    const float sg = t.neg ? -1.0f : 1.0f;
+    const float off = t.neg ? 8388608.0f : -8388608.0f;
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    const uint32_t v = (uint32_t)(t.mag >> (13 * i)) & 0x1FFFu;
-    P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
+    for (int i = 0; i < NP; ++i) {
+      const uint32_t v = (uint32_t)(t.mag >> (PB * i)) & mask;
+      P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
+    }
+  } else {
+    const Trunc t = truncate(bits, s);
+    const float sg = t.neg ? -1.0f : 1.0f;
+    const float off = t.neg ? 8388608.0f : -8388608.0f;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const uint32_t v = (uint32_t)(t.mag >> (PB * i)) & mask;
+      P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);
+    }
   }
   P.p[0] += 0.25f;
   return P;
 }
 
-// The constants of one modulus, held in registers while a tile is reduced.
+// The constants of one modulus, held in registers while a tile is reduced:
+// c[i - 1] = 2^(PB i) mod m, nearest zero.
+template <int NP>
 struct ModConst {
-  float c13, c26, c39, c52, invm, m;
+  float c[NP - 1];
+  float invm, m;
 };
 
-__device__ __forceinline__ ModConst mod_const(const OzTables& T, int q) {
-  ModConst c;
-  c.c13 = T.c13f[q];
-  c.c26 = T.c26f[q];
-  c.c39 = T.c39f[q];
-  c.c52 = T.c52f[q];
+template <int NP>
+__device__ __forceinline__ ModConst<NP> mod_const(const OzTables& T, int q) {
+  ModConst<NP> c;
+  if constexpr (NP > 5) {
+#pragma unroll
+    for (int i = 0; i < NP - 1; ++i) c.c[i] = T.c12f[i][q];
+  } else {
+    const float c13[4] = {T.c13f[q], T.c26f[q], T.c39f[q], T.c52f[q]};
+#pragma unroll
+    for (int i = 0; i < NP - 1; ++i) c.c[i] = c13[i];
+  }
   c.invm = T.invm[q];
   c.m = T.mf[q];
   return c;
@@ -77,11 +102,10 @@ __device__ __forceinline__ ModConst mod_const(const OzTables& T, int q) {
 // Representative nearest zero of a' modulo one modulus plus 1/4, as an exact
 // float (r + 1/4; see the header).
 template <int NP>
-__device__ __forceinline__ float residue_q(const ModConst& c, const Pieces<NP>& P) {
-  float y = fmaf(P.p[1], c.c13, P.p[0]);
-  y = fmaf(P.p[2], c.c26, y);
-  y = fmaf(P.p[3], c.c39, y);
-  if constexpr (NP == 5) y = fmaf(P.p[4], c.c52, y);
+__device__ __forceinline__ float residue_q(const ModConst<NP>& c, const Pieces<NP>& P) {
+  float y = P.p[0];
+#pragma unroll
+  for (int i = 1; i < NP; ++i) y = fmaf(P.p[i], c.c[i - 1], y);
   const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;   // rint(y' / m), exact
   return fmaf(-qf, c.m, y);
 }
@@ -174,7 +198,7 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
 #pragma unroll
     for (int q = 0; q < OZ_MAX_MODULI; ++q) {
       if (q < Q) {
-        const ModConst mc = mod_const(T, q);
+        const ModConst<NP> mc = mod_const<NP>(T, q);
         float r[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
@@ -253,7 +277,7 @@ __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int
 #pragma unroll
     for (int q = 0; q < OZ_MAX_MODULI; ++q) {
       if (q < Q) {
-        const ModConst mc = mod_const(T, q);
+        const ModConst<NP> mc = mod_const<NP>(T, q);
         float r[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
@@ -440,7 +464,7 @@ __device__ __forceinline__ void split_cols_block(const OzTables& T, int64_t bx, 
 #pragma unroll 1
   for (int q = 0; q < Q; ++q) {
     uint32_t* tb = tile[q & 1];
-    const ModConst mc = mod_const(T, q);
+    const ModConst<NP> mc = mod_const<NP>(T, q);
     float r[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) r[e] = residue_q(mc, P[e]);
@@ -496,40 +520,43 @@ __global__ void __launch_bounds__(256) split_cols_grouped_kernel(const __grid_co
 
 }  // namespace
 
+namespace {
+
+// pieces per entry for a bit budget: four or five of 13 bits, seven of 12
+int pieces_for(int bits) { return bits <= 52 ? 4 : bits <= 64 ? 5 : 7; }
+
+template <bool kBF16, int NP>
+void split_rows_np(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
+                   int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag, cudaStream_t st, bool given) {
+  if (k_pad <= 1024)                             // short rows: one warp per row
+    split_rows_warp_kernel<kBF16, NP><<<(unsigned)(nvec_pad / 8), 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad,
+                                                                                 shifts, planes, flag, given);
+  else
+    split_rows_kernel<kBF16, NP><<<(unsigned)nvec_pad, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts,
+                                                                      planes, flag, given);
+}
+
+template <bool kBF16, int NP>
+void split_cols_np(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
+                   int64_t k_pad, const int32_t* shifts, void* planes, cudaStream_t st) {
+  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+  split_cols_kernel<kBF16, NP><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+}
+
+}  // namespace
+
 cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
                               int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int bf16,
                               int32_t* flag, cudaStream_t st, bool given) {
   if (nvec_pad == 0) return cudaSuccess;
-  const bool np4 = t.bits <= 52;                 // |a'| < 2^52: four 13-bit pieces
-  if (k_pad <= 1024) {                           // short rows: one warp per row
-    const unsigned g = (unsigned)(nvec_pad / 8);
-    if (bf16 && np4)
-      split_rows_warp_kernel<true, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                         given);
-    else if (bf16)
-      split_rows_warp_kernel<true, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                         given);
-    else if (np4)
-      split_rows_warp_kernel<false, 4><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                         given);
-    else
-      split_rows_warp_kernel<false, 5><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                         given);
-    return cudaGetLastError();
+  switch (pieces_for(t.bits) * 2 + (bf16 ? 1 : 0)) {
+    case 9: split_rows_np<true, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
+    case 8: split_rows_np<false, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
+    case 11: split_rows_np<true, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
+    case 10: split_rows_np<false, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
+    case 15: split_rows_np<true, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
+    default: split_rows_np<false, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
   }
-  dim3 grid((unsigned)nvec_pad);
-  if (bf16 && np4)
-    split_rows_kernel<true, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                      given);
-  else if (bf16)
-    split_rows_kernel<true, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                      given);
-  else if (np4)
-    split_rows_kernel<false, 4><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                      given);
-  else
-    split_rows_kernel<false, 5><<<grid, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag,
-                                                      given);
   return cudaGetLastError();
 }
 
@@ -561,16 +588,14 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
     cudaError_t e0 = launch_shifts_cols(t.bits, nvec, len, X, ld, shifts, flag, colmax, st);
     if (e0 != cudaSuccess) return e0;
   }
-  dim3 g2((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
-  const bool np4 = t.bits <= 52;   // four 13-bit pieces
-  if (bf16 && np4)
-    split_cols_kernel<true, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
-  else if (bf16)
-    split_cols_kernel<true, 5><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
-  else if (np4)
-    split_cols_kernel<false, 4><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
-  else
-    split_cols_kernel<false, 5><<<g2, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  switch (pieces_for(t.bits) * 2 + (bf16 ? 1 : 0)) {
+    case 9: split_cols_np<true, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    case 8: split_cols_np<false, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    case 11: split_cols_np<true, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    case 10: split_cols_np<false, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    case 15: split_cols_np<true, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    default: split_cols_np<false, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+  }
   return cudaGetLastError();
 }
 
@@ -580,7 +605,7 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
 cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int nlong,
                                       int64_t total_rows, int64_t total_wrows, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
-  if (total_rows > INT32_MAX || total_wrows > INT32_MAX) return cudaErrorInvalidValue;
+  if (total_rows > INT32_MAX || total_wrows > INT32_MAX || t.bits > 64) return cudaErrorInvalidValue;
   const bool np4 = t.bits <= 52;   // four 13-bit pieces
   if (nlong > 0 && total_rows > 0) {
     if (np4)
@@ -601,7 +626,7 @@ cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* p
 cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_cm,
                                       int64_t total_sh, int64_t total_sc, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
-  if (total_cm > INT32_MAX || total_sh > INT32_MAX || total_sc > INT32_MAX) return cudaErrorInvalidValue;
+  if (total_cm > INT32_MAX || total_sh > INT32_MAX || total_sc > INT32_MAX || t.bits > 64) return cudaErrorInvalidValue;
   if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, count);
   if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, count, t.bits);
   if (total_sc > 0) {

@@ -326,3 +326,53 @@ def test_tc_fp32_accumulation_is_exact(pattern, engine):
     Yh = Y.cpu().numpy()
     for q, mq in enumerate(plan.moduli):
         assert np.array_equal(Yh[q].astype(np.int64), W % mq), f"modulus {mq}"
+
+
+@pytest.mark.parametrize("engine", [oz.OZ_ENGINE_IMMA, oz.OZ_ENGINE_TC])
+def test_widened_split_matches_oracle(engine):
+    """beta = 70 > 64 (Sec. 'Not True Emulation of DGEMM'): |a'| < 2^70 is cut
+    into seven 12-bit pieces; shifts and planes equal the oracle's."""
+    plan = oz.Plan(20, 70, 300, engine)
+    assert plan.bits == 70
+    A, _ = synth.phi_pair(300, 1, 1300, 2.0, seed=70)
+    s, P, flag = _split(plan, _dev(A), 1, 300, 1300, 1300)
+    s_ref = oracle.scale(A, 70, axis=1)
+    U_ref = oracle.planes(A, s_ref, plan.moduli, axis=1)
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(P[:, :300, :1300], U_ref)
+    At = np.ascontiguousarray(A.T)
+    s2, P2, _ = _split(plan, _dev(At), 0, 300, 1300, 300)
+    assert np.array_equal(s2, s_ref) and np.array_equal(P2[:, :300, :1300], U_ref)
+    B, _ = synth.phi_pair(77, 1, 500, 1.0, seed=71)        # short rows: the warp-per-row split
+    s3, P3, _ = _split(plan, _dev(B), 1, 77, 500, 500)
+    assert np.array_equal(P3[:, :77, :500], oracle.planes(B, oracle.scale(B, 70, axis=1), plan.moduli, axis=1))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("m,n,k,bits,ta,tb", [(300, 200, 600, 70, 0, 0), (129, 257, 1500, 66, 1, 0),
+                                              (33, 17, 129, 72, 0, 1)])
+def test_widened_dgemm_matches_oracle(engine, m, n, k, bits, ta, tb):
+    plan = oz.Plan(20, bits, k, engine)
+    A, B = synth.phi_pair(m, n, k, 2.0, seed=m + bits)
+    Ad = _dev(A.T if ta else A)
+    Bd = _dev(B.T if tb else B)
+    C = oz.dgemm(Ad, Bd, plan, trans_a=bool(ta), trans_b=bool(tb))
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(C.cpu().numpy()), _bits(oracle.dgemm(A, B, plan.moduli, bits)))
+
+
+def test_widened_product_is_fl_of_exact():
+    """Rows of A and columns of B spanning at most 2^16 (full 53-bit
+    significands): at beta = 69 the product is fl(AB), bit for bit against
+    exact rational arithmetic (Example widened)."""
+    from tests import brute
+    from tests.test_oracle_pins import _spanned
+    rng = np.random.default_rng(69)
+    M, N, K = 6, 5, 40
+    A = _spanned(rng, M, K, 16, axis=1)
+    B = _spanned(rng, N, K, 16, axis=0)
+    plan = oz.Plan(20, 69, K, oz.OZ_ENGINE_TC)
+    C = _dgemm(plan, A, B)
+    exact = brute.exact_product(A, B)
+    ref = np.array([[brute.to_float(exact[i][j]) for j in range(N)] for i in range(M)])
+    assert np.array_equal(_bits(C), _bits(ref))

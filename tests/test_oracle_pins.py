@@ -225,3 +225,42 @@ def test_truncation_error_bound(beta):
         bound = 2.0**(1 - beta) * (amax[i] * sb[j] + bmax[j] * sa[i]) + K * 2.0**(2 - 2 * beta) * amax[i] * bmax[j]
         bound += 2.0**-53 * abs(C[i, j])
         assert e <= bound * (1 + 1e-12)
+
+
+def _spanned(rng, vecs, length, d, axis):
+    """Entries with full 53-bit significands whose magnitudes, along each vector
+    (row for axis=1, column for axis=0), lie within a factor 2^(d+1) of the
+    vector's largest (exponent offsets 0..-d, offset 0 present in every vector)."""
+    shape = (vecs, length) if axis == 1 else (length, vecs)
+    sig = rng.integers(2**52, 2**53, size=shape).astype(np.float64) * rng.choice([-1.0, 1.0], size=shape)
+    off = rng.integers(-d, 1, size=shape)
+    if axis == 1:
+        off[:, 0] = 0
+        base = rng.integers(-40, 40, size=(vecs, 1))
+    else:
+        off[0, :] = 0
+        base = rng.integers(-40, 40, size=(1, vecs))
+    return np.ldexp(sig, (off + base - 52).astype(np.int64))
+
+
+@pytest.mark.parametrize("d", [8, 16])
+def test_widened_conversion_is_exact_emulation(d):
+    """Sec. 'Not True Emulation of DGEMM' and Example widened: when the entries
+    of every row of A and column of B lie within 2^d of its largest, keeping
+    53 + d bits converts them without loss, so the product is fl(AB), the
+    correctly rounded exact product; at 53 bits it is not."""
+    rng = np.random.default_rng(100 + d)
+    M, N, K = 4, 3, 24
+    A = _spanned(rng, M, K, d, axis=1)
+    B = _spanned(rng, N, K, d, axis=0)
+    mods = oracle.max_product_moduli(20, 239)
+    assert oracle.modulus_product(mods) > 2 * K * (2**(53 + d) - 1) ** 2
+    exact = brute.exact_product(A, B)
+    ref = np.array([[brute.to_float(exact[i][j]) for j in range(N)] for i in range(M)])
+    C = oracle.dgemm(A, B, mods, 53 + d)
+    assert np.array_equal(_bits(C), _bits(ref))
+    C53 = oracle.dgemm(A, B, mods, 53)
+    assert not np.array_equal(_bits(C53), _bits(ref))
+    # and the oracle's arithmetic at that budget is the exact definition
+    C_def, _, _, _ = brute.emulated(A, B, 53 + d)
+    assert np.array_equal(_bits(C), _bits(C_def))
