@@ -224,7 +224,7 @@ def run_reference(args, rank, world):
         import paper_2609_37693_gb300 as oz      # the configuration tables only (host side)
         plan = oz.PlanFP(args.format, n, args.bits)
         mods, bits, q, channels = plan.moduli, plan.bits, plan.q, plan.channels
-    per_step = max(1.0, min(args.cpu_sample_s, 20.0) / max(args.steps, 1))
+    per_step = max(0.2, min(args.cpu_sample_s, 20.0) / max(args.steps, 1))
     for _ in range(args.warmup):
         oracle_rate(A, B, n, mods, bits, per_step / 4)
     vals, ents, secs = [], 0, 0.0
