@@ -437,6 +437,18 @@ OZ_API oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int64_t
                                  double* C, int64_t ldc, void* stream);
 
 /* Short English description of a status code (static string). */
+/*
+ * oz_selftest_bounded_wait -- exercises the failure path of the GEMM kernels'
+ * waits on the device: one thread waits, with the same bounded wait the
+ * kernels use, on a shared-memory barrier of its own. arrive != 0: it arrives
+ * first and the wait completes (bit 2 of *status is set); arrive == 0: nothing
+ * arrives, the wait gives up after about 2 s and sets bit 1, as a kernel's
+ * timed-out wait does (oz_query_status then reports OZ_ERR_CUDA when status
+ * is a workspace's first word). The kernel returns either way; no fault, no
+ * hang. status: device int32, OR-ed into. Asynchronous on the stream.
+ */
+OZ_API oz_status oz_selftest_bounded_wait(int arrive, int32_t* status, void* stream);
+
 OZ_API const char* oz_status_str(oz_status status);
 
 #ifdef __cplusplus

@@ -52,7 +52,7 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
             "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry",
             "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy",
-            "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked")
+            "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked", "oz_selftest_bounded_wait")
 
 
 class OzError(RuntimeError):
@@ -99,6 +99,7 @@ def _load_library():
         "oz_plan_caps": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "oz_blocked_workspace_bytes": (SZ, [P, I64, I64, I64]),
         "oz_dgemm_blocked": (I32, [P, I32, I32, I64, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
+        "oz_selftest_bounded_wait": (I32, [I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +248,12 @@ def oz_dgemm_host(plan, m, n, k, A, lda, B, ldb, C, ldc, rows_per_chunk, cols_pe
     return _lib.oz_dgemm_host(plan, int(m), int(n), int(k), A, int(lda), B, int(ldb), C, int(ldc),
                               int(rows_per_chunk), int(cols_per_chunk), workspace, int(workspace_bytes), stream,
                               stream_h2d, stream_d2h)
+
+
+def oz_selftest_bounded_wait(arrive, status, stream) -> int:
+    """status: device pointer to an int32 (OR-ed with 4 if the wait completed,
+    2 if it ran out)."""
+    return _lib.oz_selftest_bounded_wait(int(arrive), status, stream)
 
 
 def oz_query_status(workspace, stream) -> int:

@@ -21,7 +21,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboz.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["oz_plan.cpp", "oz_api.cu", "oz_split.cu", "oz_gemm_imma.cu", "oz_gemm_tc.cu", "oz_reconstruct.cu",
-           "oz_static.cu", "oz_batched.cu", "oz_host.cu", "oz_plan_fp.cpp", "oz_fp.cu", "oz_grouped.cu"]
+           "oz_static.cu", "oz_batched.cu", "oz_host.cu", "oz_plan_fp.cpp", "oz_fp.cu", "oz_grouped.cu",
+           "oz_selftest.cu"]
 
 
 def _nvcc() -> str:
