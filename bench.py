@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch", "blocked"],
                     help="dgemm: one m=n=k product (the headline); batch: 256 uneven products")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--batch-mode", default="grouped", choices=["grouped", "streams"],
-                    help="batch: one launch per phase over grouped products, or products on autotuned streams")
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "grouped", "streams"],
+                    help="batch: autotuned over launch structure and modulus counts (auto), one launch per "
+                         "phase over grouped products, or products on autotuned streams")
     ap.add_argument("--e2e-rows", type=int, default=0, help="e2e: rows of a block of C (0: about n/4)")
     ap.add_argument("--e2e-cols", type=int, default=0, help="e2e: columns of a block of C (0: about n/4)")
     ap.add_argument("--k", type=int, default=65536, help="blocked: the inner dimension")
@@ -481,7 +482,12 @@ def run_batch(args, rank, world, local):
         Bs.append(torch.from_numpy(B).to(dev))
         Cs.append(torch.empty((m, n), dtype=torch.float64, device=dev))
     flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
-    if args.batch_mode == "grouped":
+    if args.batch_mode == "auto":
+        bg, label, tune = oz.autotune_batch(shapes, As, Bs, Cs)
+        mode_desc = "autotuned: " + label
+        launches = bg.launches() if isinstance(bg, oz.GroupedGemm) else \
+            sum(oz.launches_per_dgemm(False, False) for _ in shapes)
+    elif args.batch_mode == "grouped":
         bg = oz.GroupedGemm(As, Bs, Cs)
         bg.capture()
         tune, mode_desc, launches = None, "grouped products, one launch per phase", bg.launches()

@@ -700,6 +700,56 @@ def autotune_blocked(A, B, candidates=None, bits: int = 53, reps: int = 2, strea
     return best, timings
 
 
+def autotune_batch(shapes, As, Bs, Cs, streams=(1, 2, 4, 8, 16), bits: int = 53, reps: int = 3):
+    """Launch structure and modulus counts of a batch of uneven products,
+    chosen by timing captured-graph replays of each candidate:
+      "streams=S": oz_dgemm_batched over S streams, each product at its least Q;
+      "grouped":   oz_group_run, each product at its least Q (one set of
+                   launches per distinct Q);
+      "grouped q=16": oz_group_run with every product on the Q = 16 plan (one
+                   set of launches for the whole batch; at 53 bits Q = 16 holds
+                   the window for every k up to 159 819, so the bits are the
+                   same as at the least Q).
+    Candidates are built, timed and freed one at a time. Returns (the fastest
+    runner, captured over As/Bs/Cs and with a replay() method, its label,
+    {label: ms})."""
+    torch = _import_torch()
+    shapes = [tuple(int(x) for x in sh) for sh in shapes]
+
+    def time_replays(runner):
+        runner.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            runner.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    builders = [("streams=%d" % ns, lambda ns=ns: BatchedGemm(shapes, nstreams=ns, bits=bits)) for ns in streams]
+    builders.append(("grouped", lambda: GroupedGemm(As, Bs, Cs, bits=bits)))
+    if all(k <= 159819 for (_, _, k) in shapes):
+        q16 = Plan(16, bits, max([k for (_, _, k) in shapes] + [1]), OZ_ENGINE_TC)
+        builders.append(("grouped q=16", lambda: GroupedGemm(As, Bs, Cs, plans=[q16] * len(shapes))))
+    timings, best = {}, None
+    for label, build in builders:
+        runner = build()
+        if isinstance(runner, BatchedGemm):
+            runner.capture(As, Bs, Cs)
+        else:
+            runner.capture()
+        timings[label] = time_replays(runner)
+        if best is None or timings[label] < timings[best[0]]:
+            best = (label, runner)
+        else:
+            del runner
+        torch.cuda.empty_cache()
+    return best[1], best[0], timings
+
+
 class GroupedGemm:
     """count products C_i = A_i B_i (float64 CUDA tensors, row-major) through
     oz_group_create / oz_group_run: one launch per phase over all products of

@@ -130,3 +130,28 @@ def test_grouped_reports_nonfinite():
     gg = oz.GroupedGemm(As, Bs, Cs)
     gg.run()
     assert oz.query_status(gg.ws) == oz.OZ_ERR_NONFINITE
+
+
+def test_autotuned_batch_structures_agree():
+    """Every candidate of the batch autotuner (streams, grouped at the least Q,
+    grouped with every product on Q = 16) keeps 53 bits, so each returns the
+    products oz_dgemm computes alone; the autotuner keeps the fastest."""
+    shapes, As, Bs, Cs = _problems(20, 16, 1200, seed=9)
+    ref = _alone(shapes, As, Bs, [oz.plan_least_q(k, 53) for (_, _, k) in shapes])
+    runner, label, times = oz.autotune_batch(shapes, As, Bs, Cs, streams=(1, 4), reps=1)
+    assert set(times) == {"streams=1", "streams=4", "grouped", "grouped q=16"} and label in times
+    for C in Cs:
+        C.fill_(np.nan)
+    runner.replay()
+    torch.cuda.synchronize()
+    for C, R in zip(Cs, ref):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+    q16 = oz.Plan(16, 53, 1200, oz.OZ_ENGINE_TC)
+    gq = oz.GroupedGemm(As, Bs, Cs, plans=[q16] * len(shapes))
+    for C in Cs:
+        C.fill_(np.nan)
+    gq.run()
+    torch.cuda.synchronize()
+    assert gq.launches() <= 7
+    for C, R in zip(Cs, ref):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
