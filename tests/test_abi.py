@@ -68,7 +68,9 @@ def test_bad_plans_are_refused():
     assert oz.oz_plan_create(21, 0, 100)[0] == oz.OZ_ERR_UNSUPPORTED
     assert oz.oz_plan_create(16, oz.OZ_MAX_BITS + 1, 100)[0] == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_plan_create(16, 65, 100)[0] == oz.OZ_ERR_K_TOO_LARGE        # the window, not the budget
-    assert oz.oz_plan_create(20, 70, 100)[0] == oz.OZ_OK                     # widened (beta > 64)
+    st, h = oz.oz_plan_create(20, 70, 100)                                   # widened (beta > 64)
+    assert st == oz.OZ_OK
+    oz.oz_plan_destroy(h)
     assert oz.oz_plan_create_fp(oz.OZ_FMT_E4M3, 100, oz.OZ_MAX_BITS_FP + 1)[0] == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_plan_create(16, 0, 0)[0] == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_plan_create(16, 0, 100, 7)[0] == oz.OZ_ERR_INVALID_ARG
