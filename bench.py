@@ -381,7 +381,7 @@ def run_ours(args, rank, world, local):
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
     e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
     e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
-    hg_rows, hg_cols = hg.rows, hg.cols
+    hg_rows, hg_cols = hg.block
     del hg
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----

@@ -2,7 +2,8 @@
  * oz.h -- C ABI of the GB300 (sm_103a) Ozaki-II emulated FP64 GEMM library.
  *
  * The library computes C = op(A) op(B) for FP64 row-major matrices by the
- * Ozaki-II scheme on the INT8 alphabet (Sec. "Ozaki II", Sec. "INT4 and INT8"):
+ * Ozaki-II scheme on the INT8 alphabet (Sec. "Ozaki II", Sec. "INT4 and INT8"),
+ * or on a low-precision float alphabet (oz_plan_create_fp):
  *   1. Scale      one power-of-two shift per row of op(A) and per column of
  *                 op(B) (eq. convert);
  *   2. Reduce     truncate to integers below 2^bits and write the balanced
@@ -17,9 +18,12 @@
  *   - Matrices are row-major. op(X) = X if trans == 0, X^T if trans == 1.
  *     A is stored m x k (trans_a = 0) or k x m (trans_a = 1) with leading
  *     dimension lda >= its column count; likewise B (k x n or n x k), C (m x n).
- *   - A, B, C and the workspace are DEVICE pointers owned by the caller. The
- *     library never allocates memory during a product call; a plan owns a small
- *     table of constants (no device memory).
+ *   - A, B, C and the workspace are DEVICE pointers owned by the caller
+ *     (oz_dgemm_host takes HOST A, B, C). The library never allocates device
+ *     memory during a product call. An INT8 plan owns a small table of
+ *     constants in host memory; a float-format plan also owns a small device
+ *     table of codes; a grouped product (oz_group_create) owns a few streams
+ *     and events; oz_dgemm_host creates and destroys events per call.
  *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
  *     void*; NULL = the legacy default stream). Nothing synchronises the host
  *     except oz_query_status.

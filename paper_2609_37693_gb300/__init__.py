@@ -832,6 +832,12 @@ class HostGemm:
         torch = _import_torch()
         self.plan, self.m, self.n, self.k = plan, m, n, k
         self.rows, self.cols = rows_per_chunk, cols_per_chunk
+        # the block edges the library uses (0 picks about a quarter of m or n, a
+        # multiple of 256)
+        edge = lambda x: round_up(max((x + 3) // 4, 1), 256)
+        r = rows_per_chunk or edge(m)
+        c = cols_per_chunk or edge(n)
+        self.block = (min(r, m) if m else r, min(c, n) if n else c)
         self.device = torch.device(device or "cuda")
         nbytes = oz_host_workspace_bytes(plan.handle, m, n, k, rows_per_chunk, cols_per_chunk)
         if nbytes == 0:
