@@ -62,7 +62,7 @@ def sweep(ns, phis, qs, samples, reps=3, dgemm=True, log=print):
                 dg = 2.0 * n**3 / (ms * 1e-3) / 1e12
             for q in qs:
                 mods = oracle.max_product_moduli(q, 239)
-                bmax = min(oracle.beta_max(mods, n), 64)
+                bmax = min(oracle.beta_max(mods, n), oz.OZ_MAX_BITS)
                 betas = [bmax] + ([53] if 53 < bmax else [])
                 for beta in betas:
                     try:
