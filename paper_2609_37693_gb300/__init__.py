@@ -710,6 +710,8 @@ def autotune_batch(shapes, As, Bs, Cs, streams=(1, 2, 4, 8, 16), bits: int = 53,
                    set of launches for the whole batch; at 53 bits Q = 16 holds
                    the window for every k up to 159 819, so the bits are the
                    same as at the least Q).
+      "streams=1 pairs": one stream, the products' GEMMs on CTA pairs (256 x
+                   256 tiles instead of 128 x 256).
     Candidates are built, timed and freed one at a time. Returns (the fastest
     runner, captured over As/Bs/Cs and with a replay() method, its label,
     {label: ms})."""
@@ -730,6 +732,8 @@ def autotune_batch(shapes, As, Bs, Cs, streams=(1, 2, 4, 8, 16), bits: int = 53,
         return min(ts)
 
     builders = [("streams=%d" % ns, lambda ns=ns: BatchedGemm(shapes, nstreams=ns, bits=bits)) for ns in streams]
+    # one stream: the products may take the CTA-pair GEMM (256 x 256 tiles)
+    builders.append(("streams=1 pairs", lambda: BatchedGemm(shapes, nstreams=1, bits=bits, engine=OZ_ENGINE_TC)))
     builders.append(("grouped", lambda: GroupedGemm(As, Bs, Cs, bits=bits)))
     if all(k <= 159819 for (_, _, k) in shapes):
         q16 = Plan(16, bits, max([k for (_, _, k) in shapes] + [1]), OZ_ENGINE_TC)

@@ -139,7 +139,7 @@ def test_autotuned_batch_structures_agree():
     shapes, As, Bs, Cs = _problems(20, 16, 1200, seed=9)
     ref = _alone(shapes, As, Bs, [oz.plan_least_q(k, 53) for (_, _, k) in shapes])
     runner, label, times = oz.autotune_batch(shapes, As, Bs, Cs, streams=(1, 4), reps=1)
-    assert set(times) == {"streams=1", "streams=4", "grouped", "grouped q=16"} and label in times
+    assert set(times) == {"streams=1", "streams=4", "streams=1 pairs", "grouped", "grouped q=16"} and label in times
     for C in Cs:
         C.fill_(np.nan)
     runner.replay()
