@@ -146,3 +146,27 @@ def test_autotuned_configurations_agree():
         assert np.array_equal(_bits(C.cpu().numpy()), ref), label
     (label, plan, k_slab), times = oz.autotune_blocked(Ad, Bd, cands, reps=1)
     assert label in times and set(times) == set(labels)
+
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1)])
+def test_blocked_float_format_transposed(ta, tb):
+    plan = oz.PlanFP("E4M3", 3000, 53)
+    m, n, k = 150, 130, 2500
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=12 + ta)
+    Ad, Bd = _operands(A, B, ta, tb)
+    Cb = oz.dgemm_blocked(Ad, Bd, plan, 1000, trans_a=bool(ta), trans_b=bool(tb))
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(Cb.cpu().numpy()), _bits(oracle.dgemm(A, B, plan.moduli, plan.bits)))
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_blocked_widened_budget(engine):
+    """beta = 70 (seven 12-bit pieces per entry) through the blocked call: the
+    shifts over the whole K and the given-shift splits of each slab."""
+    plan = oz.Plan(20, 70, 3000, engine)
+    m, n, k = 140, 90, 3000
+    A, B = synth.phi_pair(m, n, k, 2.0, seed=70)
+    Ad, Bd = _dev(A), _dev(B)
+    Cb = oz.dgemm_blocked(Ad, Bd, plan, 1100)
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(Cb.cpu().numpy()), _bits(oracle.dgemm(A, B, plan.moduli, 70)))

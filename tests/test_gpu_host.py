@@ -48,3 +48,19 @@ def test_host_path_float_formats(fmt, m, n, k, rows, cols):
     ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
     assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
     assert oz.query_status(hg.ws) == oz.OZ_OK
+
+
+def test_host_path_widened_budget():
+    """beta = 70 on the host-operand path (the splits of each chunk take seven
+    12-bit pieces per entry)."""
+    plan = oz.Plan(20, 70, 900, oz.OZ_ENGINE_TC)
+    m, n, k = 600, 500, 900
+    A, B = synth.phi_pair(m, n, k, 2.0, seed=7)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
+    hg = oz.HostGemm(plan, m, n, k, 256, cols_per_chunk=256)
+    hg(Ah, Bh, Ch)
+    torch.cuda.synchronize()
+    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
+    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
