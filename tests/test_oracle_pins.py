@@ -126,6 +126,28 @@ def test_crt_invariants_and_window():
         assert back == x
 
 
+def test_garner_agrees_with_the_digit_sum():
+    """The oracle's CRT (Garner's mixed radix) and the form the GPU
+    reconstruct evaluates, X = sum_k y_k M_k mod P with M_k = P / m_k and the
+    digit y_k = (w_k (M_k^-1 mod m_k)) mod m_k, taken to [-P/2, P/2), agree on
+    random residues for every Q, in Python integers."""
+    rng = np.random.default_rng(17)
+    for q in (9, 12, 14, 16, 18, 20):
+        mods = oracle.max_product_moduli(q, 239)
+        P = oracle.modulus_product(mods)
+        w = np.stack([rng.integers(0, m, size=64) for m in mods], axis=1)
+        xs = oracle.crt(w, mods)
+        for x, row in zip(xs, w):
+            acc = 0
+            for m, r in zip(mods, row):
+                M = P // m
+                acc += (int(r) * pow(M, -1, m) % m) * M
+            acc %= P
+            if 2 * acc >= P:
+                acc -= P
+            assert acc == x
+
+
 def test_x_is_bounded_and_exact():
     """|X| <= K (2^beta - 1)^2 (eq. range), and X equals A'B' (eq. convert)."""
     A, B = synth.phi_pair(4, 4, 50, 2.0, 9)
