@@ -388,8 +388,10 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+  // barriers (2 STAGES + 5 of them) below 192; then the TMEM address and the abort flag
+  static_assert((2 * STAGES + 5) * 8 <= 192, "barriers overlap the TMEM address");
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 192);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 200);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 

@@ -52,7 +52,9 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;     // 48 KiB
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kTmemCols = 512;
-constexpr int kBarBytes = 256;
+constexpr int kBarBytes = 256;                     // barriers, then the TMEM address and the abort flag
+constexpr int kHolderOff = 192;                    // offsets in that area (past every barrier)
+constexpr int kAbortOff = 200;
 constexpr int kSmemBytes = STAGES * STAGE_BYTES + kBarBytes + 1024;
 
 // Instruction descriptor of tcgen05.mma.kind::f16: D = F32 (bits 4-5 = 1),
@@ -260,8 +262,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + kHolderOff);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + kAbortOff);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -464,10 +466,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // ---------------------------------------------------------------------------
 constexpr int P_BM = 128;                          // rows of A per CTA
 constexpr int P_BN = 128;                          // rows of B per CTA (N = 256 per pair)
-constexpr int P_STAGES = 6;
+constexpr int P_STAGES = 7;
 constexpr int P_A_BYTES = P_BM * BK * 2;           // 16 KiB
 constexpr int P_STAGE_BYTES = P_A_BYTES + P_BN * BK * 2;   // 32 KiB
 constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + kBarBytes + 1024;
+// full and empty barriers per stage, two tfull, two tempty, one drain: all below kHolderOff
+static_assert((2 * P_STAGES + 5) * 8 <= kHolderOff, "pair kernel barriers overlap the TMEM address");
+static_assert((2 * STAGES + 5) * 8 <= kHolderOff, "barriers overlap the TMEM address");
 // epilogue warps of the pair kernel (eight: with four, one warp's drain of a
 // slab outlasts the slab's products)
 constexpr int kPairEpiWarps = 8;
@@ -489,8 +494,8 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * P_STAGES + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * P_STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * P_STAGES + 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + P_STAGES * P_STAGE_BYTES + 128);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + P_STAGES * P_STAGE_BYTES + 136);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + P_STAGES * P_STAGE_BYTES + kHolderOff);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + P_STAGES * P_STAGE_BYTES + kAbortOff);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -718,8 +723,8 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
   auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 128);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 136);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + kHolderOff);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + kAbortOff);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   auto unit_begin = [](const OzGroupProblem& q) { return q.unit_begin; };
