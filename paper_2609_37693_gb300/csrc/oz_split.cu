@@ -176,22 +176,23 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
   const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
   const bool vec = live && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
-  for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
-    uint64_t b[8];
-    if (vec && h0 + 8 <= len) {
+  // four entries per thread per pass: registers for three CTAs per SM
+  for (int64_t h0 = (int64_t)tid * 4; h0 < k_pad; h0 += 256 * 4) {
+    uint64_t b[4];
+    if (vec && h0 + 4 <= len) {
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
+      for (int e = 0; e < 4; e += 2) {
         const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(row + h0 + e));
         b[e] = w.x;
         b[e + 1] = w.y;
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+      for (int e = 0; e < 4; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
     }
-    Pieces<NP> P[8];
+    Pieces<NP> P[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 4; ++e) {
       if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;  // non-finite: flagged above
       P[e] = pieces_of<NP>(b[e], s);
     }
@@ -199,22 +200,15 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
     for (int q = 0; q < OZ_MAX_MODULI; ++q) {
       if (q < Q) {
         const ModConst<NP> mc = mod_const<NP>(T, q);
-        float r[8];
+        float r[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
+        for (int e = 0; e < 4; ++e) r[e] = residue_q(mc, P[e]);
         const int64_t off = (int64_t)q * plane + v * k_pad + h0;
         if (kBF16) {
-          uint4 o;
-          o.x = bf16_pair(r[0], r[1]);
-          o.y = bf16_pair(r[2], r[3]);
-          o.z = bf16_pair(r[4], r[5]);
-          o.w = bf16_pair(r[6], r[7]);
-          *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
+          *reinterpret_cast<uint2*>(static_cast<uint16_t*>(planes) + off) =
+              make_uint2(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]));
         } else {
-          uint2 o;
-          o.x = int8_quad(r[0], r[1], r[2], r[3]);
-          o.y = int8_quad(r[4], r[5], r[6], r[7]);
-          *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
+          *reinterpret_cast<uint32_t*>(static_cast<int8_t*>(planes) + off) = int8_quad(r[0], r[1], r[2], r[3]);
         }
       }
     }
@@ -324,7 +318,7 @@ __global__ void __launch_bounds__(256) split_rows_warp_grouped_kernel(const __gr
 }
 
 template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
+__global__ void __launch_bounds__(256, 3) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
                                                          const double* __restrict__ X, int64_t ld,
                                                          int64_t nvec_pad, int64_t k_pad,
                                                          int32_t* __restrict__ shifts, void* __restrict__ planes,
