@@ -314,6 +314,36 @@ def run_ours(args, rank, world, local):
     if st != oz.OZ_OK:
         raise RuntimeError(f"status after warm-up: {oz.oz_status_str(st)}")
 
+    # (measured first: a host-operand run right after the long device-timed
+    # region was seen to run far slower than the same run on its own)
+    flops = 2.0 * n**3
+    # ---- e2e: host buffers through the public host-I/O call (oz_dgemm_host),
+    # every step copying A and B in and C out inside the timed region ----
+    all_cpus = os.sched_getaffinity(0)
+    host_binding = bind_host_to_gpu(local)            # the pinned buffers land next to the GPU
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    os.sched_setaffinity(0, all_cpus)
+    hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
+    for _ in range(2):
+        hg(A_pin, B_pin, C_pin, stream)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 10))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        hg(A_pin, B_pin, C_pin, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
+    e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
+    e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
+    hg_rows, hg_cols = hg.block
+    del hg
+
+
     # The paper's gate for a timed call (Table tab:setup): relative Frobenius
     # difference from native DGEMM below 1e-12. Native DGEMM is also the
     # throughput comparison.
@@ -370,8 +400,13 @@ def run_ours(args, rank, world, local):
         oz.oz_split(plan.handle, 1, n, n, A.data_ptr(), n, m_pad, k_pad, base + lay["s"], base + lay["u"],
                     base + lay["flag"], None, sh)
         ev[1].record(stream)
-        oz.oz_split(plan.handle, 0, n, n, B.data_ptr(), n, n_pad, k_pad, base + lay["t"], base + lay["v"],
-                    base + lay["flag"], base + lay["colmax"], sh)
+        if is_fp:
+            oz.oz_split(plan.handle, 0, n, n, B.data_ptr(), n, n_pad, k_pad, base + lay["t"], base + lay["v"],
+                        base + lay["flag"], base + lay["colmax"], sh)
+        else:                                   # as oz_dgemm does: B^T, then its rows split
+            oz.oz_transpose(n, n, B.data_ptr(), n, base + lay["bt"], sh)
+            oz.oz_split(plan.handle, 1, n, n, base + lay["bt"], n, n_pad, k_pad, base + lay["t"], base + lay["v"],
+                        base + lay["flag"], None, sh)
         ev[2].record(stream)
         oz.oz_residue_gemm(plan.handle, n, n, m_pad, n_pad, k_pad, base + lay["u"], base + lay["v"],
                            base + lay["y"], 0, base + lay["flag"], sh)
@@ -383,32 +418,6 @@ def run_ours(args, rank, world, local):
         for i, key in enumerate(phase_ms):
             phase_ms[key] += ev[i].elapsed_time(ev[i + 1]) / reps
     phase_sum = sum(phase_ms.values())
-
-    # ---- e2e: host buffers through the public host-I/O call (oz_dgemm_host),
-    # every step copying A and B in and C out inside the timed region ----
-    all_cpus = os.sched_getaffinity(0)
-    host_binding = bind_host_to_gpu(local)            # the pinned buffers land next to the GPU
-    A_pin = torch.from_numpy(A_h).pin_memory()
-    B_pin = torch.from_numpy(B_h).pin_memory()
-    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    os.sched_setaffinity(0, all_cpus)
-    hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
-    for _ in range(2):
-        hg(A_pin, B_pin, C_pin, stream)
-    torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 10))
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(e2e_steps):
-        hg(A_pin, B_pin, C_pin, stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
-    e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
-    e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
-    hg_rows, hg_cols = hg.block
-    del hg
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----
     peaks = load_peaks()
@@ -480,7 +489,7 @@ def run_ours(args, rank, world, local):
                     "api": "oz_dgemm_host (pinned host A, B, C; blocks of C overlap copies and phases)",
                     "block": [hg_rows, hg_cols], "host": host_binding,
                     "equals_device_result": e2e_exact},
-            "gpu_launches": oz.launches_per_dgemm(False, False) * args.steps,
+            "gpu_launches": (oz.launches_per_dgemm(False, False) if args.format == "int8" else 6) * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -184,7 +184,10 @@ OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
  * t (int32[n]), colmax (uint64[max(m, n)]), U planes, V planes, Y residues
  * (Q x m rows, row pitch n rounded up to 16 bytes; the phase entry points
  * below take and give row pitch n, which fits in the same region), then m_pad,
- * n_pad, k_pad (entries, not bytes).
+ * n_pad, k_pad (entries, not bytes), and out[10] the byte offset of B^T
+ * (n x k doubles; an INT8 oz_dgemm with trans_b = 0 transposes B there and
+ * splits its columns as rows; empty for float-format plans). out must hold
+ * 11 entries.
  */
 OZ_API oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t* out);
 
@@ -336,6 +339,15 @@ OZ_API oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_align
 OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t len, const double* X, int64_t ld,
                    int64_t nvec_pad, int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag,
                    uint64_t* colmax, void* stream);
+
+/*
+ * oz_transpose -- Y = X^T for X of rows x cols doubles (row pitch ld >=
+ * cols), Y of cols x rows (row pitch rows): the step an INT8 oz_dgemm takes
+ * before splitting the columns of B as contiguous rows (then
+ * oz_split(contiguous = 1) on Y is that split). Device pointers, 8-byte
+ * aligned; asynchronous on the stream.
+ */
+OZ_API oz_status oz_transpose(int64_t rows, int64_t cols, const double* X, int64_t ld, double* Y, void* stream);
 
 /*
  * oz_residue_gemm -- phases 3 and 4: for each modulus q,

@@ -52,7 +52,8 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm_static", "oz_batched_workspace_bytes", "oz_dgemm_batched", "oz_host_workspace_bytes",
             "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry",
             "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy",
-            "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked", "oz_selftest_bounded_wait")
+            "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked", "oz_selftest_bounded_wait",
+            "oz_transpose")
 
 
 class OzError(RuntimeError):
@@ -100,6 +101,7 @@ def _load_library():
         "oz_blocked_workspace_bytes": (SZ, [P, I64, I64, I64]),
         "oz_dgemm_blocked": (I32, [P, I32, I32, I64, I64, I64, I64, P, I64, P, I64, P, I64, P, SZ, P]),
         "oz_selftest_bounded_wait": (I32, [I32, P, P]),
+        "oz_transpose": (I32, [I64, I64, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -187,12 +189,12 @@ def oz_workspace_bytes(plan, m: int, n: int, k: int) -> int:
 
 
 def oz_workspace_layout(plan, m: int, n: int, k: int):
-    """Returns (status, dict of byte offsets flag/s/t/colmax/u/v/y and m_pad/n_pad/k_pad)."""
-    out = (ctypes.c_int64 * 10)()
+    """Returns (status, dict of byte offsets flag/s/t/colmax/u/v/y, m_pad/n_pad/k_pad, and bt)."""
+    out = (ctypes.c_int64 * 11)()
     st = _lib.oz_workspace_layout(plan, int(m), int(n), int(k), out)
     if st != OZ_OK:
         return st, None
-    keys = ("flag", "s", "t", "colmax", "u", "v", "y", "m_pad", "n_pad", "k_pad")
+    keys = ("flag", "s", "t", "colmax", "u", "v", "y", "m_pad", "n_pad", "k_pad", "bt")
     return st, {key: int(v) for key, v in zip(keys, out)}
 
 
@@ -254,6 +256,10 @@ def oz_selftest_bounded_wait(arrive, status, stream) -> int:
     """status: device pointer to an int32 (OR-ed with 4 if the wait completed,
     2 if it ran out)."""
     return _lib.oz_selftest_bounded_wait(int(arrive), status, stream)
+
+
+def oz_transpose(rows, cols, X, ld, Y, stream) -> int:
+    return _lib.oz_transpose(int(rows), int(cols), X, int(ld), Y, stream)
 
 
 def oz_query_status(workspace, stream) -> int:
@@ -426,10 +432,12 @@ def dgemm_blocked(A, B, plan: Plan, k_slab: int, trans_a: bool = False, trans_b:
 
 
 def launches_per_dgemm(trans_a: bool = False, trans_b: bool = False) -> int:
-    """Kernels one oz_dgemm launches: a row split is one kernel, a column split
-    three (column maxima, shifts, split), then the GEMM and the reconstruct."""
+    """Kernels one INT8 oz_dgemm launches: A's rows split in one kernel (its
+    columns, for trans_a, in three: column maxima, shifts, split); B transposed
+    and its columns split as rows (two kernels; one when trans_b); then the
+    GEMM and the reconstruct."""
     a = 3 if trans_a else 1
-    b = 1 if trans_b else 3
+    b = 1 if trans_b else 2
     return a + b + 2
 
 

@@ -15,7 +15,7 @@ using oz::round_up;
 struct Layout {
   int64_t m_pad, n_pad, k_pad;
   int64_t ldy;       // row pitch of the residue planes Y: n rounded up to 16 bytes
-  size_t flag, s, t, colmax, u, v, y, total;
+  size_t flag, s, t, colmax, u, v, y, bt, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -38,6 +38,8 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * row);
   L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
   L->y = off; off = align256(off + (size_t)p->Q * m * L->ldy * ybytes);
+  // B^T (n x k doubles): the INT8 split takes B's columns as rows of its transpose
+  L->bt = off; off = align256(off + (p->is_fp ? 0 : 8 * (size_t)n * k));
   L->total = off;
   return true;
 }
@@ -62,7 +64,15 @@ extern "C" oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int
   out[7] = L.m_pad;
   out[8] = L.n_pad;
   out[9] = L.k_pad;
+  out[10] = (int64_t)L.bt;
   return OZ_OK;
+}
+
+extern "C" oz_status oz_transpose(int64_t rows, int64_t cols, const double* X, int64_t ld, double* Y, void* stream) {
+  if (rows < 0 || cols < 0 || ld < (cols > 1 ? cols : 1)) return OZ_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return OZ_OK;
+  if (!X || !Y || !aligned(X, 8) || !aligned(Y, 8)) return OZ_ERR_INVALID_ARG;
+  return cuda_status(oz::launch_transpose(rows, cols, X, ld, Y, static_cast<cudaStream_t>(stream)));
 }
 
 extern "C" oz_status oz_plane_geometry(oz_plan plan, int64_t k_pad, int64_t* k_align, int64_t* row_bytes) {
@@ -127,9 +137,15 @@ oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n
   e = trans_a ? oz::launch_split_cols(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, colmax, st)
               : oz::launch_split_rows(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
-  // B side: vectors are the columns of op(B).
-  e = trans_b ? oz::launch_split_rows(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, st)
-              : oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
+  // B side: vectors are the columns of op(B); B (k x n) is transposed first,
+  // so that its columns are split as contiguous rows.
+  if (trans_b) {
+    e = oz::launch_split_rows(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, st);
+  } else {
+    double* Bt = reinterpret_cast<double*>(ws + L.bt);
+    e = oz::launch_transpose(k, n, B, ldb, Bt, st);
+    if (e == cudaSuccess) e = oz::launch_split_rows(T, n, k, Bt, k, L.n_pad, L.k_pad, t, V, bf16, flag, st);
+  }
   if (e != cudaSuccess) return OZ_ERR_CUDA;
   // GEMMs + epilogue
   e = (plan->engine == OZ_ENGINE_TC1 || (single_cta && plan->engine == OZ_ENGINE_TC))

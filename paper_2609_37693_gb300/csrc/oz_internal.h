@@ -212,6 +212,8 @@ cudaError_t launch_reconstruct16(const OzTables& t, int64_t m, int64_t n, const 
 // shared by the split kernels: shifts of strided vectors (colmax must be zeroed)
 cudaError_t launch_shifts_cols(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
                                int32_t* flag, uint64_t* colmax, cudaStream_t st);
+// Y (cols x rows, row pitch rows) = X^T for X rows x cols with row pitch ld
+cudaError_t launch_transpose(int64_t rows, int64_t cols, const double* X, int64_t ld, double* Y, cudaStream_t st);
 // shifts of contiguous vectors (rows), one warp per row; flags non-finite entries
 cudaError_t launch_shifts_rows(int bits, int64_t nvec, int64_t len, const double* X, int64_t ld, int32_t* shifts,
                                int32_t* flag, cudaStream_t st);

@@ -509,6 +509,28 @@ __global__ void __launch_bounds__(256) split_cols_grouped_kernel(const __grid_co
   split_cols_block<kBF16, NP>(T, l % nbx, l / nbx, P.n, P.k, P.B, P.ldb, P.n_pad, P.k_pad, P.t, P.V);
 }
 
+// Transpose of a rows x cols block of doubles (row pitch ld) into cols x rows
+// (row pitch rows), through 32 x 33 shared tiles: reads and writes both
+// coalesced. Lets the column vectors of B be split as rows.
+__global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t cols, const double* __restrict__ X,
+                                                        int64_t ld, double* __restrict__ Y) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8 threads
+  const int64_t ctiles = (cols + 31) / 32;                   // block b: tile (b / ctiles, b % ctiles)
+  const int64_t c0 = ((int64_t)blockIdx.x % ctiles) * 32, r0 = ((int64_t)blockIdx.x / ctiles) * 32;
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) {
+    const int64_t r = r0 + ty + i, c = c0 + tx;
+    if (r < rows && c < cols) tile[ty + i][tx] = __ldg(X + r * ld + c);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) {
+    const int64_t c = c0 + ty + i, r = r0 + tx;
+    if (r < rows && c < cols) Y[c * rows + r] = tile[tx][ty + i];
+  }
+}
+
 // Rows v in [nvec, nvec_pad) of the strided layout are covered by the grid
 // (grid.x spans nvec_pad), so no separate padding pass is needed.
 
@@ -551,6 +573,14 @@ cudaError_t launch_split_rows(const OzTables& t, int64_t nvec, int64_t len, cons
     case 15: split_rows_np<true, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
     default: split_rows_np<false, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int64_t rows, int64_t cols, const double* X, int64_t ld, double* Y, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  const int64_t tiles = ((cols + 31) / 32) * ((rows + 31) / 32);
+  if (tiles > INT32_MAX) return cudaErrorInvalidValue;
+  transpose_kernel<<<(unsigned)tiles, 256, 0, st>>>(rows, cols, X, ld, Y);
   return cudaGetLastError();
 }
 

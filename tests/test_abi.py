@@ -81,8 +81,9 @@ def test_workspace_bytes():
     m, n, k = 300, 200, 1000
     ws = p.workspace_bytes(m, n, k)
     planes = 16 * (512 + 256) * 1024
-    assert ws >= planes + 16 * m * n
-    assert ws < planes + 16 * m * n + 64 * 1024
+    bt = 8 * n * k                     # B transposed, so that its columns split as rows
+    assert ws >= planes + 16 * m * n + bt
+    assert ws < planes + 16 * m * n + bt + 64 * 1024
     assert p.workspace_bytes(-1, 2, 3) == 0
 
 
@@ -208,3 +209,12 @@ def test_blocked_argument_errors_are_caught_on_the_host():
     assert call(1000, 64, A=fake + 4) == oz.OZ_ERR_INVALID_ARG
     assert call(1000, 256) == oz.OZ_ERR_WORKSPACE            # workspace sized for slabs of k_pad 128
     assert oz.oz_dgemm_blocked(h, 0, 0, 0, 8, 8, 8, None, 8, None, 8, None, 8, None, 0, None) == oz.OZ_OK
+
+
+def test_transpose_argument_checks():
+    fake = 1 << 20
+    assert oz.oz_transpose(4, 8, fake, 7, fake, None) == oz.OZ_ERR_INVALID_ARG     # ld < cols
+    assert oz.oz_transpose(4, 8, None, 8, fake, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_transpose(4, 8, fake + 4, 8, fake, None) == oz.OZ_ERR_INVALID_ARG
+    assert oz.oz_transpose(0, 8, None, 8, None, None) == oz.OZ_OK
+    assert oz.oz_transpose(-1, 8, fake, 8, fake, None) == oz.OZ_ERR_INVALID_ARG

@@ -376,3 +376,15 @@ def test_widened_product_is_fl_of_exact():
     exact = brute.exact_product(A, B)
     ref = np.array([[brute.to_float(exact[i][j]) for j in range(N)] for i in range(M)])
     assert np.array_equal(_bits(C), _bits(ref))
+
+
+@pytest.mark.parametrize("rows,cols,ld", [(1, 1, 1), (33, 65, 65), (1000, 777, 800), (4096, 129, 129)])
+def test_transpose_phase_is_exact(rows, cols, ld):
+    """oz_transpose (the step oz_dgemm takes before splitting B's columns as
+    rows) moves every double unchanged, ragged tiles and row pitch included."""
+    X = np.random.default_rng(rows).standard_normal((rows, ld))
+    Xd = _dev(X)
+    Y = torch.full((cols, rows), np.nan, dtype=torch.float64, device=DEV)
+    assert oz.oz_transpose(rows, cols, Xd.data_ptr(), ld, Y.data_ptr(), _stream()) == oz.OZ_OK
+    torch.cuda.synchronize()
+    assert np.array_equal(_bits(Y.cpu().numpy()), _bits(X[:, :cols].T))
