@@ -28,7 +28,7 @@ struct HostLayout {
   int64_t rows, cols, chunk_pad, w_pad, k_pad, nbj;
   int64_t ldy;       // row pitch of the residue planes: n rounded up to 16 bytes
   size_t vplane;     // bytes of one column chunk's planes
-  size_t flag, s, t, colmax, b, a[2], c[2], u, v, y, total;
+  size_t flag, s, t, colmax, b, a[2], c[2], u, v, y, bt, total;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -69,6 +69,9 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   L->v = off; off = al(off + L->vplane * (size_t)L->nbj);
   L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
   L->y = off; off = al(off + (size_t)p->Q * rows * L->ldy * ybytes);
+  // one column chunk of B transposed (cols x k doubles): its columns are
+  // split as rows (INT8 plans)
+  L->bt = off; off = al(off + (p->is_fp ? 0 : 8 * (size_t)cols * k));
   L->total = off;
   return true;
 }
@@ -166,6 +169,14 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   }
   if (nbi > 1) copy_a(1);
 
+  // B_j (k x nc, row pitch n) transposed into Bt, then its rows split
+  double* Bt = reinterpret_cast<double*>(ws + L.bt);
+  auto launch_split_b_chunk = [&](int64_t nc, int64_t c0, void* planes) {
+    cudaError_t r = oz::launch_transpose(k, nc, Bd + c0, n, Bt, sc);
+    if (r != cudaSuccess) return r;
+    return oz::launch_split_rows(T, nc, k, Bt, k, L.w_pad, L.k_pad, t + c0, planes, bf16, flag, sc);
+  };
+
   int64_t blk = 0;   // block counter: C slot blk & 1
   for (int64_t i = 0; i < nbi && e == cudaSuccess; ++i) {
     const int slot = (int)(i & 1);
@@ -186,8 +197,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
           chk(cudaStreamWaitEvent(sc, ev_b[(size_t)j], 0));
           chk(fp ? oz::launch_split_fp(T, F, 0, nc, k, Bd + c0, n, L.w_pad, L.k_pad, t + c0,
                                        static_cast<uint8_t*>(vj(j)), flag, colmax + c0, sc)
-                 : oz::launch_split_cols(T, nc, k, Bd + c0, n, L.w_pad, L.k_pad, t + c0, vj(j), bf16, flag,
-                                         colmax + c0, sc));
+                 : launch_split_b_chunk(nc, c0, vj(j)));
         }
         chk(fp ? oz::launch_gemm_fp(F, nr, nc, L.chunk_pad, L.w_pad, L.k_pad, static_cast<const uint8_t*>(U),
                                     static_cast<const uint8_t*>(vj(j)), reinterpret_cast<uint16_t*>(Yj), L.ldy, 0,
