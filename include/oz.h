@@ -434,8 +434,9 @@ OZ_API void oz_group_destroy(oz_group group);
  *   Scratch: a file-scope __device__ array of OZ_STATIC_SCRATCH_BYTES bytes
  *   inside liboz.so. Every GPU that loads the library holds that memory until
  *   the process exits. A product fits when oz_workspace_bytes(plan, m, n, k)
- *   <= OZ_STATIC_SCRATCH_BYTES (about 800^3 at Q = 16); larger sizes return
- *   OZ_ERR_WORKSPACE before any launch.
+ *   <= OZ_STATIC_SCRATCH_BYTES (square products up to 512^3 on the TC
+ *   engine, 768^3 on IMMA, at Q = 16); larger sizes return OZ_ERR_WORKSPACE
+ *   before any launch.
  *   Allocation: none. No cudaMalloc, cudaFree or allocating library routine
  *   is called, here or in the phases it runs.
  *   Set-up: the first call on each device looks up the array's device address
