@@ -19,11 +19,7 @@ struct OzTables {
   int limbs;                              // 32-bit limbs for X in the reconstruct phase
   int pad_;
   uint32_t m[OZ_TABLE_CAP];              // moduli, decreasing
-  uint32_t half[OZ_TABLE_CAP];           // ceil(m/2): residues >= half map to r - m
   uint32_t magic[OZ_TABLE_CAP];          // floor(2^32 / m), Barrett constant
-  uint32_t c18[OZ_TABLE_CAP];            // 2^18 mod m
-  uint32_t c36[OZ_TABLE_CAP];            // 2^36 mod m
-  uint32_t c54[OZ_TABLE_CAP];            // 2^54 mod m
   uint32_t inv[OZ_TABLE_CAP];            // (P/m)^-1 mod m: CRT coefficient
   float invm[OZ_TABLE_CAP];              // 1/m rounded to fp32: quotient estimate
   float mf[OZ_TABLE_CAP];                // m as fp32
@@ -33,7 +29,6 @@ struct OzTables {
   float c52f[OZ_TABLE_CAP];
   float c12f[6][OZ_TABLE_CAP];           // 2^(12 i) mod m, i = 1..6, nearest zero: the
                                           // 12-bit pieces of widened operands (beta > 64)
-  uint32_t Mk[OZ_TABLE_CAP][OZ_MAX_LIMBS];  // P/m as 32-bit limbs, least significant first
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
   // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd
   // Q ends with a pair whose second modulus is 1 (digit 0).

@@ -143,11 +143,7 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
   for (int q = 0; q < Q; ++q) {
     uint32_t m = moduli[q];
     t.m[q] = m;
-    t.half[q] = (m + 1) / 2;
     t.magic[q] = (uint32_t)((((uint64_t)1) << 32) / m);
-    t.c18[q] = pow2_mod(18, m);
-    t.c36[q] = pow2_mod(36, m);
-    t.c54[q] = pow2_mod(54, m);
     Big Mk;
     P.divmod(m, &Mk);
     Big dummy;
@@ -161,7 +157,6 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
     t.c39f[q] = centred(pow2_mod(39, m));
     t.c52f[q] = centred(pow2_mod(52, m));
     for (int i = 0; i < 6; ++i) t.c12f[i][q] = centred(pow2_mod(12 * (i + 1), m));
-    for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Mk[q][i] = Mk.w[i];
   }
   t.npairs = (Q + 1) / 2;
   for (int pi = 0; pi < t.npairs; ++pi) {
