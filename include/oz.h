@@ -170,10 +170,12 @@ OZ_API void oz_plan_destroy(oz_plan plan);
 /*
  * oz_workspace_bytes -- device workspace a product of this shape needs: the
  * shifts, the residue planes of both operands (planes x (m_pad + n_pad) rows
- * of oz_plane_geometry's row bytes) and the residues of the product (Q x m
+ * of oz_plane_geometry's row bytes), the residues of the product (Q x m
  * rows of n entries, each row padded to a multiple of 16 bytes so that the
  * GEMM epilogue stores whole 16-byte runs; uint8, or uint16 per channel for
- * float-format plans). Returns 0 for an invalid plan or shape.
+ * float-format plans) and, for INT8 plans, B^T (n x k doubles: with
+ * trans_b = 0 the columns of B are split as rows of its transpose). Returns 0
+ * for an invalid plan or shape.
  */
 OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
 
