@@ -64,3 +64,18 @@ def test_plan_refuses_inner_dimension_above_its_configurations():
     st, h = oz.oz_plan_create_fp(oz.OZ_FMT_E4M3, 20000, 0)
     assert st == oz.OZ_ERR_K_TOO_LARGE and h is None
     assert oz.oz_plan_create_fp(99, 1000, 0)[0] == oz.OZ_ERR_UNSUPPORTED
+
+
+def test_blocked_candidates_keep_the_bits():
+    """The blocked-call configurations offered for a product keep 53 bits and
+    admit its K: the INT8 plan of the least Q (whole K and shorter slabs) and
+    each float format whose frozen configuration's window holds, in slabs of
+    its accumulation cap; past every float window only INT8 is offered."""
+    cands = oz.blocked_candidates(3000, 53, slabs=(1024,))
+    labels = [c[0] for c in cands]
+    assert labels[0].startswith("int8 q=16") and "int8 q=16 slab=1024" in labels
+    assert any(l.startswith("E4M3") for l in labels) and any(l.startswith("E2M1") for l in labels)
+    for label, plan, k_slab in cands:
+        assert plan.bits == 53 and 3000 <= plan.k_rec and k_slab <= plan.k_acc
+    far = oz.blocked_candidates(120000, 53, slabs=(8192,))
+    assert [c[0].split()[0] for c in far] == ["int8", "int8"]
