@@ -218,3 +218,51 @@ def test_transpose_argument_checks():
     assert oz.oz_transpose(4, 8, fake + 4, 8, fake, None) == oz.OZ_ERR_INVALID_ARG
     assert oz.oz_transpose(0, 8, None, 8, None, None) == oz.OZ_OK
     assert oz.oz_transpose(-1, 8, fake, 8, fake, None) == oz.OZ_ERR_INVALID_ARG
+
+
+def _layout_plans():
+    yield "tc q16", oz.Plan(16, 0, 8192, oz.OZ_ENGINE_TC), 2
+    yield "tc1 q14", oz.Plan(14, 50, 256, oz.OZ_ENGINE_TC1), 2
+    yield "imma q16", oz.Plan(16, 0, 8192, oz.OZ_ENGINE_IMMA), 1
+    yield "tc q20 widened", oz.Plan(20, 0, 4096, oz.OZ_ENGINE_TC), 2
+    for fmt in ("E4M3", "E5M2", "E2M3", "E3M2", "E2M1"):
+        yield fmt, oz.PlanFP(fmt, 8192), None
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (0, 5, 7), (300, 200, 1000), (129, 257, 4097), (8192, 8192, 8192),
+                                   (65536, 256, 256), (256, 65536, 300)])
+def test_workspace_layout_regions_are_disjoint_aligned_and_fit(m, n, k):
+    """Every region of the workspace the kernels address (shifts, column
+    maxima, the residue planes of both operands, the product's residues, B^T)
+    has the size the header documents, starts on a 256-byte boundary (16 bytes
+    is what TMA needs), overlaps no other region and ends inside
+    oz_workspace_bytes; the padded sizes are multiples of the tile and k
+    alignments. Host logic only."""
+    for name, p, elem in _layout_plans():
+        st, L = oz.oz_workspace_layout(p.handle, m, n, k)
+        assert st == oz.OZ_OK, name
+        ws = p.workspace_bytes(m, n, k)
+        _, k_align, _ = oz.oz_plane_geometry(p.handle, 0)
+        m_pad, n_pad, k_pad = L["m_pad"], L["n_pad"], L["k_pad"]
+        assert m_pad >= max(m, 1) and m_pad % 256 == 0, name
+        assert n_pad >= max(n, 1) and n_pad % 256 == 0, name
+        assert k_pad >= max(k, 1) and k_pad % k_align == 0, name
+        _, _, row = oz.oz_plane_geometry(p.handle, k_pad)
+        fp = elem is None
+        if fp:
+            nplanes, digits, digit_bytes = p.planes, len(p.moduli), 2
+            assert row == (k_pad // 2 if p.format == oz.FORMATS["E2M1"] else k_pad), name
+        else:
+            nplanes, digits, digit_bytes = p.q, p.q, 1
+            assert row == elem * k_pad, name
+        pitch = -(-max(n, 1) // (16 // digit_bytes)) * (16 // digit_bytes)
+        regions = [("flag", 16), ("s", 4 * m), ("t", 4 * n), ("colmax", 8 * max(m, n)),
+                   ("u", nplanes * m_pad * row), ("v", nplanes * n_pad * row),
+                   ("y", digits * m * pitch * digit_bytes), ("bt", 0 if fp else 8 * n * k)]
+        end = 0
+        for key, size in regions:
+            off = L[key]
+            assert off % 256 == 0, (name, key)
+            assert off >= end, (name, key, off, end)
+            end = off + size
+        assert end <= ws < end + 256, (name, end, ws)
