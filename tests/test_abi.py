@@ -248,6 +248,7 @@ def test_workspace_layout_regions_are_disjoint_aligned_and_fit(m, n, k):
         assert n_pad >= max(n, 1) and n_pad % 256 == 0, name
         assert k_pad >= max(k, 1) and k_pad % k_align == 0, name
         _, _, row = oz.oz_plane_geometry(p.handle, k_pad)
+        assert row % 16 == 0, name          # a TMA row stride is a multiple of 16 bytes
         fp = elem is None
         if fp:
             nplanes, digits, digit_bytes = p.planes, len(p.moduli), 2
