@@ -83,3 +83,19 @@ def test_beta_max_definition():
     assert oracle.beta_max(oracle.max_product_moduli(14, 239), 256) == 50
     # kappa_rec at beta = 53 by Q: 14 -> 4, 15 -> 836, 16 -> 159 819
     assert [oracle.caps(oracle.max_product_moduli(q, 239), 53)[0] for q in (14, 15, 16)] == [4, 836, 159819]
+
+
+def test_kappa_rec_reproduces_the_least_q_row_of_table():
+    """eq. caps' reconstruction cap, read against Table tab:moduli's INT8 row:
+    at each printed K, with the moduli capped where their radius still meets
+    eq. rmax (and at 256), the least Q whose kappa_rec reaches K is the
+    printed count (16, 16, 16, 18)."""
+    g = GOLD["least_q_int8"]
+    got = []
+    for K in g["K"]:
+        rm = oracle.r_max(1, K)
+        top = min(256, 2 * rm + 1)
+        while top > 2 and oracle.radius(top) > rm:
+            top -= 1
+        got.append(next(q for q in range(1, 40) if oracle.caps(oracle.max_product_moduli(q, top), 53)[0] >= K))
+    assert got == g["Q"]

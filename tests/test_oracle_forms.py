@@ -5,6 +5,7 @@ configurations checked against the oracle (no GPU)."""
 import math
 import os
 
+import numpy as np
 import pytest
 
 from oracle import forms
@@ -124,3 +125,50 @@ def test_table_moduli_e2m3_at_2p14():
     Q, mods = forms.least_q(pool.rank, 2**14)
     assert Q == 30
     assert sorted(pool.rank[m] for m in mods) == [1] * 15 + [3] * 5
+
+
+@pytest.mark.parametrize("name,K,top", [("E2M1", 2**14, None), ("E4M3", 2**13, 400), ("E3M2", 2**13, 400)])
+def test_form_tables_decode_and_recombine(name, K, top):
+    """Sec. 'Forms and Channels' for every form kind the pools hold: each
+    class c of a channel is stored as plane values of the alphabet within the
+    plane radius whose limb value (a0 for one limb, a0 + b a1 for two) is c
+    modulo m, and the form's GEMMs recombine with their weights into the
+    product of the limb values. For the four-GEMM schoolbook this is the
+    expansion of (a0 + b a1)(b0 + b b1); for Toom at 0, 1 and infinity it is
+    a0 b0 (1 - b) + (a0 + a1)(b0 + b1) b + a1 b1 (b^2 - b), the same
+    polynomial; both are exact integer identities. The three-GEMM schoolbook
+    drops a1 b1 b^2, which is 0 modulo m because m divides b^2 (eq. qm)."""
+    pool = forms.Pools(name, K, m_top=top)
+    S, _ = forms.alphabet(name)
+    r = forms.rmax1(K, forms.LAMBDA_FP32)
+    allowed = {s for s in S if abs(s) <= r}
+    by_kind = {}
+    for m, kind in sorted(pool.kind.items()):
+        by_kind.setdefault(kind, []).append(m)
+    assert set(by_kind) >= {"one", "toom", "school3"}
+    rng = np.random.default_rng(1)
+
+    def value(planes, kind, b):
+        return planes[0] if kind == "one" else planes[0] + b * planes[-1]
+
+    for kind, ms in by_kind.items():
+        for m in ms[:3] + ms[-2:]:
+            b = pool.base[m]
+            t = forms.tables(name, K, m, kind, b)
+            if kind == "toom":
+                assert all(t[1][c] == t[0][c] + t[2][c] for c in range(m))
+            for c in range(m):
+                planes = [t[p][c] for p in range(len(t))]
+                assert all(v in allowed for v in planes), (kind, m, c)
+                assert value(planes, kind, b) % m == c, (kind, m, c)
+            w = forms.weights(kind, b)
+            for c1, c2 in rng.integers(0, m, size=(64, 2)):
+                x = [t[p][c1] for p in range(len(t))]
+                y = [t[p][c2] for p in range(len(t))]
+                total = sum(lam * x[pa] * y[pb] for pa, pb, lam in w)
+                exact = value(x, kind, b) * value(y, kind, b)
+                if kind == "school3":
+                    assert (b * b) % m == 0 and total == exact - b * b * x[1] * y[1]
+                else:
+                    assert total == exact, (kind, m)
+                assert total % m == (int(c1) * int(c2)) % m
