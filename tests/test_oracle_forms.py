@@ -21,6 +21,34 @@ def test_e2m1_alphabet_and_products():
     assert len({a * b for a in S for b in S}) == 37
 
 
+def test_plane_radius_under_fp32_accumulation():
+    """Example ex:ov-equiv: r_max(1) = 32 under FP32 accumulation at K = 2^14
+    (eq. rmax with Lambda = 2^24)."""
+    assert forms.LAMBDA_FP32 == 2**24
+    assert forms.rmax1(2**14, forms.LAMBDA_FP32) == 32
+    assert forms.rmax1(2**13, forms.LAMBDA_FP32) == 45
+
+
+@pytest.mark.parametrize("name,dtype", [("E4M3", "float8_e4m3fn"), ("E5M2", "float8_e5m2")])
+def test_fp8_values_and_codes_match_a_library_decoder(name, dtype):
+    """The OCP FP8 encodings as PyTorch decodes them: every finite code's
+    value, times 2^e_S, is the oracle's code table entry, and the finite
+    values are exactly the oracle's value set (E4M3 tops out at 448, its
+    all-ones code being NaN; E5M2 keeps IEEE infinities and NaNs)."""
+    torch = pytest.importorskip("torch")
+    dt = getattr(torch, dtype, None)
+    if dt is None:
+        pytest.skip(f"torch without {dtype}")
+    vals = torch.arange(256, dtype=torch.uint8).view(dt).to(torch.float64).tolist()
+    finite = {c: v for c, v in enumerate(vals) if math.isfinite(v)}
+    _, e_s = forms.alphabet(name)
+    codes = forms.code_values(name)
+    assert set(codes) == set(finite)
+    assert all(codes[c] == finite[c] * 2**e_s for c in finite)
+    from fractions import Fraction
+    assert forms.float_values(name) == {Fraction(v) for v in finite.values()}
+
+
 def test_fp8_fp6_alphabets_agree():
     """Example ex:ov-equiv: E4M3 agrees with E2M3 up to 60 and E5M2 with E3M2 up
     to 448; Sec. 'FP8 and FP6': within radius 32, 49 values for E4M3 and E2M3

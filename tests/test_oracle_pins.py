@@ -50,6 +50,14 @@ def test_planes_are_balanced_residues_of_truncation():
                 r = int(U[k, i, h])
                 assert r == brute.balanced(a, m)
                 assert -(m // 2) <= r <= (m + 1) // 2 - 1
+    # ties of the even modulus (236) go to -m/2: the representative nearest
+    # zero read as [-m/2, m/2 - 1] (reading 3); a row maximum of 2^52 gives
+    # shift 0 at beta = 53, so these integers are their own truncations
+    row = np.array([[2.0**52, 118.0, -118.0, 354.0, -354.0, 117.0, -117.0]])
+    assert list(oracle.scale(row, 53, axis=1)) == [0]
+    U6 = oracle.planes(row, np.zeros(1, dtype=np.int32), MODS16, axis=1)
+    k236 = list(MODS16).index(236)
+    assert [int(v) for v in U6[k236, 0, 1:]] == [-118, -118, -118, -118, 117, -117]
     # B side: column shifts and the transposed planes
     _, B = synth.phi_pair(1, 5, 8, 1.0, 6)
     t = oracle.scale(B, 53, axis=0)
@@ -175,6 +183,12 @@ def test_rounding_against_exact_rationals():
         es += [-3, -7, -1075, -1075, 970, -1075]
         xs += [sgn * (2**53 - 1), sgn * (2**60)]
         es += [971, -1200]
+        # subnormal results of 55-58-bit integers where rounding to 53 bits
+        # first and then to the subnormal grid gives another answer: the
+        # rounding must be a single one
+        xs += [sgn * 62551616293623058, sgn * 41442468988376657, sgn * 71048548309309803,
+               sgn * 263350308324904376]
+        es += [-1079, -1079, -1078, -1081]
     out = oracle.round_scaled(xs, es)
     ref = [brute.to_float(Fraction(x) * Fraction(2) ** e) for x, e in zip(xs, es)]
     assert np.array_equal(_bits(out), _bits(np.array(ref)))
@@ -197,10 +211,11 @@ def test_zero_rows_and_columns():
     A, B = synth.phi_pair(5, 6, 11, 1.0, 2)
     A[2, :] = 0.0
     B[:, 4] = 0.0
-    C = oracle.dgemm(A, B, MODS16, 53)
+    C, _, s_o, t_o = oracle.dgemm(A, B, MODS16, 53, want_residues=True)
     assert np.all(_bits(C[2, :]) == 0) and np.all(_bits(C[:, 4]) == 0)
     C_ref, _, s, t = brute.emulated(A, B, 53)
-    assert s[2] == 0 and t[4] == 0
+    assert s[2] == 0 and t[4] == 0                  # eq. convert: mu = 1 for a zero row
+    assert list(s_o) == list(s) and list(t_o) == list(t)
     assert np.array_equal(_bits(C), _bits(C_ref))
 
 
