@@ -267,3 +267,62 @@ def test_workspace_layout_regions_are_disjoint_aligned_and_fit(m, n, k):
             assert off >= end, (name, key, off, end)
             end = off + size
         assert end <= ws < end + 256, (name, end, ws)
+
+
+def test_header_compiles_as_c_and_links(tmp_path):
+    """The boundary is plain C: a C11 program that includes oz.h, takes the
+    address of every declared entry point, links against liboz.so and runs
+    the host-only calls (plan, info, caps, workspace size and layout, an
+    argument error) gets what the Python binding gets."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    syms = _declared_symbols()
+    table = ",\n  ".join(f"(anyfn){s}" for s in syms)
+    src = tmp_path / "abi_client.c"
+    src.write_text(f"""
+#include <stdio.h>
+#include "oz.h"
+typedef void (*anyfn)(void);
+static const anyfn syms[] = {{
+  {table}
+}};
+int main(void) {{
+  for (size_t i = 0; i < sizeof syms / sizeof syms[0]; ++i)
+    if (!syms[i]) return 2;
+  for (int s = OZ_OK; s <= OZ_ERR_CUDA; ++s) {{
+    const char* t = oz_status_str((oz_status)s);
+    if (!t || !t[0]) return 3;
+  }}
+  oz_plan plan = NULL;
+  if (oz_plan_create(&plan, 16, 0, 8192, OZ_ENGINE_TC) != OZ_OK) return 4;
+  int q = 0, bits = 0, engine = -1;
+  int64_t kmax = 0, kacc = 0, krec = 0, lay[11];
+  uint32_t mods[32] = {{0}};
+  if (oz_plan_info(plan, &q, &bits, &kmax, &engine, mods) != OZ_OK) return 5;
+  if (oz_plan_caps(plan, &kacc, &krec) != OZ_OK) return 6;
+  if (oz_workspace_layout(plan, 1000, 300, 777, lay) != OZ_OK) return 7;
+  const size_t ws = oz_workspace_bytes(plan, 1000, 300, 777);
+  const oz_status bad = oz_dgemm(plan, 0, 0, 8, 8, 8, NULL, 8, NULL, 8, NULL, 8, NULL, 0, NULL);
+  printf("%d %d %lld %d %u %u %lld %lld %zu %lld %lld %d\\n", q, bits, (long long)kmax, engine, mods[0],
+         mods[q - 1], (long long)kacc, (long long)krec, ws, (long long)lay[4], (long long)lay[10], (int)bad);
+  oz_plan_destroy(plan);
+  if (oz_plan_create(&plan, 16, 0, 0, OZ_ENGINE_TC) != OZ_ERR_INVALID_ARG) return 8;
+  return 0;
+}}
+""")
+    libdir = os.path.dirname(oz._build.LIB)
+    exe = tmp_path / "abi_client"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", libdir, "-loz", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    got = r.stdout.split()
+    p = oz.Plan(16, 0, 8192, oz.OZ_ENGINE_TC)
+    _, lay = oz.oz_workspace_layout(p.handle, 1000, 300, 777)
+    want = [p.q, p.bits, p.k_max, p.engine, p.moduli[0], p.moduli[-1], p.k_acc, p.k_rec,
+            p.workspace_bytes(1000, 300, 777), lay["u"], lay["bt"]]
+    assert [int(x) for x in got[:-1]] == want
+    assert int(got[-1]) != oz.OZ_OK
