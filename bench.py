@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--q", type=int, default=16)
     ap.add_argument("--bits", type=int, default=0)
     ap.add_argument("--phi", type=float, default=0.5)
+    ap.add_argument("--operands", default="phi", choices=["phi", "paper"],
+                    help="phi: entries U(-0.5,0.5)*exp(phi*N(0,1)); paper: the paper's timing operands, row i "
+                         "of each operand N(0,1)*2^e_i with e_i an integer drawn from [-20, 20)")
     ap.add_argument("--engine", default="auto", choices=["auto", "imma", "tc", "tc1"])
     ap.add_argument("--format", default="int8", choices=["int8", "E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
                     help="residue alphabet: the INT8 path, or a float-format configuration")
@@ -128,8 +131,22 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def workload_name(n, phi, q, bits, fmt="int8", channels=None):
-    head = (f"emulated dgemm m=n=k={n}, entries U(-0.5,0.5)*exp({phi}*N(0,1)) seed 0 (rank r: seed r), ")
+def operands(args, m, n, k, seed):
+    """A (m x k) and B (k x n), float64, of the family --operands names."""
+    import synth
+    if args.operands == "paper":
+        return synth.row_scaled_pair(n, seed=seed, m=m, k=k)
+    return synth.phi_pair(m, n, k, args.phi, seed=seed)
+
+
+def operands_name(args):
+    if args.operands == "paper":
+        return "rows N(0,1)*2^e_i, e_i integer in [-20,20)"
+    return f"entries U(-0.5,0.5)*exp({args.phi}*N(0,1))"
+
+
+def workload_name(n, args, q, bits, fmt="int8", channels=None):
+    head = f"emulated dgemm m=n=k={n}, {operands_name(args)} seed 0 (rank r: seed r), "
     if fmt == "int8":
         return head + f"INT8 residue path Q={q} moduli<=239, beta={bits}"
     return head + f"{fmt} configuration, {q} low-precision GEMMs over {channels} channels, beta={bits}"
@@ -213,9 +230,8 @@ def oracle_rate(A, B, n, mods, bits, seconds):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    import synth
     n = args.n
-    A, B = synth.phi_pair(n, n, n, args.phi, seed=0)
+    A, B = operands(args, n, n, n, seed=0)
     import oracle
     if args.format == "int8":
         mods = oracle.max_product_moduli(args.q, 239)
@@ -240,8 +256,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": workload_name(n, args.phi, q, bits, args.format, channels),
-                   "m": n, "n": n, "k": n, "q": q, "bits": bits, "phi": args.phi, "format": args.format},
+        "config": {"workload": workload_name(n, args, q, bits, args.format, channels),
+                   "m": n, "n": n, "k": n, "q": q, "bits": bits, "phi": args.phi, "operands": args.operands,
+                   "format": args.format},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{ents} entries of C ({n}x{n}), each a full k={n} oracle evaluation "
                                    f"(scale, residues, {len(mods)} int64 dot products, CRT, rounding)"},
@@ -280,7 +297,6 @@ def bind_host_to_gpu(local):
 def run_ours(args, rank, world, local):
     import torch
     import paper_2609_37693_gb300 as oz
-    import synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -293,7 +309,7 @@ def run_ours(args, rank, world, local):
               "tc1": oz.OZ_ENGINE_TC1}[args.engine]
     plan = make_plan(oz, args, n, engine)
     is_fp = args.format != "int8"
-    A_h, B_h = synth.phi_pair(n, n, n, args.phi, seed=rank)
+    A_h, B_h = operands(args, n, n, n, seed=rank)
     A = torch.from_numpy(A_h).to(dev)
     B = torch.from_numpy(B_h).to(dev)
     C = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -471,9 +487,9 @@ def run_ours(args, rank, world, local):
             "vs_baseline": None,
             "dtype": args.format.lower() if is_fp else ("int8" if plan.engine == oz.OZ_ENGINE_IMMA else "bf16"),
             "data": "synthetic",
-            "config": {"workload": workload_name(n, args.phi, plan.q, plan.bits, args.format,
+            "config": {"workload": workload_name(n, args, plan.q, plan.bits, args.format,
                                                  getattr(plan, "channels", plan.q)),
-                       "m": n, "n": n, "k": n, "q": plan.q, "bits": plan.bits, "phi": args.phi,
+                       "m": n, "n": n, "k": n, "q": plan.q, "bits": plan.bits, "phi": args.phi, "operands": args.operands,
                        "format": args.format,
                        "engine": {1: "imma", 2: "tc", 3: "fp", 4: "tc1"}[plan.engine], "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (A and B 512 MiB each); no flush",
@@ -588,11 +604,10 @@ def run_blocked(args, rank, world, local):
     and a check that both give the same bits."""
     import torch
     import paper_2609_37693_gb300 as oz
-    import synth
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n, k, kt = args.n, args.k, args.k_slab
-    A, B = synth.phi_pair(n, n, k, args.phi, seed=rank)
+    A, B = operands(args, n, n, k, seed=rank)
     Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
     del A, B
     engine = {"auto": oz.OZ_ENGINE_TC, "imma": oz.OZ_ENGINE_IMMA, "tc": oz.OZ_ENGINE_TC,
@@ -637,7 +652,7 @@ def run_blocked(args, rank, world, local):
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": f"m=n={n}, k={k} in {nslabs} slabs of {kt}, phi={args.phi}, Q={plan.q}, "
+            "config": {"workload": f"m=n={n}, k={k} in {nslabs} slabs of {kt}, {operands_name(args)}, Q={plan.q}, "
                                    f"beta={plan.bits}, engine {args.engine}",
                        "unblocked_ms": ms_u,
                        "unblocked_tflops": flops / (ms_u * 1e-3) / 1e12 if ms_u else None,

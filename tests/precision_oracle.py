@@ -1,0 +1,73 @@
+"""Error of the emulated product on both operand families, taken from the
+oracle on a grid of sampled entries (no GPU).
+
+    python tests/precision_oracle.py --n 8192 16384 --rows 64 --cols 64
+
+The CUDA path returns the oracle's bits (the parity tests check this entry by
+entry, at 8192 too), so these are the errors of the GPU result as well. Row i
+of op(A) and column j of op(B) hold everything entry (i, j) depends on (its
+shifts included), so the sampled rows of A and columns of B are multiplied on
+their own. For each sampled entry the error is |C_ij - (AB)_ij|, formed
+exactly and rounded once, in units of u (|A||B|)_ij with u = 2^-53.
+
+Operand families (synth):
+* phi: entries U(-0.5, 0.5) exp(phi N(0, 1));
+* paper: the paper's timing operands (Table tab:setup), row i of each operand
+  N(0, 1) 2^e_i with e_i an integer drawn from [-20, 20).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+def errors(A, B, mods, beta, rows, cols):
+    As = np.ascontiguousarray(A[rows, :])
+    Bs = np.ascontiguousarray(B[:, cols])
+    C = oracle.dgemm(As, Bs, mods, beta)
+    r, c = np.divmod(np.arange(len(rows) * len(cols)), len(cols))
+    err, ab = oracle.exact_error(As, Bs, C, r, c)
+    return err / (2.0**-53 * ab)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, nargs="+", default=[8192, 16384])
+    ap.add_argument("--operands", nargs="+", default=["phi0.5", "paper"])
+    ap.add_argument("--q", type=int, default=16)
+    ap.add_argument("--rows", type=int, default=64)
+    ap.add_argument("--cols", type=int, default=64)
+    args = ap.parse_args()
+    mods = oracle.max_product_moduli(args.q, 239)
+    print("| n | operands | Q | beta | entries | max error / u(|A||B|) | median | share above 2 |")
+    print("|---|---|---|---|---|---|---|---|")
+    for n in args.n:
+        rng = np.random.default_rng(2)
+        rows = np.sort(rng.choice(n, size=args.rows, replace=False))
+        cols = np.sort(rng.choice(n, size=args.cols, replace=False))
+        for ops in args.operands:
+            if ops == "paper":
+                A, B = synth.row_scaled_pair(n, seed=0)
+            else:
+                A, B = synth.phi_pair(n, n, n, float(ops[3:]), seed=0)
+            bmax = oracle.beta_max(mods, n)
+            for beta in sorted({53, bmax}):
+                t = time.time()
+                rel = errors(A, B, mods, beta, rows, cols)
+                print(f"| {n} | {ops} | {args.q} | {beta} | {rel.size} | {rel.max():.3g} | {np.median(rel):.3g} | "
+                      f"{np.mean(rel > 2):.3g} |", flush=True)
+                print(f"  ({time.time() - t:.1f} s)", file=sys.stderr)
+            del A, B
+
+
+if __name__ == "__main__":
+    main()
