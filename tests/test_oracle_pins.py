@@ -301,3 +301,19 @@ def test_widened_conversion_is_exact_emulation(d):
     # and the oracle's arithmetic at that budget is the exact definition
     C_def, _, _, _ = brute.emulated(A, B, 53 + d)
     assert np.array_equal(_bits(C), _bits(C_def))
+
+
+def test_sampled_rows_and_columns_give_the_same_entries():
+    """Entry (i, j) depends only on row i of A and column j of B, their
+    shifts included (eq. convert), so the product of sampled rows and columns
+    equals those entries of the whole product. The error report on large
+    sizes samples this way."""
+    A, B = synth.row_scaled_pair(96, seed=3, m=80, k=130)
+    rows = np.array([0, 7, 41, 79])
+    cols = np.array([2, 3, 50, 95])
+    C_sub = oracle.dgemm(np.ascontiguousarray(A[rows]), np.ascontiguousarray(B[:, cols]), MODS16, 53)
+    r, c = np.meshgrid(rows, cols, indexing="ij")
+    C_ent = oracle.dgemm_entries(A, B, MODS16, 53, r.ravel(), c.ravel())
+    assert np.array_equal(_bits(C_sub.ravel()), _bits(C_ent))
+    C_full = oracle.dgemm(A, B, MODS16, 53)
+    assert np.array_equal(_bits(C_sub), _bits(C_full[np.ix_(rows, cols)]))
