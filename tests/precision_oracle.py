@@ -1,7 +1,8 @@
 """Error of the emulated product on both operand families, taken from the
 oracle on a grid of sampled entries (no GPU).
 
-    python tests/precision_oracle.py --n 8192 16384 --rows 64 --cols 64
+    python tests/precision_oracle.py --n 8192 16384
+    python tests/precision_oracle.py --n 8192 --operands paper --q 14 15 16 17 18 19 20
 
 The CUDA path returns the oracle's bits (the parity tests check this entry by
 entry, at 8192 too), so these are the errors of the GPU result as well. Row i
@@ -43,11 +44,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, nargs="+", default=[8192, 16384])
     ap.add_argument("--operands", nargs="+", default=["phi0.5", "paper"])
-    ap.add_argument("--q", type=int, default=16)
-    ap.add_argument("--rows", type=int, default=64)
-    ap.add_argument("--cols", type=int, default=64)
+    ap.add_argument("--q", type=int, nargs="+", default=[16])
+    ap.add_argument("--rows", type=int, default=256)
+    ap.add_argument("--cols", type=int, default=256)
     args = ap.parse_args()
-    mods = oracle.max_product_moduli(args.q, 239)
     print("| n | operands | Q | beta | entries | max error / u(|A||B|) | median | share above 2 |")
     print("|---|---|---|---|---|---|---|---|")
     for n in args.n:
@@ -59,13 +59,16 @@ def main():
                 A, B = synth.row_scaled_pair(n, seed=0)
             else:
                 A, B = synth.phi_pair(n, n, n, float(ops[3:]), seed=0)
-            bmax = oracle.beta_max(mods, n)
-            for beta in sorted({53, bmax}):
-                t = time.time()
-                rel = errors(A, B, mods, beta, rows, cols)
-                print(f"| {n} | {ops} | {args.q} | {beta} | {rel.size} | {rel.max():.3g} | {np.median(rel):.3g} | "
-                      f"{np.mean(rel > 2):.3g} |", flush=True)
-                print(f"  ({time.time() - t:.1f} s)", file=sys.stderr)
+            for q in args.q:
+                mods = oracle.max_product_moduli(q, 239)
+                bmax = oracle.beta_max(mods, n)
+                # the paper's 53 where the window admits it, and the widest beta
+                for beta in sorted({b for b in (53, bmax) if b <= bmax}):
+                    t = time.time()
+                    rel = errors(A, B, mods, beta, rows, cols)
+                    print(f"| {n} | {ops} | {q} | {beta} | {rel.size} | {rel.max():.3g} | {np.median(rel):.3g} | "
+                          f"{np.mean(rel > 2):.3g} |", flush=True)
+                    print(f"  ({time.time() - t:.1f} s)", file=sys.stderr)
             del A, B
 
 
