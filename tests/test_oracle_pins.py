@@ -51,8 +51,9 @@ def test_planes_are_balanced_residues_of_truncation():
                 assert r == brute.balanced(a, m)
                 assert -(m // 2) <= r <= (m + 1) // 2 - 1
     # ties of the even modulus (236) go to -m/2: the representative nearest
-    # zero read as [-m/2, m/2 - 1] (reading 3); a row maximum of 2^52 gives
-    # shift 0 at beta = 53, so these integers are their own truncations
+    # zero (Sec. "Ozaki II") taken in [-m/2, m/2 - 1], which is two's
+    # complement at m = 256; a row maximum of 2^52 gives shift 0 at
+    # beta = 53, so these integers are their own truncations
     row = np.array([[2.0**52, 118.0, -118.0, 354.0, -354.0, 117.0, -117.0]])
     assert list(oracle.scale(row, 53, axis=1)) == [0]
     U6 = oracle.planes(row, np.zeros(1, dtype=np.int32), MODS16, axis=1)
