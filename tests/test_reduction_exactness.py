@@ -46,3 +46,38 @@ def test_single_rint_reduction_is_exact(m):
     ri = r.astype(np.int64)
     assert ri.min() >= -(m // 2) and ri.max() <= (m + 1) // 2 - 1
     assert np.array_equal(ri % m, k % m)                          # r = a' mod m: y' - 1/4 = k
+
+
+T_MAX = 1024 * 119 * 119 + 2 * 120    # a slab's sum plus the residue it lands on (and the other chain's)
+
+
+@pytest.mark.parametrize("m", MODULI)
+def test_slab_drain_reduction_bounds_the_residue(m):
+    """The TC GEMM epilogue reduces each FP32 accumulator value t (an integer,
+    |t| <= 1024 * 119^2 + 240 < 2^24) to r = t - m rint(t fl(1/m)), one fma
+    rounding for the quotient. Claim: r = t mod m and |r| <= 120, so the next
+    slab's sum on top of r stays below 2^24 (eq. ov-accgen) and r + 128 fits
+    in a byte. Every t in range is tried."""
+    assert T_MAX < 2**24
+    invm = float(np.float32(1.0) / np.float32(m))
+    step = 1 << 22
+    for lo in range(-T_MAX, T_MAX + 1, step):
+        t = np.arange(lo, min(lo + step, T_MAX + 1), dtype=np.int64)
+        q = np.rint(t.astype(np.float64) * invm)              # exact product, one rounding
+        r = t - q.astype(np.int64) * m
+        assert np.abs(r).max() <= 120
+        assert np.array_equal(r % m, t % m)
+
+
+@pytest.mark.parametrize("m", MODULI)
+def test_digit_step_lands_in_range(m):
+    """The last slab's digit: y = (W mod m) inv with inv = (P/m)^-1 mod m, an
+    integer below 239^2 (exact in fp32), then y - m rint(y fl(1/m)) and one
+    correction by +m if negative. Claim: the result is y mod m in [0, m)."""
+    invm = float(np.float32(1.0) / np.float32(m))
+    y = np.arange(0, (m - 1) * (m - 1) + 1, dtype=np.int64)
+    q = np.rint(y.astype(np.float64) * invm).astype(np.int64)
+    d = y - q * m
+    d = np.where(d < 0, d + m, d)
+    assert d.min() >= 0 and d.max() < m
+    assert np.array_equal(d, y % m)
