@@ -544,7 +544,7 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                   __int_as_float(0x4B000000u | ((acc16[ch * 16 + w] >> (16 * j)) & 0xffffu)) - 8390656.0f;
               const float W = __uint_as_float(v[2 * w + j]) * wscale;               // exact integer, |W| <= 2^24
               const float wq = fmaf(W, invm, 12582912.0f) - 12582912.0f;
-              const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.51 m
+              const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.65 m
               const float tsum = fmaf(lam, wm, prev);                              // exact: < 2^24
               const float q2 = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
               const float r = fmaf(-q2, mf, tsum);                                 // |r| < 0.51 m

@@ -17,6 +17,8 @@ Here every reachable y' (|y'| <= 8191 (1 + 4 * 119) + 1/4) is tried for every
 modulus the INT8 plans use (the 20 of the nested max-product list up to 239),
 against exact integer arithmetic. fl(1/m) is the float32 quotient 1.0f / m.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -81,3 +83,32 @@ def test_digit_step_lands_in_range(m):
     d = np.where(d < 0, d + m, d)
     assert d.min() >= 0 and d.max() < m
     assert np.array_equal(d, y % m)
+
+
+@pytest.mark.parametrize("fmt", ["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"])
+@pytest.mark.parametrize("k_hint", [8192, 16384])
+def test_float_format_fold_stays_exact(fmt, k_hint):
+    """The float-format GEMM epilogue folds each GEMM's integer W of a channel
+    (|W| <= K rho^2 <= 2^24, rho the plane radius) into the channel's running
+    residue r, all in fp32: wm = W - m rint(W fl(1/m)), t = lambda wm + r,
+    r' = t - m rint(t fl(1/m)), with 0 <= lambda < m. From the exact error of
+    fl(1/m) this bounds |wm|, shows t below 2^24 (so exact), and gives a bound
+    R >= |r'| that holds for every fold: R < 0.51 m, and r + 2048 fits its
+    16-bit field. At the end, r is taken to [0, m) and multiplied by the CRT
+    coefficient (below m^2 < 2^24), and one more quotient lands in (-m, m)."""
+    import paper_2609_37693_gb300 as oz
+    plan = oz.PlanFP(fmt, k_hint)
+    K = plan.k_cfg
+    rho = int(np.floor(np.sqrt(2**24 / K)))
+    w_max = K * rho * rho
+    assert w_max <= 2**24
+    for m in plan.moduli:
+        assert m < 4096
+        delta = abs(Fraction(float(np.float32(1.0) / np.float32(m))) - Fraction(1, m))
+        wm_max = Fraction(m, 2) + m * w_max * delta
+        assert wm_max < Fraction(65, 100) * m
+        # R = m/2 + m delta ((m - 1) wm_max + R), the bound that reproduces itself
+        R = (Fraction(m, 2) + m * delta * (m - 1) * wm_max) / (1 - m * delta)
+        assert (m - 1) * wm_max + R < 2**24
+        assert R < Fraction(51, 100) * m and R < 2048
+        assert (m - 1) ** 2 < 2**24 and Fraction(1, 2) + (m - 1) ** 2 * delta < 1
