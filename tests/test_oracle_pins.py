@@ -318,3 +318,19 @@ def test_sampled_rows_and_columns_give_the_same_entries():
     assert np.array_equal(_bits(C_sub.ravel()), _bits(C_ent))
     C_full = oracle.dgemm(A, B, MODS16, 53)
     assert np.array_equal(_bits(C_sub), _bits(C_full[np.ix_(rows, cols)]))
+
+
+def test_error_report_helper_on_a_small_case():
+    """The sampled-grid error of tests/precision_oracle.py against entries
+    computed one by one: the same values, and within 2u at the widest beta."""
+    from tests import precision_oracle
+    A, B = synth.phi_pair(200, 150, 300, 0.5, seed=4)
+    rows, cols = np.array([0, 5, 199]), np.array([1, 149])
+    beta = oracle.beta_max(MODS16, 300)
+    rel = precision_oracle.errors(A, B, MODS16, beta, rows, cols)
+    r, c = np.meshgrid(rows, cols, indexing="ij")
+    C = np.zeros((200, 150))
+    C[r.ravel(), c.ravel()] = oracle.dgemm_entries(A, B, MODS16, beta, r.ravel(), c.ravel())
+    err, ab = oracle.exact_error(A, B, C, r.ravel(), c.ravel())
+    assert np.array_equal(rel, err / (2.0**-53 * ab))
+    assert rel.max() <= 2.0
