@@ -441,21 +441,34 @@ OZ_API void oz_group_destroy(oz_group group);
  *   before any launch.
  *   Allocation: none. No cudaMalloc, cudaFree or allocating library routine
  *   is called, here or in the phases it runs.
- *   Set-up: the first call on each device looks up the array's device address
- *   with cudaGetSymbolAddress, with that device current, and caches it; make
- *   that first call before any stream capture on that device.
+ *   Set-up: every call looks up the array's device address with
+ *   cudaGetSymbolAddress in the caller's current device and context (the
+ *   address differs between contexts). The first call on a device may load
+ *   the library's device code there; make that first call before any stream
+ *   capture on that device.
  *   Sharing: every call on a device uses the same array and leaves its
  *   contents behind; each call clears what must start at zero. Two calls that
  *   overlap on the GPU (other streams, other host threads) race on the array
  *   and give undefined results: serialise them.
- *   Non-finite input is not reported (oz_query_status needs a workspace
- *   pointer); C is then unspecified.
+ *   Status: non-finite input and a bounded device wait that ran out are
+ *   recorded in the array's status word, which oz_static_query_status reads;
+ *   C is then unspecified.
  */
 OZ_API oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
                                  const double* A, int64_t lda, const double* B, int64_t ldb,
                                  double* C, int64_t ldc, void* stream);
 
-/* Short English description of a status code (static string). */
+/*
+ * oz_static_query_status -- the status of the last oz_dgemm_static call on
+ * the current device, as oz_query_status reports it for a workspace: waits
+ * for the stream, then reads the status word of the built-in array (no
+ * allocation; a copy from the device symbol) and returns OZ_ERR_NONFINITE for
+ * NaN or Inf input, OZ_ERR_CUDA if the stream has a CUDA error or a bounded
+ * device wait ran out, else OZ_OK. Meaningful only while no other
+ * oz_dgemm_static call on the device has run since the one it reports.
+ */
+OZ_API oz_status oz_static_query_status(void* stream);
+
 /*
  * oz_selftest_bounded_wait -- exercises the failure path of the GEMM kernels'
  * waits on the device: one thread waits, with the same bounded wait the
@@ -468,6 +481,7 @@ OZ_API oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int64_t
  */
 OZ_API oz_status oz_selftest_bounded_wait(int arrive, int32_t* status, void* stream);
 
+/* Short English description of a status code (static string). */
 OZ_API const char* oz_status_str(oz_status status);
 
 #ifdef __cplusplus

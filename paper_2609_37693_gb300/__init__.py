@@ -53,7 +53,7 @@ EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_b
             "oz_dgemm_host", "oz_plan_create_fp", "oz_plan_info_fp", "oz_plane_geometry",
             "oz_grouped_workspace_bytes", "oz_group_create", "oz_group_run", "oz_group_destroy",
             "oz_plan_caps", "oz_blocked_workspace_bytes", "oz_dgemm_blocked", "oz_selftest_bounded_wait",
-            "oz_transpose")
+            "oz_transpose", "oz_static_query_status")
 
 
 class OzError(RuntimeError):
@@ -86,6 +86,7 @@ def _load_library():
         "oz_reconstruct": (I32, [P, I64, I64, P, P, P, P, I64, P]),
         "oz_status_str": (ctypes.c_char_p, [I32]),
         "oz_dgemm_static": (I32, [P, I32, I32, I64, I64, I64, P, I64, P, I64, P, I64, P]),
+        "oz_static_query_status": (I32, [P]),
         "oz_batched_workspace_bytes": (SZ, [I32, P, P, I32]),
         "oz_host_workspace_bytes": (SZ, [P, I64, I64, I64, I64, I64]),
         "oz_plan_create_fp": (I32, [ctypes.POINTER(P), I32, I64, I32]),
@@ -226,6 +227,11 @@ def oz_dgemm_static(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, str
     callers that cannot allocate device memory. Calls overlapping on the GPU race."""
     return _lib.oz_dgemm_static(plan, int(trans_a), int(trans_b), int(m), int(n), int(k), A, int(lda), B, int(ldb),
                                 C, int(ldc), stream)
+
+
+def oz_static_query_status(stream) -> int:
+    """Status of the last oz_dgemm_static call on the current device (waits for the stream)."""
+    return _lib.oz_static_query_status(stream)
 
 
 def oz_batched_workspace_bytes(count, plans, mnk, nstreams) -> int:

@@ -2,10 +2,9 @@
 // array built into the library, for callers that cannot allocate device
 // memory (a BLAS-style dgemm interface has no workspace argument; some host
 // programs own every device allocation themselves). The paper has no
-// counterpart to this entry point.
+// counterpart to this entry point. oz_static_query_status reads the status
+// word the last such product left in the array.
 #include <stdint.h>
-
-#include <atomic>
 
 #include "oz_internal.h"
 
@@ -14,27 +13,15 @@ namespace {
 // One array per GPU that loads the library, held until the process exits.
 static __device__ __align__(256) unsigned char g_oz_scratch[OZ_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::atomic<void*> g_scratch_ptr[kMaxDevices];
-
-// In host code g_oz_scratch names a host-side stand-in, not device memory:
-// the device address comes from cudaGetSymbolAddress, looked up once per
-// device with that device current.
+// In host code g_oz_scratch names a host-side stand-in, not device memory.
+// The device address comes from cudaGetSymbolAddress, looked up on every call
+// with the caller's device and context current: a __device__ symbol has its
+// own address in each context, so an address kept from another context (or
+// from before a cudaDeviceReset) could be stale. The lookup is a host call.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < kMaxDevices) {
-    void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
-    if (p) {
-      *out = p;
-      return cudaSuccess;
-    }
-  }
   void* p = nullptr;
-  e = cudaGetSymbolAddress(&p, g_oz_scratch);
+  cudaError_t e = cudaGetSymbolAddress(&p, g_oz_scratch);
   if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < kMaxDevices) g_scratch_ptr[dev].store(p, std::memory_order_release);
   *out = p;
   return cudaSuccess;
 }
@@ -51,8 +38,19 @@ extern "C" oz_status oz_dgemm_static(oz_plan plan, int trans_a, int trans_b, int
   if (m == 0 || n == 0) return oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, nullptr, 0, stream);
   void* ws = nullptr;
   if (scratch_address(&ws) != cudaSuccess || !ws) return OZ_ERR_CUDA;
-  // oz_dgemm clears the status flag and the column-maximum words it reuses;
+  // oz_dgemm clears the status word and the column-maximum words it reuses;
   // every plane and residue it reads was written earlier in the same call.
   return oz_dgemm(plan, trans_a, trans_b, m, n, k, A, lda, B, ldb, C, ldc, ws, (size_t)OZ_STATIC_SCRATCH_BYTES,
                   stream);
+}
+
+extern "C" oz_status oz_static_query_status(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OZ_ERR_CUDA;
+  // the status word is the first word of the workspace layout (oz_workspace_layout)
+  int32_t flag = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_oz_scratch, sizeof flag, 0, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OZ_ERR_CUDA;
+  if (flag & 2) return OZ_ERR_CUDA;   // a bounded device wait ran out
+  return (flag & 1) ? OZ_ERR_NONFINITE : OZ_OK;
 }

@@ -1,11 +1,14 @@
 """The differentiable emulated product (EmuMatmul): gradients dA = dC B^T and
-dB = A^T dC through the same kernels, checked against central finite
-differences, torch.autograd.gradcheck, and FP64 autograd within the error
-bound of the two computations."""
+dB = A^T dC through the same kernels, checked bit for bit against the oracle's
+products (each is an emulated product of its own, rounded once from the exact
+product of its truncated operands), against central finite differences,
+torch.autograd.gradcheck, and FP64 autograd within the error bound of the two
+computations."""
 import numpy as np
 import pytest
 
 import synth
+from tests.oracle_check import assert_oracle_bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,6 +53,13 @@ def test_gradients_match_fp64_autograd_and_finite_differences(m, k, n):
     A, B, dC = _t(A_h, True), _t(B_h, True), _t(dC_h)
     C = oz.emu_matmul(A, B)
     C.backward(dC)
+    # the forward product and both gradients against the oracle, bit for bit:
+    # every entry at 300 x 70 x 129, 2048 sampled entries (with the last row
+    # and column) at the large shapes
+    pc, pa, pb = oz.plan_for(k), oz.plan_for(n), oz.plan_for(m)
+    assert_oracle_bits(C, A_h, B_h, pc.moduli, pc.bits, what="C = A B", count=2048, seed=1)
+    assert_oracle_bits(A.grad, dC_h, B_h.T, pa.moduli, pa.bits, what="dA = dC B^T", count=2048, seed=2)
+    assert_oracle_bits(B.grad, A_h.T, dC_h, pb.moduli, pb.bits, what="dB = A^T dC", count=2048, seed=3)
     # FP64 autograd
     A2, B2 = _t(A_h, True), _t(B_h, True)
     (A2 @ B2).backward(dC)

@@ -1,9 +1,12 @@
 """Batched uneven products (one oz_dgemm_batched call, optionally one CUDA
-graph): every product equals the one oz_dgemm computes alone, bit for bit."""
+graph) and grouped products (one launch per phase): every product equals the
+oracle's, bit for bit (Sec. "Emulation Problem": C = fl(2^-(s+t) A'B') for
+each problem at its plan's bit budget)."""
 import numpy as np
 import pytest
 
 import synth
+from tests.oracle_check import assert_oracle_bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,11 +30,10 @@ def _problems(count, lo, hi, seed):
     return shapes, As, Bs, Cs
 
 
-def _alone(shapes, As, Bs, plans):
-    out = []
-    for (m, n, k), A, B, p in zip(shapes, As, Bs, plans):
-        out.append(oz.dgemm(A, B, p).cpu().numpy())
-    return out
+def _check_oracle(shapes, As, Bs, Cs, plans, what):
+    """Every product against the oracle at its own plan's moduli and bits."""
+    for i, ((m, n, k), A, B, C, p) in enumerate(zip(shapes, As, Bs, Cs, plans)):
+        assert_oracle_bits(C, A, B, p.moduli, p.bits, what=f"{what}, problem {i}", seed=i)
 
 
 @pytest.mark.parametrize("nstreams", [1, 3])
@@ -42,9 +44,7 @@ def test_batched_equals_individual_products(nstreams):
     assert [p.q for p in bg.plans] == [14 if k <= 4 else 15 if k <= 836 else 16 for (_, _, k) in shapes]
     bg.run(As, Bs, Cs)
     torch.cuda.synchronize()
-    ref = _alone(shapes, As, Bs, bg.plans)
-    for C, R in zip(Cs, ref):
-        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+    _check_oracle(shapes, As, Bs, Cs, bg.plans, f"batched, {nstreams} streams")
 
 
 def test_graph_capture_replays_on_new_inputs():
@@ -60,9 +60,7 @@ def test_graph_capture_replays_on_new_inputs():
             B.copy_(torch.from_numpy(b))
         bg.replay()
         torch.cuda.synchronize()
-        ref = _alone(shapes, As, Bs, bg.plans)
-        for C, R in zip(Cs, ref):
-            assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+        _check_oracle(shapes, As, Bs, Cs, bg.plans, f"batched graph, replay {rnd}")
 
 
 def test_autotuner_picks_a_stream_count():
@@ -70,9 +68,7 @@ def test_autotuner_picks_a_stream_count():
     bg, timings = oz.autotune_batched(shapes, As, Bs, Cs, candidates=(1, 2, 4))
     assert set(timings) == {1, 2, 4} and bg.nstreams == min(timings, key=timings.get)
     torch.cuda.synchronize()
-    ref = _alone(shapes, As, Bs, bg.plans)
-    for C, R in zip(Cs, ref):
-        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+    _check_oracle(shapes, As, Bs, Cs, bg.plans, "autotuned streams")
 
 
 # ---- grouped products: one launch per phase (oz_group_create / oz_group_run) ----
@@ -100,9 +96,7 @@ def test_grouped_equals_individual_products(which):
     gg.run()
     torch.cuda.synchronize()
     assert oz.query_status(gg.ws) == oz.OZ_OK
-    ref = _alone(shapes, As, Bs, gg.plans)
-    for (m, n, k), C, R in zip(shapes, Cs, ref):
-        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64)), (m, n, k)
+    _check_oracle(shapes, As, Bs, Cs, gg.plans, f"grouped ({which})")
 
 
 def test_grouped_graph_replays_on_new_inputs():
@@ -118,9 +112,7 @@ def test_grouped_graph_replays_on_new_inputs():
             B.copy_(torch.from_numpy(b))
         gg.replay()
         torch.cuda.synchronize()
-        ref = _alone(shapes, As, Bs, gg.plans)
-        for C, R in zip(Cs, ref):
-            assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+        _check_oracle(shapes, As, Bs, Cs, gg.plans, f"grouped graph, replay {rnd}")
 
 
 def test_grouped_reports_nonfinite():
@@ -135,17 +127,16 @@ def test_grouped_reports_nonfinite():
 def test_autotuned_batch_structures_agree():
     """Every candidate of the batch autotuner (streams, grouped at the least Q,
     grouped with every product on Q = 16) keeps 53 bits, so each returns the
-    products oz_dgemm computes alone; the autotuner keeps the fastest."""
+    oracle's products at 53 bits; the autotuner keeps the fastest."""
     shapes, As, Bs, Cs = _problems(20, 16, 1200, seed=9)
-    ref = _alone(shapes, As, Bs, [oz.plan_least_q(k, 53) for (_, _, k) in shapes])
+    least = [oz.plan_least_q(k, 53) for (_, _, k) in shapes]
     runner, label, times = oz.autotune_batch(shapes, As, Bs, Cs, streams=(1, 4), reps=1)
     assert set(times) == {"streams=1", "streams=4", "streams=1 pairs", "grouped", "grouped q=16"} and label in times
     for C in Cs:
         C.fill_(np.nan)
     runner.replay()
     torch.cuda.synchronize()
-    for C, R in zip(Cs, ref):
-        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+    _check_oracle(shapes, As, Bs, Cs, least, f"autotuned batch ({label})")
     q16 = oz.Plan(16, 53, 1200, oz.OZ_ENGINE_TC)
     gq = oz.GroupedGemm(As, Bs, Cs, plans=[q16] * len(shapes))
     for C in Cs:
@@ -153,5 +144,4 @@ def test_autotuned_batch_structures_agree():
     gq.run()
     torch.cuda.synchronize()
     assert gq.launches() <= 7
-    for C, R in zip(Cs, ref):
-        assert np.array_equal(C.cpu().numpy().view(np.uint64), R.view(np.uint64))
+    _check_oracle(shapes, As, Bs, Cs, least, "grouped, every product on Q = 16")

@@ -1,11 +1,12 @@
 """oz_dgemm_host (host-resident operands, C in blocks, copies overlapped with
-the phases of neighbouring blocks) gives the product oz_dgemm gives, bit for
-bit, whatever the block shape (ragged last blocks, edges not multiples of 16,
-one block, k = 0)."""
+the phases of neighbouring blocks) gives the oracle's product bit for bit
+(Sec. "Emulation Problem"), whatever the block shape (ragged last blocks,
+edges not multiples of 16, one block, k = 0)."""
 import numpy as np
 import pytest
 
 import synth
+from tests.oracle_check import assert_oracle_bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,9 +30,8 @@ def test_host_path_equals_device_path(engine, m, n, k, rows, cols):
     hg = oz.HostGemm(plan, m, n, k, rows, cols_per_chunk=cols)
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
-    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
-    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
     assert oz.query_status(hg.ws) == oz.OZ_OK
+    assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, plan.bits, what=f"host path {m}x{n}x{k}")
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E3M2", "E2M1"])
@@ -45,9 +45,8 @@ def test_host_path_float_formats(fmt, m, n, k, rows, cols):
     hg = oz.HostGemm(plan, m, n, k, rows, cols_per_chunk=cols)
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
-    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
-    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
     assert oz.query_status(hg.ws) == oz.OZ_OK
+    assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, plan.bits, what=f"host path {m}x{n}x{k}")
 
 
 def test_host_path_widened_budget():
@@ -62,5 +61,4 @@ def test_host_path_widened_budget():
     hg = oz.HostGemm(plan, m, n, k, 256, cols_per_chunk=256)
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
-    ref = oz.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), plan).cpu().numpy()
-    assert np.array_equal(Ch.numpy().view(np.uint64), ref.view(np.uint64))
+    assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, 70, what="host path, beta = 70")

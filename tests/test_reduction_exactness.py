@@ -89,7 +89,9 @@ def test_digit_step_lands_in_range(m):
 @pytest.mark.parametrize("k_hint", [8192, 16384])
 def test_float_format_fold_stays_exact(fmt, k_hint):
     """The float-format GEMM epilogue folds each GEMM's integer W of a channel
-    (|W| <= K rho^2 <= 2^24, rho the plane radius) into the channel's running
+    (|W| <= K rho^2 <= 2^24, rho the largest plane value of the plan and K
+    its accumulation cap k_acc, the longest inner dimension one GEMM may take,
+    Sec. "Slabs") into the channel's running
     residue r, all in fp32: wm = W - m rint(W fl(1/m)), t = lambda wm + r,
     r' = t - m rint(t fl(1/m)), with 0 <= lambda < m. From the exact error of
     fl(1/m) this bounds |wm|, shows t below 2^24 (so exact), and gives a bound
@@ -98,8 +100,10 @@ def test_float_format_fold_stays_exact(fmt, k_hint):
     coefficient (below m^2 < 2^24), and one more quotient lands in (-m, m)."""
     import paper_2609_37693_gb300 as oz
     plan = oz.PlanFP(fmt, k_hint)
-    K = plan.k_cfg
-    rho = int(np.floor(np.sqrt(2**24 / K)))
+    # the premise, from the plan itself: its plane tables and its cap
+    rho = max(max(abs(int(v)) for v in tab) for tab in plan.plane_values())
+    K = plan.k_acc
+    assert K >= plan.k_cfg
     w_max = K * rho * rho
     assert w_max <= 2**24
     for m in plan.moduli:
