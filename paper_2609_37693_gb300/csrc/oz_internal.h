@@ -9,6 +9,7 @@
 
 #define OZ_MAX_LIMBS 6     // 32-bit limbs of the CRT sum: Q P < 2^192 for Q <= 20
 #define OZ_TABLE_CAP 32    // moduli a constant table can hold (INT8 plans use at most 20)
+#define OZ_RG_MAX 8        // groups of the byte-digit reconstruct (Q <= 16 gives at most 6)
 
 // Everything a kernel needs about a configuration. Passed by value as a kernel
 // parameter, so it lives in the constant bank and every access indexed by a
@@ -37,6 +38,17 @@ struct OzTables {
   uint32_t pb[(OZ_TABLE_CAP + 1) / 2];   // m_b (1 for a lone last modulus)
   float pinv[(OZ_TABLE_CAP + 1) / 2];    // 1 / (m_a m_b) rounded to fp32
   uint32_t Np[(OZ_TABLE_CAP + 1) / 2][OZ_MAX_LIMBS];  // P / (m_a m_b), 32-bit limbs
+  // Moduli in groups for the reconstruct of byte digits (Q <= 16): rg_nt
+  // triples, then rg_np2 pairs or rg_nq4 quads, over consecutive moduli. A
+  // group g of moduli M_g = prod m_q contributes t_g = sum_q y_q (M_g / m_q)
+  // (below (size) M_g; a quad reduces each of its pairs first, t_g < 2 M_g)
+  // times N_g = P / M_g to the CRT sum. rg_nt = rg_np2 = rg_nq4 = 0: not
+  // available (the pairs above serve).
+  int rg_nt, rg_np2, rg_nq4;
+  uint32_t rg_w0[OZ_RG_MAX], rg_w1[OZ_RG_MAX];   // dp2a weights: two 16-bit per word
+  uint32_t rg_m2a[OZ_RG_MAX], rg_m2b[OZ_RG_MAX]; // quad: the products of its two pairs
+  uint32_t rg_N[OZ_RG_MAX][4];                   // N_g = P / M_g, 32-bit limbs
+  float rg_invM[OZ_RG_MAX];                      // 1 / M_g rounded to fp32 (S / P = sum_g t_g / M_g)
 };
 
 // A low-precision float configuration (Sec. "Forms and Channels"): channels

@@ -122,6 +122,81 @@ int64_t kappa_rec(const Big& P, int beta) {
 
 namespace oz {
 
+// Groups of moduli for the reconstruct of byte digits (oz_reconstruct.cu): as
+// many triples as fit, the remaining one or two moduli joined to the last
+// groups as one quad (when its product is below 2^31) or as pairs. Left
+// unset (rg_nt = rg_np2 = rg_nq4 = 0) unless every bound the kernel relies on
+// holds: digits and moduli below 256 (dp2a takes bytes), weights below 2^16,
+// the sum of the groups' largest t_g below 2^32 (each 64-bit limb
+// accumulator then stays below 2^64), N_g below 2^128, the CRT sum below
+// 15 P (its quotient fits the kernel's table of 16 multiples of P), and
+// 3P / 2 below 2^127 (the two's-complement candidate X).
+void fill_group_tables(OzTables* tp, const uint32_t* moduli, int Q, const Big& P) {
+  OzTables& t = *tp;
+  t.rg_nt = t.rg_np2 = t.rg_nq4 = 0;
+  if (Q < 2 || Q > 16 || P.bitlen() > 125) return;
+  for (int q = 0; q < Q; ++q)
+    if (moduli[q] >= 256) return;
+  int nt = Q / 3, np2 = 0, nq4 = 0;
+  if (Q % 3 == 2) np2 = 1;
+  if (Q % 3 == 1) {
+    --nt;                                   // the last triple and the lone modulus: a quad, or two pairs
+    const uint64_t m4 = (uint64_t)moduli[Q - 4] * moduli[Q - 3] * moduli[Q - 2] * moduli[Q - 1];
+    if (m4 < ((uint64_t)1 << 31)) nq4 = 1; else np2 = 2;
+  }
+  if (nt < 0 || nt + np2 + nq4 > OZ_RG_MAX) return;
+  double tsum = 0.0, ksum = 0.0;            // sum of the largest t_g, sum of t_max / M_g
+  int q = 0;
+  for (int g = 0; g < nt + np2 + nq4; ++g) {
+    uint64_t Mg = 1;
+    int size = g < nt ? 3 : g < nt + np2 ? 2 : 4;
+    for (int i = 0; i < size; ++i) Mg *= moduli[q + i];
+    const uint32_t ma = moduli[q], mb = moduli[q + 1];
+    if (size == 3) {
+      const uint32_t mc = moduli[q + 2];
+      if ((uint64_t)mb * mc >= 65536 || (uint64_t)ma * mc >= 65536 || (uint64_t)ma * mb >= 65536) return;
+      t.rg_w0[g] = (mb * mc) | ((ma * mc) << 16);        // y_a (m_b m_c) + y_b (m_a m_c)
+      t.rg_w1[g] = ma * mb;                               // y_c (m_a m_b)
+      tsum += 3.0 * (double)Mg;
+      ksum += 3.0;
+    } else if (size == 2) {
+      t.rg_w0[g] = mb | (ma << 16);                       // y_a m_b + y_b m_a
+      t.rg_w1[g] = 0;
+      tsum += 2.0 * (double)Mg;
+      ksum += 2.0;
+    } else {
+      const uint32_t mc = moduli[q + 2], md = moduli[q + 3];
+      t.rg_w0[g] = mb | (ma << 16);
+      t.rg_w1[g] = md | (mc << 16);
+      t.rg_m2a[g] = ma * mb;
+      t.rg_m2b[g] = mc * md;
+      if (ma * mb >= 65536 || mc * md >= 65536 || Mg >= ((uint64_t)1 << 31)) return;
+      tsum += 2.0 * (double)Mg;
+      ksum += 2.0;
+    }
+    Big N;
+    Big Mb(1);
+    for (int i = 0; i < size; ++i) Mb = Mb.mul(moduli[q + i]);
+    // N = P / M_g by two exact divisions (M_g may exceed 2^32)
+    Big N1;
+    P.divmod(moduli[q], &N1);
+    N = N1;
+    for (int i = 1; i < size; ++i) {
+      Big N2;
+      N.divmod(moduli[q + i], &N2);
+      N = N2;
+    }
+    if (N.bitlen() > 128) return;
+    for (int l = 0; l < 4; ++l) t.rg_N[g][l] = N.w[l];
+    t.rg_invM[g] = (float)(1.0 / (double)Mg);
+    q += size;
+  }
+  if (q != Q || tsum >= 4294967296.0 || ksum > 15.0) return;
+  t.rg_nt = nt;
+  t.rg_np2 = np2;
+  t.rg_nq4 = nq4;
+}
+
 // Per-modulus constants and the CRT sum's limbs for moduli m[0..Q-1] (pairwise
 // coprime, each below 2^12): Barrett and reduction constants for the split
 // kernels, (P/m)^-1 mod m for the epilogue, and P, P/m, and the pair products
@@ -168,6 +243,7 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
     P.divmod(ma * mb, &Np);
     for (int i = 0; i < OZ_MAX_LIMBS; ++i) t.Np[pi][i] = Np.w[i];
   }
+  fill_group_tables(&t, moduli, Q, P);
   return true;
 }
 

@@ -15,11 +15,27 @@
 // [-P/2, P/2). The window (eq. ov-crtgen) makes that X the exact integer
 // product (A'B')_ij.
 //
+// For byte digits with Q <= 16 the moduli are taken in groups instead
+// (reconstruct_groups_kernel): triples (a, b, c) with
+//   t = y_a (m_b m_c) + y_b (m_a m_c) + y_c (m_a m_b) < 3 m_a m_b m_c < 2^26,
+// two packed 16-bit x 8-bit dot products (dp2a) of the three digit bytes,
+// and for Q = 16 a last quad whose two pairs are reduced first (t < 2 M_4 <
+// 2^32). S = sum_g t_g (P / M_g) then takes five groups of four 32-bit
+// limbs instead of eight pairs: 20 wide multiply-adds per entry against 32,
+// and no reduction inside the triples. S is formed modulo 2^128 (it can reach
+// 15 P); its quotient by P comes from S / P = sum_g t_g / M_g in fp32 (all
+// terms non-negative: within 2^-18), X = S - qP from a shared table of qP,
+// and an estimate within 2^-10 of a tie is settled exactly. The kernel is persistent: each thread loads the digits of its next
+// four entries before it reconstructs the current ones, so the loads of one
+// chunk overlap the arithmetic of the last.
+//
 // The binary64 result fl(X 2^-(s_i + t_j)) is assembled from integer fields:
 // the leading 53 bits (fewer below 2^-1022), round to nearest even from the
 // round bit and the sticky bits, overflow to +-inf. No floating-point
 // operation touches the value, so the rounding happens exactly once.
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "oz_internal.h"
 
@@ -431,6 +447,277 @@ __global__ void __launch_bounds__(256) reconstruct128_kernel(const __grid_consta
                                   C, ldc);
 }
 
+// ---------------------------------------------------------------------------
+// Byte digits in groups of moduli (Q <= 16; tables rg_* of OzTables).
+// ---------------------------------------------------------------------------
+
+// t_g of group g for entry e of the digit words w (byte e of each word is that
+// entry's digit for one modulus)
+template <int NT, int NP2, int NQ4>
+__device__ __forceinline__ uint32_t group_t(int g, const uint32_t* w, int e, uint32_t w0, uint32_t w1, uint32_t m2a,
+                                            uint32_t m2b) {
+  const uint32_t s2 = (uint32_t)e | ((uint32_t)(4 + e) << 4);         // bytes [w_a.e, w_b.e, -, -]
+  if (g < NT) {                                    // triple: moduli 3g, 3g+1, 3g+2
+    const int q = 3 * g;
+    const uint32_t s3 = 0x0010u | ((uint32_t)(4 + e) << 8);           // bytes [y.0, y.1, w_c.e, -]
+    const uint32_t y = __byte_perm(__byte_perm(w[q], w[q + 1], s2), w[q + 2], s3);
+    return __dp2a_lo(w0, y, __dp2a_hi(w1, y, 0u));
+  }
+  if (g < NT + NP2) {                              // pair
+    const int q = 3 * NT + 2 * (g - NT);
+    return __dp2a_lo(w0, __byte_perm(w[q], w[q + 1], s2), 0u);
+  }
+  const int q = 3 * NT + 2 * NP2;                  // quad: both pairs reduced, then combined
+  const uint32_t zab = __dp2a_lo(w0, __byte_perm(w[q], w[q + 1], s2), 0u);
+  const uint32_t zcd = __dp2a_lo(w1, __byte_perm(w[q + 2], w[q + 3], s2), 0u);
+  const uint32_t wab = min(zab, zab - m2a);        // z < 2 M_2: z mod M_2
+  const uint32_t wcd = min(zcd, zcd - m2b);
+  return wab * m2b + wcd * m2a;                    // < 2 M_4 < 2^32
+}
+
+// The CRT sum of entry e of the digit words w[0..Q-1]: S modulo 2^128 as
+// 32-bit limbs s[0..3], and f = sum_g fl(t_g) fl(1 / M_g), an estimate of
+// S / P. Per limb l, a_l = sum_g t_g n_{g,l} in 64 bits (below 2^64: the sum
+// of the largest t_g is below 2^32); only the low 32 bits of a_3 reach S.
+template <int NT, int NP2, int NQ4>
+__device__ __forceinline__ void crt_groups(const OzTables& T, const uint32_t* w, int e, uint32_t (&s)[4], float& f) {
+  uint64_t a0 = 0, a1 = 0, a2 = 0;
+  uint32_t a3 = 0;
+  f = 0.0f;
+#pragma unroll
+  for (int g = 0; g < NT + NP2 + NQ4; ++g) {
+    const bool quad = g >= NT + NP2;
+    const uint32_t tg = group_t<NT, NP2, NQ4>(g, w, e, T.rg_w0[g], T.rg_w1[g], quad ? T.rg_m2a[g] : 0u,
+                                              quad ? T.rg_m2b[g] : 0u);
+    a0 += (uint64_t)tg * T.rg_N[g][0];
+    a1 += (uint64_t)tg * T.rg_N[g][1];
+    a2 += (uint64_t)tg * T.rg_N[g][2];
+    a3 += tg * T.rg_N[g][3];
+    f = fmaf(__uint2float_rn(tg), T.rg_invM[g], f);
+  }
+  // S = a0 + a1 2^32 + a2 2^64 + a3 2^96 modulo 2^128
+  s[0] = (uint32_t)a0;
+  asm("add.cc.u32 %0, %3, %4;\n\taddc.cc.u32 %1, %5, %6;\n\taddc.u32 %2, %7, %8;"
+      : "=r"(s[1]), "=r"(s[2]), "=r"(s[3])
+      : "r"((uint32_t)(a0 >> 32)), "r"((uint32_t)a1), "r"((uint32_t)(a1 >> 32)), "r"((uint32_t)a2),
+        "r"((uint32_t)(a2 >> 32)), "r"(a3));
+}
+
+// x -= y over four 32-bit limbs (modulo 2^128)
+__device__ __forceinline__ void sub128(uint32_t (&x)[4], const uint32_t (&y)[4]) {
+  asm("sub.cc.u32 %0, %0, %4;\n\tsubc.cc.u32 %1, %1, %5;\n\tsubc.cc.u32 %2, %2, %6;\n\tsubc.u32 %3, %3, %7;"
+      : "+r"(x[0]), "+r"(x[1]), "+r"(x[2]), "+r"(x[3])
+      : "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]));
+}
+
+__device__ __forceinline__ u128 to_u128(const uint32_t (&x)[4]) {
+  return ((u128)(((uint64_t)x[3] << 32) | x[2]) << 64) | (((uint64_t)x[1] << 32) | x[0]);
+}
+
+// fl(X 2^ex) for X = S - qP, q the quotient estimate; kP[q] = q P (shared),
+// in the usual case: the estimate clear of a tie, 2^96 <= |X| and a normal
+// result. It runs in 32-bit limbs: the magnitude by a sign mask, the leading
+// bit by clz of the top limb, 64 bits below it by funnel shifts, one
+// round-to-nearest-even increment. Returns false (out unset) otherwise.
+__device__ __forceinline__ bool round_groups_fast(const uint4* kP, const uint32_t (&s)[4], float f, int ex,
+                                                  uint64_t& out) {
+  const float kf = rintf(f);
+  const int k = min((int)kf, 15);
+  const uint4 kp = kP[k];
+  uint32_t x[4] = {s[0], s[1], s[2], s[3]};
+  const uint32_t kq[4] = {kp.x, kp.y, kp.z, kp.w};
+  sub128(x, kq);
+  // magnitude: (x ^ mask) - mask
+  const uint32_t mask = (uint32_t)((int32_t)x[3] >> 31);
+  uint32_t m[4] = {x[0] ^ mask, x[1] ^ mask, x[2] ^ mask, x[3] ^ mask};
+  const uint32_t mk[4] = {mask, mask, mask, mask};
+  sub128(m, mk);
+  const int lz = __clz((int)m[3]);
+  const int E = 127 - lz + ex;                             // exponent of the leading bit
+  if (fabsf(f - kf) > 0.499f || m[3] == 0 || (unsigned)(E + 1022) > 2045u) return false;
+  // 64 bits from the leading one down (h1:h0), and whether any bit below is set
+  const uint32_t h1 = __funnelshift_l(m[2], m[3], lz);
+  const uint32_t h0 = __funnelshift_l(m[1], m[2], lz);
+  const uint32_t r = __funnelshift_l(m[0], m[1], lz) | (m[0] << lz);
+  const uint64_t mant = (((uint64_t)h1 << 32) | h0) >> 11;  // 53 bits, leading one at bit 52
+  const uint32_t half = (h0 >> 10) & 1u;
+  const uint32_t sticky = ((h0 & 0x3ffu) | r) != 0u;
+  const uint64_t q = mant + (half & (sticky | (uint32_t)mant));
+  uint64_t b = ((uint64_t)(E + 1022) << 52) + q;            // a carry out of the significand bumps E
+  if (b >= 0x7ff0000000000000ull) b = 0x7ff0000000000000ull;
+  out = ((uint64_t)(mask & 1u) << 63) | b;
+  return true;
+}
+
+// Every other case, recomputed from the digits (wsm[q * 256], this thread's
+// shared-memory slots): the CRT sum S exactly in 128 bits (S < 15 P < 2^128),
+// X = S - qP corrected exactly into [-P/2, P/2), and the general rounding.
+template <int NT, int NP2, int NQ4>
+__device__ __noinline__ uint64_t round_groups_slow(const OzTables& T, const uint4* kP, const uint32_t* wsm, int e,
+                                                   int ex) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  uint32_t w[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) w[q] = wsm[q * 256];
+  uint32_t s[4];
+  float f;
+  crt_groups<NT, NP2, NQ4>(T, w, e, s, f);
+  const int k = min((int)rintf(f), 15);
+  const uint4 kp = kP[k];
+  const uint32_t kq[4] = {kp.x, kp.y, kp.z, kp.w};
+  sub128(s, kq);
+  __int128 X = (__int128)to_u128(s);
+  const uint4 p = kP[1];
+  const u128 P = ((u128)(((uint64_t)p.w << 32) | p.z) << 64) | (((uint64_t)p.y << 32) | p.x);
+  if (2 * X >= (__int128)P) X -= (__int128)P;
+  else if (2 * X < -(__int128)P) X += (__int128)P;
+  const uint32_t neg = X < 0;
+  const u128 mag = neg ? (u128)(-X) : (u128)X;
+  return round128(mag, neg, ex);
+}
+
+// kP[q] = q P for q = 0..15, as four 32-bit limbs (threads 0..15 of the block)
+__device__ __forceinline__ void fill_kP(const OzTables& T, uint4* kP) {
+  if (threadIdx.x < 16) {
+    const u128 P = ((u128)(((uint64_t)T.P[3] << 32) | T.P[2]) << 64) | (((uint64_t)T.P[1] << 32) | T.P[0]);
+    const u128 v = P * (u128)threadIdx.x;
+    kP[threadIdx.x] = make_uint4((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)(v >> 64), (uint32_t)(v >> 96));
+  }
+}
+
+// Four entries (i, j0 .. j0 + 3), j0 < n, from their digit words, which this
+// thread holds in its shared-memory slots wsm[q * 256].
+template <int NT, int NP2, int NQ4>
+__device__ __forceinline__ void rec4_groups(const OzTables& T, const uint4* kP, const uint32_t* wsm, int64_t i,
+                                            int64_t j0, int64_t n, int32_t si, const int32_t* __restrict__ t,
+                                            double* __restrict__ C, int64_t ldc) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  int32_t tj[4];
+  if (j0 + 4 <= n && (reinterpret_cast<uintptr_t>(t + j0) & 15) == 0) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(t + j0));
+    tj[0] = v.x, tj[1] = v.y, tj[2] = v.z, tj[3] = v.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tj[e] = j0 + e < n ? __ldg(t + j0 + e) : 0;
+  }
+  uint32_t w[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) w[q] = wsm[q * 256];
+  uint64_t out[4];
+  uint32_t slow = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    uint32_t S[4];
+    float f;
+    crt_groups<NT, NP2, NQ4>(T, w, e, S, f);
+    if (!round_groups_fast(kP, S, f, -(si + tj[e]), out[e])) slow |= 1u << e;
+  }
+  if (slow) {                                              // rare: one branch for the four entries
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((slow >> e) & 1u) out[e] = round_groups_slow<NT, NP2, NQ4>(T, kP, wsm, e, -(si + tj[e]));
+  }
+  double* cp = C + i * ldc + j0;
+  if (j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+    __stcs(reinterpret_cast<double2*>(cp), make_double2(__longlong_as_double((long long)out[0]),
+                                                        __longlong_as_double((long long)out[1])));
+    __stcs(reinterpret_cast<double2*>(cp) + 1, make_double2(__longlong_as_double((long long)out[2]),
+                                                            __longlong_as_double((long long)out[3])));
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (j0 + e < n) cp[e] = __longlong_as_double((long long)out[e]);
+  }
+}
+
+// Asynchronous 4-byte copy global -> shared (cp.async, cached at all levels)
+// and its group commit / wait.
+__device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// The digit words of the four entries (i, j0 .. j0 + 3) into this thread's
+// slots buf[q * 256] of a shared buffer (nothing when j0 >= n). Whole words:
+// the row pitch ldy is a multiple of 4 and j0 + 4 <= ldy.
+template <int Q>
+__device__ __forceinline__ void issue_digits(const uint8_t* __restrict__ Y, int64_t plane, int64_t ldy, int64_t i,
+                                             int64_t j0, int64_t n, uint32_t* buf) {
+  if (j0 < n) {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(Y + i * ldy + j0);
+    const int64_t pw = plane >> 2;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cp_async4(buf + q * 256, p + q * pw);
+  }
+}
+
+// Persistent: block task b = (row i, chunk c) of 1024 entries, b advancing by
+// the grid size. Every thread copies the next task's digit words into its own
+// shared-memory slots (cp.async, two buffers) before it reconstructs the
+// current task's four entries, so the loads of one task overlap the arithmetic
+// of the last without holding registers; each thread reads only the slots it
+// filled, so no barrier is needed.
+template <int NT, int NP2, int NQ4>
+__global__ void __launch_bounds__(256, 2) reconstruct_groups_kernel(const __grid_constant__ OzTables T, int64_t m,
+                                                                    int64_t n, const uint8_t* __restrict__ Y,
+                                                                    int64_t ldy, const int32_t* __restrict__ s,
+                                                                    const int32_t* __restrict__ t,
+                                                                    double* __restrict__ C, int64_t ldc,
+                                                                    int64_t nch) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  __shared__ uint4 kP[16];
+  __shared__ uint32_t buf[2][Q * 256];
+  fill_kP(T, kP);
+  __syncthreads();
+  const int64_t plane = m * ldy;
+  const int64_t total = m * nch;
+  const int64_t step_i = gridDim.x / nch, step_c = gridDim.x % nch;
+  int64_t b = blockIdx.x, i = b / nch, c = b % nch;
+  uint32_t* const mine = buf[0] + threadIdx.x;       // slot s: mine + s * Q * 256
+  int slot = 0;
+  if (b < total) issue_digits<Q>(Y, plane, ldy, i, (c * 256 + threadIdx.x) * 4, n, mine);
+  cp_async_commit();
+  while (b < total) {
+    int64_t bn = b + gridDim.x, in = i + step_i, cn = c + step_c;
+    if (cn >= nch) cn -= nch, ++in;
+    if (bn < total) issue_digits<Q>(Y, plane, ldy, in, (cn * 256 + threadIdx.x) * 4, n, mine + (slot ^ 1) * Q * 256);
+    cp_async_commit();
+    cp_async_wait1();                       // this task's copies have landed
+    const int64_t j0 = (c * 256 + threadIdx.x) * 4;
+    if (j0 < n) rec4_groups<NT, NP2, NQ4>(T, kP, mine + slot * Q * 256, i, j0, n, __ldg(s + i), t, C, ldc);
+    slot ^= 1;
+    b = bn, i = in, c = cn;
+  }
+}
+
+// Grouped products: as reconstruct128_grouped_kernel, with the groups' sum.
+template <int NT, int NP2, int NQ4>
+__global__ void __launch_bounds__(256) reconstruct_groups_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                         const OzGroupProblem* __restrict__ probs,
+                                                                         int count) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  __shared__ uint4 kP[16];
+  __shared__ uint32_t buf[Q * 256];
+  fill_kP(T, kP);
+  __syncthreads();
+  const int64_t b = blockIdx.x;
+  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rec_begin; });
+  const OzGroupProblem& P = probs[pi];
+  const int tpr = P.rec_tpr, rows = 256 / tpr;
+  const int64_t l = b - P.rec_begin, nch = (P.n + 4 * tpr - 1) / (4 * tpr);
+  const int64_t i = (l / nch) * rows + threadIdx.x / tpr;
+  const int64_t j0 = ((l % nch) * tpr + threadIdx.x % tpr) * 4;
+  if (i >= P.m || j0 >= P.n) return;
+  uint32_t* const mine = buf + threadIdx.x;
+  issue_digits<Q>(P.Y, P.m * P.ldy, P.ldy, i, j0, P.n, mine);
+  cp_async_commit();
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  rec4_groups<NT, NP2, NQ4>(T, kP, mine, i, j0, P.n, __ldg(P.s + i), P.t, P.C, P.ldc);
+}
+
 // Grouped: a block covers 256 / tpr rows of one column chunk of 4 tpr entries
 // (tpr = rec_tpr threads per row chunk, so short rows share a block); block b
 // is row group l / nch, chunk l % nch of its problem, l = b - rec_begin.
@@ -466,12 +753,73 @@ cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, 
   return cudaGetLastError();
 }
 
+// CTAs of a kernel resident per SM, times the SM count (cached per device)
+template <typename K>
+int persistent_grid(K kernel, int threads) {
+  static int cache[64][2];                    // [device] = {kernel-independent SM count, CTAs per SM}
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) return 0;
+  (void)cache;
+  return sms * (per > 0 ? per : 1);
+}
+
+template <int NT, int NP2, int NQ4>
+cudaError_t launch_groups(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
+                          const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  const int64_t nch = (n + 1023) / 1024;
+  const int64_t total = m * nch;
+  int grid = persistent_grid(reconstruct_groups_kernel<NT, NP2, NQ4>, 256);
+  if (grid <= 0) return cudaErrorInvalidValue;
+  if ((int64_t)grid > total) grid = (int)total;
+  reconstruct_groups_kernel<NT, NP2, NQ4><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc, nch);
+  return cudaGetLastError();
+}
+
+// The group shape of a plan (oz_plan.cpp, fill_group_tables), as a switch
+// over the shapes Q = 9 .. 16 give: -1 if the plan has none.
+int group_shape(const OzTables& T) {
+  const int key = T.rg_nt * 100 + T.rg_np2 * 10 + T.rg_nq4;
+  switch (key) {
+    case 300: case 220: case 310: case 400: case 301: case 320: case 410: case 500: case 401: case 420:
+      return key;
+    default: return -1;
+  }
+}
+
+template <typename F>
+cudaError_t with_shape(int key, F f) {
+  switch (key) {
+    case 300: return f(std::integral_constant<int, 3>(), std::integral_constant<int, 0>(), std::integral_constant<int, 0>());
+    case 220: return f(std::integral_constant<int, 2>(), std::integral_constant<int, 2>(), std::integral_constant<int, 0>());
+    case 310: return f(std::integral_constant<int, 3>(), std::integral_constant<int, 1>(), std::integral_constant<int, 0>());
+    case 400: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 0>(), std::integral_constant<int, 0>());
+    case 301: return f(std::integral_constant<int, 3>(), std::integral_constant<int, 0>(), std::integral_constant<int, 1>());
+    case 320: return f(std::integral_constant<int, 3>(), std::integral_constant<int, 2>(), std::integral_constant<int, 0>());
+    case 410: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 1>(), std::integral_constant<int, 0>());
+    case 500: return f(std::integral_constant<int, 5>(), std::integral_constant<int, 0>(), std::integral_constant<int, 0>());
+    case 401: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 0>(), std::integral_constant<int, 1>());
+    case 420: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 2>(), std::integral_constant<int, 0>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
                                const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
   if (ldy < n) return cudaErrorInvalidValue;
+  // byte digits in groups: whole 4-byte digit words need a row pitch and base
+  // that are multiples of 4
+  const int shape = group_shape(T);
+  if (shape >= 0 && (ldy & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 3) == 0) {
+    return with_shape(shape, [&](auto nt, auto np2, auto nq4) {
+      return launch_groups<decltype(nt)::value, decltype(np2)::value, decltype(nq4)::value>(T, m, n, Y, ldy, s, t, C,
+                                                                                            ldc, st);
+    });
+  }
   if (T.limbs <= 4) {
     switch (T.npairs) {
       case 5: return launch128<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
@@ -491,7 +839,17 @@ cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const ui
 cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* probs, int count, int64_t total_rec,
                                        cudaStream_t st) {
   if (count == 0 || total_rec == 0) return cudaSuccess;
-  if (total_rec > INT32_MAX || T.limbs > 4) return cudaErrorInvalidValue;
+  if (total_rec > INT32_MAX) return cudaErrorInvalidValue;
+  // every grouped problem's digit rows have a pitch of a multiple of 16 bytes
+  const int shape = group_shape(T);
+  if (shape >= 0) {
+    return with_shape(shape, [&](auto nt, auto np2, auto nq4) {
+      reconstruct_groups_grouped_kernel<decltype(nt)::value, decltype(np2)::value, decltype(nq4)::value>
+          <<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count);
+      return cudaGetLastError();
+    });
+  }
+  if (T.limbs > 4) return cudaErrorInvalidValue;
   switch (T.npairs) {
     case 5: reconstruct128_grouped_kernel<5><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
     case 6: reconstruct128_grouped_kernel<6><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;

@@ -152,10 +152,22 @@ def _digits(x, moduli):
     return [((x % mq) * pow((P // mq) % mq, -1, mq)) % mq for mq in moduli]
 
 
-@pytest.mark.parametrize("q", [9, 11, 13, 14, 15, 16, 17, 20])
-def test_reconstruct_edge_integers(q):
+def _from_digits(d, moduli):
+    """The integer in [-P/2, P/2) whose CRT digits are d."""
+    P = oracle.modulus_product(moduli)
+    x = sum(int(dq) * (P // mq) for dq, mq in zip(d, moduli)) % P
+    return x - P if x >= P - P // 2 else x
+
+
+@pytest.mark.parametrize("q", [9, 10, 11, 12, 13, 14, 15, 16, 17, 20])
+@pytest.mark.parametrize("pitch4", [True, False])
+def test_reconstruct_edge_integers(q, pitch4):
     """Integers at the window's edges, ties of the final rounding, subnormal and
-    overflowing results, fed as CRT digits straight to the reconstruct phase."""
+    overflowing results, and digit patterns at the extremes of the CRT sum
+    (every digit m_q - 1: the largest sum; every digit 0 but one), fed as CRT
+    digits straight to the reconstruct phase. pitch4: a row length that is a
+    multiple of 4 (whole digit words, the grouped-moduli kernel for Q <= 16)
+    or one that is not (the byte-wise kernel)."""
     plan = oz.Plan(q, 0, 4, oz.OZ_ENGINE_IMMA)
     P = oracle.modulus_product(plan.moduli)
     rng = np.random.default_rng(q)
@@ -163,8 +175,14 @@ def test_reconstruct_edge_integers(q):
           3 << 70, (2**53 + 1), -(2**53 + 3)]
     xs += [int(v) for v in rng.integers(-2**62, 2**62, size=20)]
     xs += [int(rng.integers(1, 2**62)) << int(rng.integers(0, 60)) for _ in range(20)]
+    xs += [_from_digits([mq - 1 for mq in plan.moduli], plan.moduli)]
+    for r in range(q):
+        xs.append(_from_digits([mq - 1 if i == r else 0 for i, mq in enumerate(plan.moduli)], plan.moduli))
+    xs += [_from_digits([int(rng.integers(0, mq)) for mq in plan.moduli], plan.moduli) for _ in range(24)]
     xs = [x for x in xs if -(P // 2) <= x < P // 2]
-    exps = [0, -1, 5, -1074, -1100, -1200, 1000, 900, 1023, -1022, -30, 60]
+    while (len(xs) % 4 == 0) != pitch4:
+        xs.append(int(rng.integers(-2**40, 2**40)))
+    exps = [0, -1, 5, -1074, -1100, -1200, 1000, 900, 1023, -1022, -30, 60, -120, -140]
     n = len(xs)
     m = len(exps)
     # C[i][j] = X_j * 2^-(s_i + t_j): take t = 0, s_i = -exps[i]

@@ -17,6 +17,7 @@ Here every reachable y' (|y'| <= 8191 (1 + 4 * 119) + 1/4) is tried for every
 modulus the INT8 plans use (the 20 of the nested max-product list up to 239),
 against exact integer arithmetic. fl(1/m) is the float32 quotient 1.0f / m.
 """
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -116,3 +117,87 @@ def test_float_format_fold_stays_exact(fmt, k_hint):
         assert (m - 1) * wm_max + R < 2**24
         assert R < Fraction(51, 100) * m and R < 2048
         assert (m - 1) ** 2 < 2**24 and Fraction(1, 2) + (m - 1) ** 2 * delta < 1
+
+
+def _groups(moduli):
+    """The grouping of the byte-digit reconstruct: triples, then the last one
+    or two moduli joined into a quad (product below 2^31) or pairs."""
+    Q = len(moduli)
+    nt, rest = Q // 3, Q % 3
+    sizes = [3] * nt
+    if rest == 2:
+        sizes.append(2)
+    elif rest == 1:
+        sizes.pop()
+        if math.prod(moduli[Q - 4:]) < 2**31:
+            sizes.append(4)
+        else:
+            sizes += [2, 2]
+    out, q = [], 0
+    for sz in sizes:
+        out.append(tuple(moduli[q:q + sz]))
+        q += sz
+    return out
+
+
+def _group_t(grp, y):
+    """t_g as the kernel forms it: sum y_q (M_g / m_q); a quad reduces each pair first."""
+    if len(grp) == 4:
+        ma, mb, mc, md = grp
+        zab, zcd = y[0] * mb + y[1] * ma, y[2] * md + y[3] * mc
+        wab, wcd = zab % (ma * mb), zcd % (mc * md)
+        assert zab < 2 * ma * mb and zcd < 2 * mc * md    # one conditional subtraction reduces each
+        return wab * (mc * md) + wcd * (ma * mb)
+    Mg = math.prod(grp)
+    return sum(yq * (Mg // mq) for yq, mq in zip(y, grp))
+
+
+@pytest.mark.parametrize("Q", list(range(9, 17)))
+def test_grouped_crt_sum_is_exact(Q):
+    """The reconstruct of byte digits in groups of moduli (Sec. "Around the
+    GEMMs", Reconstruct): every t_g fits 32 bits and the sum of their maxima
+    stays below 2^32 (so each 64-bit accumulator of t_g times a 32-bit limb of
+    P / M_g is exact), P / M_g fits four limbs, S = sum_g t_g (P / M_g) is
+    congruent to X modulo P and below 15 P (the table of qP has 16 entries),
+    and the fp32 quotient estimate sum_g fl(t_g) fl(1 / M_g) (fused
+    multiply-adds, every term non-negative) is within 2^-18 of S / P, far
+    inside the 2^-10 margin below which the kernel settles a tie exactly.
+    Checked on the largest digits, single-digit patterns and random digits
+    against Python integers."""
+    import numpy as np
+    mods = oracle.max_product_moduli(Q)
+    P = math.prod(mods)
+    assert P.bit_length() <= 125 and all(m < 256 for m in mods)
+    groups = _groups(mods)
+    tmax = [(2 if len(g) == 4 else len(g)) * math.prod(g) for g in groups]
+    assert sum(tmax) < 2**32 and sum(t // math.prod(g) for t, g in zip(tmax, groups)) <= 15
+    for g in groups:
+        if len(g) == 3:
+            assert all(a * b < 2**16 for a, b in ((g[1], g[2]), (g[0], g[2]), (g[0], g[1])))
+        assert (P // math.prod(g)).bit_length() <= 128
+    invM = [np.float32(1.0 / math.prod(g)) for g in groups]
+    inv = [pow(P // m, -1, m) for m in mods]
+    rng = np.random.default_rng(Q)
+    cases = [[m - 1 for m in mods], [0] * Q]
+    cases += [[m - 1 if i == r else 0 for i, m in enumerate(mods)] for r in range(Q)]
+    cases += [[int(rng.integers(0, m)) for m in mods] for _ in range(2000)]
+    for y in cases:
+        acc = [0, 0, 0, 0]
+        q = 0
+        f = np.float32(0.0)
+        for gi, g in enumerate(groups):
+            t = _group_t(g, y[q:q + len(g)])
+            assert 0 <= t < 2**32
+            # fmaf: one rounding of fl(t) * fl(1/M) + f
+            f = np.float32(Fraction(float(np.float32(t))) * Fraction(float(invM[gi])) + Fraction(float(f)))
+            N = P // math.prod(g)
+            for l in range(4):
+                acc[l] += t * ((N >> (32 * l)) & 0xffffffff)
+            q += len(g)
+        assert max(acc) < 2**64
+        S = acc[0] + (acc[1] << 32) + (acc[2] << 64) + (acc[3] << 96)
+        X = sum(yq * (P // m) for yq, m in zip(y, mods)) % P
+        assert S % P == X and S < 15 * P
+        # the residues the digits encode: y_q = (X mod m_q) inv_q mod m_q
+        assert all((X % m) * iv % m == yq for yq, m, iv in zip(y, mods, inv))
+        assert abs(Fraction(float(f)) - Fraction(S, P)) < Fraction(1, 2**18)
