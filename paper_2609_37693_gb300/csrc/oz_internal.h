@@ -24,12 +24,12 @@ struct OzTables {
   uint32_t inv[OZ_TABLE_CAP];            // (P/m)^-1 mod m: CRT coefficient
   float invm[OZ_TABLE_CAP];              // 1/m rounded to fp32: quotient estimate
   float mf[OZ_TABLE_CAP];                // m as fp32
-  float c13f[OZ_TABLE_CAP];              // 2^13 mod m, 2^26, 2^39, 2^52 mod m, each as the
-  float c26f[OZ_TABLE_CAP];              // representative nearest zero (|c| <= 119)
-  float c39f[OZ_TABLE_CAP];
-  float c52f[OZ_TABLE_CAP];
-  float c12f[6][OZ_TABLE_CAP];           // 2^(12 i) mod m, i = 1..6, nearest zero: the
+  float c13f[4][OZ_TABLE_CAP];           // 2^(22 + 13 i) mod m, i = 0..3, each as the
+                                          // representative nearest zero (|c| <= 119): the
+                                          // split's pieces above its first 22 bits
+  float c12f[6][OZ_TABLE_CAP];           // 2^(22 + 12 i) mod m, i = 0..5, nearest zero: the
                                           // 12-bit pieces of widened operands (beta > 64)
+  float halfm[OZ_TABLE_CAP];             // m / 2 for an even m (the split maps +m/2 to -m/2)
   uint32_t P[OZ_MAX_LIMBS];               // P = product of the moduli, 32-bit limbs
   // Moduli taken in pairs (a, b) = (2p, 2p+1) for the reconstruct phase; an odd
   // Q ends with a pair whose second modulus is 1 (digit 0).

@@ -227,11 +227,9 @@ bool fill_crt_tables(OzTables* tp, const uint32_t* moduli, int Q, int bits) {
     t.invm[q] = 1.0f / (float)m;
     t.mf[q] = (float)m;
     auto centred = [m](uint32_t c) { return (float)(c >= (m + 1) / 2 ? (int)c - (int)m : (int)c); };
-    t.c13f[q] = centred(pow2_mod(13, m));
-    t.c26f[q] = centred(pow2_mod(26, m));
-    t.c39f[q] = centred(pow2_mod(39, m));
-    t.c52f[q] = centred(pow2_mod(52, m));
-    for (int i = 0; i < 6; ++i) t.c12f[i][q] = centred(pow2_mod(12 * (i + 1), m));
+    for (int i = 0; i < 4; ++i) t.c13f[i][q] = centred(pow2_mod(22 + 13 * i, m));
+    for (int i = 0; i < 6; ++i) t.c12f[i][q] = centred(pow2_mod(22 + 12 * i, m));
+    t.halfm[q] = (m & 1u) ? 0.0f : (float)(m / 2);
   }
   t.npairs = (Q + 1) / 2;
   for (int pi = 0; pi < t.npairs; ++pi) {
@@ -294,6 +292,10 @@ extern "C" oz_status oz_plan_create(oz_plan* out, int num_moduli, int bits, int6
   if (k_hint > p->k_max) { delete p; return OZ_ERR_K_TOO_LARGE; }
 
   if (!oz::fill_crt_tables(&p->tab, kModuli, Q, beta)) { delete p; return OZ_ERR_UNSUPPORTED; }
+  // the split kernels map the tie +m/2 of an even modulus to -m/2 for the
+  // modulus at index 2 only (236 in the list); every other modulus is odd
+  for (int q = 0; q < Q; ++q)
+    if (q != 2 && (kModuli[q] & 1u) == 0) { delete p; return OZ_ERR_UNSUPPORTED; }
   p->gemms = Q;
   *out = p;
   return OZ_OK;

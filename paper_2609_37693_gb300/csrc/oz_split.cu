@@ -9,22 +9,23 @@
 // 53-bit significand f and exponent E, x 2^s = f 2^(E - 1075 + s), so a'
 // is f shifted left or right (the right shift truncates toward zero). The
 // residue modulo m (m <= 239) is formed in exact fp32 arithmetic (twice the
-// integer issue rate): |a'| < 2^64 is cut once per entry into signed 13-bit
-// pieces P0..P4 (P0..P3 when beta <= 52), P0 biased by 1/4, and per modulus
-//   y' = P0 + 1/4 + P1 c13 + P2 c26 + P3 c39 + P4 c52,   c_k = 2^k mod m, |c_k| <= 119,
-// a multiple of 1/4 congruent to a' + 1/4 with |y'| < 8191 * 477 + 1 < 2^22,
-// so every partial sum is exact. Widened operands (beta up to 84, Sec. "Not
-// True Emulation of DGEMM") take seven 12-bit pieces of a 128-bit a', with
-// |y'| < 4095 * 715 + 1 < 2^22 as well. One quotient q = rint(y' * fl(1/m)) (an
-// fma against the 1.5 * 2^23 rounding constant) is the integer nearest to
-// y'/m: the estimate is off by at most |y'/m| 2^-24 < 1/(4m), and y'/m is at
-// least 1/(4m) away from every half-integer (2y' - (2k+1)m is an odd
-// multiple of 1/2 for odd m, and 1/2 away from an even integer for even m).
-// So r = y' - q m - 1/4 is exactly the representative nearest zero,
-// [-floor(m/2), ceil(m/2) - 1]: the bias sends the tie of an even modulus
-// to -m/2, and no compare is needed. (The paper reduces a one-byte modulus
-// in two 32-bit Barrett steps, Sec. "Around the GEMMs"; this is the same
-// reduction in the fp32 pipe.)
+// integer issue rate): |a'| is cut once per entry into signed pieces, a first
+// piece P0 of 22 bits and then pieces of 13 bits (P1..P3 when beta <= 61,
+// P1..P4 when beta <= 64) or, for widened operands (beta up to 84, Sec. "Not
+// True Emulation of DGEMM", a' in 128 bits), six of 12 bits. Per modulus
+//   y = P0 + P1 c_1 + P2 c_2 + ...,   c_i = 2^(bits below piece i) mod m, |c_i| <= 119,
+// an integer congruent to a' with |y| < 2^22 + 4 * 8191 * 119 < 2^23, so every
+// partial sum is exact. One quotient q = rint(y * fl(1/m)) (an fma against
+// the 1.5 * 2^23 rounding constant) is the integer nearest to y/m: the
+// estimate is off by at most |y/m| 2^-24 < 1/(2m), and for odd m, y/m is at
+// least 1/(2m) away from every half-integer. So r = y - q m is exactly the
+// representative nearest zero. For the even modulus (236, always at index
+// 2 of an INT8 plan) y/m can be a half-integer; the estimate then picks
+// either neighbour, r is +-m/2, and +m/2 is mapped to -m/2: the result lies
+// in [-floor(m/2), ceil(m/2) - 1] for every modulus. (The paper reduces a
+// one-byte modulus in two 32-bit Barrett steps, Sec. "Around the GEMMs";
+// this is the same reduction in the fp32 pipe: six fp32 operations per
+// modulus and entry.)
 //
 // Planes are written K-major, Q planes of nvec_pad x k_pad entries, int8
 // (two's complement, IMMA engine) or bf16 (TC engine; integers below 2^8 are
@@ -37,12 +38,12 @@
 namespace oz {
 namespace {
 
-// Signed pieces of a' as exact floats, NP of them: 13-bit pieces when NP <= 5
-// (NP = 4 covers |a'| < 2^52, NP = 5 every |a'| < 2^64), 12-bit pieces when
-// NP = 7 (widened operands, |a'| < 2^84). P_0 carries the bias of 1/4. With
-// 12-bit pieces |y'| <= 4095 (1 + 6 * 119) + 1/4 < 2^22 as well.
+// Signed pieces of a' as exact floats, NP of them: a 22-bit first piece,
+// then 13-bit pieces (NP = 4: |a'| < 2^61; NP = 5: |a'| < 2^74) or 12-bit
+// pieces (NP = 7, widened operands, |a'| < 2^84).
 template <int NP>
 struct Pieces {
+  static constexpr int kW0 = 22;
   static constexpr int kBits = NP > 5 ? 12 : 13;
   float p[NP];
 };
@@ -50,33 +51,34 @@ struct Pieces {
 template <int NP>
 __device__ __forceinline__ Pieces<NP> pieces_of(uint64_t bits, int32_t s) {
   Pieces<NP> P;
-  constexpr int PB = Pieces<NP>::kBits;
+  constexpr int W0 = Pieces<NP>::kW0, PB = Pieces<NP>::kBits;
   constexpr uint32_t mask = (1u << PB) - 1u;
   if constexpr (NP > 5) {
     const TruncWide t = truncate_wide(bits, s);
     const float sg = t.neg ? -1.0f : 1.0f;
     const float off = t.neg ? 8388608.0f : -8388608.0f;
+    P.p[0] = fmaf(__int_as_float(0x4B000000u | ((uint32_t)t.mag & ((1u << W0) - 1u))), sg, off);   // +-v, exact
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const uint32_t v = (uint32_t)(t.mag >> (PB * i)) & mask;
-      P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);   // +-v, exact
+    for (int i = 1; i < NP; ++i) {
+      const uint32_t v = (uint32_t)(t.mag >> (W0 + PB * (i - 1))) & mask;
+      P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);
     }
   } else {
     const Trunc t = truncate(bits, s);
     const float sg = t.neg ? -1.0f : 1.0f;
     const float off = t.neg ? 8388608.0f : -8388608.0f;
+    P.p[0] = fmaf(__int_as_float(0x4B000000u | ((uint32_t)t.mag & ((1u << W0) - 1u))), sg, off);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const uint32_t v = (uint32_t)(t.mag >> (PB * i)) & mask;
+    for (int i = 1; i < NP; ++i) {
+      const uint32_t v = (uint32_t)(t.mag >> (W0 + PB * (i - 1))) & mask;
       P.p[i] = fmaf(__int_as_float(0x4B000000u | v), sg, off);
     }
   }
-  P.p[0] += 0.25f;
   return P;
 }
 
 // The constants of one modulus, held in registers while a tile is reduced:
-// c[i - 1] = 2^(PB i) mod m, nearest zero.
+// c[i - 1] = 2^(bits below piece i) mod m, nearest zero.
 template <int NP>
 struct ModConst {
   float c[NP - 1];
@@ -86,42 +88,85 @@ struct ModConst {
 template <int NP>
 __device__ __forceinline__ ModConst<NP> mod_const(const OzTables& T, int q) {
   ModConst<NP> c;
-  if constexpr (NP > 5) {
 #pragma unroll
-    for (int i = 0; i < NP - 1; ++i) c.c[i] = T.c12f[i][q];
-  } else {
-    const float c13[4] = {T.c13f[q], T.c26f[q], T.c39f[q], T.c52f[q]};
-#pragma unroll
-    for (int i = 0; i < NP - 1; ++i) c.c[i] = c13[i];
-  }
+  for (int i = 0; i < NP - 1; ++i) c.c[i] = NP > 5 ? T.c12f[i][q] : T.c13f[i][q];
   c.invm = T.invm[q];
   c.m = T.mf[q];
   return c;
 }
 
-// Representative nearest zero of a' modulo one modulus plus 1/4, as an exact
-// float (r + 1/4; see the header).
+// Representative of a' nearest zero modulo one modulus, as an exact float in
+// [-m/2, m/2] (see the header); for an odd m it is below m/2 in magnitude.
 template <int NP>
-__device__ __forceinline__ float residue_q(const ModConst<NP>& c, const Pieces<NP>& P) {
+__device__ __forceinline__ float residue_any(const ModConst<NP>& c, const Pieces<NP>& P) {
   float y = P.p[0];
 #pragma unroll
   for (int i = 1; i < NP; ++i) y = fmaf(P.p[i], c.c[i - 1], y);
-  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;   // rint(y' / m), exact
+  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;   // rint(y / m), exact
   return fmaf(-qf, c.m, y);
 }
 
-// bf16 bit pattern of the integers r = rq - 1/4 (rq from residue_q): |r| < 2^8
-// needs at most 8 significand bits, so the upper half of the float is exact.
-__device__ __forceinline__ uint32_t bf16_pair(float rq_lo, float rq_hi) {
-  return __byte_perm(__float_as_uint(rq_lo - 0.25f), __float_as_uint(rq_hi - 0.25f), 0x7632u);
+// The tie of the even modulus (index 2): +m/2 becomes -m/2.
+__device__ __forceinline__ float fix_tie(const OzTables& T, float r) {
+  const float h = T.halfm[2];
+  return r == h ? -h : r;
 }
 
-// two's-complement byte of r = rq - 1/4: rq + 1.5 * 2^23 rounds to r + 1.5 * 2^23
-__device__ __forceinline__ uint32_t int8_bits(float rq) { return __float_as_uint(rq + 12582912.0f); }
+// Representative in [-floor(m/2), ceil(m/2) - 1] of modulus q, q a
+// compile-time index after unrolling: only q = 2 takes the tie fix.
+template <int NP>
+__device__ __forceinline__ float residue_q(const OzTables& T, int q, const ModConst<NP>& c, const Pieces<NP>& P) {
+  const float r = residue_any(c, P);
+  return q == 2 ? fix_tie(T, r) : r;
+}
+
+// bf16 bit pattern of the integers r (|r| < 2^8 needs at most 8 significand
+// bits, so the upper half of the float is exact)
+__device__ __forceinline__ uint32_t bf16_pair(float r_lo, float r_hi) {
+  return __byte_perm(__float_as_uint(r_lo), __float_as_uint(r_hi), 0x7632u);
+}
+
+// two's-complement byte of r: r + 1.5 * 2^23 has r in its low byte
+__device__ __forceinline__ uint32_t int8_bits(float r) { return __float_as_uint(r + 12582912.0f); }
 
 __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d) {
   return __byte_perm(__byte_perm(int8_bits(a), int8_bits(b), 0x0040u), __byte_perm(int8_bits(c), int8_bits(d), 0x0040u),
                      0x5410u);
+}
+
+// The residues of EPT consecutive entries (pieces P) modulo every modulus,
+// stored at planes[q plane + off]: one 16- or 8-byte store of bf16 (EPT = 8
+// or 4), or 8 or 4 bytes of int8, per modulus. QT > 0: the modulus count is QT
+// at compile time (no per-modulus test); QT = 0: T.Q at run time.
+template <bool kBF16, int NP, int EPT, int QT>
+__device__ __forceinline__ void store_residues(const OzTables& T, const Pieces<NP> (&P)[EPT], void* __restrict__ planes,
+                                               int64_t plane, int64_t off) {
+  static_assert(EPT == 4 || EPT == 8, "four or eight entries");
+  const int Q = QT > 0 ? QT : T.Q;
+#pragma unroll
+  for (int q = 0; q < (QT > 0 ? QT : OZ_MAX_MODULI); ++q) {
+    if (QT > 0 || q < Q) {
+      const ModConst<NP> mc = mod_const<NP>(T, q);
+      float r[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) r[e] = residue_q(T, q, mc, P[e]);
+      const int64_t o = (int64_t)q * plane + off;
+      if (kBF16) {
+        uint16_t* dst = static_cast<uint16_t*>(planes) + o;
+        if constexpr (EPT == 8)
+          *reinterpret_cast<uint4*>(dst) = make_uint4(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]),
+                                                      bf16_pair(r[4], r[5]), bf16_pair(r[6], r[7]));
+        else
+          *reinterpret_cast<uint2*>(dst) = make_uint2(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]));
+      } else {
+        int8_t* dst = static_cast<int8_t*>(planes) + o;
+        if constexpr (EPT == 8)
+          *reinterpret_cast<uint2*>(dst) = make_uint2(int8_quad(r[0], r[1], r[2], r[3]), int8_quad(r[4], r[5], r[6], r[7]));
+        else
+          *reinterpret_cast<uint32_t*>(dst) = int8_quad(r[0], r[1], r[2], r[3]);
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -129,7 +174,7 @@ __device__ __forceinline__ uint32_t int8_quad(float a, float b, float c, float d
 // vector. Pass 1 finds the max bits; pass 2 re-reads the row (from L2) and
 // writes 8 consecutive entries per thread per plane.
 // ---------------------------------------------------------------------------
-template <bool kBF16, int NP>
+template <bool kBF16, int NP, int QT>
 __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                           const double* __restrict__ X, int64_t ld, int64_t nvec_pad, int64_t k_pad,
                                           int32_t* __restrict__ shifts, void* __restrict__ planes,
@@ -173,51 +218,35 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
     s = s_sh;
   }
 
-  const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
   const bool vec = live && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
-  // four entries per thread per pass: registers for three CTAs per SM
-  for (int64_t h0 = (int64_t)tid * 4; h0 < k_pad; h0 += 256 * 4) {
-    uint64_t b[4];
-    if (vec && h0 + 4 <= len) {
+  // eight entries per thread per pass
+  for (int64_t h0 = (int64_t)tid * 8; h0 < k_pad; h0 += 256 * 8) {
+    uint64_t b[8];
+    if (vec && h0 + 8 <= len) {
 #pragma unroll
-      for (int e = 0; e < 4; e += 2) {
+      for (int e = 0; e < 8; e += 2) {
         const ulonglong2 w = __ldg(reinterpret_cast<const ulonglong2*>(row + h0 + e));
         b[e] = w.x;
         b[e + 1] = w.y;
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
+      for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
     }
-    Pieces<NP> P[4];
+    Pieces<NP> P[8];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < 8; ++e) {
       if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;  // non-finite: flagged above
       P[e] = pieces_of<NP>(b[e], s);
     }
-#pragma unroll
-    for (int q = 0; q < OZ_MAX_MODULI; ++q) {
-      if (q < Q) {
-        const ModConst<NP> mc = mod_const<NP>(T, q);
-        float r[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) r[e] = residue_q(mc, P[e]);
-        const int64_t off = (int64_t)q * plane + v * k_pad + h0;
-        if (kBF16) {
-          *reinterpret_cast<uint2*>(static_cast<uint16_t*>(planes) + off) =
-              make_uint2(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]));
-        } else {
-          *reinterpret_cast<uint32_t*>(static_cast<int8_t*>(planes) + off) = int8_quad(r[0], r[1], r[2], r[3]);
-        }
-      }
-    }
+    store_residues<kBF16, NP, 8, QT>(T, P, planes, plane, v * k_pad + h0);
   }
 }
 
 // The same for a short row (k_pad <= 1024): one warp per row, eight rows
 // per block; the row's maximum is a warp reduction.
-template <bool kBF16, int NP>
+template <bool kBF16, int NP, int QT>
 __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                                const double* __restrict__ X, int64_t ld, int64_t nvec_pad,
                                                int64_t k_pad, int32_t* __restrict__ shifts,
@@ -246,7 +275,6 @@ __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int
       if (live) shifts[v] = s;
     }
   }
-  const int Q = T.Q;
   const int64_t plane = nvec_pad * k_pad;
   const bool vec = live && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
   for (int64_t h0 = (int64_t)lane * 8; h0 < k_pad; h0 += 32 * 8) {
@@ -268,33 +296,11 @@ __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int
       if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;
       P[e] = pieces_of<NP>(b[e], s);
     }
-#pragma unroll
-    for (int q = 0; q < OZ_MAX_MODULI; ++q) {
-      if (q < Q) {
-        const ModConst<NP> mc = mod_const<NP>(T, q);
-        float r[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) r[e] = residue_q(mc, P[e]);
-        const int64_t off = (int64_t)q * plane + v * k_pad + h0;
-        if (kBF16) {
-          uint4 o;
-          o.x = bf16_pair(r[0], r[1]);
-          o.y = bf16_pair(r[2], r[3]);
-          o.z = bf16_pair(r[4], r[5]);
-          o.w = bf16_pair(r[6], r[7]);
-          *reinterpret_cast<uint4*>(static_cast<uint16_t*>(planes) + off) = o;
-        } else {
-          uint2 o;
-          o.x = int8_quad(r[0], r[1], r[2], r[3]);
-          o.y = int8_quad(r[4], r[5], r[6], r[7]);
-          *reinterpret_cast<uint2*>(static_cast<int8_t*>(planes) + off) = o;
-        }
-      }
-    }
+    store_residues<kBF16, NP, 8, QT>(T, P, planes, plane, v * k_pad + h0);
   }
 }
 
-template <bool kBF16, int NP>
+template <bool kBF16, int NP, int QT>
 __global__ void __launch_bounds__(256) split_rows_warp_kernel(const __grid_constant__ OzTables T, int64_t nvec,
                                                               int64_t len, const double* __restrict__ X, int64_t ld,
                                                               int64_t nvec_pad, int64_t k_pad,
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(256) split_rows_warp_kernel(const __grid_const
                                                               void* __restrict__ planes, int32_t* __restrict__ flag,
                                                               bool given) {
   const int64_t v = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  split_row_warp<kBF16, NP>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
+  split_row_warp<kBF16, NP, QT>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
 // Grouped, short rows: block b holds rows 8 (b - rows_begin) .. + 7 of its problem.
@@ -314,16 +320,16 @@ __global__ void __launch_bounds__(256) split_rows_warp_grouped_kernel(const __gr
   const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
   const OzGroupProblem& P = probs[pi];
   const int64_t v = (b - P.rows_begin) * 8 + (threadIdx.x >> 5);
-  split_row_warp<kBF16, NP>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
+  split_row_warp<kBF16, NP, 0>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
-template <bool kBF16, int NP>
+template <bool kBF16, int NP, int QT>
 __global__ void __launch_bounds__(256, 3) split_rows_kernel(const __grid_constant__ OzTables T, int64_t nvec, int64_t len,
                                                          const double* __restrict__ X, int64_t ld,
                                                          int64_t nvec_pad, int64_t k_pad,
                                                          int32_t* __restrict__ shifts, void* __restrict__ planes,
                                                          int32_t* __restrict__ flag, bool given) {
-  split_row<kBF16, NP>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
+  split_row<kBF16, NP, QT>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
 // Grouped: block b is row b - rows_begin of its problem's A.
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(256) split_rows_grouped_kernel(const __grid_co
   const int64_t b = blockIdx.x;
   const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
   const OzGroupProblem& P = probs[pi];
-  split_row<kBF16, NP>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
+  split_row<kBF16, NP, 0>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,7 +467,11 @@ __device__ __forceinline__ void split_cols_block(const OzTables& T, int64_t bx, 
     const ModConst<NP> mc = mod_const<NP>(T, q);
     float r[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = residue_q(mc, P[e]);
+    for (int e = 0; e < 16; ++e) r[e] = residue_any(mc, P[e]);
+    if (q == 2) {                                    // block-uniform branch: the even modulus
+#pragma unroll
+      for (int e = 0; e < 16; ++e) r[e] = fix_tie(T, r[e]);
+    }
     if (kBF16) {
 #pragma unroll
       for (int w = 0; w < 8; ++w) tb[jl * kPitchWords + hg * 8 + w] = bf16_pair(r[2 * w], r[2 * w + 1]);
@@ -538,18 +548,31 @@ __global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t co
 
 namespace {
 
-// pieces per entry for a bit budget: four or five of 13 bits, seven of 12
-int pieces_for(int bits) { return bits <= 52 ? 4 : bits <= 64 ? 5 : 7; }
+// pieces per entry for a bit budget: 22 bits and three or four of 13 bits,
+// or 22 bits and six of 12 (widened operands)
+int pieces_for(int bits) { return bits <= 61 ? 4 : bits <= 64 ? 5 : 7; }
 
+template <bool kBF16, int NP, int QT>
+void split_rows_qt(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
+                   int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag, cudaStream_t st, bool given) {
+  if (k_pad <= 1024)                             // short rows: one warp per row
+    split_rows_warp_kernel<kBF16, NP, QT><<<(unsigned)(nvec_pad / 8), 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad,
+                                                                                     k_pad, shifts, planes, flag,
+                                                                                     given);
+  else
+    split_rows_kernel<kBF16, NP, QT><<<(unsigned)nvec_pad, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts,
+                                                                          planes, flag, given);
+}
+
+// Q = 16 (the paper's INT8 configuration) with the modulus count fixed at
+// compile time; other counts read it from the table
 template <bool kBF16, int NP>
 void split_rows_np(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
                    int64_t k_pad, int32_t* shifts, void* planes, int32_t* flag, cudaStream_t st, bool given) {
-  if (k_pad <= 1024)                             // short rows: one warp per row
-    split_rows_warp_kernel<kBF16, NP><<<(unsigned)(nvec_pad / 8), 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad,
-                                                                                 shifts, planes, flag, given);
+  if (t.Q == 16)
+    split_rows_qt<kBF16, NP, 16>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given);
   else
-    split_rows_kernel<kBF16, NP><<<(unsigned)nvec_pad, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts,
-                                                                      planes, flag, given);
+    split_rows_qt<kBF16, NP, 0>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given);
 }
 
 template <bool kBF16, int NP>
@@ -630,7 +653,7 @@ cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* p
                                       int64_t total_rows, int64_t total_wrows, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   if (total_rows > INT32_MAX || total_wrows > INT32_MAX || t.bits > 64) return cudaErrorInvalidValue;
-  const bool np4 = t.bits <= 52;   // four 13-bit pieces
+  const bool np4 = t.bits <= 61;   // 22 bits and three 13-bit pieces
   if (nlong > 0 && total_rows > 0) {
     if (np4)
       split_rows_grouped_kernel<true, 4><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
@@ -654,7 +677,7 @@ cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* p
   if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, count);
   if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, count, t.bits);
   if (total_sc > 0) {
-    if (t.bits <= 52)
+    if (t.bits <= 61)
       split_cols_grouped_kernel<true, 4><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
     else
       split_cols_grouped_kernel<true, 5><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);

@@ -1,19 +1,21 @@
 """Exhaustive check of the claim that the split's fp32 reduction is exact
 (no GPU).
 
-The split forms, per modulus m, the quarter-integer y' = P0 + 1/4 + sum_i P_i c_i
-from signed pieces of the truncated integer (13-bit pieces, |P_i| <= 8191,
-at most four constants; or 12-bit pieces, at most six) and constants c_i =
-2^(bits i) mod m taken nearest zero (|c_i| <= floor(m/2) <= 119). It then
-takes q = rint(y' fl(1/m)) with one rounding of the exact product (an fma
-against 1.5 * 2^23) and r = y' - q m - 1/4. The claim: q is the integer
-nearest y'/m for every reachable y', so r is the representative of a' modulo
-m nearest zero in [-floor(m/2), ceil(m/2) - 1] (Sec. "Ozaki II"). It holds
-because fl(1/m) is off by at most half an ulp, which moves y'/m by less than
-1/(4m), while a quarter-integer over m is at least 1/(4m) from every
-half-integer.
+The split forms, per modulus m, the integer y = P0 + sum_i P_i c_i from
+signed pieces of the truncated integer (a first piece of 22 bits,
+|P0| <= 2^22 - 1, then 13-bit pieces, |P_i| <= 8191, at most four of them;
+or 12-bit pieces, at most six) and constants c_i = 2^(bits below piece i)
+mod m taken nearest zero (|c_i| <= floor(m/2) <= 119). It then takes
+q = rint(y fl(1/m)) with one rounding of the exact product (an fma against
+1.5 * 2^23) and r = y - q m, and for the even modulus maps r = +m/2 to -m/2.
+The claim: r is the representative of a' modulo m nearest zero in
+[-floor(m/2), ceil(m/2) - 1] for every reachable y (Sec. "Ozaki II"). It
+holds because fl(1/m) is off by at most half an ulp, which moves y/m by less
+than |y| 2^-24 / m < 1/(2m), while for odd m an integer over m is at least
+1/(2m) from every half-integer; for even m a half-integer y/m may round
+either way, and the fix takes the tie to -m/2.
 
-Here every reachable y' (|y'| <= 8191 (1 + 4 * 119) + 1/4) is tried for every
+Here every reachable y (|y| <= 2^22 - 1 + 4 * 8191 * 119) is tried for every
 modulus the INT8 plans use (the 20 of the nested max-product list up to 239),
 against exact integer arithmetic. fl(1/m) is the float32 quotient 1.0f / m.
 """
@@ -26,29 +28,31 @@ import pytest
 import oracle
 
 MODULI = oracle.max_product_moduli(20, 239)
-Y_MAX = 8191 * (1 + 4 * 119)          # 13-bit pieces; the 12-bit case (4095 * (1 + 6 * 119)) is smaller
+Y_MAX = (2**22 - 1) + 4 * 8191 * 119      # 22 + 4 x 13 bits; 22 + 6 x 12 bits reaches less
 
 
-def test_reachable_range_covers_both_piece_widths():
-    assert 4095 * (1 + 6 * 119) < Y_MAX < 2**22
+def test_reachable_range_covers_both_piece_layouts():
+    assert (2**22 - 1) + 6 * 4095 * 119 < Y_MAX < 2**23
+    assert (2**22 - 1) + 3 * 8191 * 119 < Y_MAX
     assert max(m // 2 for m in MODULI) == 119
+    # 22 + 3 x 13 = 61 bits (beta <= 61), 22 + 4 x 13 = 74, 22 + 6 x 12 = 94 (widened a' < 2^84)
+    assert 22 + 3 * 13 == 61 and 22 + 4 * 13 >= 64 and 22 + 6 * 12 >= 84
+    # the only even modulus is the third of the list (the split's tie fix is for index 2 only)
+    assert [i for i, m in enumerate(MODULI) if m % 2 == 0] == [2]
 
 
 @pytest.mark.parametrize("m", MODULI)
 def test_single_rint_reduction_is_exact(m):
-    k = np.arange(-Y_MAX - 1, Y_MAX + 1, dtype=np.int64)        # y' = k + 1/4
-    y = k.astype(np.float64) + 0.25
     invm = float(np.float32(1.0) / np.float32(m))
-    t = y * invm                                                  # exact: 24-bit by 24-bit significands
-    q = np.rint(t)                                                # the fma's one rounding, ties to even
-    # the integer nearest (4k + 1) / (4m); no ties, since 4k + 1 is odd
-    nearest = (4 * k + 1 + 2 * m) // (4 * m)
-    assert np.array_equal(q.astype(np.int64), nearest)
-    r = y - q * m - 0.25                                          # exact in float64 (and in fp32: |r| < 2^8)
-    assert np.array_equal(r, np.rint(r))
-    ri = r.astype(np.int64)
-    assert ri.min() >= -(m // 2) and ri.max() <= (m + 1) // 2 - 1
-    assert np.array_equal(ri % m, k % m)                          # r = a' mod m: y' - 1/4 = k
+    step = 1 << 22
+    for lo in range(-Y_MAX, Y_MAX + 1, step):
+        y = np.arange(lo, min(lo + step, Y_MAX + 1), dtype=np.int64)
+        q = np.rint(y.astype(np.float64) * invm)             # exact product, the fma's one rounding
+        r = y - q.astype(np.int64) * m                          # exact in fp32 too: |r| <= m/2 < 2^8
+        if m % 2 == 0:
+            r = np.where(r == m // 2, -(m // 2), r)             # the tie fix of the even modulus
+        assert r.min() >= -(m // 2) and r.max() <= (m + 1) // 2 - 1
+        assert np.array_equal(r % m, y % m)
 
 
 T_MAX = 1024 * 119 * 119 + 2 * 120    # a slab's sum plus the residue it lands on (and the other chain's)
