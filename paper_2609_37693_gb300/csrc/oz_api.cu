@@ -16,11 +16,15 @@ struct Layout {
   int64_t m_pad, n_pad, k_pad;
   int64_t ldy;       // row pitch of the residue planes Y: n rounded up to 16 bytes
   size_t flag, s, t, colmax, u, v, y, bt, total;
+  oz::KSplit split;  // split-K of the TC GEMM (nsplit sets of residues, ysplit bytes apart)
+  size_t ysplit;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
+// allow_split: reserve the residue sets of a split-K GEMM (oz_dgemm on a TC
+// engine with too few output tiles for the GPU); a blocked call does not split.
+bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L, bool allow_split = true) {
   if (!p || m < 0 || n < 0 || k < 0) return false;
   const int64_t elem = oz::engine_bf16(p->engine) ? 2 : 1;     // bf16 planes; int8 residues or float codes
   const int64_t nplanes = p->is_fp ? p->fp.nplanes : p->Q;
@@ -37,7 +41,15 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L) {
   L->u = off; off = align256(off + (size_t)nplanes * L->m_pad * row);
   L->v = off; off = align256(off + (size_t)nplanes * L->n_pad * row);
   L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
-  L->y = off; off = align256(off + (size_t)p->Q * m * L->ldy * ybytes);
+  L->split = {1, (int)(L->k_pad / 64)};
+  if (allow_split && !p->is_fp && oz::engine_bf16(p->engine) && m > 0 && n > 0 && k > 0) {
+    const bool pairs = p->engine == OZ_ENGINE_TC;
+    const int64_t tm = pairs ? 256 : 128;
+    const int64_t tiles = (int64_t)p->Q * ((m + tm - 1) / tm) * ((n + 255) / 256);
+    L->split = oz::ksplit_for(L->k_pad / 64, tiles, pairs ? oz::kPairWorkers : oz::kCtaWorkers);
+  }
+  L->ysplit = align256((size_t)p->Q * m * L->ldy * ybytes);
+  L->y = off; off = align256(off + L->ysplit * L->split.nsplit);
   // B^T (n x k doubles): the INT8 split takes B's columns as rows of its transpose
   L->bt = off; off = align256(off + (p->is_fp ? 0 : 8 * (size_t)n * k));
   L->total = off;
@@ -147,13 +159,23 @@ oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n
     if (e == cudaSuccess) e = oz::launch_split_rows(T, n, k, Bt, k, L.n_pad, L.k_pad, t, V, bf16, flag, st);
   }
   if (e != cudaSuccess) return OZ_ERR_CUDA;
-  // GEMMs + epilogue
-  e = (plan->engine == OZ_ENGINE_TC1 || (single_cta && plan->engine == OZ_ENGINE_TC))
-          ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
-      : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st)
+  // GEMMs + epilogue; with too few output tiles, the inner dimension split into
+  // ranges whose residue sets are then added modulo m (the layout's split: a
+  // TC plan forced onto one CTA per tile runs unsplit)
+  const bool forced_single = single_cta && plan->engine == OZ_ENGINE_TC;
+  const oz::KSplit split = forced_single ? oz::KSplit{1, 0} : L.split;
+  e = (plan->engine == OZ_ENGINE_TC1 || forced_single)
+          ? oz::launch_gemm_tc_single(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st, split,
+                                      (int64_t)L.ysplit)
+      : bf16 ? oz::launch_gemm_tc(T, m, n, L.m_pad, L.n_pad, L.k_pad, U, V, Y, L.ldy, 0, flag, st, split,
+                                  (int64_t)L.ysplit)
              : oz::launch_gemm_imma(T, m, n, L.k_pad, static_cast<const int8_t*>(U), L.m_pad * L.k_pad,
                                     static_cast<const int8_t*>(V), L.n_pad * L.k_pad, Y, L.ldy, 0, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
+  if (split.nsplit > 1) {
+    e = oz::launch_combine_digits(T, m, L.ldy, Y, split.nsplit, (int64_t)L.ysplit, st);
+    if (e != cudaSuccess) return OZ_ERR_CUDA;
+  }
   // Reconstruct
   e = oz::launch_reconstruct(T, m, n, Y, L.ldy, s, t, C, ldc, st);
   return cuda_status(e);
@@ -176,7 +198,9 @@ extern "C" oz_status oz_dgemm(oz_plan plan, int trans_a, int trans_b, int64_t m,
 
 extern "C" size_t oz_blocked_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k_slab) {
   if (k_slab < 1) return 0;
-  return oz_workspace_bytes(plan, m, n, k_slab);
+  Layout L;
+  if (!make_layout(plan, m, n, k_slab, &L, false)) return 0;
+  return L.total;
 }
 
 extern "C" oz_status oz_dgemm_blocked(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k,
@@ -193,7 +217,7 @@ extern "C" oz_status oz_dgemm_blocked(oz_plan plan, int trans_a, int trans_b, in
   if (k > 0 && (!A || !B || !aligned(A, 8) || !aligned(B, 8))) return OZ_ERR_INVALID_ARG;
   const int64_t kt = k_slab < k ? k_slab : (k > 0 ? k : 1);
   Layout L;
-  make_layout(plan, m, n, kt, &L);
+  make_layout(plan, m, n, kt, &L, false);
   if (!workspace || workspace_bytes < L.total || !aligned(workspace, 256)) return OZ_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);

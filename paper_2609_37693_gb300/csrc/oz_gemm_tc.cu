@@ -201,17 +201,32 @@ __device__ __forceinline__ Coord tile_coord(int t, int tiles_m, int tiles_n) {
   return c;
 }
 
+// The last slab's value r (|r| <= 120, r == W mod m) as the byte the
+// epilogue stores: raw, W mod m in [0, m); else the CRT digit
+// (W mod m) (P/m)^-1 mod m, formed as r inv (|r inv| <= 120 * 238 < 2^15,
+// exact), one rint quotient and one sign correction into [0, m).
+__device__ __forceinline__ float digit_of(float r, float mf, float invm, float invf, int raw) {
+  float y = raw ? r : r * invf;
+  if (!raw) {
+    const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
+    y = fmaf(-q2, mf, y);
+  }
+  return y < 0.0f ? y + mf : y;
+}
+
 // One thread's 128 digits of a tile row (one byte each, packed in words) to
 // Y: whole 16-byte runs up to `left` (the columns of the row from here to n)
 // rounded up to 16 when the row pitch is a multiple of 16 (bytes past n are
 // never read), byte stores otherwise. acc: add into the digits in Y modulo m.
+template <int NW>
 __device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, int left, bool runs, int acc,
                                              uint32_t m) {
+  static_assert(NW == 32 || NW == 16, "128 or 64 digits");
   if (runs) {
-    const int chunks = min(8, (left + 15) >> 4);
+    const int chunks = min(NW / 4, (left + 15) >> 4);
     const uint32_t mm = m * 0x01010101u;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < NW / 4; ++i) {
       if (i < chunks) {
         uint4 o = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
         if (acc) {
@@ -226,7 +241,7 @@ __device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, in
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NW; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (4 * i + j < left) {
@@ -246,7 +261,27 @@ struct Params {
   uint8_t* Y;
   int64_t ldy;       // row pitch of Y
   int32_t* status;
+  // split-K: the inner dimension in nsplit ranges of kbps k-blocks (whole
+  // slabs); unit u is split u / num_tiles of tile u % num_tiles, and split j
+  // writes its digits to Y + j ysplit
+  int nsplit, kbps;
+  int64_t ysplit;
 };
+
+// The tile, split and k-block range [kb0, kb1) of unit u.
+struct Unit {
+  Coord c;
+  int ks, kb0, kb1, nslabs;
+};
+__device__ __forceinline__ Unit unit_of(const Params& p, int u) {
+  Unit w;
+  w.ks = u / p.num_tiles;
+  w.c = tile_coord(u - w.ks * p.num_tiles, p.tiles_m, p.tiles_n);
+  w.kb0 = w.ks * p.kbps;
+  w.kb1 = min(p.kblocks, w.kb0 + p.kbps);
+  w.nslabs = (w.kb1 - w.kb0 + kSlabBlocks - 1) / kSlabBlocks;
+  return w;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -292,7 +327,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  const int nslabs = (p.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+  const int num_units = p.num_tiles * p.nsplit;
 
   if (warp == 0) {
     // ------------------------------ TMA producer ------------------------------
@@ -303,11 +338,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       bool outstanding[STAGES];
       for (int i = 0; i < STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-        const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
-        const int ya = c.q * p.m_pad + c.tm * BM;
-        const int yb = c.q * p.n_pad + c.tn * BN;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
+      for (int t = blockIdx.x; t < num_units && ok; t += gridDim.x) {
+        const Unit u = unit_of(p, t);
+        const int ya = u.c.q * p.m_pad + u.c.tm * BM;
+        const int yb = u.c.q * p.n_pad + u.c.tn * BN;
+        for (int kb = u.kb0; kb < u.kb1; ++kb) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
           outstanding[s] = false;
           const uint32_t sa = base + s * STAGE_BYTES;
@@ -331,14 +366,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       uint32_t ph = 0;
       uint32_t g = 0;  // slab counter across tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-        for (int sl = 0; sl < nslabs && ok; ++sl, ++g) {
+      for (int t = blockIdx.x; t < num_units && ok; t += gridDim.x) {
+        const Unit u = unit_of(p, t);
+        for (int sl = 0; sl < u.nslabs && ok; ++sl, ++g) {
           const uint32_t b = g & 1u, use = g >> 1;
           if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dtm = tmem_base + b * BN;
-          const int kb0 = sl * kSlabBlocks;
-          const int kb1 = min(p.kblocks, kb0 + kSlabBlocks);
+          const int kb0 = u.kb0 + sl * kSlabBlocks;
+          const int kb1 = min(u.kb1, kb0 + kSlabBlocks);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
             tc_fence_after();
@@ -371,8 +407,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-      const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+    for (int t = blockIdx.x; t < num_units && ok; t += gridDim.x) {
+      const Unit u = unit_of(p, t);
+      const Coord c = u.c;
+      const int nslabs = u.nslabs;
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
       const float invf = (float)T.inv[c.q];
@@ -412,14 +450,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
                 const float r = fmaf(-qf, mf, tv);
                 if (last) {
-                  float y = r < 0.0f ? r + mf : r;
-                  if (!p.raw) {
-                    y *= invf;
-                    const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
-                    y = fmaf(-q2, mf, y);
-                    y = y < 0.0f ? y + mf : y;
-                  }
-                  out[j] = __float_as_uint(y + 8388608.0f);
+                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, p.raw) + 8388608.0f);
                 } else {
                   out[j] = __float_as_uint(r + 8388736.0f);
                 }
@@ -438,9 +469,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int col0 = c.tn * BN + half * 128;
       if (row < p.m && col0 < p.n) {
         const uint32_t* outw = acc8;
-        uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-        store_digits(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
-                     p.acc, T.m[c.q]);
+        uint8_t* dst = p.Y + (size_t)u.ks * p.ysplit + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
+        store_digits<32>(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
+                         p.acc, T.m[c.q]);
       }
     }
   }
@@ -473,17 +504,18 @@ constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + kBarBytes + 1024;
 // full and empty barriers per stage, two tfull, two tempty, one drain: all below kHolderOff
 static_assert((2 * P_STAGES + 5) * 8 <= kHolderOff, "pair kernel barriers overlap the TMEM address");
 static_assert((2 * STAGES + 5) * 8 <= kHolderOff, "barriers overlap the TMEM address");
-// epilogue warps of the pair kernel (eight: with four, one warp's drain of a
-// slab outlasts the slab's products)
-constexpr int kPairEpiWarps = 8;
+// epilogue warps of the pair kernel (with four, one warp's drain of a slab
+// outlasts the slab's products)
+constexpr int kPairEpiWarps = 16;
 
-// EW epilogue warps (4 or 8): every warp drains the 32 TMEM lanes of its
-// quarter (warp index mod 4), over 256 / (EW / 4) columns.
+// EW epilogue warps (4, 8 or 16): every warp drains the 32 TMEM lanes of its
+// quarter (warp index mod 4), over CPW = 256 / (EW / 4) columns.
 template <int EW>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((2 + EW) * 32, 1)
 gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ OzTables T, const Params p) {
-  constexpr int NH = 8 / EW;                // 128-column halves per epilogue warp
+  constexpr int CPW = 1024 / EW;            // columns per epilogue warp
+  static_assert(EW == 4 || EW == 8 || EW == 16, "4, 8 or 16 epilogue warps");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_base = smem_u32(smem_raw);
   const uint32_t base = (raw_base + 1023u) & ~1023u;
@@ -528,7 +560,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  const int nslabs = (p.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+  const int num_units = p.num_tiles * p.nsplit;
 
   if (warp == 0) {
     // ------------------------------ TMA producer (both CTAs) ------------------------------
@@ -539,11 +571,11 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       bool outstanding[P_STAGES];
       for (int i = 0; i < P_STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
       bool ok = true;
-      for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-        const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
-        const int ya = c.q * p.m_pad + c.tm * 2 * P_BM + (int)rank * P_BM;
-        const int yb = c.q * p.n_pad + c.tn * 2 * P_BN + (int)rank * P_BN;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
+      for (int t = pair; t < num_units && ok; t += npairs) {
+        const Unit u = unit_of(p, t);
+        const int ya = u.c.q * p.m_pad + u.c.tm * 2 * P_BM + (int)rank * P_BM;
+        const int yb = u.c.q * p.n_pad + u.c.tn * 2 * P_BN + (int)rank * P_BN;
+        for (int kb = u.kb0; kb < u.kb1; ++kb) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
           outstanding[s] = false;
           const uint32_t sa = base + s * P_STAGE_BYTES;
@@ -570,14 +602,15 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       uint32_t ph = 0;
       uint32_t g = 0;
       bool ok = true;
-      for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-        for (int sl = 0; sl < nslabs && ok; ++sl, ++g) {
+      for (int t = pair; t < num_units && ok; t += npairs) {
+        const Unit u = unit_of(p, t);
+        for (int sl = 0; sl < u.nslabs && ok; ++sl, ++g) {
           const uint32_t b = g & 1u, use = g >> 1;
           if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dtm = tmem_base + b * 256;
-          const int kb0 = sl * kSlabBlocks;
-          const int kb1 = min(p.kblocks, kb0 + kSlabBlocks);
+          const int kb0 = u.kb0 + sl * kSlabBlocks;
+          const int kb1 = min(u.kb1, kb0 + kSlabBlocks);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
             tc_fence_after();
@@ -605,21 +638,24 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     // r = t - m rint(t / m), |r| <= 120, and writes r back when slab sl + 2
     // accumulates on it; the residue of slab nsl - 2 is kept as one byte per
     // entry and added to that of the last slab (eq. ov-comrtc: every partial
-    // sum stays below 2^24, so the FP32 arithmetic is exact).
+    // sum stays below 2^24, so the FP32 arithmetic is exact). Each warp drains
+    // the 32 TMEM lanes of its quarter (warp index mod 4) over CPW columns.
     const int e = warp - 2;
     const int quarter = warp & 3;
-    const int half0 = NH == 1 ? (e >> 2) : 0;   // first 128-column half this warp drains
+    const int cbase = (e >> 2) * CPW;          // first column this warp drains
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
-    for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-      const Coord c = tile_coord(t, p.tiles_m, p.tiles_n);
+    for (int t = pair; t < num_units && ok; t += npairs) {
+      const Unit u = unit_of(p, t);
+      const Coord c = u.c;
+      const int nslabs = u.nslabs;
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
       const float invf = (float)T.inv[c.q];
-      uint32_t acc8[32 * NH];                // residue + 128 of the chain of slab nsl - 2, one byte per column
+      uint32_t acc8[CPW / 4];                // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
-      for (int i = 0; i < 32 * NH; ++i) acc8[i] = 0x80808080u;
+      for (int i = 0; i < CPW / 4; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
@@ -627,50 +663,37 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
-        for (int hh = 0; hh < NH; ++hh) {
+        for (int ch = 0; ch < CPW / 32; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * 256 + cbase + ch * 32;
+          uint32_t v[32];
+          tmem_ld32(taddr, v);
+          tmem_ld_wait();
+          if (write_back) {
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) {
-            const uint32_t taddr = tmem_base + lane_addr + b * 256 + (half0 + hh) * 128 + ch * 32;
-            uint32_t v[32];
-            tmem_ld32(taddr, v);
-            tmem_ld_wait();
-            if (write_back) {
+            for (int j = 0; j < 32; ++j) {
+              const float tv = __uint_as_float(v[j]);
+              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
+              v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
+            }
+            tmem_st32(taddr, v);
+          } else {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const float tv = __uint_as_float(v[j]);
-                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
-                v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
+            for (int w = 0; w < 8; ++w) {
+              uint32_t out[4];
+              uint32_t& a8 = acc8[ch * 8 + w];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float tv = __uint_as_float(v[4 * w + j]);
+                if (last && nslabs > 1)      // plus the residue of the other chain, r + 128 in a byte
+                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
+                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+                const float r = fmaf(-qf, mf, tv);                          // exact, |r| <= 120
+                if (last)
+                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, p.raw) + 8388608.0f);   // low byte
+                else
+                  out[j] = __float_as_uint(r + 8388736.0f);                 // low byte = r + 128
               }
-              tmem_st32(taddr, v);
-            } else {
-#pragma unroll
-              for (int w = 0; w < 8; ++w) {
-                uint32_t out[4];
-                uint32_t& a8 = acc8[hh * 32 + ch * 8 + w];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  float tv = __uint_as_float(v[4 * w + j]);
-                  if (last && nslabs > 1)      // plus the residue of the other chain, r + 128 in a byte
-                    tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
-                  const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                  const float r = fmaf(-qf, mf, tv);                          // exact, |r| <= 120
-                  if (last) {
-                    // W mod m in [0, m), then (raw == 0) the CRT digit (W mod m) inv mod m:
-                    // y = rr inv < 239^2 is exact, one rint quotient, one sign correction
-                    float y = r < 0.0f ? r + mf : r;
-                    if (!p.raw) {
-                      y *= invf;
-                      const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
-                      y = fmaf(-q2, mf, y);
-                      y = y < 0.0f ? y + mf : y;
-                    }
-                    out[j] = __float_as_uint(y + 8388608.0f);                 // low byte = y
-                  } else {
-                    out[j] = __float_as_uint(r + 8388736.0f);                 // low byte = r + 128
-                  }
-                }
-                a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
-              }
+              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
             }
           }
         }
@@ -681,14 +704,13 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       if (!ok) break;
       // ---- tile done: acc8 holds the digits (or W mod m), one byte per entry ----
       const int row = c.tm * 2 * P_BM + (int)rank * P_BM + quarter * 32 + lane;
+      const bool runs = (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
 #pragma unroll
-      for (int hh = 0; hh < NH; ++hh) {
-        const int col0 = c.tn * 256 + (half0 + hh) * 128;
+      for (int part = 0; part < (CPW + 127) / 128; ++part) {
+        const int col0 = c.tn * 256 + cbase + part * 128;
         if (row < p.m && col0 < p.n) {
-          const uint32_t* outw = acc8 + hh * 32;
-          uint8_t* dst = p.Y + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-          store_digits(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
-                       p.acc, T.m[c.q]);
+          uint8_t* dst = p.Y + (size_t)u.ks * p.ysplit + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
+          store_digits<(CPW < 128 ? CPW : 128) / 4>(dst, acc8 + part * 32, p.n - col0, runs, p.acc, T.m[c.q]);
         }
       }
     }
@@ -884,12 +906,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
                 const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
                 const float r = fmaf(-qf, mf, tv);
                 if (last) {
-                  float y = r < 0.0f ? r + mf : r;          // W mod m, then the CRT digit
-                  y *= invf;
-                  const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
-                  y = fmaf(-q2, mf, y);
-                  y = y < 0.0f ? y + mf : y;
-                  out[j] = __float_as_uint(y + 8388608.0f);
+                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, 0) + 8388608.0f);   // the CRT digit
                 } else {
                   out[j] = __float_as_uint(r + 8388736.0f);
                 }
@@ -962,11 +979,30 @@ bool make_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t k_pad,
   return r == CUDA_SUCCESS;
 }
 
+// The split-K fields of the kernel parameters: one range (the whole K) or
+// the ranges of ksplit_for, whole slabs each, none of them empty.
+bool set_split(Params* p, KSplit split, int64_t ysplit) {
+  if (split.nsplit <= 1) {
+    p->nsplit = 1;
+    p->kbps = p->kblocks;
+    p->ysplit = 0;
+    return true;
+  }
+  if (split.kbps <= 0 || split.kbps % kSlabBlocks || (int64_t)(split.nsplit - 1) * split.kbps >= p->kblocks ||
+      (int64_t)split.nsplit * split.kbps < p->kblocks || (int64_t)p->num_tiles * split.nsplit > INT32_MAX ||
+      ysplit <= 0)
+    return false;
+  p->nsplit = split.nsplit;
+  p->kbps = split.kbps;
+  p->ysplit = ysplit;
+  return true;
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
-                           cudaStream_t st) {
+                           cudaStream_t st, KSplit split, int64_t ysplit) {
   if (m == 0 || n == 0) return cudaSuccess;
   if (ldy < n) return cudaErrorInvalidValue;
   // pair tiles: 256 x 256 per CTA pair
@@ -1009,7 +1045,9 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   p.Y = Y;
   p.ldy = ldy;
   p.status = status;
-  const int64_t pairs = num_tiles < sms / 2 ? num_tiles : sms / 2;
+  if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
+  const int64_t units = num_tiles * p.nsplit;
+  const int64_t pairs = units < sms / 2 ? units : sms / 2;
   gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(
       mapA, mapB, t, p);
   return cudaGetLastError();
@@ -1041,8 +1079,7 @@ cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* prob
 // The one-CTA kernel (128 x 256 tiles), kept for comparison.
 cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad,
                                   int64_t k_pad, const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw,
-                                  int32_t* status,
-                                  cudaStream_t st) {
+                                  int32_t* status, cudaStream_t st, KSplit split, int64_t ysplit) {
   if (m == 0 || n == 0) return cudaSuccess;
   if (ldy < n) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(U) & 127) || (reinterpret_cast<uintptr_t>(V) & 127) || k_pad % BK ||
@@ -1076,7 +1113,9 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
   p.Y = Y;
   p.ldy = ldy;
   p.status = status;
-  const int grid = (int)(num_tiles < sms ? num_tiles : sms);
+  if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
+  const int64_t units = num_tiles * p.nsplit;
+  const int grid = (int)(units < sms ? units : sms);
   gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, t, p);
   return cudaGetLastError();
 }

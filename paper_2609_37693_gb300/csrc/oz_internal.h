@@ -168,6 +168,33 @@ oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n
 // Engines that hold the INT8 residues in BF16 planes.
 inline bool engine_bf16(int e) { return e == OZ_ENGINE_TC || e == OZ_ENGINE_TC1; }
 
+// Split-K of a TC-engine product: the inner dimension's kblocks k-blocks (64
+// entries each) cut into nsplit ranges of kbps k-blocks, whole 1024-term slabs
+// (16 k-blocks), each range's digits in a set of their own, added modulo m
+// afterwards (the digits are linear in W). The count minimises the estimated
+// time, waves of units times (slabs per range + one slab of overhead), over
+// `workers` units at once (CTA pairs or CTAs of a GB300: 76 or 152); ties go
+// to fewer ranges. Without a shortage of tiles it is one range. Depends on
+// the shape only, so that the workspace size can be computed on the host.
+struct KSplit {
+  int nsplit, kbps;
+};
+inline KSplit ksplit_for(int64_t kblocks, int64_t tiles, int64_t workers) {
+  const int64_t slab = 16, nslabs = (kblocks + slab - 1) / slab;
+  KSplit best = {1, (int)kblocks};
+  if (tiles >= workers || nslabs < 2) return best;
+  int64_t best_t = ((tiles + workers - 1) / workers) * (nslabs + 1);
+  for (int64_t s = 2; s <= nslabs && s <= 32; ++s) {
+    const int64_t per = (nslabs + s - 1) / s;          // slabs per range
+    const int64_t ns = (nslabs + per - 1) / per;       // ranges actually used
+    const int64_t t = ((tiles * ns + workers - 1) / workers) * (per + 1);
+    if (t < best_t) best_t = t, best.nsplit = (int)ns, best.kbps = (int)(per * slab);
+  }
+  return best;
+}
+constexpr int64_t kPairWorkers = 76;     // CTA pairs of a GB300 (152 SMs)
+constexpr int64_t kCtaWorkers = 152;
+
 // Geometry of a float-format plan's planes: k padding (entries) and bytes per
 // row of k_pad entries.
 inline int64_t fp_k_align(const OzFpTables& f) { return f.code_bits == 4 ? 256 : kPadK; }
@@ -188,12 +215,17 @@ cudaError_t launch_gemm_imma(const OzTables& t, int64_t m, int64_t n, int64_t k_
                              int64_t u_plane, const int8_t* V, int64_t v_plane, uint8_t* Y, int64_t ldy, int raw,
                              cudaStream_t st);
 // Y: residue planes [Q][m][ldy] (ldy >= n; a multiple of 16 lets the epilogue store whole 16-byte runs)
+// split: the ranges of ksplit_for (nsplit 1: none), digit set j at Y + j ysplit
 cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
-                           cudaStream_t st);
+                           cudaStream_t st, KSplit split = {1, 0}, int64_t ysplit = 0);
 cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                            const void* U, const void* V, uint8_t* Y, int64_t ldy, int raw, int32_t* status,
-                           cudaStream_t st);
+                           cudaStream_t st, KSplit split = {1, 0}, int64_t ysplit = 0);
+// Y[0] = sum of the nsplit digit sets Y[j] (at Y + j ysplit) modulo each
+// modulus, over Q planes of m rows of ldy bytes (ldy a multiple of 16)
+cudaError_t launch_combine_digits(const OzTables& t, int64_t m, int64_t ldy, uint8_t* Y, int nsplit, int64_t ysplit,
+                                  cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
                                const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
 // grouped products (oz_grouped.cu): one launch per phase over count problems

@@ -38,6 +38,7 @@
 #include <type_traits>
 
 #include "oz_internal.h"
+#include "oz_device.cuh"
 
 namespace oz {
 namespace {
@@ -654,42 +655,48 @@ __device__ __forceinline__ void issue_digits(const uint8_t* __restrict__ Y, int6
   }
 }
 
-// Persistent: block task b = (row i, chunk c) of 1024 entries, b advancing by
-// the grid size. Every thread copies the next task's digit words into its own
-// shared-memory slots (cp.async, two buffers) before it reconstructs the
-// current task's four entries, so the loads of one task overlap the arithmetic
-// of the last without holding registers; each thread reads only the slots it
-// filled, so no barrier is needed.
+// Persistent: block task b = (row group, column chunk), b advancing by the
+// grid size. A task covers 256 / tpr rows of one chunk of 4 tpr entries (tpr
+// threads per row: 256 for long rows, fewer for rows shorter than 1024, so
+// that short rows do not leave threads idle). Every thread copies the next
+// task's digit words into its own shared-memory slots (cp.async, two buffers)
+// before it reconstructs the current task's four entries, so the loads of one
+// task overlap the arithmetic of the last without holding registers; each
+// thread reads only the slots it filled, so no barrier is needed.
 template <int NT, int NP2, int NQ4>
 __global__ void __launch_bounds__(256, 2) reconstruct_groups_kernel(const __grid_constant__ OzTables T, int64_t m,
                                                                     int64_t n, const uint8_t* __restrict__ Y,
                                                                     int64_t ldy, const int32_t* __restrict__ s,
                                                                     const int32_t* __restrict__ t,
                                                                     double* __restrict__ C, int64_t ldc,
-                                                                    int64_t nch) {
+                                                                    int64_t nch, int tpr_log2) {
   constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
   __shared__ uint4 kP[16];
   __shared__ uint32_t buf[2][Q * 256];
   fill_kP(T, kP);
   __syncthreads();
+  const int tpr = 1 << tpr_log2, rows = 256 >> tpr_log2;
+  const int r_in = threadIdx.x >> tpr_log2, c_in = threadIdx.x & (tpr - 1);
   const int64_t plane = m * ldy;
-  const int64_t total = m * nch;
-  const int64_t step_i = gridDim.x / nch, step_c = gridDim.x % nch;
-  int64_t b = blockIdx.x, i = b / nch, c = b % nch;
+  const int64_t ngroups = (m + rows - 1) / rows, total = ngroups * nch;
+  const int64_t step_g = gridDim.x / nch, step_c = gridDim.x % nch;
+  int64_t b = blockIdx.x, gi = b / nch, c = b % nch;
   uint32_t* const mine = buf[0] + threadIdx.x;       // slot s: mine + s * Q * 256
   int slot = 0;
-  if (b < total) issue_digits<Q>(Y, plane, ldy, i, (c * 256 + threadIdx.x) * 4, n, mine);
+  auto row_of = [&](int64_t g) { return g * rows + r_in; };
+  auto col_of = [&](int64_t cc) { return (cc * tpr + c_in) * 4; };
+  if (b < total && row_of(gi) < m) issue_digits<Q>(Y, plane, ldy, row_of(gi), col_of(c), n, mine);
   cp_async_commit();
   while (b < total) {
-    int64_t bn = b + gridDim.x, in = i + step_i, cn = c + step_c;
-    if (cn >= nch) cn -= nch, ++in;
-    if (bn < total) issue_digits<Q>(Y, plane, ldy, in, (cn * 256 + threadIdx.x) * 4, n, mine + (slot ^ 1) * Q * 256);
+    int64_t bn = b + gridDim.x, gn = gi + step_g, cn = c + step_c;
+    if (cn >= nch) cn -= nch, ++gn;
+    if (bn < total && row_of(gn) < m) issue_digits<Q>(Y, plane, ldy, row_of(gn), col_of(cn), n, mine + (slot ^ 1) * Q * 256);
     cp_async_commit();
     cp_async_wait1();                       // this task's copies have landed
-    const int64_t j0 = (c * 256 + threadIdx.x) * 4;
-    if (j0 < n) rec4_groups<NT, NP2, NQ4>(T, kP, mine + slot * Q * 256, i, j0, n, __ldg(s + i), t, C, ldc);
+    const int64_t i = row_of(gi), j0 = col_of(c);
+    if (i < m && j0 < n) rec4_groups<NT, NP2, NQ4>(T, kP, mine + slot * Q * 256, i, j0, n, __ldg(s + i), t, C, ldc);
     slot ^= 1;
-    b = bn, i = in, c = cn;
+    b = bn, gi = gn, c = cn;
   }
 }
 
@@ -768,12 +775,15 @@ int persistent_grid(K kernel, int threads) {
 template <int NT, int NP2, int NQ4>
 cudaError_t launch_groups(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
                           const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
-  const int64_t nch = (n + 1023) / 1024;
-  const int64_t total = m * nch;
+  int tpr_log2 = 5;                                  // 32 .. 256 threads per row chunk of 4 tpr entries
+  while (tpr_log2 < 8 && ((int64_t)4 << tpr_log2) < n) ++tpr_log2;
+  const int64_t rows = 256 >> tpr_log2;
+  const int64_t nch = (n + (4 << tpr_log2) - 1) / (4 << tpr_log2);
+  const int64_t total = ((m + rows - 1) / rows) * nch;
   int grid = persistent_grid(reconstruct_groups_kernel<NT, NP2, NQ4>, 256);
   if (grid <= 0) return cudaErrorInvalidValue;
   if ((int64_t)grid > total) grid = (int)total;
-  reconstruct_groups_kernel<NT, NP2, NQ4><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc, nch);
+  reconstruct_groups_kernel<NT, NP2, NQ4><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc, nch, tpr_log2);
   return cudaGetLastError();
 }
 
@@ -834,6 +844,43 @@ cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const ui
     case 6: return launch_L<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+namespace {
+
+// Y[0] += Y[1] + ... + Y[nsplit - 1] modulo the plane's modulus, 16 bytes per
+// thread (byte-wise modular adds; bytes past n in a row are summed too and
+// never read).
+__global__ void __launch_bounds__(256) combine_digits_kernel(const __grid_constant__ OzTables T, int64_t plane16,
+                                                             int64_t total16, uint8_t* __restrict__ Y, int nsplit,
+                                                             int64_t ysplit) {
+  const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (c >= total16) return;
+  const int q = (int)(c / plane16);
+  const uint32_t mm = T.m[q] * 0x01010101u;
+  uint4* dst = reinterpret_cast<uint4*>(Y) + c;
+  uint4 a = *dst;
+  for (int j = 1; j < nsplit; ++j) {
+    const uint4 b = __ldcs(reinterpret_cast<const uint4*>(Y + j * ysplit) + c);
+    a.x = addmod_bytes(a.x, b.x, mm);
+    a.y = addmod_bytes(a.y, b.y, mm);
+    a.z = addmod_bytes(a.z, b.z, mm);
+    a.w = addmod_bytes(a.w, b.w, mm);
+  }
+  *dst = a;
+}
+
+}  // namespace
+
+cudaError_t launch_combine_digits(const OzTables& T, int64_t m, int64_t ldy, uint8_t* Y, int nsplit, int64_t ysplit,
+                                  cudaStream_t st) {
+  if (nsplit <= 1 || m == 0) return cudaSuccess;
+  if ((ldy & 15) || (ysplit & 15) || (reinterpret_cast<uintptr_t>(Y) & 15)) return cudaErrorInvalidValue;
+  const int64_t plane16 = m * ldy / 16, total16 = plane16 * T.Q;
+  const int64_t blocks = (total16 + 255) / 256;
+  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  combine_digits_kernel<<<(unsigned)blocks, 256, 0, st>>>(T, plane16, total16, Y, nsplit, ysplit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* probs, int count, int64_t total_rec,

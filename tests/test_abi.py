@@ -326,3 +326,22 @@ int main(void) {{
             p.workspace_bytes(1000, 300, 777), lay["u"], lay["bt"]]
     assert [int(x) for x in got[:-1]] == want
     assert int(got[-1]) != oz.OZ_OK
+
+
+def test_split_k_workspace_holds_the_extra_residue_sets():
+    """A TC product with too few output tiles for the GPU splits its inner
+    dimension (whole 1024-term slabs per range) and keeps one residue set per
+    range: 256 x 256 x 65536 on CTA pairs has 16 tiles (one per modulus) and
+    64 slabs, split four ways, so its workspace holds three more sets of
+    Q m ldy bytes than the unsplit layout of a blocked call; a product with
+    enough tiles (8192^3) does not split."""
+    plan = oz.Plan(16, 53, 65536, oz.OZ_ENGINE_TC)
+    m = n = 256
+    k = 65536
+    split = oz.oz_workspace_bytes(plan.handle, m, n, k)
+    unsplit = oz.oz_blocked_workspace_bytes(plan.handle, m, n, k)
+    assert split - unsplit == 3 * 16 * m * 256
+    big = oz.Plan(16, 0, 8192, oz.OZ_ENGINE_TC)
+    assert oz.oz_workspace_bytes(big.handle, 8192, 8192, 8192) == oz.oz_blocked_workspace_bytes(big.handle, 8192, 8192, 8192)
+    imma = oz.Plan(16, 53, 65536, oz.OZ_ENGINE_IMMA)
+    assert oz.oz_workspace_bytes(imma.handle, m, n, 100000) == oz.oz_blocked_workspace_bytes(imma.handle, m, n, 100000)

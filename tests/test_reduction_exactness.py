@@ -78,16 +78,23 @@ def test_slab_drain_reduction_bounds_the_residue(m):
 
 @pytest.mark.parametrize("m", MODULI)
 def test_digit_step_lands_in_range(m):
-    """The last slab's digit: y = (W mod m) inv with inv = (P/m)^-1 mod m, an
-    integer below 239^2 (exact in fp32), then y - m rint(y fl(1/m)) and one
-    correction by +m if negative. Claim: the result is y mod m in [0, m)."""
+    """The last slab's digit: from the balanced residue r of W (|r| <= 120),
+    y = r inv with inv = (P/m)^-1 mod m (|y| <= 120 * 238 < 2^15, exact in
+    fp32), then y - m rint(y fl(1/m)) and one correction by +m if negative.
+    Claim: the result is (W mod m) inv mod m in [0, m), for every r and every
+    coefficient below m (so for whatever (P/m)^-1 a plan has). The raw value
+    (W mod m in [0, m)) is r with the same correction."""
     invm = float(np.float32(1.0) / np.float32(m))
-    y = np.arange(0, (m - 1) * (m - 1) + 1, dtype=np.int64)
-    q = np.rint(y.astype(np.float64) * invm).astype(np.int64)
-    d = y - q * m
-    d = np.where(d < 0, d + m, d)
-    assert d.min() >= 0 and d.max() < m
-    assert np.array_equal(d, y % m)
+    r = np.arange(-120, 121, dtype=np.int64)
+    raw = np.where(r < 0, r + m, r)
+    assert np.array_equal(raw, r % m)
+    for inv in range(m):
+        y = r * inv
+        q = np.rint(y.astype(np.float64) * invm).astype(np.int64)
+        d = y - q * m
+        d = np.where(d < 0, d + m, d)
+        assert d.min() >= 0 and d.max() < m
+        assert np.array_equal(d, (r * inv) % m)
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"])
