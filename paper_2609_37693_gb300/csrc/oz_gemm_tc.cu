@@ -49,7 +49,8 @@ constexpr int kBand = 8;                           // n-tiles per band of the ti
 constexpr int A_BYTES = BM * BK * 2;               // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;               // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;     // 48 KiB
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;                      // epilogue warps of the one-CTA kernels
+constexpr int CPW1 = 1024 / kEpiWarps;             // columns of a 256-column tile per epilogue warp
 constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kTmemCols = 512;
 constexpr int kBarBytes = 256;                     // barriers, then the TMEM address and the abort flag
@@ -401,9 +402,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // it holds; the epilogue writes each residue r (|r| <= 120) back while slab
     // sl + 2 accumulates on it, keeps the residue of slab nsl - 2 as a byte,
     // and turns the last slab's sum into the digit in fp32.
-    const int e = warp - 2;                  // 0..7
+    const int e = warp - 2;
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-    const int half = e >> 2;                 // columns 128*half .. +127
+    const int cbase = (e >> 2) * CPW1;       // columns cbase .. cbase + CPW1 - 1
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
@@ -414,9 +415,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
       const float invf = (float)T.inv[c.q];
-      uint32_t acc8[32];
+      uint32_t acc8[CPW1 / 4];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int i = 0; i < CPW1 / 4; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
@@ -424,8 +425,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          const uint32_t taddr = tmem_base + lane_addr + b * BN + half * 128 + ch * 32;
+        for (int ch = 0; ch < CPW1 / 32; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * BN + cbase + ch * 32;
           uint32_t v[32];
           tmem_ld32(taddr, v);
           tmem_ld_wait();
@@ -466,12 +467,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) break;
       // ---- tile done: acc8 holds the digits (or W mod m), one byte per entry ----
       const int row = c.tm * BM + quarter * 32 + lane;
-      const int col0 = c.tn * BN + half * 128;
+      const int col0 = c.tn * BN + cbase;
       if (row < p.m && col0 < p.n) {
-        const uint32_t* outw = acc8;
         uint8_t* dst = p.Y + (size_t)u.ks * p.ysplit + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-        store_digits<32>(dst, outw, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
-                         p.acc, T.m[c.q]);
+        store_digits<CPW1 / 4>(dst, acc8, p.n - col0, (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0,
+                               p.acc, T.m[c.q]);
       }
     }
   }
@@ -857,7 +857,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
     // ------------------------------ epilogue ------------------------------
     const int e = warp - 2;
     const int quarter = warp & 3;
-    const int half = e >> 2;
+    const int cbase = (e >> 2) * CPW1;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
@@ -870,9 +870,9 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
       const float mf = (float)T.m[c.q];
       const float invm = T.invm[c.q];
       const float invf = (float)T.inv[c.q];
-      uint32_t acc8[32];
+      uint32_t acc8[CPW1 / 4];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc8[i] = 0x80808080u;
+      for (int i = 0; i < CPW1 / 4; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, status)) { ok = false; break; }
@@ -880,8 +880,8 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          const uint32_t taddr = tmem_base + lane_addr + b * BN + half * 128 + ch * 32;
+        for (int ch = 0; ch < CPW1 / 32; ++ch) {
+          const uint32_t taddr = tmem_base + lane_addr + b * BN + cbase + ch * 32;
           uint32_t v[32];
           tmem_ld32(taddr, v);
           tmem_ld_wait();
@@ -921,22 +921,11 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
       }
       if (!ok) break;
       const int row = c.tm * BM + quarter * 32 + lane;
-      const int col0 = c.tn * BN + half * 128;
+      const int col0 = c.tn * BN + cbase;
       if (row < P.m && col0 < P.n) {
         uint8_t* dst = P.Y + (size_t)c.q * P.m * P.ldy + (size_t)row * P.ldy + col0;
-        if ((P.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(P.Y) & 15) == 0) {
-          const int chunks = min(8, (int)((P.n - col0 + 15) >> 4));   // 16-byte runs up to n rounded up
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (i < chunks)
-              reinterpret_cast<uint4*>(dst)[i] = make_uint4(acc8[4 * i], acc8[4 * i + 1], acc8[4 * i + 2], acc8[4 * i + 3]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (col0 + 4 * i + j < P.n) dst[4 * i + j] = (uint8_t)(acc8[i] >> (8 * j));
-        }
+        store_digits<CPW1 / 4>(dst, acc8, P.n - col0, (P.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(P.Y) & 15) == 0,
+                               0, T.m[c.q]);
       }
     }
   }
