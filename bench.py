@@ -53,8 +53,18 @@ def parse():
                     help="residue alphabet: the INT8 path, or a float-format configuration")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0, help="target seconds of oracle work")
-    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "batch", "blocked"],
-                    help="dgemm: one m=n=k product (the headline); batch: 256 uneven products")
+    ap.add_argument("--workload", default="dgemm",
+                    choices=["dgemm", "batch", "blocked", "autograd", "fp-sweep", "precision", "peaks"],
+                    help="dgemm: one m=n=k product (the headline); batch: 256 uneven products; blocked: the "
+                         "inner dimension in slabs; autograd: forward + backward of the differentiable matmul; "
+                         "fp-sweep: every float format next to the INT8 path; precision: throughput over n, phi, "
+                         "Q and beta; peaks: library GEMM rates of this GPU (the roofline denominators)")
+    ap.add_argument("--sweep-n", type=int, nargs="+", default=None, help="fp-sweep / precision: sizes")
+    ap.add_argument("--sweep-phi", type=float, nargs="+", default=None, help="fp-sweep / precision: phi values")
+    ap.add_argument("--sweep-q", type=int, nargs="+", default=None, help="precision: modulus counts")
+    ap.add_argument("--formats", nargs="+", default=["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
+                    help="fp-sweep: float formats")
+    ap.add_argument("--reps", type=int, default=5, help="sweeps: timed repetitions (median)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-mode", default="auto", choices=["auto", "grouped", "streams"],
                     help="batch: autotuned over launch structure and modulus counts (auto), one launch per "
@@ -198,6 +208,15 @@ def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
+        return {}
+
+
+def load_library_peaks():
+    """FP8 and INT8 library GEMM rates measured on this GPU model by
+    `bench.py --workload peaks` (profiles/library_gemm_peaks.json)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", "library_gemm_peaks.json")))["tflops"]
+    except (OSError, ValueError, KeyError):
         return {}
 
 
@@ -440,9 +459,15 @@ def run_ours(args, rank, world, local):
     gemm_ops = 2.0 * plan.q * n**3                       # algorithmic low-precision ops per launch
     gemm_s = phase_ms["gemm"] * 1e-3
     achieved = gemm_ops / gemm_s / 1e12
-    if is_fp:
-        # no measured FP8/FP4 peak: the measured bf16 burst times the nominal dense
-        # ratio (FP8 4.5 / bf16 2.25 PFLOP/s; FP4 13.5 / 2.25)
+    lib = load_library_peaks()
+    if is_fp and args.format != "E2M1" and "fp8_e4m3" in lib:
+        peak = lib["fp8_e4m3"]
+        peak_src = "FP8 E4M3 dense, measured (torch._scaled_mm, profiles/library_gemm_peaks.json)"
+    elif is_fp and "fp8_e4m3" in lib:
+        peak = lib["fp8_e4m3"] * 3.0
+        peak_src = ("FP4 dense = measured FP8 E4M3 (profiles/library_gemm_peaks.json) x 3, the nominal dense "
+                    "ratio 13.5 / 4.5 PFLOP/s (no block-scaled FP4 library GEMM could be timed)")
+    elif is_fp:
         ratio = 6.0 if args.format == "E2M1" else 2.0
         peak = peaks.get("bf16_tflops", 1900.0) * ratio
         peak_src = (f"{'FP4' if ratio == 6.0 else 'FP8'} dense = measured bf16 burst (MEASURED_PEAKS.json "
@@ -450,6 +475,9 @@ def run_ours(args, rank, world, local):
     elif plan.engine in (oz.OZ_ENGINE_TC, oz.OZ_ENGINE_TC1):
         peak = peaks.get("bf16_tflops", 1900.0)
         peak_src = "bf16 dense, measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    elif "int8" in lib:
+        peak = lib["int8"]
+        peak_src = "INT8 dense, measured (torch._int_mm, cuBLASLt; profiles/library_gemm_peaks.json)"
     else:
         peak = 167.0
         peak_src = "INT8 dense on B300 as stated in the paper (Sec. 'Speedup'); no measured INT8 peak exists"
@@ -668,6 +696,197 @@ def run_blocked(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def _median_ms(fn, reps):
+    """Median of reps timed calls (CUDA events on the current stream) after one
+    untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(statistics.median(ts))
+
+
+def _best_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def run_peaks(args, rank, world, local):
+    """Library GEMM rates of this GPU at m = n = k = --n, best of 10 (CUDA
+    events, one untimed call first): cuBLAS DGEMM, bf16 (torch.matmul), FP8
+    E4M3 (torch._scaled_mm, unit scales, bf16 output), INT8 (torch._int_mm,
+    cuBLASLt, int32 output) and block-scaled FP4 E2M1 (torch._scaled_mm with
+    UE8M0 block scales of 1) where this PyTorch has it. These are the
+    denominators of the INT8 and float-format rooflines."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    g = torch.Generator(device=dev).manual_seed(0)
+    out = {}
+    a64 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    b64 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    out["fp64_dgemm"] = 2.0 * n**3 / (_best_ms(lambda: a64 @ b64, 3) * 1e-3) / 1e12
+    a = a64.to(torch.bfloat16)
+    b = b64.to(torch.bfloat16)
+    del a64, b64
+    out["bf16"] = 2.0 * n**3 / (_best_ms(lambda: a @ b, 10) * 1e-3) / 1e12
+    one = torch.ones((), dtype=torch.float32, device=dev)
+    a8 = (a * 4).to(torch.float8_e4m3fn)
+    b8 = (b * 4).to(torch.float8_e4m3fn).t().contiguous().t()        # column-major second operand
+    out["fp8_e4m3"] = 2.0 * n**3 / (_best_ms(lambda: torch._scaled_mm(a8, b8, one, one, out_dtype=torch.bfloat16),
+                                              10) * 1e-3) / 1e12
+    ai = torch.randint(-100, 100, (n, n), dtype=torch.int8, device=dev, generator=g)
+    bi = torch.randint(-100, 100, (n, n), dtype=torch.int8, device=dev, generator=g).t().contiguous().t()
+    out["int8"] = 2.0 * n**3 / (_best_ms(lambda: torch._int_mm(ai, bi), 10) * 1e-3) / 1e12
+    notes = {}
+    try:
+        a4 = torch.randint(0, 256, (n, n // 2), dtype=torch.uint8, device=dev, generator=g).view(torch.float4_e2m1fn_x2)
+        b4 = torch.randint(0, 256, (n, n // 2), dtype=torch.uint8, device=dev, generator=g).view(torch.float4_e2m1fn_x2)
+        sa = torch.full((n * (n // 32),), 127, dtype=torch.uint8, device=dev).view(torch.float8_e8m0fnu)
+        sb = torch.full((n * (n // 32),), 127, dtype=torch.uint8, device=dev).view(torch.float8_e8m0fnu)
+        fn = lambda: torch._scaled_mm(a4, b4.t(), sa, sb, out_dtype=torch.bfloat16)  # noqa: E731
+        out["fp4_e2m1_mx"] = 2.0 * n**3 / (_best_ms(fn, 10) * 1e-3) / 1e12
+    except Exception as e:                        # not every PyTorch build has a block-scaled FP4 GEMM
+        notes["fp4_e2m1_mx"] = f"unavailable: {type(e).__name__}: {str(e)[:160]}"
+    if rank == 0:
+        print(json.dumps({"metric": f"library GEMM TFLOP/s at m=n=k={n}", "value": out.get("fp8_e4m3"),
+                          "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+                          "config": {"workload": "library GEMM peaks", "n": n, "rates": out, "notes": notes,
+                                     "torch": torch.__version__,
+                                     "how": "best of 10 after one untimed call, CUDA events"}}), flush=True)
+
+
+def run_autograd(args, rank, world, local):
+    """Forward + backward of EmuMatmul (C = A B, dA = dC B^T, dB = A^T dC
+    through the emulated product) against float64 autograd, at m = n = k =
+    4096 and at m = 65536, k = n = 256. Operands and dC ~ N(0, 1) (torch
+    generator seeded 0); best of 3 timed passes after one untimed pass;
+    TFLOP/s counts the three products, 3 * 2mnk."""
+    import torch
+    import paper_2609_37693_gb300 as oz
+    torch.cuda.set_device(local)
+    rows = []
+    for (m, k, n) in ((4096, 4096, 4096), (65536, 256, 256)):
+        g = torch.Generator(device="cuda").manual_seed(0)
+        A = torch.randn(m, k, dtype=torch.float64, device="cuda", generator=g).requires_grad_()
+        B = torch.randn(k, n, dtype=torch.float64, device="cuda", generator=g).requires_grad_()
+        dC = torch.randn(m, n, dtype=torch.float64, device="cuda", generator=g)
+
+        def emu():
+            A.grad = None
+            B.grad = None
+            oz.EmuMatmul.apply(A, B).backward(dC)
+
+        def nat():
+            A.grad = None
+            B.grad = None
+            (A @ B).backward(dC)
+
+        te, tn = _best_ms(emu, 3), _best_ms(nat, 3)
+        fl = 3 * 2.0 * m * n * k
+        rows.append({"m": m, "k": k, "n": n, "emulated_ms": te, "emulated_tflops": fl / te / 1e9,
+                     "fp64_autograd_ms": tn, "fp64_autograd_tflops": fl / tn / 1e9, "speedup": tn / te})
+    if rank == 0:
+        print(json.dumps({"metric": "emulated-FP64 matmul forward+backward TFLOP/s (3 products)",
+                          "value": rows[0]["emulated_tflops"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                          "data": "synthetic", "config": {"workload": "EmuMatmul fwd+bwd", "rows": rows}}),
+              flush=True)
+
+
+def run_fp_sweep(args, rank, world, local):
+    """Every float-format configuration (E4M3, E5M2, E2M3, E3M2, E2M1) next to
+    the INT8 path at m = n = k = n: GEMM count Q, channels, bit budget beta
+    (the widest the window allows at K = n, and the paper's 53), median
+    product time, emulated TFLOP/s, GEMM-phase time and its low-precision
+    TFLOP/s, and cuBLAS DGEMM on the same operands. One JSON line per row.
+    The error of each row is a property of beta alone (every configuration
+    returns the oracle's bits at its beta; tests/test_gpu_fp.py checks this):
+    oracle/precision.py tabulates it."""
+    import torch
+    import paper_2609_37693_gb300 as oz
+    import synth
+    torch.cuda.set_device(local)
+    st = oz._stream_handle()
+    for n in args.sweep_n or [8192]:
+        for phi in args.sweep_phi or [0.5, 2.0]:
+            A, B = synth.phi_pair(n, n, n, phi, seed=0)
+            Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            del A, B
+            dg = 2.0 * n**3 / (_median_ms(lambda: Ad @ Bd, 2) * 1e-3) / 1e12
+            for fmt in ["INT8"] + list(args.formats):
+                for bits in (0, 53):
+                    plan = oz.Plan(16, bits, n) if fmt == "INT8" else oz.PlanFP(fmt, n, bits)
+                    ws = oz.workspace(plan, n, n, n)
+                    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+                    ms = _median_ms(lambda: oz.dgemm(Ad, Bd, plan, out=C, ws=ws), args.reps)
+                    lay = oz.oz_workspace_layout(plan.handle, n, n, n)[1]
+                    base = ws.data_ptr()
+                    gms = _median_ms(lambda: oz.oz_residue_gemm(
+                        plan.handle, n, n, lay["m_pad"], lay["n_pad"], lay["k_pad"], base + lay["u"],
+                        base + lay["v"], base + lay["y"], 0, base + lay["flag"], st), args.reps)
+                    row = {"workload": "fp-sweep", "n": n, "phi": phi, "format": fmt, "q": plan.q,
+                           "channels": getattr(plan, "channels", plan.q), "bits": plan.bits, "ms": ms,
+                           "tflops": 2.0 * n**3 / (ms * 1e-3) / 1e12, "gemm_ms": gms,
+                           "gemm_lp_tflops": 2.0 * n**3 * plan.q / (gms * 1e-3) / 1e12, "dgemm_tflops": dg}
+                    if rank == 0:
+                        print(json.dumps(row), flush=True)
+                    del C, ws
+                    torch.cuda.empty_cache()
+            del Ad, Bd
+            torch.cuda.empty_cache()
+
+
+def run_precision(args, rank, world, local):
+    """The emulated product's throughput over sizes n, exponent spreads phi and
+    modulus counts Q, each Q at the widest beta its window allows at K = n and,
+    where the window holds, at the paper's 53: median product time and
+    emulated TFLOP/s next to cuBLAS DGEMM, one JSON line per row. The error of
+    each (n, phi, Q, beta) is the oracle's (the GPU returns its bits, checked
+    by the parity tests): oracle/precision.py tabulates it."""
+    import torch
+    import paper_2609_37693_gb300 as oz
+    import synth
+    torch.cuda.set_device(local)
+    for n in args.sweep_n or [1024, 4096, 8192]:
+        for phi in args.sweep_phi or [0.5, 1.0, 2.0, 4.0]:
+            A, B = synth.phi_pair(n, n, n, phi, seed=0)
+            Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            del A, B
+            dg = 2.0 * n**3 / (_median_ms(lambda: Ad @ Bd, 2) * 1e-3) / 1e12
+            for q in args.sweep_q or list(range(10, 21)):
+                bmax = oz.Plan(q, 0, n).bits
+                for bits in [bmax] + ([53] if 53 < bmax else []):
+                    plan = oz.Plan(q, bits, n)
+                    ws = oz.workspace(plan, n, n, n)
+                    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+                    ms = _median_ms(lambda: oz.dgemm(Ad, Bd, plan, out=C, ws=ws), args.reps)
+                    row = {"workload": "precision", "n": n, "phi": phi, "q": q, "bits": plan.bits, "ms": ms,
+                           "tflops": 2.0 * n**3 / (ms * 1e-3) / 1e12, "dgemm_tflops": dg}
+                    if rank == 0:
+                        print(json.dumps(row), flush=True)
+                    del C, ws
+            del Ad, Bd
+            torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -679,6 +898,10 @@ def main():
         return
     if args.workload == "blocked":
         run_blocked(args, rank, world, local)
+        return
+    others = {"autograd": run_autograd, "fp-sweep": run_fp_sweep, "precision": run_precision, "peaks": run_peaks}
+    if args.workload in others:
+        others[args.workload](args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

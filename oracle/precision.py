@@ -1,18 +1,24 @@
-"""Error of the emulated product on both operand families, taken from the
-oracle on a grid of sampled entries (no GPU).
+"""Error tables of the emulated product, from the oracle alone (no GPU).
 
-    python tests/precision_oracle.py --n 8192 16384
-    python tests/precision_oracle.py --n 8192 --operands paper --q 14 15 16 17 18 19 20
+TEST INFRASTRUCTURE, like the rest of oracle/: a report tool, run by hand.
 
-The CUDA path returns the oracle's bits (the parity tests check this entry by
-entry, at 8192 too), so these are the errors of the GPU result as well. Row i
-of op(A) and column j of op(B) hold everything entry (i, j) depends on (its
-shifts included), so the sampled rows of A and columns of B are multiplied on
-their own. For each sampled entry the error is |C_ij - (AB)_ij|, formed
-exactly and rounded once, in units of u (|A||B|)_ij with u = 2^-53.
+    python -m oracle.precision --n 8192 16384
+    python -m oracle.precision --n 8192 --operands paper --q 14 15 16 17 18 19 20
+    python -m oracle.precision --n 1024 4096 8192 --operands phi0.5 phi1 phi2 phi4 --q 10 12 14 16 18 20
+
+Every configuration of the library returns the oracle's bits at its modulus
+set and bit budget (the GPU parity tests check this entry by entry, at 8192
+too), and within the window the result depends on beta alone, not on the
+moduli or the alphabet (Sec. "Emulation Problem": C = fl(2^-(s+t) A'B')). So
+these are the errors of the GPU results, for the INT8 path and every float
+format at the same beta. Row i of op(A) and column j of op(B) hold everything
+entry (i, j) depends on (its shifts included), so the sampled rows of A and
+columns of B are multiplied on their own. For each sampled entry the error is
+|C_ij - (AB)_ij|, formed exactly and rounded once, in units of u (|A||B|)_ij
+with u = 2^-53.
 
 Operand families (synth):
-* phi: entries U(-0.5, 0.5) exp(phi N(0, 1));
+* phiX: entries U(-0.5, 0.5) exp(X N(0, 1));
 * paper: the paper's timing operands (Table tab:setup), row i of each operand
   N(0, 1) 2^e_i with e_i an integer drawn from [-20, 20).
 """
@@ -25,19 +31,27 @@ import time
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
 
 
 def errors(A, B, mods, beta, rows, cols):
+    """|C - AB| / (u |A||B|) on the grid rows x cols (row-major)."""
     As = np.ascontiguousarray(A[rows, :])
     Bs = np.ascontiguousarray(B[:, cols])
     C = oracle.dgemm(As, Bs, mods, beta)
     r, c = np.divmod(np.arange(len(rows) * len(cols)), len(cols))
     err, ab = oracle.exact_error(As, Bs, C, r, c)
     return err / (2.0**-53 * ab)
+
+
+def operands(name, n):
+    if name == "paper":
+        return synth.row_scaled_pair(n, seed=0)
+    return synth.phi_pair(n, n, n, float(name[3:]), seed=0)
 
 
 def main():
@@ -52,16 +66,13 @@ def main():
     print("|---|---|---|---|---|---|---|---|")
     for n in args.n:
         rng = np.random.default_rng(2)
-        rows = np.sort(rng.choice(n, size=args.rows, replace=False))
-        cols = np.sort(rng.choice(n, size=args.cols, replace=False))
+        rows = np.sort(rng.choice(n, size=min(args.rows, n), replace=False))
+        cols = np.sort(rng.choice(n, size=min(args.cols, n), replace=False))
         for ops in args.operands:
-            if ops == "paper":
-                A, B = synth.row_scaled_pair(n, seed=0)
-            else:
-                A, B = synth.phi_pair(n, n, n, float(ops[3:]), seed=0)
+            A, B = operands(ops, n)
             for q in args.q:
                 mods = oracle.max_product_moduli(q, 239)
-                bmax = oracle.beta_max(mods, n)
+                bmax = min(oracle.beta_max(mods, n), 80)
                 # the paper's 53 where the window admits it, and the widest beta
                 for beta in sorted({b for b in (53, bmax) if b <= bmax}):
                     t = time.time()

@@ -1,7 +1,12 @@
 """Accuracy per modulus count (the precision trade-off): errors against the
 exact product fall as Q (and with it the bit budget) grows, and at Q = 16 and
-phi = 0.5 they stay within 2 u (|A||B|)_ij."""
+phi = 0.5 they stay within 2 u (|A||B|)_ij. Every sampled entry of each GPU
+product is first checked bit for bit against the oracle."""
+import numpy as np
 import pytest
+
+import oracle
+import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -9,11 +14,34 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from tests.precision_sweep import sweep  # noqa: E402
+import paper_2609_37693_gb300 as oz  # noqa: E402
+
+U = 2.0**-53
+
+
+def _sweep(n, phis, qs, samples):
+    """Rows (phi, q, bits, max error in u |A||B|) of GPU products at the widest
+    beta each Q's window allows at K = n, and also at 53 where it holds."""
+    rows = []
+    for phi in phis:
+        A, B = synth.phi_pair(n, n, n, phi, seed=0)
+        Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        r, c = synth.sample_entries(n, n, samples, seed=7)
+        for q in qs:
+            bmax = oz.Plan(q, 0, n).bits
+            for bits in [bmax] + ([53] if 53 < bmax else []):
+                plan = oz.Plan(q, bits, n)
+                C = oz.dgemm(Ad, Bd, plan).cpu().numpy()
+                ref = oracle.dgemm_entries(A, B, plan.moduli, plan.bits, r, c)
+                assert np.array_equal(C[r, c].view(np.uint64), ref.view(np.uint64)), (phi, q, bits)
+                err, ab = oracle.exact_error(A, B, C, r, c)
+                rel = np.where(ab > 0, err / (U * np.where(ab > 0, ab, 1.0)), np.where(err > 0, np.inf, 0.0))
+                rows.append({"phi": phi, "q": q, "bits": plan.bits, "max_err_u": float(rel.max())})
+    return rows
 
 
 def test_error_falls_with_q_and_meets_2u_at_q16():
-    rows = sweep([1024], [0.5, 2.0], [10, 12, 14, 16, 18, 20], samples=4096, reps=1, dgemm=False, log=lambda s: None)
+    rows = _sweep(1024, [0.5, 2.0], [10, 12, 14, 16, 18, 20], samples=4096)
     for phi in (0.5, 2.0):
         top = [r for r in rows if r["phi"] == phi and r["bits"] == max(x["bits"] for x in rows
                                                                        if x["phi"] == phi and x["q"] == r["q"])]

@@ -321,9 +321,9 @@ def test_sampled_rows_and_columns_give_the_same_entries():
 
 
 def test_error_report_helper_on_a_small_case():
-    """The sampled-grid error of tests/precision_oracle.py against entries
-    computed one by one: the same values, and within 2u at the widest beta."""
-    from tests import precision_oracle
+    """The sampled-grid error of oracle/precision.py against entries computed
+    one by one: the same values, and within 2u at the widest beta."""
+    from oracle import precision as precision_oracle
     A, B = synth.phi_pair(200, 150, 300, 0.5, seed=4)
     rows, cols = np.array([0, 5, 199]), np.array([1, 149])
     beta = oracle.beta_max(MODS16, 300)
