@@ -349,36 +349,6 @@ def run_ours(args, rank, world, local):
     if st != oz.OZ_OK:
         raise RuntimeError(f"status after warm-up: {oz.oz_status_str(st)}")
 
-    # (measured first: a host-operand run right after the long device-timed
-    # region was seen to run far slower than the same run on its own)
-    flops = 2.0 * n**3
-    # ---- e2e: host buffers through the public host-I/O call (oz_dgemm_host),
-    # every step copying A and B in and C out inside the timed region ----
-    all_cpus = os.sched_getaffinity(0)
-    host_binding = bind_host_to_gpu(local)            # the pinned buffers land next to the GPU
-    A_pin = torch.from_numpy(A_h).pin_memory()
-    B_pin = torch.from_numpy(B_h).pin_memory()
-    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    os.sched_setaffinity(0, all_cpus)
-    hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
-    for _ in range(2):
-        hg(A_pin, B_pin, C_pin, stream)
-    torch.cuda.synchronize()
-    e2e_steps = max(2, min(args.steps, 10))
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(e2e_steps):
-        hg(A_pin, B_pin, C_pin, stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
-    e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
-    e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
-    hg_rows, hg_cols = hg.block
-    del hg
-
-
     # The paper's gate for a timed call (Table tab:setup): relative Frobenius
     # difference from native DGEMM below 1e-12. Native DGEMM is also the
     # throughput comparison.
@@ -422,6 +392,34 @@ def run_ours(args, rank, world, local):
     ms_per_step = elapsed_ms / args.steps
     flops = 2.0 * n**3
     value = throughput_tflops(flops, args.steps, elapsed_ms, world)
+
+    # ---- e2e: host buffers through the public host-I/O call (oz_dgemm_host),
+    # every step copying A and B in and C out inside the timed region; timed
+    # after the device region (C_pin is compared with C, which holds the same
+    # product) ----
+    all_cpus = os.sched_getaffinity(0)
+    host_binding = bind_host_to_gpu(local)            # the pinned buffers land next to the GPU
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    B_pin = torch.from_numpy(B_h).pin_memory()
+    C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    os.sched_setaffinity(0, all_cpus)
+    hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
+    for _ in range(2):
+        hg(A_pin, B_pin, C_pin, stream)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 10))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        hg(A_pin, B_pin, C_pin, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
+    e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
+    e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
+    hg_rows, hg_cols = hg.block
+    del hg
 
     # ---- per-phase times through the phase entry points (same kernels) ----
     _, lay = oz.oz_workspace_layout(plan.handle, n, n, n)
