@@ -313,6 +313,46 @@ def bind_host_to_gpu(local):
         return f"not bound ({type(e).__name__})"
 
 
+def host_copy_rates(A_pin, C_pin, stream):
+    """One timed host-to-device copy of A_pin and one device-to-host copy into
+    C_pin (CUDA events on the stream), in GB/s, and the NUMA nodes that hold
+    A_pin's pages as /proc/self/numa_maps reports them: the host-operand
+    product's speed follows these copies."""
+    import torch
+    dev_buf = torch.empty(A_pin.shape, dtype=A_pin.dtype, device=stream.device)
+    rates = {}
+    for name, dst, src in (("h2d", dev_buf, A_pin), ("d2h", C_pin, dev_buf[: C_pin.shape[0]])):
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        rates[name] = src.numel() * src.element_size() / best / 1e6
+    del dev_buf
+    rates["numa"] = "unknown"
+    try:
+        addr, start = A_pin.data_ptr(), None
+        for line in open("/proc/self/maps"):
+            lo, hi = (int(x, 16) for x in line.split()[0].split("-"))
+            if lo <= addr < hi:
+                start = lo
+                break
+        for line in open("/proc/self/numa_maps"):
+            f = line.split()
+            if start is not None and int(f[0], 16) == start:
+                rates["numa"] = " ".join(x for x in f[1:] if x[:1] == "N" or x.split(":")[0] in
+                                         ("bind", "default", "prefer", "interleave", "local")) or f[1]
+                break
+    except (OSError, ValueError, IndexError):
+        pass
+    return rates
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2609_37693_gb300 as oz
@@ -403,19 +443,23 @@ def run_ours(args, rank, world, local):
     B_pin = torch.from_numpy(B_h).pin_memory()
     C_pin = torch.empty((n, n), dtype=torch.float64).pin_memory()
     os.sched_setaffinity(0, all_cpus)
+    copy_gbs = host_copy_rates(A_pin, C_pin, stream)
     hg = oz.HostGemm(plan, n, n, n, args.e2e_rows, dev, cols_per_chunk=args.e2e_cols)
-    for _ in range(2):
+    for _ in range(max(3, args.warmup)):
         hg(A_pin, B_pin, C_pin, stream)
     torch.cuda.synchronize()
     e2e_steps = max(2, min(args.steps, 10))
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(e2e_steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
+    e2e_clocks = ClockSampler(local)
+    e2e_clocks.start()
+    ev[0].record(stream)
+    for i in range(e2e_steps):
         hg(A_pin, B_pin, C_pin, stream)
-    t1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e2e_steps, dist, dev)
+    e2e_clk = e2e_clocks.stop()
+    e2e_step_ms = [round(ev[i].elapsed_time(ev[i + 1]), 3) for i in range(e2e_steps)]
+    e2e_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]) / e2e_steps, dist, dev)
     e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
     e2e_exact = bool(np.array_equal(C_pin.numpy().view(np.uint64), C.cpu().numpy().view(np.uint64)))
     hg_rows, hg_cols = hg.block
@@ -433,10 +477,10 @@ def run_ours(args, rank, world, local):
         oz.oz_split(plan.handle, 1, n, n, A.data_ptr(), n, m_pad, k_pad, base + lay["s"], base + lay["u"],
                     base + lay["flag"], None, sh)
         ev[1].record(stream)
-        if is_fp:
+        if is_fp or plan.engine != oz.OZ_ENGINE_IMMA:   # as oz_dgemm does: B's columns split in place
             oz.oz_split(plan.handle, 0, n, n, B.data_ptr(), n, n_pad, k_pad, base + lay["t"], base + lay["v"],
                         base + lay["flag"], base + lay["colmax"], sh)
-        else:                                   # as oz_dgemm does: B^T, then its rows split
+        else:                                   # int8 planes: B^T, then its rows split
             oz.oz_transpose(n, n, B.data_ptr(), n, base + lay["bt"], sh)
             oz.oz_split(plan.handle, 1, n, n, base + lay["bt"], n, n_pad, k_pad, base + lay["t"], base + lay["v"],
                         base + lay["flag"], None, sh)
@@ -527,7 +571,8 @@ def run_ours(args, rank, world, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
-                    "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms,
+                    "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms, "step_ms": e2e_step_ms,
+                    "copy_gbs": copy_gbs, "clocks": e2e_clk,
                     "api": "oz_dgemm_host (pinned host A, B, C; blocks of C overlap copies and phases)",
                     "block": [hg_rows, hg_cols], "host": host_binding,
                     "equals_device_result": e2e_exact},

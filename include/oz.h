@@ -54,7 +54,7 @@ extern "C" {
 #define OZ_MAX_MODULI 20   /* largest Q the library accepts */
 #define OZ_MIN_MODULI 9    /* smallest Q the library accepts */
 #define OZ_MAX_BITS 80     /* largest bit budget beta (|A'| < 2^beta) of an INT8 plan */
-#define OZ_MAX_BITS_FP 64  /* largest bit budget of a float-format plan */
+#define OZ_MAX_BITS_FP 72  /* largest bit budget of a float-format plan (widened configurations) */
 
 typedef enum {
   OZ_OK = 0,
@@ -123,14 +123,20 @@ OZ_API oz_status oz_plan_info(oz_plan plan, int* q, int* bits, int64_t* k_max, i
  * (Sec. "Forms and Channels", Sec. "Instantiation"): pairwise-coprime channels,
  * each a modulus with a one-limb, schoolbook or Toom (Karatsuba) form whose
  * tables take values in the format's alphabet S (its finite values scaled to
- * integers), found by an exact least-GEMM-count search and frozen in the
- * library for inner dimensions K_cfg = 8192 and 16384; the plan takes the
- * least K_cfg >= k_hint. Every plane value is at most floor(sqrt(2^24/K_cfg)),
- * so each GEMM's FP32 accumulator is exact (eq. ov-accgen).
+ * integers), found by an exact least-GEMM-count search (Sec. "Solving the
+ * Program") and frozen in the library: for inner dimensions K_cfg = 8192,
+ * 16384 and 65536 at beta = 53, and widened for K_cfg = 16384 at beta = 69
+ * (Example ex:widened: E2M1 78 GEMMs, E4M3 / E2M3 39). The plan takes the
+ * beta = 53 configuration of the least K_cfg >= k_hint whose window holds
+ * `bits`, else the widened one. Every plane value is at most
+ * floor(sqrt(2^24/K_cfg)), so each GEMM's FP32 accumulator is exact (eq.
+ * ov-accgen).
  *   format   an oz_format value.
  *   k_hint   the largest inner dimension the caller intends to use.
  *   bits     as for oz_plan_create, up to OZ_MAX_BITS_FP (0: the largest beta
- *            <= OZ_MAX_BITS_FP the window allows).
+ *            the beta = 53 configuration's window allows, 53 to 55).
+ * Returns OZ_ERR_K_TOO_LARGE when no configuration holds the window at
+ * (k_hint, bits).
  * The plan owns a small device table of codes (allocated here on the current
  * device, freed by oz_plan_destroy). Without a CUDA device the plan is still
  * made and describes the configuration (oz_plan_info_fp), but products on it
@@ -173,9 +179,10 @@ OZ_API void oz_plan_destroy(oz_plan plan);
  * of oz_plane_geometry's row bytes), the residues of the product (Q x m
  * rows of n entries, each row padded to a multiple of 16 bytes so that the
  * GEMM epilogue stores whole 16-byte runs; uint8, or uint16 per channel for
- * float-format plans) and, for INT8 plans, B^T (n x k doubles: with
- * trans_b = 0 the columns of B are split as rows of its transpose). Returns 0
- * for an invalid plan or shape.
+ * float-format plans) and, for the IMMA engine's int8 planes, B^T (n x k
+ * doubles: with trans_b = 0 the columns of B are split as rows of its
+ * transpose; the bf16 planes of the TC engines are split from B's columns in
+ * place). Returns 0 for an invalid plan or shape.
  */
 OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
 
@@ -187,9 +194,10 @@ OZ_API size_t oz_workspace_bytes(oz_plan plan, int64_t m, int64_t n, int64_t k);
  * (Q x m rows, row pitch n rounded up to 16 bytes; the phase entry points
  * below take and give row pitch n, which fits in the same region), then m_pad,
  * n_pad, k_pad (entries, not bytes), and out[10] the byte offset of B^T
- * (n x k doubles; an INT8 oz_dgemm with trans_b = 0 transposes B there and
- * splits its columns as rows; empty for float-format plans). out must hold
- * 11 entries.
+ * (n x k doubles; an IMMA-engine oz_dgemm with trans_b = 0 transposes B there
+ * and splits its columns as rows; empty for the TC engines, which split B's
+ * columns with oz_split(contiguous = 0), and for float-format plans). out
+ * must hold 11 entries.
  */
 OZ_API oz_status oz_workspace_layout(oz_plan plan, int64_t m, int64_t n, int64_t k, int64_t* out);
 
@@ -344,8 +352,8 @@ OZ_API oz_status oz_split(oz_plan plan, int contiguous, int64_t nvec, int64_t le
 
 /*
  * oz_transpose -- Y = X^T for X of rows x cols doubles (row pitch ld >=
- * cols), Y of cols x rows (row pitch rows): the step an INT8 oz_dgemm takes
- * before splitting the columns of B as contiguous rows (then
+ * cols), Y of cols x rows (row pitch rows): the step an IMMA-engine oz_dgemm
+ * takes before splitting the columns of B as contiguous rows (then
  * oz_split(contiguous = 1) on Y is that split). Device pointers, 8-byte
  * aligned; asynchronous on the stream.
  */

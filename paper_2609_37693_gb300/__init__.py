@@ -43,7 +43,7 @@ FORMATS = {"E4M3": OZ_FMT_E4M3, "E2M3": OZ_FMT_E2M3, "E3M2": OZ_FMT_E3M2, "E2M1"
 OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
 OZ_MAX_BITS = 80
-OZ_MAX_BITS_FP = 64
+OZ_MAX_BITS_FP = 72
 OZ_STATIC_SCRATCH_BYTES = 32 << 20
 
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
@@ -437,13 +437,14 @@ def dgemm_blocked(A, B, plan: Plan, k_slab: int, trans_a: bool = False, trans_b:
     return C
 
 
-def launches_per_dgemm(trans_a: bool = False, trans_b: bool = False) -> int:
-    """Kernels one INT8 oz_dgemm launches: A's rows split in one kernel (its
-    columns, for trans_a, in three: column maxima, shifts, split); B transposed
-    and its columns split as rows (two kernels; one when trans_b); then the
-    GEMM and the reconstruct."""
+def launches_per_dgemm(trans_a: bool = False, trans_b: bool = False, engine: int = OZ_ENGINE_TC) -> int:
+    """Kernels one INT8 oz_dgemm launches without a split of K: A's rows split
+    in one kernel (its columns, for trans_a, in three: column maxima, shifts,
+    split); B's columns in three (bf16 planes) or transposed and split as rows
+    (two, int8 planes of the IMMA engine); one when trans_b; then the GEMM and
+    the reconstruct."""
     a = 3 if trans_a else 1
-    b = 1 if trans_b else 2
+    b = 1 if trans_b else (2 if engine == OZ_ENGINE_IMMA else 3)
     return a + b + 2
 
 

@@ -50,8 +50,9 @@ bool make_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, Layout* L, bo
   }
   L->ysplit = align256((size_t)p->Q * m * L->ldy * ybytes);
   L->y = off; off = align256(off + L->ysplit * L->split.nsplit);
-  // B^T (n x k doubles): the INT8 split takes B's columns as rows of its transpose
-  L->bt = off; off = align256(off + (p->is_fp ? 0 : 8 * (size_t)n * k));
+  // B^T (n x k doubles): the IMMA engine's split takes B's columns as rows of
+  // its transpose (the bf16 planes are split from B's columns directly)
+  L->bt = off; off = align256(off + (p->is_fp || elem == 2 ? 0 : 8 * (size_t)n * k));
   L->total = off;
   return true;
 }
@@ -149,10 +150,14 @@ oz_status dgemm_run(oz_plan plan, int trans_a, int trans_b, int64_t m, int64_t n
   e = trans_a ? oz::launch_split_cols(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, colmax, st)
               : oz::launch_split_rows(T, m, k, A, lda, L.m_pad, L.k_pad, s, U, bf16, flag, st);
   if (e != cudaSuccess) return OZ_ERR_CUDA;
-  // B side: vectors are the columns of op(B); B (k x n) is transposed first,
-  // so that its columns are split as contiguous rows.
+  // B side: vectors are the columns of op(B). Bf16 planes are split from
+  // B's columns in place (column maxima, then tiles staged through shared
+  // memory); for int8 planes B (k x n) is transposed first, so that its
+  // columns are split as contiguous rows.
   if (trans_b) {
     e = oz::launch_split_rows(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, st);
+  } else if (bf16) {
+    e = oz::launch_split_cols(T, n, k, B, ldb, L.n_pad, L.k_pad, t, V, bf16, flag, colmax, st);
   } else {
     double* Bt = reinterpret_cast<double*>(ws + L.bt);
     e = oz::launch_transpose(k, n, B, ldb, Bt, st);

@@ -40,7 +40,7 @@ namespace {
 // =========================================================================
 
 struct ChConst {
-  uint32_t m, magic, c16, c32, c48;
+  uint32_t m, magic, c16, c32, c48, c64;
 };
 
 __device__ __forceinline__ ChConst ch_const(const OzFpTables& F, int c) {
@@ -50,27 +50,32 @@ __device__ __forceinline__ ChConst ch_const(const OzFpTables& F, int c) {
   k.c16 = F.c16[c];
   k.c32 = F.c32[c];
   k.c48 = F.c48[c];
+  k.c64 = F.c64[c];
   return k;
 }
 
-// 16-bit pieces of |a'| (the sign is kept apart, one bit per entry)
+// 16-bit pieces of |a'| (the sign is kept apart, one bit per entry); p4 (bits
+// 64..79) only for a widened budget, beta > 64
 struct Pieces16 {
-  uint32_t p0, p1, p2, p3;
+  uint32_t p0, p1, p2, p3, p4;
 };
 
-__device__ __forceinline__ Pieces16 pieces16(uint64_t mag) {
+__device__ __forceinline__ Pieces16 pieces16(uint64_t mag, uint32_t top = 0) {
   Pieces16 P;
   P.p0 = (uint32_t)mag & 0xffffu;
   P.p1 = (uint32_t)(mag >> 16) & 0xffffu;
   P.p2 = (uint32_t)(mag >> 32) & 0xffffu;
   P.p3 = (uint32_t)(mag >> 48);
+  P.p4 = top;
   return P;
 }
 
-// Index of the code word of a' = +-|a'|: the class r of |a'| (y < 2^16 (1 + 3 * 4095)
+// Index of the code word of a' = +-|a'|: the class r of |a'| (y < 2^16 (1 + 4 * 4095)
 // < 2^32, one Barrett step), plus m for a negative entry, whose class is (m - r) mod m.
+template <bool WIDE>
 __device__ __forceinline__ uint32_t word_index(const ChConst& k, const Pieces16& P, uint32_t neg) {
-  const uint32_t y = P.p0 + P.p1 * k.c16 + P.p2 * k.c32 + P.p3 * k.c48;
+  uint32_t y = P.p0 + P.p1 * k.c16 + P.p2 * k.c32 + P.p3 * k.c48;
+  if (WIDE) y += P.p4 * k.c64;
   return mod_barrett(y, k.m, k.magic) + (neg ? k.m : 0u);
 }
 
@@ -107,18 +112,26 @@ __device__ __forceinline__ uint4 chunk6(uint64_t a, uint64_t b) {
   return make_uint4((uint32_t)a, (uint32_t)(a >> 32) | ((uint32_t)b << 16), (uint32_t)(b >> 16), 0u);
 }
 
-// Entry bits: |a'| pieces and sign of x (non-finite entries count as 0).
+// Entry bits: |a'| pieces and sign of x (non-finite entries count as 0);
+// WIDE: |a'| < 2^80 in 128 bits (beta up to 72).
+template <bool WIDE>
 __device__ __forceinline__ Pieces16 load_entry(uint64_t b, int32_t s, uint32_t& neg) {
   if (((b >> 52) & 0x7ff) == 0x7ff) b = 0;
-  const Trunc t = truncate(b, s);
-  neg = t.neg && t.mag;
-  return pieces16(t.mag);
+  if constexpr (WIDE) {
+    const TruncWide t = truncate_wide(b, s);
+    neg = t.neg && t.mag != 0;
+    return pieces16((uint64_t)t.mag, (uint32_t)(t.mag >> 64) & 0xffffu);
+  } else {
+    const Trunc t = truncate(b, s);
+    neg = t.neg && t.mag;
+    return pieces16(t.mag);
+  }
 }
 
 // Contiguous vectors: one CTA of 256 threads per vector, 8 entries per thread
 // and pass; planes [nplanes][nvec_pad][row bytes of k_pad entries]. For 6-bit
 // codes the two threads of a 16-entry chunk meet by a shuffle.
-template <int CB>
+template <int CB, bool WIDE>
 __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constant__ OzFpTables F, int bits,
                                                             int64_t nvec, int64_t len, const double* __restrict__ X,
                                                             int64_t ld, int64_t nvec_pad, int64_t k_pad,
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
     for (int e = 0; e < 8; ++e) {
       const uint64_t b = (live && h0 + e < len) ? __ldg(row + h0 + e) : 0ull;
       uint32_t ng;
-      P[e] = load_entry(b, s, ng);
+      P[e] = load_entry<WIDE>(b, s, ng);
       negm |= ng << e;
     }
     for (int c = 0; c < F.nch; ++c) {
@@ -183,7 +196,7 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
       const uint32_t* tw = F.words + F.ch_woff[c];
       uint32_t w[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index(k, P[e], (negm >> e) & 1u));
+      for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index<WIDE>(k, P[e], (negm >> e) & 1u));
       const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -207,7 +220,7 @@ __global__ void __launch_bounds__(256) split_fp_rows_kernel(const __grid_constan
 // groups of 4 take the 32 entries of one vector, 8 each, so that a vector's
 // plane bits leave the group as one 32-, 24- (two chunks) or 16-byte piece of
 // its plane row; 6-bit pairs meet by a shuffle. No shared memory.
-template <int CB>
+template <int CB, bool WIDE>
 __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constant__ OzFpTables F, int64_t nvec,
                                                             int64_t len, const double* __restrict__ X, int64_t ld,
                                                             int64_t nvec_pad, int64_t k_pad,
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
     const int64_t h = hbase + hg * 8 + e;
     const uint64_t b = (live && h < len) ? __ldg(Xb + h * ld + j) : 0ull;
     uint32_t ng;
-    P[e] = load_entry(b, s, ng);
+    P[e] = load_entry<WIDE>(b, s, ng);
     negm |= ng << e;
   }
   const int64_t row_bytes = CB == 4 ? k_pad / 2 : k_pad;
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(256) split_fp_cols_kernel(const __grid_constan
     const uint32_t* tw = F.words + F.ch_woff[c];
     uint32_t w[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index(k, P[e], (negm >> e) & 1u));
+    for (int e = 0; e < 8; ++e) w[e] = __ldg(tw + word_index<WIDE>(k, P[e], (negm >> e) & 1u));
     const int p0 = F.ch_plane0[c], np = F.ch_nplanes[c];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -798,13 +811,13 @@ cudaError_t launch16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y,
   return cudaGetLastError();
 }
 
-template <int CB>
-cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
-                     const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts, uint8_t* planes,
-                     int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
+template <int CB, bool WIDE>
+cudaError_t split_fp_w(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
+                       const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,
+                       uint8_t* planes, int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
   if (contiguous) {
-    split_fp_rows_kernel<CB><<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad, k_pad,
-                                                                 shifts, planes, flag, given);
+    split_fp_rows_kernel<CB, WIDE><<<(unsigned)nvec_pad, 256, 0, st>>>(f, t.bits, nvec, len, X, ld, nvec_pad,
+                                                                       k_pad, shifts, planes, flag, given);
     return cudaGetLastError();
   }
   if (!given) {
@@ -812,8 +825,20 @@ cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int
     if (e != cudaSuccess) return e;
   }
   dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 32));
-  split_fp_cols_kernel<CB><<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+  split_fp_cols_kernel<CB, WIDE><<<g, 256, 0, st>>>(f, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
   return cudaGetLastError();
+}
+
+// beta > 64: |a'| in 128 bits and a fifth 16-bit piece
+template <int CB>
+cudaError_t split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
+                     const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts, uint8_t* planes,
+                     int32_t* flag, uint64_t* colmax, cudaStream_t st, bool given) {
+  if (t.bits > 64)
+    return split_fp_w<CB, true>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax,
+                                st, given);
+  return split_fp_w<CB, false>(t, f, contiguous, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, colmax,
+                               st, given);
 }
 
 }  // namespace
@@ -904,7 +929,7 @@ cudaError_t launch_reconstruct16(const OzTables& T, int64_t m, int64_t n, const 
                                  const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
   if (m == 0 || n == 0) return cudaSuccess;
   if (ldy < n) return cudaErrorInvalidValue;
-  if (T.limbs > 4) return cudaErrorInvalidValue;
+  if (T.limbs > 4) return launch_reconstruct16_wide(T, m, n, Y, ldy, s, t, C, ldc, st);   // widened budgets
   switch (T.npairs) {
     case 5: return launch16<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
     case 6: return launch16<6>(T, m, n, Y, ldy, s, t, C, ldc, st);

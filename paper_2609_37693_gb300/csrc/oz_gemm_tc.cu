@@ -508,12 +508,102 @@ static_assert((2 * STAGES + 5) * 8 <= kHolderOff, "barriers overlap the TMEM add
 // outlasts the slab's products)
 constexpr int kPairEpiWarps = 16;
 
+// What a CTA pair needs to know about one unit of work: the tensor maps and
+// first plane rows of its 256 x 256 tile, its k-block range, its modulus and
+// where its digits go.
+struct PairUnit {
+  const CUtensorMap* mA;
+  const CUtensorMap* mB;
+  int ya, yb;               // first rows of the pair tile in the stacked planes of A and B
+  int kb0, kb1, nslabs;     // k blocks [kb0, kb1) in nslabs slabs
+  int q;                    // modulus index
+  uint8_t* Y;               // digit plane of this unit (row pitch ldy, m rows, n columns)
+  int64_t ldy;
+  int m, n, row0, col0;     // the output's size and the tile's first row and column
+  int acc, raw;
+};
+
+// One product (oz_dgemm): units are (split, modulus, tile), as unit_of orders them.
+struct PairSingle {
+  CUtensorMap mapA, mapB;
+  Params p;
+  __device__ __forceinline__ int units() const { return p.num_tiles * p.nsplit; }
+  __device__ __forceinline__ int32_t* status() const { return p.status; }
+  __device__ __forceinline__ int first(int) const { return 0; }
+  __device__ __forceinline__ void prefetch() const {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+  }
+  __device__ __forceinline__ PairUnit unit(int t, int&) const {
+    const Unit u = unit_of(p, t);
+    PairUnit w;
+    w.mA = &mapA;
+    w.mB = &mapB;
+    w.ya = u.c.q * p.m_pad + u.c.tm * 2 * P_BM;
+    w.yb = u.c.q * p.n_pad + u.c.tn * 2 * P_BN;
+    w.kb0 = u.kb0;
+    w.kb1 = u.kb1;
+    w.nslabs = u.nslabs;
+    w.q = u.c.q;
+    w.Y = p.Y + (size_t)u.ks * p.ysplit + (size_t)u.c.q * p.m * p.ldy;
+    w.ldy = p.ldy;
+    w.m = p.m;
+    w.n = p.n;
+    w.row0 = u.c.tm * 2 * P_BM;
+    w.col0 = u.c.tn * 2 * P_BN;
+    w.acc = p.acc;
+    w.raw = p.raw;
+    return w;
+  }
+};
+
+// Grouped products (oz_group_run): unit t belongs to the problem whose unit
+// range holds it (problems in decreasing order of k, so the longest units go
+// first); a role carries the index of its current problem forward, since a
+// pair visits its units in increasing order. Tensor maps in global memory,
+// 128-row boxes for both operands.
+struct PairGrouped {
+  const OzGroupProblem* probs;
+  int count, total;
+  int32_t* st;
+  __device__ __forceinline__ int units() const { return total; }
+  __device__ __forceinline__ int32_t* status() const { return st; }
+  __device__ __forceinline__ int first(int t) const {
+    return group_find(probs, count, (int64_t)(t < total ? t : 0), [](const OzGroupProblem& q) { return q.unit_begin; });
+  }
+  __device__ __forceinline__ void prefetch() const {}
+  __device__ __forceinline__ PairUnit unit(int t, int& pi) const {
+    while (pi + 1 < count && probs[pi + 1].unit_begin <= t) ++pi;
+    const OzGroupProblem& P = probs[pi];
+    const int tiles_m = (int)((P.m + 2 * P_BM - 1) / (2 * P_BM));
+    const Coord c = tile_coord(t - (int)P.unit_begin, tiles_m, P.tiles_n);
+    PairUnit w;
+    w.mA = &P.mapA;
+    w.mB = &P.mapB;
+    w.ya = c.q * (int)P.m_pad + c.tm * 2 * P_BM;
+    w.yb = c.q * (int)P.n_pad + c.tn * 2 * P_BN;
+    w.kb0 = 0;
+    w.kb1 = P.kblocks;
+    w.nslabs = (P.kblocks + kSlabBlocks - 1) / kSlabBlocks;
+    w.q = c.q;
+    w.Y = P.Y + (size_t)c.q * P.m * P.ldy;
+    w.ldy = P.ldy;
+    w.m = (int)P.m;
+    w.n = (int)P.n;
+    w.row0 = c.tm * 2 * P_BM;
+    w.col0 = c.tn * 2 * P_BN;
+    w.acc = 0;
+    w.raw = 0;
+    return w;
+  }
+};
+
 // EW epilogue warps (4, 8 or 16): every warp drains the 32 TMEM lanes of its
 // quarter (warp index mod 4), over CPW = 256 / (EW / 4) columns.
-template <int EW>
+// S: the unit scheduler (PairSingle or PairGrouped).
+template <int EW, typename S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((2 + EW) * 32, 1)
-gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const __grid_constant__ OzTables T, const Params p) {
+gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzTables T) {
   constexpr int CPW = 1024 / EW;            // columns per epilogue warp
   static_assert(EW == 4 || EW == 8 || EW == 16, "4, 8 or 16 epilogue warps");
   extern __shared__ uint8_t smem_raw[];
@@ -547,8 +637,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    sched.prefetch();
   }
   if (warp == 1) {                          // one warp of each CTA: the pair's allocation
     tmem_alloc_pair(smem_u32(tmem_holder), kTmemCols);
@@ -560,7 +649,8 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
 
-  const int num_units = p.num_tiles * p.nsplit;
+  const int num_units = sched.units();
+  int32_t* const status = sched.status();
 
   if (warp == 0) {
     // ------------------------------ TMA producer (both CTAs) ------------------------------
@@ -571,18 +661,19 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       bool outstanding[P_STAGES];
       for (int i = 0; i < P_STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
       bool ok = true;
+      int pi = sched.first(pair);
       for (int t = pair; t < num_units && ok; t += npairs) {
-        const Unit u = unit_of(p, t);
-        const int ya = u.c.q * p.m_pad + u.c.tm * 2 * P_BM + (int)rank * P_BM;
-        const int yb = u.c.q * p.n_pad + u.c.tn * 2 * P_BN + (int)rank * P_BN;
+        const PairUnit u = sched.unit(t, pi);
+        const int ya = u.ya + (int)rank * P_BM;
+        const int yb = u.yb + (int)rank * P_BN;
         for (int kb = u.kb0; kb < u.kb1; ++kb) {
-          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, status)) { ok = false; break; }
           outstanding[s] = false;
           const uint32_t sa = base + s * P_STAGE_BYTES;
           if (leader) mbar_expect_tx(full_bar(s), 2 * P_STAGE_BYTES);
           const uint32_t fb = mapa(full_bar(s), 0);
-          tma_load_2d_pair(sa, &tmA, fb, kb * BK, ya);
-          tma_load_2d_pair(sa + P_A_BYTES, &tmB, fb, kb * BK, yb);
+          tma_load_2d_pair(sa, u.mA, fb, kb * BK, ya);
+          tma_load_2d_pair(sa + P_A_BYTES, u.mB, fb, kb * BK, yb);
           outstanding[s] = true;
           issued_parity[s] = ph;
           if (++s == P_STAGES) { s = 0; ph ^= 1u; }
@@ -602,17 +693,18 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       uint32_t ph = 0;
       uint32_t g = 0;
       bool ok = true;
+      int pi = sched.first(pair);
       for (int t = pair; t < num_units && ok; t += npairs) {
-        const Unit u = unit_of(p, t);
+        const PairUnit u = sched.unit(t, pi);
         for (int sl = 0; sl < u.nslabs && ok; ++sl, ++g) {
           const uint32_t b = g & 1u, use = g >> 1;
-          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dtm = tmem_base + b * 256;
           const int kb0 = u.kb0 + sl * kSlabBlocks;
           const int kb1 = min(u.kb1, kb0 + kSlabBlocks);
           for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
+            if (!mbar_wait(full_bar(s), ph, abort_flag, status)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sa = base + s * P_STAGE_BYTES;
             const uint32_t sb = sa + P_A_BYTES;
@@ -646,19 +738,19 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     uint32_t g = 0;
     bool ok = true;
+    int pi = sched.first(pair);
     for (int t = pair; t < num_units && ok; t += npairs) {
-      const Unit u = unit_of(p, t);
-      const Coord c = u.c;
+      const PairUnit u = sched.unit(t, pi);
       const int nslabs = u.nslabs;
-      const float mf = (float)T.m[c.q];
-      const float invm = T.invm[c.q];
-      const float invf = (float)T.inv[c.q];
+      const float mf = (float)T.m[u.q];
+      const float invm = T.invm[u.q];
+      const float invf = (float)T.inv[u.q];
       uint32_t acc8[CPW / 4];                // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
       for (int i = 0; i < CPW / 4; ++i) acc8[i] = 0x80808080u;
       for (int sl = 0; sl < nslabs; ++sl, ++g) {
         const uint32_t b = g & 1u, use = g >> 1;
-        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, status)) { ok = false; break; }
         tc_fence_after();
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
@@ -689,7 +781,7 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
                 const float r = fmaf(-qf, mf, tv);                          // exact, |r| <= 120
                 if (last)
-                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, p.raw) + 8388608.0f);   // low byte
+                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, u.raw) + 8388608.0f);   // low byte
                 else
                   out[j] = __float_as_uint(r + 8388736.0f);                 // low byte = r + 128
               }
@@ -703,14 +795,14 @@ gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
       }
       if (!ok) break;
       // ---- tile done: acc8 holds the digits (or W mod m), one byte per entry ----
-      const int row = c.tm * 2 * P_BM + (int)rank * P_BM + quarter * 32 + lane;
-      const bool runs = (p.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
+      const int row = u.row0 + (int)rank * P_BM + quarter * 32 + lane;
+      const bool runs = (u.ldy & 15) == 0 && (reinterpret_cast<uintptr_t>(u.Y) & 15) == 0;
 #pragma unroll
       for (int part = 0; part < (CPW + 127) / 128; ++part) {
-        const int col0 = c.tn * 256 + cbase + part * 128;
-        if (row < p.m && col0 < p.n) {
-          uint8_t* dst = p.Y + (size_t)u.ks * p.ysplit + (size_t)c.q * p.m * p.ldy + (size_t)row * p.ldy + col0;
-          store_digits<(CPW < 128 ? CPW : 128) / 4>(dst, acc8 + part * 32, p.n - col0, runs, p.acc, T.m[c.q]);
+        const int col0 = u.col0 + cbase + part * 128;
+        if (row < u.m && col0 < u.n) {
+          uint8_t* dst = u.Y + (size_t)row * u.ldy + col0;
+          store_digits<(CPW < 128 ? CPW : 128) / 4>(dst, acc8 + part * 32, u.n - col0, runs, u.acc, T.m[u.q]);
         }
       }
     }
@@ -1017,10 +1109,13 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const int smem_bytes = smem_optin > P_SMEM_BYTES ? smem_optin : P_SMEM_BYTES;
-  e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem_bytes);
+  e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps, PairSingle>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  Params p;
+  PairSingle sched;
+  sched.mapA = mapA;
+  sched.mapB = mapB;
+  Params& p = sched.p;
   p.m = (int)m;
   p.n = (int)n;
   p.tiles_m = (int)tiles_m;
@@ -1037,20 +1132,21 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
   const int64_t units = num_tiles * p.nsplit;
   const int64_t pairs = units < sms / 2 ? units : sms / 2;
-  gemm_tc_pair_kernel<kPairEpiWarps><<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(
-      mapA, mapB, t, p);
+  gemm_tc_pair_kernel<kPairEpiWarps, PairSingle>
+      <<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
   return cudaGetLastError();
 }
 
-// Tensor maps of one grouped problem's planes (rows of Q planes, 128-row boxes
-// for A and 256-row boxes for B, as the one-CTA kernel stages them).
-bool group_maps_tc(OzGroupProblem* pr, int Q) {
+// Tensor maps of one grouped problem's planes (rows of Q planes): 128-row
+// boxes for A; for B 128-row boxes (CTA pairs) or 256-row boxes (the one-CTA
+// kernel).
+bool group_maps_tc(OzGroupProblem* pr, int Q, bool pairs) {
   return make_map(&pr->mapA, pr->U, (int64_t)Q * pr->m_pad, pr->k_pad, BM) &&
-         make_map(&pr->mapB, pr->V, (int64_t)Q * pr->n_pad, pr->k_pad, BN);
+         make_map(&pr->mapB, pr->V, (int64_t)Q * pr->n_pad, pr->k_pad, pairs ? P_BN : BN);
 }
 
 cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
-                                   int32_t* status, cudaStream_t st) {
+                                   int32_t* status, cudaStream_t st, bool pairs) {
   if (count == 0 || total_units == 0) return cudaSuccess;
   if (total_units > INT32_MAX) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
@@ -1058,6 +1154,25 @@ cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* prob
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (pairs) {
+    // as launch_gemm_tc: each CTA of a pair claims all the shared memory a block may have
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int smem_bytes = smem_optin > P_SMEM_BYTES ? smem_optin : P_SMEM_BYTES;
+    e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    PairGrouped sched;
+    sched.probs = probs;
+    sched.count = count;
+    sched.total = (int)total_units;
+    sched.st = status;
+    const int64_t pairs_n = total_units < sms / 2 ? total_units : sms / 2;
+    gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped>
+        <<<(unsigned)(2 * pairs_n), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
+    return cudaGetLastError();
+  }
   e = cudaFuncSetAttribute(gemm_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = (int)(total_units < sms ? total_units : sms);

@@ -1,15 +1,18 @@
 // oz_grouped.cu -- many products in one launch per phase (oz_group_create /
 // oz_group_run): the five phases of Sec. "Structure" run over all products
 // of a plan at once, the split of every A, then of every B, the GEMMs of
-// every product as one persistent kernel, and one reconstruct. Each block (or
-// GEMM unit) finds its product by a binary search over the products' first
-// block indices in a device table written once, at create time.
+// every product as one persistent kernel, and one reconstruct. A block of a
+// split or reconstruct launch finds its product in a block map (one int per
+// block, per phase); a GEMM CTA finds the product of its first unit by a binary
+// search over the products' first unit indices and walks forward from there.
+// Both the product table and the maps are device memory written once, at
+// create time.
 //
 // Products of different tables form separate groups, and the groups run side
 // by side on streams the group object owns (forked from and joined back to
 // the caller's stream, so a run can be captured into a CUDA graph); within a
-// group the splits of A and of B run side by side too. The GEMMs are the
-// one-CTA-per-tile kind, which may share SMs with other kernels.
+// group the splits of A and of B run side by side too. The groups' GEMMs run
+// one after another, on CTA pairs or one CTA per tile (group_uses_pairs).
 #include <stdint.h>
 #include <string.h>
 
@@ -25,11 +28,30 @@ using oz::round_up;
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// A group's GEMMs run on CTA pairs (256 x 256 tiles: a third less shared-memory
+// traffic per product than one CTA per 128 x 256 tile) when its units hold at
+// least one 1024-term slab on average; groups of shorter products run one CTA
+// per 128 x 256 tile, which pads fewer rows (their units are bound by the
+// epilogue, not by the products). Measured on the 256-product batch: the
+// k > 836 set 6.14 ms with pairs against 6.39 ms, the k <= 836 set 3.50 ms
+// against 2.86 ms.
+bool group_uses_pairs(const std::vector<int>& mem, const int64_t* mnk) {
+  double units = 0, kb = 0;
+  for (int i : mem) {
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    const double u = (double)((m + 255) / 256) * ((n + 255) / 256);
+    units += u;
+    kb += u * (double)(round_up(k, oz::kPadK) / 64);
+  }
+  return units > 0 && kb >= 16.0 * units;
+}
+
 struct Group {
   oz_plan plan;
   int first, count;                     // range of the device table
-  int nlong;                            // its first nlong products have rows longer than 1024
   int64_t total_rows, total_wrows, total_cm, total_sh, total_sc, total_units, total_rec;
+  bool pairs;                           // GEMMs on CTA pairs (else one CTA per tile)
+  oz::GroupMaps maps;                   // block -> problem (index from `first`) per phase
 };
 
 // threads per row chunk of the grouped reconstruct: the least power of two
@@ -62,6 +84,25 @@ Part part_of(const oz_plan p, int64_t m, int64_t n, int64_t k) {
   return P;
 }
 
+// Blocks of one product in each phase's launch.
+struct Blocks {
+  int64_t rows, wrows, cm, sh, sc, rec;
+  int64_t total() const { return rows + wrows + cm + sh + sc + rec; }
+};
+
+Blocks blocks_of(const Part& P, int64_t m, int64_t n, int64_t k) {
+  Blocks b;
+  const bool long_rows = P.k_pad > 1024;       // one block per row, else one warp per row
+  b.rows = long_rows ? P.m_pad : 0;
+  b.wrows = long_rows ? 0 : P.m_pad / 8;
+  b.cm = ((n + 31) / 32) * ((k + 255) / 256);
+  b.sh = (n + 255) / 256;
+  b.sc = (P.n_pad / 32) * (P.k_pad / 64);
+  const int tpr = rec_tpr(n);
+  b.rec = ((m + 256 / tpr - 1) / (256 / tpr)) * ((n + 4 * tpr - 1) / (4 * tpr));
+  return b;
+}
+
 // Plans with the same moduli and bit budget have the same tables: their
 // products can share every launch.
 bool same_tables(const oz_plan a, const oz_plan b) {
@@ -77,9 +118,10 @@ bool plan_ok(const oz_plan p) {
          p->tab.npairs <= 8 && p->tab.bits <= 64;
 }
 
-// Layout of the whole workspace: status word, table, column maxima, parts.
+// Layout of the whole workspace: status word, table, block maps, column
+// maxima, parts.
 struct Layout {
-  size_t table, colmax, parts, total;
+  size_t table, maps, colmax, parts, total;
   std::vector<size_t> part_off;         // per caller index (0 for skipped products)
   std::vector<size_t> colmax_off;
 };
@@ -89,6 +131,14 @@ bool layout(int count, const oz_plan* plans, const int64_t* mnk, Layout* L) {
   size_t off = 256;                                       // status word (oz_query_status reads it)
   L->table = off;
   off = al256(off + sizeof(OzGroupProblem) * (size_t)(count > 0 ? count : 1));
+  L->maps = off;
+  for (int i = 0; i < count; ++i) {
+    const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+    if (m < 0 || n < 0 || k < 0 || !plan_ok(plans[i])) return false;
+    if (m == 0 || n == 0 || k == 0) continue;
+    off += sizeof(int32_t) * (size_t)blocks_of(part_of(plans[i], m, n, k), m, n, k).total();
+  }
+  off = al256(off);
   L->colmax = off;
   L->colmax_off.assign(count, 0);
   for (int i = 0; i < count; ++i) {
@@ -115,13 +165,14 @@ bool layout(int count, const oz_plan* plans, const int64_t* mnk, Layout* L) {
 
 struct oz_group_s {
   char* ws;
-  size_t table_off, colmax_off, colmax_bytes;
+  size_t table_off, maps_off, colmax_off, colmax_bytes;
   std::vector<Group> groups;
   // products with k == 0: C = 0
   std::vector<double*> zero_c;
   std::vector<int64_t> zero_m, zero_n, zero_ldc;
   // per group: a stream for the A side (then GEMMs and reconstruct) and one
-  // for the B side; events: fork, per group the B side done and the group done
+  // for the B side; events: fork, per group the B side done, the group done
+  // and its GEMMs done
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   ~oz_group_s() {
@@ -166,6 +217,7 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
   if (!g) return OZ_ERR_INVALID_ARG;
   g->ws = static_cast<char*>(workspace);
   g->table_off = L.table;
+  g->maps_off = L.maps;
   g->colmax_off = L.colmax;
   g->colmax_bytes = L.parts - L.colmax;
 
@@ -191,6 +243,7 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
     members[gi].push_back(i);
   }
   std::vector<OzGroupProblem> table;
+  std::vector<int32_t> maps;              // every group's block maps, phase after phase
   int32_t* status = reinterpret_cast<int32_t*>(g->ws);
   for (size_t gi = 0; gi < distinct.size(); ++gi) {
     std::vector<int>& mem = members[gi];
@@ -200,9 +253,11 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
     G.plan = p;
     G.first = (int)table.size();
     G.count = (int)mem.size();
+    G.pairs = group_uses_pairs(mem, mnk);
     for (int i : mem) {
       const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
       const Part P = part_of(p, m, n, k);
+      const Blocks nb = blocks_of(P, m, n, k);
       char* base = g->ws + L.part_off[i];
       OzGroupProblem pr;
       memset(&pr, 0, sizeof pr);
@@ -226,39 +281,55 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
       pr.t = reinterpret_cast<int32_t*>(base + P.t);
       pr.colmax = reinterpret_cast<uint64_t*>(g->ws + L.colmax_off[i]);
       pr.flag = status;
-      pr.tiles_m = (int)((m + oz::kTileM - 1) / oz::kTileM);
+      pr.tiles_m = (int)((m + oz::kTileM - 1) / oz::kTileM);   // one-CTA tiles (pairs: ceil(m / 256))
       pr.tiles_n = (int)((n + 255) / 256);
       pr.kblocks = (int)(P.k_pad / 64);
-      if (P.k_pad > 1024) {             // one block per row (the long products come first)
+      if (nb.rows > 0) {                // one block per row (the long products come first)
         pr.rows_begin = G.total_rows;
-        G.total_rows += P.m_pad;
-        ++G.nlong;
+        G.total_rows += nb.rows;
       } else {                          // one warp per row, eight rows per block
         pr.rows_begin = G.total_wrows;
-        G.total_wrows += P.m_pad / 8;
+        G.total_wrows += nb.wrows;
       }
       pr.cm_begin = G.total_cm;
-      G.total_cm += ((n + 31) / 32) * ((k + 255) / 256);
+      G.total_cm += nb.cm;
       pr.sh_begin = G.total_sh;
-      G.total_sh += (n + 255) / 256;
+      G.total_sh += nb.sh;
       pr.sc_begin = G.total_sc;
-      G.total_sc += (P.n_pad / 64) * (P.k_pad / 64);
+      G.total_sc += nb.sc;
       pr.unit_begin = G.total_units;
-      G.total_units += (int64_t)p->Q * pr.tiles_m * pr.tiles_n;
+      G.total_units += (int64_t)p->Q * (G.pairs ? (m + 255) / 256 : pr.tiles_m) * pr.tiles_n;
       pr.rec_tpr = rec_tpr(n);
       pr.rec_begin = G.total_rec;
-      G.total_rec += ((m + 256 / pr.rec_tpr - 1) / (256 / pr.rec_tpr)) * ((n + 4 * pr.rec_tpr - 1) / (4 * pr.rec_tpr));
-      if (!oz::group_maps_tc(&pr, p->Q)) {
+      G.total_rec += nb.rec;
+      if (!oz::group_maps_tc(&pr, p->Q, G.pairs)) {
         delete g;
         return OZ_ERR_INVALID_ARG;
       }
       table.push_back(pr);
     }
+    // block maps of the group: per phase, the index (from G.first) of the
+    // problem of each block, in the order the begin fields were assigned
+    auto append = [&](int64_t Blocks::*field) {
+      const size_t at = maps.size();
+      for (int li = 0; li < G.count; ++li) {
+        const int i = mem[li];
+        const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
+        maps.insert(maps.end(), (size_t)(blocks_of(part_of(p, m, n, k), m, n, k).*field), (int32_t)li);
+      }
+      return at;
+    };
+    const size_t at_rows = append(&Blocks::rows), at_wrows = append(&Blocks::wrows), at_cm = append(&Blocks::cm),
+                 at_sh = append(&Blocks::sh), at_sc = append(&Blocks::sc), at_rec = append(&Blocks::rec);
+    const int32_t* mb = reinterpret_cast<const int32_t*>(g->ws + L.maps);
+    G.maps = {mb + at_rows, mb + at_wrows, mb + at_cm, mb + at_sh, mb + at_sc, mb + at_rec};
     g->groups.push_back(G);
   }
-  if (!table.empty() &&
-      cudaMemcpy(g->ws + L.table, table.data(), sizeof(OzGroupProblem) * table.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+  if ((!table.empty() &&
+       cudaMemcpy(g->ws + L.table, table.data(), sizeof(OzGroupProblem) * table.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess) ||
+      (!maps.empty() &&
+       cudaMemcpy(g->ws + L.maps, maps.data(), sizeof(int32_t) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
     delete g;
     return OZ_ERR_CUDA;
@@ -273,7 +344,7 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
     }
     g->streams.push_back(st);
   }
-  for (size_t i = 0; i < 1 + 2 * ng; ++i) {
+  for (size_t i = 0; i < 1 + 3 * ng; ++i) {
     cudaEvent_t ev = nullptr;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
@@ -308,15 +379,20 @@ extern "C" oz_status oz_group_run(oz_group g, void* stream) {
     const OzTables& T = G.plan->tab;
     const OzGroupProblem* probs = table + G.first;
     cudaStream_t sa = g->streams[2 * gi], sb = g->streams[2 * gi + 1];
-    cudaEvent_t b_done = g->events[1 + 2 * gi], done = g->events[2 + 2 * gi];
+    cudaEvent_t b_done = g->events[1 + 3 * gi], done = g->events[2 + 3 * gi], gemm_done = g->events[3 + 3 * gi];
     chk(cudaStreamWaitEvent(sa, fork, 0));
     chk(cudaStreamWaitEvent(sb, fork, 0));
-    if (e == cudaSuccess) e = oz::launch_split_rows_grouped(T, probs, G.count, G.nlong, G.total_rows, G.total_wrows, sa);
-    if (e == cudaSuccess) e = oz::launch_split_cols_grouped(T, probs, G.count, G.total_cm, G.total_sh, G.total_sc, sb);
+    if (e == cudaSuccess) e = oz::launch_split_rows_grouped(T, probs, G.maps, G.total_rows, G.total_wrows, sa);
+    if (e == cudaSuccess) e = oz::launch_split_cols_grouped(T, probs, G.maps, G.total_cm, G.total_sh, G.total_sc, sb);
     chk(cudaEventRecord(b_done, sb));
     chk(cudaStreamWaitEvent(sa, b_done, 0));
-    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, sa);
-    if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.count, G.total_rec, sa);
+    // the groups' GEMMs run one after another: each fills every SM (a pair's
+    // CTA all of its shared memory), so little is lost, and no two
+    // tensor-memory users of this call run at once
+    if (gi > 0) chk(cudaStreamWaitEvent(sa, g->events[3 + 3 * (gi - 1)], 0));
+    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, sa, G.pairs);
+    chk(cudaEventRecord(gemm_done, sa));
+    if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.maps, G.total_rec, sa);
     chk(cudaEventRecord(done, sa));
     chk(cudaStreamWaitEvent(st, done, 0));
   }

@@ -70,8 +70,9 @@ bool host_layout(const oz_plan p, int64_t m, int64_t n, int64_t k, int64_t rows,
   L->ldy = round_up(n > 0 ? n : 1, 16 / ybytes);
   L->y = off; off = al(off + (size_t)p->Q * rows * L->ldy * ybytes);
   // one column chunk of B transposed (cols x k doubles): its columns are
-  // split as rows (INT8 plans)
-  L->bt = off; off = al(off + (p->is_fp ? 0 : 8 * (size_t)cols * k));
+  // split as rows (int8 planes of the IMMA engine; bf16 planes are split from
+  // the columns in place)
+  L->bt = off; off = al(off + (p->is_fp || oz::engine_bf16(p->engine) ? 0 : 8 * (size_t)cols * k));
   L->total = off;
   return true;
 }
@@ -169,9 +170,12 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   }
   if (nbi > 1) copy_a(1);
 
-  // B_j (k x nc, row pitch n) transposed into Bt, then its rows split
+  // B_j (k x nc, row pitch n): bf16 planes split from its columns in place;
+  // int8 planes from the rows of its transpose Bt
   double* Bt = reinterpret_cast<double*>(ws + L.bt);
   auto launch_split_b_chunk = [&](int64_t nc, int64_t c0, void* planes) {
+    if (bf16) return oz::launch_split_cols(T, nc, k, Bd + c0, n, L.w_pad, L.k_pad, t + c0, planes, bf16, flag,
+                                           colmax + c0, sc);
     cudaError_t r = oz::launch_transpose(k, nc, Bd + c0, n, Bt, sc);
     if (r != cudaSuccess) return r;
     return oz::launch_split_rows(T, nc, k, Bt, k, L.w_pad, L.k_pad, t + c0, planes, bf16, flag, sc);

@@ -69,6 +69,7 @@ struct OzFpTables {
   uint32_t m[OZ_TABLE_CAP];               // channel moduli (also in OzTables::m)
   uint32_t magic[OZ_TABLE_CAP];           // floor(2^32 / m)
   uint32_t c16[OZ_TABLE_CAP], c32[OZ_TABLE_CAP], c48[OZ_TABLE_CAP];  // 2^16k mod m
+  uint32_t c64[OZ_TABLE_CAP];             // 2^64 mod m (widened budgets, beta > 64)
   uint32_t inv[OZ_TABLE_CAP];             // (P/m)^-1 mod m
   float mf[OZ_TABLE_CAP], invm[OZ_TABLE_CAP];
   uint8_t g_pa[OZ_MAX_FP_GEMMS], g_pb[OZ_MAX_FP_GEMMS];  // planes of GEMM g
@@ -122,7 +123,7 @@ struct OzGroupProblem {
   int64_t rows_begin;   // split of A: one block per row of m_pad
   int64_t cm_begin;     // column maxima of B: ceil(n/32) * ceil(k/256) blocks
   int64_t sh_begin;     // shifts of B: ceil(n/256) blocks
-  int64_t sc_begin;     // split of B: (n_pad/64) * (k_pad/64) blocks
+  int64_t sc_begin;     // split of B: (n_pad/32) * (k_pad/64) blocks
   int64_t unit_begin;   // GEMMs: Q * tiles_m * tiles_n units
   int64_t rec_begin;    // reconstruct: m * ceil(n/1024) blocks
   int tiles_m, tiles_n, kblocks;
@@ -228,17 +229,31 @@ cudaError_t launch_combine_digits(const OzTables& t, int64_t m, int64_t ldy, uin
                                   cudaStream_t st);
 cudaError_t launch_reconstruct(const OzTables& t, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
                                const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
+cudaError_t launch_reconstruct16_wide(const OzTables& t, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy,
+                                      const int32_t* s, const int32_t* tt, double* C, int64_t ldc, cudaStream_t st);
 // grouped products (oz_grouped.cu): one launch per phase over count problems
-// of one plan; probs is device memory; totals are the launch sizes.
-cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int nlong,
+// of one plan; probs is device memory; totals are the launch sizes. Per
+// phase, a device array maps each block of the launch to its problem (an
+// index into probs), written once when the group is created.
+struct GroupMaps {
+  const int32_t* rows;   // split of A, long rows: one block per row
+  const int32_t* wrows;  // split of A, short rows: eight rows per block
+  const int32_t* cm;     // column maxima of B
+  const int32_t* sh;     // shifts of B
+  const int32_t* sc;     // split of B
+  const int32_t* rec;    // reconstruct
+};
+cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
                                       int64_t total_rows, int64_t total_wrows, cudaStream_t st);
-cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_cm,
-                                      int64_t total_sh, int64_t total_sc, cudaStream_t st);
+cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
+                                      int64_t total_cm, int64_t total_sh, int64_t total_sc, cudaStream_t st);
+// pairs: CTA pairs on 256 x 256 tiles (units Q ceil(m/256) tiles_n), else one
+// CTA per 128 x 256 tile (units Q tiles_m tiles_n)
 cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
-                                   int32_t* status, cudaStream_t st);
-bool group_maps_tc(OzGroupProblem* pr, int Q);   // host: the TMA maps of a grouped problem's planes
-cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_rec,
-                                       cudaStream_t st);
+                                   int32_t* status, cudaStream_t st, bool pairs);
+bool group_maps_tc(OzGroupProblem* pr, int Q, bool pairs);   // host: the TMA maps of a grouped problem's planes
+cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
+                                       int64_t total_rec, cudaStream_t st);
 // float-format path: planes of codes, 16-bit digits
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,

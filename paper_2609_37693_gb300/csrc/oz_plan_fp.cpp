@@ -4,8 +4,12 @@
 // one-limb, schoolbook or Toom form over the format's alphabet S.
 //
 // The channel lists are frozen (oz_fp_configs.inc, written by
-// gen_fp_configs.py from the exact search of fpsearch.py); building a plan
-// makes the forms' tables, weights and codes from them:
+// gen_fp_configs.py from the exact search of fpsearch.py): per format, the
+// least configuration for K_cfg = 2^13, 2^14 and 2^16 at beta = 53, and a
+// widened one (beta = 69 at K_cfg = 2^14, Example ex:widened). A plan takes
+// the base configuration of the least K_cfg >= k_hint, or, for a requested
+// budget its window does not hold, the first widened one that holds it.
+// Building a plan makes the forms' tables, weights and codes from them:
 //   * alphabet S: the format's finite values scaled by 2^e_S, the least power of
 //     two making them integers; a plane value v is stored as the code of v 2^-e_S;
 //   * every plane value is at most r = floor(sqrt(2^24 / K_cfg)) in magnitude, so
@@ -38,6 +42,7 @@ struct FpChannel {
 struct FpConfig {
   int fmt;
   int64_t K;
+  int beta;          // the bit budget it was searched for (53: base; wider: widened)
   int Q, nch;
   FpChannel ch[OZ_TABLE_CAP];
 };
@@ -220,10 +225,25 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
   std::map<int64_t, int> code_of;
   int e_s = 0;
   if (!alphabet(format, &code_of, &e_s)) return OZ_ERR_UNSUPPORTED;
-  // the configuration of the format built for the least K_cfg >= k_hint
+  // the configuration: the base one (beta = 53) of the least K_cfg >= k_hint
+  // whose window holds the requested bits (bits = 0: the base one of the least
+  // K_cfg), else the widened one of the least K_cfg >= k_hint that holds them
   const FpConfig* cfg = nullptr;
+  auto holds = [&](const FpConfig& c) {
+    if (bits == 0) return true;
+    U256 P = {};
+    P.w[0] = 1;
+    for (int i = 0; i < c.nch; ++i) u_mul(&P, c.ch[i].m);
+    return u_cmp(u_window(k_hint, bits), P) < 0;
+  };
+  auto better = [&](const FpConfig& c) {
+    if (!cfg) return true;
+    const bool cw = c.beta > 53, bw = cfg->beta > 53;
+    if (cw != bw) return !cw;                    // base configurations first
+    return c.K < cfg->K || (c.K == cfg->K && c.Q < cfg->Q);
+  };
   for (const FpConfig& c : kFpConfigs)
-    if (c.fmt == format && c.K >= k_hint && (!cfg || c.K < cfg->K)) cfg = &c;
+    if (c.fmt == format && c.K >= k_hint && holds(c) && better(c)) cfg = &c;
   if (!cfg) return OZ_ERR_K_TOO_LARGE;
   const int64_t r = (int64_t)std::sqrt((double)((1ll << 24) / cfg->K));
   int64_t rr = r;
@@ -266,6 +286,7 @@ extern "C" oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint,
     f.c16[c] = pow2_mod(16, m);
     f.c32[c] = pow2_mod(32, m);
     f.c48[c] = pow2_mod(48, m);
+    f.c64[c] = pow2_mod(64, m);
     f.mf[c] = (float)m;
     f.invm[c] = 1.0f / (float)m;
     f.ch_plane0[c] = (int)planes.size();

@@ -189,24 +189,29 @@ __device__ __forceinline__ uint64_t round_to_binary64(const Limbs<L>& mag, uint3
   return sign | b;
 }
 
-template <int L, int EPT>
+// D: the digit type, uint8_t (moduli below 256, Q <= 20) or uint16_t (the
+// 16-bit digits of float-format configurations, moduli up to 4000 and up to
+// OZ_TABLE_CAP channels).
+template <int L, int EPT, typename D = uint8_t>
 __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant__ OzTables T, int64_t m, int64_t n,
-                                                          const uint8_t* __restrict__ Y, int64_t ldy,
+                                                          const D* __restrict__ Y, int64_t ldy,
                                                           const int32_t* __restrict__ s,
                                                           const int32_t* __restrict__ t, double* __restrict__ C,
                                                           int64_t ldc) {
-  constexpr int kMaxPairs = (OZ_MAX_MODULI + 1) / 2;
+  constexpr int kMaxPairs = ((sizeof(D) == 1 ? OZ_MAX_MODULI : OZ_TABLE_CAP) + 1) / 2;
+  using W = typename std::conditional<sizeof(D) == 1, uint32_t, unsigned long long>::type;   // four digits
   const int64_t i = blockIdx.x;
   const int64_t j0 = ((int64_t)blockIdx.y * 256 + threadIdx.x) * EPT;
   if (i >= m || j0 >= n) return;
   const int Q = T.Q;
   const int npairs = T.npairs;
   const int64_t plane = m * ldy;
-  const uint8_t* yp = Y + i * ldy + j0;
-  const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & 3) == 0) &&
+  const D* yp = Y + i * ldy + j0;
+  const bool vec = (EPT == 4) && (j0 + 4 <= n) && ((reinterpret_cast<uintptr_t>(yp) & (sizeof(W) - 1)) == 0) &&
                    ((plane & 3) == 0);
-  // S = sum over pairs (a, b) of z (P / (m_a m_b)), z = y_a m_b + y_b m_a < 2^17,
-  // since y_a (P/m_a) + y_b (P/m_b) = (P / (m_a m_b)) (y_a m_b + y_b m_a).
+  // S = sum over pairs (a, b) of z (P / (m_a m_b)), z = y_a m_b + y_b m_a
+  // (< 2^17 for byte digits, < 2^25 for 16-bit ones), since
+  // y_a (P/m_a) + y_b (P/m_b) = (P / (m_a m_b)) (y_a m_b + y_b m_a).
   uint64_t acc[EPT][L];
   float f[EPT];
 #pragma unroll
@@ -221,12 +226,14 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
       const int qa = 2 * pi, qb = 2 * pi + 1;
       uint32_t da[EPT], db[EPT];
       if (vec) {
-        const uint32_t wa = __ldg(reinterpret_cast<const uint32_t*>(yp + qa * plane));
-        const uint32_t wb = qb < Q ? __ldg(reinterpret_cast<const uint32_t*>(yp + qb * plane)) : 0u;
+        constexpr int kb = 8 * (int)sizeof(D);
+        constexpr uint32_t mask = sizeof(D) == 1 ? 0xffu : 0xffffu;
+        const W wa = __ldg(reinterpret_cast<const W*>(yp + qa * plane));
+        const W wb = qb < Q ? __ldg(reinterpret_cast<const W*>(yp + qb * plane)) : (W)0;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-          da[e] = (wa >> (8 * e)) & 0xffu;
-          db[e] = (wb >> (8 * e)) & 0xffu;
+          da[e] = (uint32_t)(wa >> (kb * e)) & mask;
+          db[e] = (uint32_t)(wb >> (kb * e)) & mask;
         }
       } else {
 #pragma unroll
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const __grid_constant_
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
         const uint32_t z = da[e] * mb + db[e] * ma;
-        f[e] = fmaf(__int_as_float(0x4B000000 | z) - 8388608.0f, pinv, f[e]);
+        f[e] = fmaf(sizeof(D) == 1 ? __int_as_float(0x4B000000 | z) - 8388608.0f : __uint2float_rn(z), pinv, f[e]);
 #pragma unroll
         for (int l = 0; l < L; ++l) acc[e][l] += (uint64_t)z * T.Np[pi][l];
       }
@@ -550,16 +557,16 @@ __device__ __forceinline__ bool round_groups_fast(const uint4* kP, const uint32_
   return true;
 }
 
-// Every other case, recomputed from the digits (wsm[q * 256], this thread's
+// Every other case, recomputed from the digits (wsm[q * QS], this thread's
 // shared-memory slots): the CRT sum S exactly in 128 bits (S < 15 P < 2^128),
 // X = S - qP corrected exactly into [-P/2, P/2), and the general rounding.
-template <int NT, int NP2, int NQ4>
+template <int NT, int NP2, int NQ4, int QS>
 __device__ __noinline__ uint64_t round_groups_slow(const OzTables& T, const uint4* kP, const uint32_t* wsm, int e,
                                                    int ex) {
   constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
   uint32_t w[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) w[q] = wsm[q * 256];
+  for (int q = 0; q < Q; ++q) w[q] = wsm[q * QS];
   uint32_t s[4];
   float f;
   crt_groups<NT, NP2, NQ4>(T, w, e, s, f);
@@ -587,8 +594,8 @@ __device__ __forceinline__ void fill_kP(const OzTables& T, uint4* kP) {
 }
 
 // Four entries (i, j0 .. j0 + 3), j0 < n, from their digit words, which this
-// thread holds in its shared-memory slots wsm[q * 256].
-template <int NT, int NP2, int NQ4>
+// thread holds in its shared-memory slots wsm[q * QS].
+template <int NT, int NP2, int NQ4, int QS = 256>
 __device__ __forceinline__ void rec4_groups(const OzTables& T, const uint4* kP, const uint32_t* wsm, int64_t i,
                                             int64_t j0, int64_t n, int32_t si, const int32_t* __restrict__ t,
                                             double* __restrict__ C, int64_t ldc) {
@@ -603,7 +610,7 @@ __device__ __forceinline__ void rec4_groups(const OzTables& T, const uint4* kP, 
   }
   uint32_t w[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) w[q] = wsm[q * 256];
+  for (int q = 0; q < Q; ++q) w[q] = wsm[q * QS];
   uint64_t out[4];
   uint32_t slow = 0;
 #pragma unroll
@@ -616,7 +623,7 @@ __device__ __forceinline__ void rec4_groups(const OzTables& T, const uint4* kP, 
   if (slow) {                                              // rare: one branch for the four entries
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if ((slow >> e) & 1u) out[e] = round_groups_slow<NT, NP2, NQ4>(T, kP, wsm, e, -(si + tj[e]));
+      if ((slow >> e) & 1u) out[e] = round_groups_slow<NT, NP2, NQ4, QS>(T, kP, wsm, e, -(si + tj[e]));
   }
   double* cp = C + i * ldc + j0;
   if (j0 + 4 <= n && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
@@ -638,6 +645,11 @@ __device__ __forceinline__ void cp_async4(uint32_t* smem_dst, const uint32_t* gs
                "l"(gsrc)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(uint32_t* smem_dst, const uint32_t* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
@@ -652,6 +664,21 @@ __device__ __forceinline__ void issue_digits(const uint8_t* __restrict__ Y, int6
     const int64_t pw = plane >> 2;
 #pragma unroll
     for (int q = 0; q < Q; ++q) cp_async4(buf + q * 256, p + q * pw);
+  }
+}
+
+// The digit words of the eight entries (i, j0 .. j0 + 7) into this thread's
+// slots buf[q * 512 + 0, 1] (two words per modulus: entries j0 .. j0 + 3 and
+// j0 + 4 .. j0 + 7). Whole 8-byte runs: the row pitch ldy is a multiple of 8
+// and j0 + 8 <= ldy.
+template <int Q>
+__device__ __forceinline__ void issue_digits8(const uint8_t* __restrict__ Y, int64_t plane, int64_t ldy, int64_t i,
+                                              int64_t j0, int64_t n, uint32_t* buf) {
+  if (j0 < n) {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(Y + i * ldy + j0);
+    const int64_t pw = plane >> 2;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cp_async8(buf + q * 512, p + q * pw);
   }
 }
 
@@ -700,19 +727,69 @@ __global__ void __launch_bounds__(256, 2) reconstruct_groups_kernel(const __grid
   }
 }
 
-// Grouped products: as reconstruct128_grouped_kernel, with the groups' sum.
+// As reconstruct_groups_kernel with eight entries per thread and task (a
+// task covers 256 / tpr rows of one chunk of 8 tpr entries): one 8-byte copy
+// per modulus per eight entries. The two digit buffers are dynamic shared
+// memory, [2][Q][256 threads][2 words].
+template <int NT, int NP2, int NQ4>
+__global__ void __launch_bounds__(256, 2) reconstruct_groups8_kernel(const __grid_constant__ OzTables T, int64_t m,
+                                                                     int64_t n, const uint8_t* __restrict__ Y,
+                                                                     int64_t ldy, const int32_t* __restrict__ s,
+                                                                     const int32_t* __restrict__ t,
+                                                                     double* __restrict__ C, int64_t ldc,
+                                                                     int64_t nch, int tpr_log2) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  __shared__ uint4 kP[16];
+  extern __shared__ uint32_t dbuf[];
+  fill_kP(T, kP);
+  __syncthreads();
+  const int tpr = 1 << tpr_log2, rows = 256 >> tpr_log2;
+  const int r_in = threadIdx.x >> tpr_log2, c_in = threadIdx.x & (tpr - 1);
+  const int64_t plane = m * ldy;
+  const int64_t ngroups = (m + rows - 1) / rows, total = ngroups * nch;
+  const int64_t step_g = gridDim.x / nch, step_c = gridDim.x % nch;
+  int64_t b = blockIdx.x, gi = b / nch, c = b % nch;
+  uint32_t* const mine = dbuf + 2 * threadIdx.x;    // slot s: mine + s * Q * 512
+  int slot = 0;
+  auto row_of = [&](int64_t g) { return g * rows + r_in; };
+  auto col_of = [&](int64_t cc) { return (cc * tpr + c_in) * 8; };
+  if (b < total && row_of(gi) < m) issue_digits8<Q>(Y, plane, ldy, row_of(gi), col_of(c), n, mine);
+  cp_async_commit();
+  while (b < total) {
+    int64_t bn = b + gridDim.x, gn = gi + step_g, cn = c + step_c;
+    if (cn >= nch) cn -= nch, ++gn;
+    if (bn < total && row_of(gn) < m)
+      issue_digits8<Q>(Y, plane, ldy, row_of(gn), col_of(cn), n, mine + (slot ^ 1) * Q * 512);
+    cp_async_commit();
+    cp_async_wait1();                       // this task's copies have landed
+    const int64_t i = row_of(gi), j0 = col_of(c);
+    if (i < m && j0 < n) {
+      const int32_t si = __ldg(s + i);
+      const uint32_t* w = mine + slot * Q * 512;
+      rec4_groups<NT, NP2, NQ4, 512>(T, kP, w, i, j0, n, si, t, C, ldc);
+      if (j0 + 4 < n) rec4_groups<NT, NP2, NQ4, 512>(T, kP, w + 1, i, j0 + 4, n, si, t, C, ldc);
+    }
+    slot ^= 1;
+    b = bn, gi = gn, c = cn;
+  }
+}
+
+// Grouped products: one block per task (256 / tpr rows of one column chunk
+// of 4 tpr entries of problem map[b], tpr = rec_tpr threads per row chunk, so
+// that short rows share a block), with the groups' sum. (A persistent form
+// with a task of lookahead, as reconstruct_groups_kernel, ran the 256-product
+// batch 3-8 % slower.)
 template <int NT, int NP2, int NQ4>
 __global__ void __launch_bounds__(256) reconstruct_groups_grouped_kernel(const __grid_constant__ OzTables T,
                                                                          const OzGroupProblem* __restrict__ probs,
-                                                                         int count) {
+                                                                         const int32_t* __restrict__ map) {
   constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
   __shared__ uint4 kP[16];
   __shared__ uint32_t buf[Q * 256];
   fill_kP(T, kP);
   __syncthreads();
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rec_begin; });
-  const OzGroupProblem& P = probs[pi];
+  const OzGroupProblem& P = probs[__ldg(map + b)];
   const int tpr = P.rec_tpr, rows = 256 / tpr;
   const int64_t l = b - P.rec_begin, nch = (P.n + 4 * tpr - 1) / (4 * tpr);
   const int64_t i = (l / nch) * rows + threadIdx.x / tpr;
@@ -731,10 +808,9 @@ __global__ void __launch_bounds__(256) reconstruct_groups_grouped_kernel(const _
 template <int NP>
 __global__ void __launch_bounds__(256) reconstruct128_grouped_kernel(const __grid_constant__ OzTables T,
                                                                      const OzGroupProblem* __restrict__ probs,
-                                                                     int count) {
+                                                                     const int32_t* __restrict__ map) {
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rec_begin; });
-  const OzGroupProblem& P = probs[pi];
+  const OzGroupProblem& P = probs[__ldg(map + b)];
   const int tpr = P.rec_tpr, rows = 256 / tpr;
   const int64_t l = b - P.rec_begin, nch = (P.n + 4 * tpr - 1) / (4 * tpr);
   const int64_t i = (l / nch) * rows + threadIdx.x / tpr;
@@ -760,6 +836,15 @@ cudaError_t launch_L(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, 
   return cudaGetLastError();
 }
 
+template <int L>
+cudaError_t launch_L16(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy, const int32_t* s,
+                       const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int EPT = 4;
+  dim3 grid((unsigned)m, (unsigned)((n + 256 * EPT - 1) / (256 * EPT)));
+  reconstruct_kernel<L, EPT, uint16_t><<<grid, 256, 0, st>>>(T, m, n, Y, ldy, s, t, C, ldc);
+  return cudaGetLastError();
+}
+
 // CTAs of a kernel resident per SM, times the SM count (cached per device)
 template <typename K>
 int persistent_grid(K kernel, int threads) {
@@ -775,6 +860,29 @@ int persistent_grid(K kernel, int threads) {
 template <int NT, int NP2, int NQ4>
 cudaError_t launch_groups(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy, const int32_t* s,
                           const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
+  if ((ldy & 7) == 0 && (reinterpret_cast<uintptr_t>(Y) & 7) == 0) {   // eight entries per thread
+    int tpr_log2 = 5;                                // 32 .. 256 threads per row chunk of 8 tpr entries
+    while (tpr_log2 < 8 && ((int64_t)8 << tpr_log2) < n) ++tpr_log2;
+    const int64_t rows = 256 >> tpr_log2;
+    const int64_t nch = (n + (8 << tpr_log2) - 1) / (8 << tpr_log2);
+    const int64_t total = ((m + rows - 1) / rows) * nch;
+    const int smem = 2 * Q * 256 * 8;
+    cudaError_t e = cudaFuncSetAttribute(reconstruct_groups8_kernel<NT, NP2, NQ4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, reconstruct_groups8_kernel<NT, NP2, NQ4>, 256, smem) !=
+            cudaSuccess)
+      return cudaErrorInvalidValue;
+    int64_t grid = (int64_t)sms * (per > 0 ? per : 1);
+    if (grid > total) grid = total;
+    reconstruct_groups8_kernel<NT, NP2, NQ4><<<(unsigned)grid, 256, smem, st>>>(T, m, n, Y, ldy, s, t, C, ldc, nch,
+                                                                               tpr_log2);
+    return cudaGetLastError();
+  }
   int tpr_log2 = 5;                                  // 32 .. 256 threads per row chunk of 4 tpr entries
   while (tpr_log2 < 8 && ((int64_t)4 << tpr_log2) < n) ++tpr_log2;
   const int64_t rows = 256 >> tpr_log2;
@@ -816,6 +924,18 @@ cudaError_t with_shape(int key, F f) {
 }
 
 }  // namespace
+
+// 16-bit digits with P of five or six 32-bit limbs (widened float-format plans)
+cudaError_t launch_reconstruct16_wide(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy,
+                                      const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  if (ldy < n || T.npairs > (OZ_TABLE_CAP + 1) / 2) return cudaErrorInvalidValue;
+  switch (T.limbs) {
+    case 5: return launch_L16<5>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    case 6: return launch_L16<6>(T, m, n, Y, ldy, s, t, C, ldc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_reconstruct(const OzTables& T, int64_t m, int64_t n, const uint8_t* Y, int64_t ldy,
                                const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
@@ -883,25 +1003,25 @@ cudaError_t launch_combine_digits(const OzTables& T, int64_t m, int64_t ldy, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* probs, int count, int64_t total_rec,
-                                       cudaStream_t st) {
-  if (count == 0 || total_rec == 0) return cudaSuccess;
+cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* probs, const GroupMaps& maps,
+                                       int64_t total_rec, cudaStream_t st) {
+  if (total_rec == 0) return cudaSuccess;
   if (total_rec > INT32_MAX) return cudaErrorInvalidValue;
   // every grouped problem's digit rows have a pitch of a multiple of 16 bytes
   const int shape = group_shape(T);
   if (shape >= 0) {
     return with_shape(shape, [&](auto nt, auto np2, auto nq4) {
       reconstruct_groups_grouped_kernel<decltype(nt)::value, decltype(np2)::value, decltype(nq4)::value>
-          <<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count);
+          <<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec);
       return cudaGetLastError();
     });
   }
   if (T.limbs > 4) return cudaErrorInvalidValue;
   switch (T.npairs) {
-    case 5: reconstruct128_grouped_kernel<5><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
-    case 6: reconstruct128_grouped_kernel<6><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
-    case 7: reconstruct128_grouped_kernel<7><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
-    case 8: reconstruct128_grouped_kernel<8><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, count); break;
+    case 5: reconstruct128_grouped_kernel<5><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec); break;
+    case 6: reconstruct128_grouped_kernel<6><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec); break;
+    case 7: reconstruct128_grouped_kernel<7><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec); break;
+    case 8: reconstruct128_grouped_kernel<8><<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -32,6 +32,8 @@
 // exact in bf16).
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "oz_internal.h"
 #include "oz_device.cuh"
 
@@ -311,16 +313,17 @@ __global__ void __launch_bounds__(256) split_rows_warp_kernel(const __grid_const
   split_row_warp<kBF16, NP, QT>(T, v, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
-// Grouped, short rows: block b holds rows 8 (b - rows_begin) .. + 7 of its problem.
-template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_rows_warp_grouped_kernel(const __grid_constant__ OzTables T,
-                                                                      const OzGroupProblem* __restrict__ probs,
-                                                                      int count) {
+// Grouped, short rows: block b holds rows 8 (b - rows_begin) .. + 7 of its
+// problem; map[b] is the problem.
+// (three blocks per SM where the registers allow it without spilling)
+template <int NP, int QT>
+__global__ void __launch_bounds__(256, (QT > 0 && NP == 4) ? 3 : 2) split_rows_warp_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                         const OzGroupProblem* __restrict__ probs,
+                                                                         const int32_t* __restrict__ map) {
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
-  const OzGroupProblem& P = probs[pi];
+  const OzGroupProblem& P = probs[__ldg(map + b)];
   const int64_t v = (b - P.rows_begin) * 8 + (threadIdx.x >> 5);
-  split_row_warp<kBF16, NP, 0>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
+  split_row_warp<true, NP, QT>(T, v, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
 template <bool kBF16, int NP, int QT>
@@ -332,14 +335,14 @@ __global__ void __launch_bounds__(256, 3) split_rows_kernel(const __grid_constan
   split_row<kBF16, NP, QT>(T, blockIdx.x, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, given);
 }
 
-// Grouped: block b is row b - rows_begin of its problem's A.
-template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_rows_grouped_kernel(const __grid_constant__ OzTables T,
-                                                                 const OzGroupProblem* __restrict__ probs, int count) {
+// Grouped: block b is row b - rows_begin of its problem's A; map[b] is the problem.
+template <int NP, int QT>
+__global__ void __launch_bounds__(256, (QT > 0 && NP == 4) ? 3 : 2) split_rows_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                    const OzGroupProblem* __restrict__ probs,
+                                                                    const int32_t* __restrict__ map) {
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.rows_begin; });
-  const OzGroupProblem& P = probs[pi];
-  split_row<kBF16, NP, 0>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
+  const OzGroupProblem& P = probs[__ldg(map + b)];
+  split_row<true, NP, QT>(T, b - P.rows_begin, P.m, P.k, P.A, P.lda, P.m_pad, P.k_pad, P.s, P.U, P.flag, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,15 +356,16 @@ __device__ __forceinline__ void colmax_block(int64_t bx, int64_t by, int64_t nve
                                              uint64_t* __restrict__ colmax, int32_t* __restrict__ flag) {
   __shared__ uint64_t red[8][32];
   const int64_t j = bx * 32 + threadIdx.x;
-  const int64_t h0 = by * 256;
+  const int64_t h0 = by * 256 + threadIdx.y;
   uint64_t mx = 0;
   uint32_t bad = 0;
   if (j < nvec) {
     const uint64_t* col = reinterpret_cast<const uint64_t*>(X) + j;
-    for (int i = threadIdx.y; i < 256; i += 8) {
-      int64_t h = h0 + i;
-      if (h >= len) break;
-      uint64_t b = __ldg(col + h * ld) & kAbsMask;
+    // 32 rows per thread, loads issued together (predicated, no early exit)
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int64_t h = h0 + 8 * i;
+      const uint64_t b = h < len ? __ldg(col + h * ld) & kAbsMask : 0ull;
       bad |= (uint32_t)((b >> 52) == 0x7ff);
       mx = b > mx ? b : mx;
     }
@@ -383,11 +387,11 @@ __global__ void __launch_bounds__(256) colmax_kernel(int64_t nvec, int64_t len, 
 }
 
 // Grouped: block b is block b - cm_begin of its problem's (ceil(n/32) x
-// ceil(k/256)) grid, x fastest.
-__global__ void __launch_bounds__(256) colmax_grouped_kernel(const OzGroupProblem* __restrict__ probs, int count) {
+// ceil(k/256)) grid, x fastest; map[b] is the problem.
+__global__ void __launch_bounds__(256) colmax_grouped_kernel(const OzGroupProblem* __restrict__ probs,
+                                                             const int32_t* __restrict__ map) {
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.cm_begin; });
-  const OzGroupProblem& P = probs[pi];
+  const OzGroupProblem& P = probs[__ldg(map + b)];
   const int64_t l = b - P.cm_begin, nbx = (P.n + 31) / 32;
   colmax_block(l % nbx, l / nbx, P.n, P.k, P.B, P.ldb, P.colmax, P.flag);
 }
@@ -398,10 +402,10 @@ __global__ void shifts_from_colmax_kernel(int64_t nvec, const uint64_t* __restri
   if (j < nvec) shifts[j] = shift_from_maxbits(colmax[j], beta);
 }
 
-__global__ void shifts_grouped_kernel(const OzGroupProblem* __restrict__ probs, int count, int beta) {
+__global__ void shifts_grouped_kernel(const OzGroupProblem* __restrict__ probs, const int32_t* __restrict__ map,
+                                      int beta) {
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.sh_begin; });
-  const OzGroupProblem& P = probs[pi];
+  const OzGroupProblem& P = probs[__ldg(map + b)];
   const int64_t j = (b - P.sh_begin) * blockDim.x + threadIdx.x;
   if (j < P.n) P.t[j] = shift_from_maxbits(P.colmax[j], beta);
 }
@@ -508,15 +512,86 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const __grid_constant__
   split_cols_block<kBF16, NP>(T, blockIdx.x, blockIdx.y, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
 }
 
-// Grouped: block b is block b - sc_begin of its problem's (n_pad/64 x k_pad/64) grid, x fastest.
-template <bool kBF16, int NP>
-__global__ void __launch_bounds__(256) split_cols_grouped_kernel(const __grid_constant__ OzTables T,
-                                                                 const OzGroupProblem* __restrict__ probs, int count) {
+// bf16 planes (TC engine): tiles of 32 vectors x 64 h. Lane l holds vector
+// j0 + l, warp w the eight h = hbase + 8w .. + 7 (each load instruction reads
+// 32 consecutive doubles of one row of X). The residues of every modulus are
+// staged in shared memory, [q][32 vectors][64 h + 8 pad] bf16 (rows of 144
+// bytes: the 16-byte stores and loads of a quarter-warp fall in distinct
+// banks), and after one barrier each thread writes one 16-byte run per
+// modulus, so the planes (K-major per vector) receive whole 128-byte rows.
+constexpr int kColTileJ = 32, kColTileH = 64;
+constexpr int kColPitchWords = 36;
+constexpr int kColPlaneWords = kColTileJ * kColPitchWords;     // 1152 words = 4608 bytes per modulus
+
+template <int NP, int QT>
+__device__ __forceinline__ void split_cols_tile(const OzTables& T, int64_t j0, int64_t hbase, int64_t nvec,
+                                                int64_t len, const double* __restrict__ X, int64_t ld,
+                                                int64_t nvec_pad, int64_t k_pad, const int32_t* __restrict__ shifts,
+                                                uint16_t* __restrict__ planes, uint32_t* tile) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t j = j0 + lane;
+  const bool live = j < nvec;
+  const int32_t s = live ? __ldg(shifts + j) : 0;
+  const uint64_t* Xb = reinterpret_cast<const uint64_t*>(X);
+  const int64_t h0 = hbase + 8 * w;
+  uint64_t b[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) b[e] = (live && h0 + e < len) ? __ldg(Xb + (h0 + e) * ld + j) : 0ull;
+  Pieces<NP> P[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    if (((b[e] >> 52) & 0x7ff) == 0x7ff) b[e] = 0;   // non-finite: flagged by the column maxima
+    P[e] = pieces_of<NP>(b[e], s);
+  }
+  const int Q = QT > 0 ? QT : T.Q;
+  uint4* const mine = reinterpret_cast<uint4*>(tile + lane * kColPitchWords + 4 * w);
+#pragma unroll
+  for (int q = 0; q < (QT > 0 ? QT : OZ_MAX_MODULI); ++q) {
+    if (QT > 0 || q < Q) {
+      const ModConst<NP> mc = mod_const<NP>(T, q);
+      float r[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) r[e] = residue_q(T, q, mc, P[e]);
+      mine[q * (kColPlaneWords / 4)] =
+          make_uint4(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]), bf16_pair(r[4], r[5]), bf16_pair(r[6], r[7]));
+    }
+  }
+  __syncthreads();
+  // thread t: vector row t / 8 of the tile, 16-byte chunk t % 8 of its 64 h
+  const int row = threadIdx.x >> 3, ch = threadIdx.x & 7;
+  if (j0 + row < nvec_pad) {
+    const int64_t plane = nvec_pad * k_pad;
+    uint16_t* dst = planes + (j0 + row) * k_pad + hbase + 8 * ch;
+    const uint4* src = reinterpret_cast<const uint4*>(tile + row * kColPitchWords + 4 * ch);
+#pragma unroll 4
+    for (int q = 0; q < Q; ++q)
+      *reinterpret_cast<uint4*>(dst + q * plane) = src[q * (kColPlaneWords / 4)];
+  }
+}
+
+template <int NP, int QT>
+__global__ void __launch_bounds__(256, 3) split_cols_bf16_kernel(const __grid_constant__ OzTables T, int64_t nvec,
+                                                                int64_t len, const double* __restrict__ X, int64_t ld,
+                                                                int64_t nvec_pad, int64_t k_pad,
+                                                                const int32_t* __restrict__ shifts,
+                                                                uint16_t* __restrict__ planes) {
+  extern __shared__ uint4 col_tile[];
+  split_cols_tile<NP, QT>(T, (int64_t)blockIdx.x * kColTileJ, (int64_t)blockIdx.y * kColTileH, nvec, len, X, ld,
+                          nvec_pad, k_pad, shifts, planes, reinterpret_cast<uint32_t*>(col_tile));
+}
+
+// Grouped: block b is tile l = b - sc_begin of its problem's
+// (n_pad / 32) x (k_pad / 64) grid, vectors fastest; map[b] is its problem.
+template <int NP, int QT>
+__global__ void __launch_bounds__(256, 3) split_cols_grouped_kernel(const __grid_constant__ OzTables T,
+                                                                   const OzGroupProblem* __restrict__ probs,
+                                                                   const int32_t* __restrict__ map) {
+  extern __shared__ uint4 col_tile[];
   const int64_t b = blockIdx.x;
-  const int pi = group_find(probs, count, b, [](const OzGroupProblem& q) { return q.sc_begin; });
-  const OzGroupProblem& P = probs[pi];
-  const int64_t l = b - P.sc_begin, nbx = P.n_pad / 64;
-  split_cols_block<kBF16, NP>(T, l % nbx, l / nbx, P.n, P.k, P.B, P.ldb, P.n_pad, P.k_pad, P.t, P.V);
+  const OzGroupProblem& P = probs[__ldg(map + b)];
+  const int64_t l = b - P.sc_begin, nbx = P.n_pad / kColTileJ;
+  split_cols_tile<NP, QT>(T, (l % nbx) * kColTileJ, (l / nbx) * kColTileH, P.n, P.k, P.B, P.ldb, P.n_pad, P.k_pad,
+                          P.t, static_cast<uint16_t*>(P.V), reinterpret_cast<uint32_t*>(col_tile));
 }
 
 // Transpose of a rows x cols block of doubles (row pitch ld) into cols x rows
@@ -575,11 +650,30 @@ void split_rows_np(const OzTables& t, int64_t nvec, int64_t len, const double* X
     split_rows_qt<kBF16, NP, 0>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, flag, st, given);
 }
 
+template <int NP, int QT>
+cudaError_t split_cols_bf16_qt(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld,
+                               int64_t nvec_pad, int64_t k_pad, const int32_t* shifts, void* planes, cudaStream_t st) {
+  const int smem = (QT > 0 ? QT : t.Q) * kColPlaneWords * 4;
+  cudaError_t e = cudaFuncSetAttribute(split_cols_bf16_kernel<NP, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (QT > 0 ? QT : OZ_MAX_MODULI) * kColPlaneWords * 4);
+  if (e != cudaSuccess) return e;
+  dim3 g((unsigned)(nvec_pad / kColTileJ), (unsigned)(k_pad / kColTileH));
+  split_cols_bf16_kernel<NP, QT><<<g, 256, smem, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts,
+                                                       static_cast<uint16_t*>(planes));
+  return cudaGetLastError();
+}
+
 template <bool kBF16, int NP>
-void split_cols_np(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
-                   int64_t k_pad, const int32_t* shifts, void* planes, cudaStream_t st) {
-  dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
-  split_cols_kernel<kBF16, NP><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+cudaError_t split_cols_np(const OzTables& t, int64_t nvec, int64_t len, const double* X, int64_t ld, int64_t nvec_pad,
+                          int64_t k_pad, const int32_t* shifts, void* planes, cudaStream_t st) {
+  if constexpr (kBF16 && NP <= 5) {
+    if (t.Q == 16) return split_cols_bf16_qt<NP, 16>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    return split_cols_bf16_qt<NP, 0>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+  } else {
+    dim3 g((unsigned)(nvec_pad / 64), (unsigned)(k_pad / 64));
+    split_cols_kernel<kBF16, NP><<<g, 256, 0, st>>>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes);
+    return cudaGetLastError();
+  }
 }
 
 }  // namespace
@@ -636,53 +730,65 @@ cudaError_t launch_split_cols(const OzTables& t, int64_t nvec, int64_t len, cons
     if (e0 != cudaSuccess) return e0;
   }
   switch (pieces_for(t.bits) * 2 + (bf16 ? 1 : 0)) {
-    case 9: split_cols_np<true, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
-    case 8: split_cols_np<false, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
-    case 11: split_cols_np<true, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
-    case 10: split_cols_np<false, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
-    case 15: split_cols_np<true, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
-    default: split_cols_np<false, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st); break;
+    case 9: return split_cols_np<true, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    case 8: return split_cols_np<false, 4>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    case 11: return split_cols_np<true, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    case 10: return split_cols_np<false, 5>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    case 15: return split_cols_np<true, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
+    default: return split_cols_np<false, 7>(t, nvec, len, X, ld, nvec_pad, k_pad, shifts, planes, st);
   }
-  return cudaGetLastError();
 }
 
-// Problems [0, nlong) have long rows (one block per row, total_rows blocks),
-// the rest short rows (eight per block, total_wrows blocks); each range has its
-// own rows_begin numbering.
-cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int nlong,
+// Long rows (one block per row, total_rows blocks, problems in map_rows) and
+// short rows (eight per block, total_wrows blocks, map_wrows); each range has
+// its own rows_begin numbering. The map entries index probs.
+cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
                                       int64_t total_rows, int64_t total_wrows, cudaStream_t st) {
-  if (count == 0) return cudaSuccess;
   if (total_rows > INT32_MAX || total_wrows > INT32_MAX || t.bits > 64) return cudaErrorInvalidValue;
-  const bool np4 = t.bits <= 61;   // 22 bits and three 13-bit pieces
-  if (nlong > 0 && total_rows > 0) {
-    if (np4)
-      split_rows_grouped_kernel<true, 4><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
-    else
-      split_rows_grouped_kernel<true, 5><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, nlong);
-  }
-  if (count > nlong && total_wrows > 0) {
-    if (np4)
-      split_rows_warp_grouped_kernel<true, 4><<<(unsigned)total_wrows, 256, 0, st>>>(t, probs + nlong, count - nlong);
-    else
-      split_rows_warp_grouped_kernel<true, 5><<<(unsigned)total_wrows, 256, 0, st>>>(t, probs + nlong, count - nlong);
+  auto launch = [&](auto np, auto qt) {
+    constexpr int NP = decltype(np)::value, QT = decltype(qt)::value;
+    if (total_rows > 0)
+      split_rows_grouped_kernel<NP, QT><<<(unsigned)total_rows, 256, 0, st>>>(t, probs, maps.rows);
+    if (total_wrows > 0)
+      split_rows_warp_grouped_kernel<NP, QT><<<(unsigned)total_wrows, 256, 0, st>>>(t, probs, maps.wrows);
+  };
+  using I4 = std::integral_constant<int, 4>;
+  using I5 = std::integral_constant<int, 5>;
+  if (t.bits <= 61) {   // 22 bits and three 13-bit pieces
+    if (t.Q == 16) launch(I4{}, std::integral_constant<int, 16>{});
+    else if (t.Q == 15) launch(I4{}, std::integral_constant<int, 15>{});
+    else launch(I4{}, std::integral_constant<int, 0>{});
+  } else {
+    launch(I5{}, std::integral_constant<int, 0>{});
   }
   return cudaGetLastError();
 }
 
 // column maxima, shifts and split of the B operands (colmax zeroed by the caller)
-cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_cm,
-                                      int64_t total_sh, int64_t total_sc, cudaStream_t st) {
-  if (count == 0) return cudaSuccess;
+cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
+                                      int64_t total_cm, int64_t total_sh, int64_t total_sc, cudaStream_t st) {
   if (total_cm > INT32_MAX || total_sh > INT32_MAX || total_sc > INT32_MAX || t.bits > 64) return cudaErrorInvalidValue;
-  if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, count);
-  if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, count, t.bits);
-  if (total_sc > 0) {
-    if (t.bits <= 61)
-      split_cols_grouped_kernel<true, 4><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
-    else
-      split_cols_grouped_kernel<true, 5><<<(unsigned)total_sc, 256, 0, st>>>(t, probs, count);
+  if (total_cm > 0) colmax_grouped_kernel<<<(unsigned)total_cm, dim3(32, 8), 0, st>>>(probs, maps.cm);
+  if (total_sh > 0) shifts_grouped_kernel<<<(unsigned)total_sh, 256, 0, st>>>(probs, maps.sh, t.bits);
+  if (total_sc == 0) return cudaGetLastError();
+  auto launch = [&](auto np, auto qt) {
+    constexpr int NP = decltype(np)::value, QT = decltype(qt)::value;
+    const int smem = (QT > 0 ? QT : t.Q) * kColPlaneWords * 4;
+    cudaError_t e = cudaFuncSetAttribute(split_cols_grouped_kernel<NP, QT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (QT > 0 ? QT : OZ_MAX_MODULI) * kColPlaneWords * 4);
+    if (e != cudaSuccess) return e;
+    split_cols_grouped_kernel<NP, QT><<<(unsigned)total_sc, 256, smem, st>>>(t, probs, maps.sc);
+    return cudaGetLastError();
+  };
+  using I4 = std::integral_constant<int, 4>;
+  using I5 = std::integral_constant<int, 5>;
+  if (t.bits <= 61) {
+    if (t.Q == 16) return launch(I4{}, std::integral_constant<int, 16>{});
+    if (t.Q == 15) return launch(I4{}, std::integral_constant<int, 15>{});
+    return launch(I4{}, std::integral_constant<int, 0>{});
   }
-  return cudaGetLastError();
+  return launch(I5{}, std::integral_constant<int, 0>{});
 }
 
 }  // namespace oz

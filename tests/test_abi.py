@@ -233,7 +233,8 @@ def _layout_plans():
                                    (65536, 256, 256), (256, 65536, 300)])
 def test_workspace_layout_regions_are_disjoint_aligned_and_fit(m, n, k):
     """Every region of the workspace the kernels address (shifts, column
-    maxima, the residue planes of both operands, the product's residues, B^T)
+    maxima, the residue planes of both operands, the product's residues, and
+    B^T for int8 planes)
     has the size the header documents, starts on a 256-byte boundary (16 bytes
     is what TMA needs), overlaps no other region and ends inside
     oz_workspace_bytes; the padded sizes are multiples of the tile and k
@@ -259,7 +260,7 @@ def test_workspace_layout_regions_are_disjoint_aligned_and_fit(m, n, k):
         pitch = -(-max(n, 1) // (16 // digit_bytes)) * (16 // digit_bytes)
         regions = [("flag", 16), ("s", 4 * m), ("t", 4 * n), ("colmax", 8 * max(m, n)),
                    ("u", nplanes * m_pad * row), ("v", nplanes * n_pad * row),
-                   ("y", digits * m * pitch * digit_bytes), ("bt", 0 if fp else 8 * n * k)]
+                   ("y", digits * m * pitch * digit_bytes), ("bt", 0 if fp or elem == 2 else 8 * n * k)]
         end = 0
         for key, size in regions:
             off = L[key]

@@ -18,7 +18,7 @@ def _plan(fmt, K):
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E2M3", "E3M2", "E5M2", "E2M1"])
-@pytest.mark.parametrize("K", [8192, 16384])
+@pytest.mark.parametrize("K", [8192, 16384, 65536])
 def test_configuration_is_valid_and_tables_match_oracle(fmt, K):
     p = _plan(fmt, K)
     assert p.k_cfg == K
@@ -44,11 +44,14 @@ def test_configuration_is_valid_and_tables_match_oracle(fmt, K):
     assert i == len(vals)
 
 
-@pytest.mark.parametrize("K", [8192, 16384])
-def test_e2m1_least_q_equals_oracle(K):
+@pytest.mark.parametrize("K,Q", [(8192, 59), (16384, 59), (65536, 61)])
+def test_e2m1_least_q_equals_oracle(K, Q):
+    """Table tab:moduli prints 59 GEMMs for E2M1 at K = 2^14; at K = 2^16 the
+    window needs two more bits of P (eq. ov-crtgen) and the oracle's search
+    takes two more GEMMs."""
     p = _plan("E2M1", K)
     pool = forms.Pools("E2M1", K)
-    assert p.q == forms.least_q(pool.rank, K)[0] == 59
+    assert p.q == forms.least_q(pool.rank, K)[0] == Q
 
 
 def test_fp8_counts_match_the_paper():
@@ -61,7 +64,10 @@ def test_fp8_counts_match_the_paper():
 
 
 def test_plan_refuses_inner_dimension_above_its_configurations():
-    st, h = oz.oz_plan_create_fp(oz.OZ_FMT_E4M3, 20000, 0)
+    """Configurations exist for K_cfg = 2^13, 2^14 and 2^16 (Sec. 'Solving the
+    Program': each K re-searched); past 2^16 a float plan is refused."""
+    assert oz.PlanFP("E4M3", 20000).k_cfg == 65536
+    st, h = oz.oz_plan_create_fp(oz.OZ_FMT_E4M3, 65537, 0)
     assert st == oz.OZ_ERR_K_TOO_LARGE and h is None
     assert oz.oz_plan_create_fp(99, 1000, 0)[0] == oz.OZ_ERR_UNSUPPORTED
 

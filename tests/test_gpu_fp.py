@@ -156,6 +156,23 @@ def test_dgemm_at_configured_k_sampled(fmt):
     assert np.array_equal(C[rows, cols].view(np.uint64), ref.view(np.uint64))
 
 
+@pytest.mark.parametrize("fmt", ["E4M3", "E3M2", "E2M1"])
+def test_dgemm_at_k_cfg_65536_sampled(fmt):
+    """An inner dimension past 2^14 takes the configuration searched for
+    K = 2^16 (plane radius 16, more or larger moduli): sampled entries of the
+    product against the oracle's one-by-one entries, bit for bit."""
+    plan = oz.PlanFP(fmt, 40000)
+    assert plan.k_cfg == 65536 and plan.bits >= 53
+    m, n, k = 136, 200, 40000
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=11)
+    C = oz.dgemm(_dev(A), _dev(B), plan).cpu().numpy()
+    rng = np.random.default_rng(2)
+    rows = np.concatenate([rng.integers(0, m, 150), [0, m - 1, 128]])
+    cols = np.concatenate([rng.integers(0, n, 150), [n - 1, 0, 199]])
+    ref = oracle.dgemm_entries(A, B, plan.moduli, plan.bits, rows, cols)
+    assert np.array_equal(C[rows, cols].view(np.uint64), ref.view(np.uint64))
+
+
 def test_inner_dimension_above_k_max_is_refused():
     plan = oz.PlanFP("E4M3", 8192)
     A = torch.zeros((4, plan.k_max + 200), dtype=torch.float64, device=DEV)
