@@ -55,6 +55,7 @@ extern "C" {
 #define OZ_MIN_MODULI 9    /* smallest Q the library accepts */
 #define OZ_MAX_BITS 80     /* largest bit budget beta (|A'| < 2^beta) of an INT8 plan */
 #define OZ_MAX_BITS_FP 72  /* largest bit budget of a float-format plan (widened configurations) */
+#define OZ_MAX_CHANNELS 32 /* most channels a float-format configuration has */
 
 typedef enum {
   OZ_OK = 0,
@@ -153,7 +154,8 @@ OZ_API oz_status oz_plan_create_fp(oz_plan* out, int format, int64_t k_hint, int
  * plane count, and (if plane_values is given, values_len entries long) the
  * plane value tables: plane p (channels in order, planes of a channel in the
  * order a0 | a0, a1 | a0, a0 + a1, a1) holds m_c scaled alphabet values, one
- * per class. Any output pointer may be NULL.
+ * per class. moduli, forms and bases, if given, must hold OZ_MAX_CHANNELS
+ * entries. Any output pointer may be NULL.
  */
 OZ_API oz_status oz_plan_info_fp(oz_plan plan, int* channels, int* gemms, int64_t* k_cfg, uint32_t* moduli,
                                  int* forms, int* bases, int* plane_count, int16_t* plane_values,

@@ -36,7 +36,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OZO_MAXQ 24
+#define OZO_MAXQ 32   /* moduli; their product must also stay below 2^254 (moduli_ok) */
 
 typedef unsigned __int128 u128;
 
@@ -162,6 +162,20 @@ static void crt_garner(const int32_t* w, const int32_t* mod, int Q, u256* mag, i
   if (u256_bitlen(mag) == 0) *neg = 0;
 }
 
+/* The moduli fit the 256-bit CRT: 1 <= Q <= OZO_MAXQ, every m >= 2, and the
+ * sum of their bit lengths (a bound on that of P) at most 254, so that 2X < 2^256. */
+static int moduli_ok(const int32_t* mod, int Q) {
+  if (Q < 1 || Q > OZO_MAXQ) return 0;
+  int bits = 0;
+  for (int k = 0; k < Q; ++k) {
+    if (mod[k] < 2) return 0;
+    int b = 0;
+    for (uint32_t m = (uint32_t)mod[k]; m; m >>= 1) ++b;
+    bits += b;
+  }
+  return bits <= 254;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Step 6: round (-1)^neg * mag * 2^e to binary64, nearest-even.           */
 /* ---------------------------------------------------------------------- */
@@ -201,7 +215,7 @@ int ozo_scale(const double* X, int64_t nvec, int64_t len, int64_t s_vec, int64_t
 /* Balanced residue planes out[k][v][h] of trunc(X * 2^s[v]) modulo mod[k]. */
 int ozo_residue_planes(const double* X, int64_t nvec, int64_t len, int64_t s_vec, int64_t s_elem,
                        const int32_t* s, const int32_t* mod, int Q, int16_t* out) {
-  if (Q < 1 || Q > OZO_MAXQ) return -1;
+  if (!moduli_ok(mod, Q)) return -1;
   for (int64_t v = 0; v < nvec; ++v)
     for (int64_t h = 0; h < len; ++h) {
       double x = X[v * s_vec + h * s_elem];
@@ -218,7 +232,7 @@ int ozo_residue_planes(const double* X, int64_t nvec, int64_t len, int64_t s_vec
 int ozo_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
               const double* B, int64_t ldb, const int32_t* mod, int Q, int beta,
               double* C, int64_t ldc, uint16_t* w_out, int32_t* s_out, int32_t* t_out) {
-  if (M < 0 || N < 0 || K < 0 || Q < 1 || Q > OZO_MAXQ || beta < 1 || beta > 120) return -1;
+  if (M < 0 || N < 0 || K < 0 || !moduli_ok(mod, Q) || beta < 1 || beta > 120) return -1;
   int32_t* s = (int32_t*)malloc(sizeof(int32_t) * (size_t)(M + 1));
   int32_t* t = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N + 1));
   int16_t* U = (int16_t*)malloc(sizeof(int16_t) * (size_t)(Q * M * K + 1));
@@ -269,7 +283,7 @@ int ozo_dgemm_entries(int64_t M, int64_t N, int64_t K, const double* A, int64_t 
                       const double* B, int64_t ldb, const int32_t* mod, int Q, int beta,
                       int64_t n_entries, const int64_t* rows, const int64_t* cols,
                       double* out, uint64_t* x_out) {
-  if (M < 0 || N < 0 || K < 0 || Q < 1 || Q > OZO_MAXQ || beta < 1 || beta > 120) return -1;
+  if (M < 0 || N < 0 || K < 0 || !moduli_ok(mod, Q) || beta < 1 || beta > 120) return -1;
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
   for (int64_t e = 0; e < n_entries; ++e) {
@@ -302,7 +316,7 @@ int ozo_dgemm_entries(int64_t M, int64_t N, int64_t K, const double* A, int64_t 
 
 /* CRT alone: residues w[e][k] in [0, m_k) -> X as two's-complement 256-bit words. */
 int ozo_crt(int64_t n, const int32_t* w, const int32_t* mod, int Q, uint64_t* x_out) {
-  if (Q < 1 || Q > OZO_MAXQ) return -1;
+  if (!moduli_ok(mod, Q)) return -1;
   for (int64_t e = 0; e < n; ++e) {
     u256 mag; int neg;
     crt_garner(w + e * Q, mod, Q, &mag, &neg);

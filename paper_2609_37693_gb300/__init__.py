@@ -44,6 +44,7 @@ OZ_MAX_MODULI = 20
 OZ_MIN_MODULI = 9
 OZ_MAX_BITS = 80
 OZ_MAX_BITS_FP = 72
+OZ_MAX_CHANNELS = 32
 OZ_STATIC_SCRATCH_BYTES = 32 << 20
 
 EXPORTED = ("oz_plan_create", "oz_plan_info", "oz_plan_destroy", "oz_workspace_bytes", "oz_workspace_layout",
@@ -141,9 +142,9 @@ def oz_plan_info_fp(plan, want_values: bool = False):
     """Returns (status, dict(channels, gemms, k_cfg, moduli, forms, bases, planes[, values]))."""
     ch, gm, npl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     kc = ctypes.c_int64()
-    mods = (ctypes.c_uint32 * 32)()
-    forms = (ctypes.c_int * 32)()
-    bases = (ctypes.c_int * 32)()
+    mods = (ctypes.c_uint32 * OZ_MAX_CHANNELS)()
+    forms = (ctypes.c_int * OZ_MAX_CHANNELS)()
+    bases = (ctypes.c_int * OZ_MAX_CHANNELS)()
     st = _lib.oz_plan_info_fp(plan, ctypes.byref(ch), ctypes.byref(gm), ctypes.byref(kc), mods, forms, bases,
                               ctypes.byref(npl), None, 0)
     if st != OZ_OK:

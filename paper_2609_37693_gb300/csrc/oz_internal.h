@@ -9,6 +9,7 @@
 
 #define OZ_MAX_LIMBS 6     // 32-bit limbs of the CRT sum: Q P < 2^192 for Q <= 20
 #define OZ_TABLE_CAP 32    // moduli a constant table can hold (INT8 plans use at most 20)
+static_assert(OZ_TABLE_CAP == OZ_MAX_CHANNELS, "a float configuration's channels fill a table");
 #define OZ_RG_MAX 8        // groups of the byte-digit reconstruct (Q <= 16 gives at most 6)
 
 // Everything a kernel needs about a configuration. Passed by value as a kernel

@@ -4,6 +4,7 @@ counts equal to the oracle's search or the paper's printed values, and plane
 tables equal to the oracle's enumeration."""
 import itertools
 import math
+import os
 
 import pytest
 
@@ -11,6 +12,7 @@ import paper_2609_37693_gb300 as oz
 from oracle import forms
 
 KIND = {1: "one", 2: "school3", 3: "toom", 4: "school4"}
+SLOW = os.environ.get("OZ_SLOW_TESTS") == "1"
 
 
 def _plan(fmt, K):
@@ -18,13 +20,13 @@ def _plan(fmt, K):
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E2M3", "E3M2", "E5M2", "E2M1"])
-@pytest.mark.parametrize("K", [8192, 16384, 65536])
-def test_configuration_is_valid_and_tables_match_oracle(fmt, K):
-    p = _plan(fmt, K)
-    assert p.k_cfg == K
+@pytest.mark.parametrize("K,beta", [(8192, 53), (16384, 53), (65536, 53), (16384, 69)])
+def test_configuration_is_valid_and_tables_match_oracle(fmt, K, beta):
+    p = oz.PlanFP(fmt, K, beta if beta > 53 else 0)
+    assert p.k_cfg == K and p.bits >= beta
     assert all(math.gcd(a, b) == 1 for a, b in itertools.combinations(p.moduli, 2))
     P = math.prod(p.moduli)
-    assert P > 2 * K * (2**53 - 1) ** 2                        # eq. ov-crtgen at 53 bits
+    assert P > 2 * K * (2**beta - 1) ** 2                      # eq. ov-crtgen at beta bits
     assert p.q == sum(len(forms.weights(KIND[f], b)) for f, b in zip(p.forms, p.bases))
     r = forms.rmax1(K, forms.LAMBDA_FP32)
     vals = p.plane_values()
@@ -52,6 +54,29 @@ def test_e2m1_least_q_equals_oracle(K, Q):
     p = _plan("E2M1", K)
     pool = forms.Pools("E2M1", K)
     assert p.q == forms.least_q(pool.rank, K)[0] == Q
+
+
+def test_widened_e2m1_takes_78_gemms():
+    """Example ex:widened: at E2M1 and K = 2^14, operands spanning 2^16 more
+    keep 53 + 16 bits with 78 GEMMs. The library's frozen widened configuration
+    has that count, equals the oracle's least-Q search at beta = 69, and is
+    what a plan asking for more bits than the base configuration holds gets;
+    without such a request the base configuration (59 GEMMs) serves."""
+    p = oz.PlanFP("E2M1", 16384, 69)
+    pool = forms.Pools("E2M1", 16384)
+    assert p.q == forms.least_q(pool.rank, 16384, beta=69)[0] == 78
+    assert oz.PlanFP("E2M1", 16384).q == 59
+    assert oz.PlanFP("E2M1", 16384, 60).q == 78          # 60 bits: past the base window, within the widened
+    st, _ = oz.oz_plan_create_fp(oz.OZ_FMT_E2M1, 16384, 72)
+    assert st == oz.OZ_ERR_K_TOO_LARGE                    # no configuration holds 72 bits at K = 2^14
+
+
+@pytest.mark.skipif(not SLOW, reason="minutes of CPU; set OZ_SLOW_TESTS=1")
+@pytest.mark.parametrize("fmt,Q", [("E2M3", 39), ("E3M2", 52)])
+def test_widened_fp6_least_q_equals_oracle(fmt, Q):
+    p = oz.PlanFP(fmt, 16384, 69)
+    pool = forms.Pools(fmt, 16384)
+    assert p.q == forms.least_q(pool.rank, 16384, beta=69)[0] == Q
 
 
 def test_fp8_counts_match_the_paper():

@@ -173,6 +173,30 @@ def test_dgemm_at_k_cfg_65536_sampled(fmt):
     assert np.array_equal(C[rows, cols].view(np.uint64), ref.view(np.uint64))
 
 
+@pytest.mark.parametrize("fmt", ["E2M1", "E4M3", "E3M2"])
+def test_widened_dgemm_bit_exact(fmt):
+    """A plan asked for 69 bits takes the widened configuration (Example
+    ex:widened; E2M1: 78 GEMMs over 26 channels, P about 2^154.5, a five-limb
+    CRT; the split cuts |a'| < 2^69 into five 16-bit pieces). The product is
+    bit-exact against the oracle, and on skewed rows (phi = 4) the widened
+    budget's error is below the base configuration's."""
+    plan = oz.PlanFP(fmt, 2000, 69)
+    base = oz.PlanFP(fmt, 2000)
+    assert plan.bits == 69 and plan.k_cfg == 16384 and plan.q > base.q
+    m, n, k = 150, 136, 2000
+    A, B = synth.phi_pair(m, n, k, 4.0, seed=23)
+    C = oz.dgemm(_dev(A), _dev(B), plan).cpu().numpy()
+    ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
+    assert np.array_equal(C.view(np.uint64), ref.view(np.uint64))
+    C0 = oz.dgemm(_dev(A), _dev(B), base).cpu().numpy()
+    rows, cols = np.arange(0, m, 7), np.arange(0, n, 5)
+    r, c = np.meshgrid(rows, cols, indexing="ij")
+    r, c = r.ravel(), c.ravel()
+    e69, _ = oracle.exact_error(A, B, C, r, c)
+    e53, _ = oracle.exact_error(A, B, C0, r, c)
+    assert e69.max() < e53.max()
+
+
 def test_inner_dimension_above_k_max_is_refused():
     plan = oz.PlanFP("E4M3", 8192)
     A = torch.zeros((4, plan.k_max + 200), dtype=torch.float64, device=DEV)

@@ -12,6 +12,10 @@ from tests import brute
 
 MODS16 = oracle.max_product_moduli(16, 239)
 MODS14 = oracle.max_product_moduli(14, 239)
+# 26 pairwise-coprime moduli, P about 2^154.5: the channel moduli of the widened
+# E2M1 configuration (Example ex:widened, beta = 53 + 16 at K = 2^14)
+MODS26 = [169, 157, 151, 149, 139, 137, 131, 127, 113, 89, 85, 83, 79, 73, 71, 67, 61, 59, 53, 47, 43, 41, 11, 9,
+          8, 7]
 
 
 def _bits(x):
@@ -19,7 +23,7 @@ def _bits(x):
 
 
 @pytest.mark.parametrize("seed,phi,beta,mods", [(0, 0.5, 53, MODS16), (1, 2.0, 55, MODS16), (2, 1.0, 50, MODS14),
-                                                (3, 4.0, 53, MODS16)])
+                                                (3, 4.0, 53, MODS16), (4, 4.0, 69, MODS26), (5, 1.0, 71, MODS26)])
 def test_oracle_equals_exact_definition(seed, phi, beta, mods):
     """C, X = A'B' and every W mod m equal the exact big-integer evaluation of
     eq. convert and C = fl(mu^-1 A'B' nu^-1)."""
@@ -334,3 +338,16 @@ def test_error_report_helper_on_a_small_case():
     err, ab = oracle.exact_error(A, B, C, r.ravel(), c.ravel())
     assert np.array_equal(rel, err / (2.0**-53 * ab))
     assert rel.max() <= 2.0
+
+
+def test_moduli_beyond_the_256_bit_crt_are_refused():
+    """The oracle's CRT works in 256 bits: 33 moduli, or moduli whose product
+    could reach 2^254, are refused rather than wrapped."""
+    assert math.gcd(*MODS26) == 1 and all(math.gcd(a, b) == 1 for i, a in enumerate(MODS26) for b in MODS26[:i])
+    A, B = synth.phi_pair(2, 2, 3, 1.0, 0)
+    with pytest.raises(Exception):
+        oracle.dgemm(A, B, list(range(3, 69, 2)), 53)          # 33 moduli
+    big = [4093, 4091, 4079, 4073, 4057, 4051, 4049, 4027, 4021, 4019, 4013, 4007, 4003, 4001, 3989, 3967, 3947,
+           3943, 3931, 3929, 3919, 3917]                      # 22 primes near 2^12: 264 bits of moduli
+    with pytest.raises(Exception):
+        oracle.dgemm(A, B, big, 53)
