@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--formats", nargs="+", default=["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
                     help="fp-sweep: float formats")
     ap.add_argument("--reps", type=int, default=5, help="sweeps: timed repetitions (median)")
+    ap.add_argument("--autograd-shapes", nargs="+", default=None,
+                    help="autograd: m,k,n triples (default 4096,4096,4096 65536,256,256)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-mode", default="auto", choices=["auto", "grouped", "streams"],
                     help="batch: autotuned over launch structure and modulus counts (auto), one launch per "
@@ -827,7 +829,9 @@ def run_autograd(args, rank, world, local):
     import paper_2609_37693_gb300 as oz
     torch.cuda.set_device(local)
     rows = []
-    for (m, k, n) in ((4096, 4096, 4096), (65536, 256, 256)):
+    shapes = [tuple(int(x) for x in t.split(",")) for t in args.autograd_shapes] if args.autograd_shapes else \
+        [(4096, 4096, 4096), (65536, 256, 256)]
+    for (m, k, n) in shapes:
         g = torch.Generator(device="cuda").manual_seed(0)
         A = torch.randn(m, k, dtype=torch.float64, device="cuda", generator=g).requires_grad_()
         B = torch.randn(k, n, dtype=torch.float64, device="cuda", generator=g).requires_grad_()

@@ -31,6 +31,7 @@
 #include "oz_device.cuh"
 #include "oz_internal.h"
 #include "oz_sync.cuh"
+#include "oz_pair.cuh"
 
 namespace oz {
 namespace {
@@ -385,6 +386,111 @@ struct FpParams {
   int32_t* status;
 };
 
+// ---- epilogue pieces shared by the one-CTA and the CTA-pair kernels ----
+
+// Fold one GEMM of a channel into the running residues: this warp's 32 TMEM
+// lanes, columns taddr0 .. + 32 NCH - 1 of the accumulator, W = acc 2^e2 (an
+// exact integer, |W| <= 2^24), r <- r + lambda (W mod m) (mod m), r kept as
+// r + 2048 in 16-bit fields. The accumulator is released (tempty: this CTA's
+// barrier, or the leader's for a pair) once its last columns are loaded.
+template <int NCH, bool PAIR>
+__device__ __forceinline__ void fold_gemm(uint32_t (&acc16)[NCH * 16], uint32_t taddr0, uint32_t tempty, float lam,
+                                          float wscale, float mf, float invm) {
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    uint32_t v[32];
+    tmem_ld32(taddr0 + ch * 32, v);
+    tmem_ld_wait();
+    if (ch == NCH - 1) {
+      tc_fence_before();
+      if (PAIR) mbar_arrive_cluster(tempty);
+      else mbar_arrive(tempty);
+    }
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+      uint32_t out[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        // previous residue r from its 16-bit field r + 2048
+        const float prev = __int_as_float(0x4B000000u | ((acc16[ch * 16 + w] >> (16 * j)) & 0xffffu)) - 8390656.0f;
+        const float W = __uint_as_float(v[2 * w + j]) * wscale;               // exact integer, |W| <= 2^24
+        const float wq = fmaf(W, invm, 12582912.0f) - 12582912.0f;
+        const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.65 m
+        const float tsum = fmaf(lam, wm, prev);                              // exact: < 2^24
+        const float q2 = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
+        const float r = fmaf(-q2, mf, tsum);                                 // |r| < 0.51 m
+        out[j] = __float_as_uint(r + 8390656.0f) & 0xffffu;                  // r + 2048
+      }
+      acc16[ch * 16 + w] = out[0] | (out[1] << 16);
+    }
+  }
+}
+
+// The unit's HC entries of row `row` from column col0 on, as W mod m or the
+// CRT digit (W mod m) (P/m)^-1 mod m, 16 bits each, to channel c's plane of Y;
+// acc: added modulo m to the digits already there (blocked call).
+template <int HC>
+__device__ __forceinline__ void store_unit(const OzFpTables& F, int c, const uint32_t (&acc16)[HC / 2],
+                                           uint16_t* Y, int64_t ldy, int m, int n, int row, int col0, int raw,
+                                           int acc) {
+  if (row >= m || col0 >= n) return;
+  const float mf = F.mf[c], invm = F.invm[c];
+  const float inv = (float)F.inv[c];
+  uint16_t* dst = Y + (size_t)c * m * ldy + (size_t)row * ldy + col0;
+  const bool vec = col0 + HC <= n && (ldy & 7) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+#pragma unroll
+  for (int i4 = 0; i4 < HC / 8; ++i4) {
+    uint32_t o4[4];
+    uint32_t prev[4] = {0u, 0u, 0u, 0u};
+    if (acc) {                       // the digits of the earlier slabs
+      if (vec) {
+        const uint4 w = reinterpret_cast<const uint4*>(dst)[i4];
+        prev[0] = w.x;
+        prev[1] = w.y;
+        prev[2] = w.z;
+        prev[3] = w.w;
+      } else {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            if (col0 + 8 * i4 + 2 * ii + j < n) prev[ii] |= (uint32_t)dst[8 * i4 + 2 * ii + j] << (16 * j);
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      uint32_t o = 0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float r = __int_as_float(0x4B000000u | ((acc16[4 * i4 + ii] >> (16 * j)) & 0xffffu)) - 8390656.0f;
+        r = r < 0.f ? r + mf : r;                                            // W mod m in [0, m)
+        float y = r;
+        if (!raw) {
+          const float tt = r * inv;                                          // < m^2 < 2^24: exact
+          const float q = fmaf(tt, invm, 12582912.0f) - 12582912.0f;
+          y = fmaf(-q, mf, tt);
+          y = y < 0.f ? y + mf : y;
+        }
+        if (acc) {
+          y += (float)((prev[ii] >> (16 * j)) & 0xffffu);
+          y = y >= mf ? y - mf : y;
+        }
+        o |= (__float_as_uint(y + 8388608.0f) & 0xffffu) << (16 * j);
+      }
+      o4[ii] = o;
+    }
+    if (vec) {
+      reinterpret_cast<uint4*>(dst)[i4] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+    } else {
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          if (col0 + 8 * i4 + 2 * ii + j < n) dst[8 * i4 + 2 * ii + j] = (uint16_t)(o4[ii] >> (16 * j));
+    }
+  }
+}
+
 template <bool MX>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -537,96 +643,13 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
-        const float lam = F.g_lam[g0 + gi];
-#pragma unroll
-        for (int ch = 0; ch < C::NCH; ++ch) {
-          uint32_t v[32];
-          tmem_ld32(tmem_base + lane_addr + b * BN + half * C::HC + ch * 32, v);
-          tmem_ld_wait();
-          if (ch == C::NCH - 1) {
-            tc_fence_before();
-            mbar_arrive(tempty_bar(b));
-          }
-#pragma unroll
-          for (int w = 0; w < 16; ++w) {
-            uint32_t out[2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              // previous residue r from its 16-bit field r + 2048
-              const float prev =
-                  __int_as_float(0x4B000000u | ((acc16[ch * 16 + w] >> (16 * j)) & 0xffffu)) - 8390656.0f;
-              const float W = __uint_as_float(v[2 * w + j]) * wscale;               // exact integer, |W| <= 2^24
-              const float wq = fmaf(W, invm, 12582912.0f) - 12582912.0f;
-              const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.65 m
-              const float tsum = fmaf(lam, wm, prev);                              // exact: < 2^24
-              const float q2 = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
-              const float r = fmaf(-q2, mf, tsum);                                 // |r| < 0.51 m
-              out[j] = __float_as_uint(r + 8390656.0f) & 0xffffu;                  // r + 2048
-            }
-            acc16[ch * 16 + w] = out[0] | (out[1] << 16);
-          }
-        }
+        fold_gemm<C::NCH, false>(acc16, tmem_base + lane_addr + b * BN + half * C::HC, tempty_bar(b),
+                                 F.g_lam[g0 + gi], wscale, mf, invm);
       }
       if (!ok) break;
       // ---- unit done: W mod m or the CRT digit, 16 bits per entry ----
-      const int row = u.tm * BM + quarter * 32 + lane;
-      const int col0 = u.tn * BN + half * C::HC;
-      if (row < p.m && col0 < p.n) {
-        const float inv = (float)F.inv[u.c];
-        uint16_t* dst = p.Y + (size_t)u.c * p.m * p.ldy + (size_t)row * p.ldy + col0;
-        const bool vec = col0 + C::HC <= p.n && (p.ldy & 7) == 0 && (reinterpret_cast<uintptr_t>(p.Y) & 15) == 0;
-#pragma unroll
-        for (int i4 = 0; i4 < C::HC / 8; ++i4) {
-          uint32_t o4[4];
-          uint32_t prev[4] = {0u, 0u, 0u, 0u};
-          if (p.acc) {                       // the digits of the earlier slabs
-            if (vec) {
-              const uint4 w = reinterpret_cast<const uint4*>(dst)[i4];
-              prev[0] = w.x;
-              prev[1] = w.y;
-              prev[2] = w.z;
-              prev[3] = w.w;
-            } else {
-#pragma unroll
-              for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                  if (col0 + 8 * i4 + 2 * ii + j < p.n) prev[ii] |= (uint32_t)dst[8 * i4 + 2 * ii + j] << (16 * j);
-            }
-          }
-#pragma unroll
-          for (int ii = 0; ii < 4; ++ii) {
-            uint32_t o = 0;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              float r = __int_as_float(0x4B000000u | ((acc16[4 * i4 + ii] >> (16 * j)) & 0xffffu)) - 8390656.0f;
-              r = r < 0.f ? r + mf : r;                                            // W mod m in [0, m)
-              float y = r;
-              if (!p.raw) {
-                const float tt = r * inv;                                          // < m^2 < 2^24: exact
-                const float q = fmaf(tt, invm, 12582912.0f) - 12582912.0f;
-                y = fmaf(-q, mf, tt);
-                y = y < 0.f ? y + mf : y;
-              }
-              if (p.acc) {
-                y += (float)((prev[ii] >> (16 * j)) & 0xffffu);
-                y = y >= mf ? y - mf : y;
-              }
-              o |= (__float_as_uint(y + 8388608.0f) & 0xffffu) << (16 * j);
-            }
-            o4[ii] = o;
-          }
-          if (vec) {
-            reinterpret_cast<uint4*>(dst)[i4] = make_uint4(o4[0], o4[1], o4[2], o4[3]);
-          } else {
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-              for (int j = 0; j < 2; ++j)
-                if (col0 + 8 * i4 + 2 * ii + j < p.n) dst[8 * i4 + 2 * ii + j] = (uint16_t)(o4[ii] >> (16 * j));
-          }
-        }
-      }
+      store_unit<C::HC>(F, u.c, acc16, p.Y, p.ldy, p.m, p.n, u.tm * BM + quarter * 32 + lane,
+                        u.tn * BN + half * C::HC, p.raw, p.acc);
     }
   }
 
@@ -635,6 +658,227 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same GEMMs on CTA pairs (cluster of 2, cta_group::2): a pair computes a
+// 256 x BN tile (BN = 256 for kind::f8f6f4; 192 for the block-scaled 4-bit
+// kind, whose two accumulators leave TMEM room for the scales); each CTA
+// stages its 128 rows of A and BN / 2 rows of B, so that per product a CTA
+// reads a quarter (f8f6f4) or an eighth (4-bit) less shared memory than one
+// CTA on a 128 x BN tile, and the leader issues M = 256 products that write
+// 128 rows into each CTA's tensor memory. Barriers as in the INT8 pair kernel:
+//   full[s]   leader only: both CTAs' copies of stage s;
+//   empty[s]  each CTA: its stage s may be refilled (multicast commit);
+//   tfull[b]  each CTA: accumulator b holds a GEMM (multicast commit);
+//   tempty[b] leader only: both CTAs' epilogues have loaded accumulator b.
+// Every wait is bounded, as in the one-CTA kernel.
+// ---------------------------------------------------------------------------
+template <bool MX>
+struct PairCfg {
+  static constexpr int BN = MX ? 192 : 256;         // N of a pair's products
+  static constexpr int BNC = BN / 2;                // rows of B per CTA
+  static constexpr int HC = BN / 2;                 // columns per epilogue warp (two halves)
+  static constexpr int NCH = HC / 32;
+  static constexpr int STAGE_BYTES = A_BYTES + BNC * BK;
+  static constexpr int STAGES = MX ? 7 : 6;
+  static constexpr int kSmemBytes = STAGES * STAGE_BYTES + 256 + 1024;
+  static constexpr int KSTAGE = MX ? 2 * BK : BK;
+};
+
+__device__ __forceinline__ void umma_f8f6f4_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_mxf4_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+
+template <bool MX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+gemm_fp_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ OzFpTables F, const FpParams p) {
+  using C = PairCfg<MX>;
+  constexpr int BN = C::BN, BNC = C::BNC, STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_base = smem_u32(smem_raw);
+  const uint32_t base = (raw_base + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw_base);
+  const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  static_assert((2 * STAGES + 5) * 8 <= 192, "barriers overlap the TMEM address");
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 192);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + STAGES * STAGE_BYTES + 200);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 2 * kEpiWarps * 32);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {                          // one warp of each CTA: the pair's allocation
+    tmem_alloc_pair(smem_u32(tmem_holder), kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  if constexpr (MX) {
+    // every byte of columns 448..511 of both CTAs = 0x7F, the UE8M0 scale 2^0:
+    // the products are unscaled whichever scale layout the pair's MMA reads
+    if (warp >= 2) {
+      const uint32_t lane_q = (uint32_t)((warp & 3) * 32) << 16;
+      tmem_st32_fill(tmem_base + lane_q + kSfaCol + ((warp - 2) >> 2) * 32, 0x7F7F7F7Fu);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  cluster_sync();                           // both CTAs' barriers and scales exist before any remote use
+  tc_fence_after();
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer (both CTAs) ------------------------------
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued_parity[STAGES];
+      bool outstanding[STAGES];
+      for (int i = 0; i < STAGES; ++i) outstanding[i] = false, issued_parity[i] = 0;
+      bool ok = true;
+      for (int t = pair; t < p.num_units && ok; t += npairs) {
+        const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+        const int g0 = F.ch_gemm0[u.c], ng = F.ch_ngemm[u.c];
+        for (int g = g0; g < g0 + ng && ok; ++g) {
+          const int ya = (int)F.g_pa[g] * p.m_pad + u.tm * 2 * BM + (int)rank * BM;
+          const int yb = (int)F.g_pb[g] * p.n_pad + u.tn * BN + (int)rank * BNC;
+          for (int kb = 0; kb < p.kblocks; ++kb) {
+            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.status)) { ok = false; break; }
+            outstanding[s] = false;
+            const uint32_t sa = base + s * STAGE_BYTES;
+            if (leader) mbar_expect_tx(full_bar(s), 2 * STAGE_BYTES);
+            const uint32_t fb = mapa(full_bar(s), 0);
+            tma_load_2d_pair(sa, &tmA, fb, kb * BK, ya);
+            tma_load_2d_pair(sa + A_BYTES, &tmB, fb, kb * BK, yb);
+            outstanding[s] = true;
+            issued_parity[s] = ph;
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+        }
+      }
+      // both CTAs' copies complete on the leader's barriers: the leader waits
+      // (bounded) for every stage it expected before the pair may exit
+      if (!ok && leader) {
+        for (int i = 0; i < STAGES; ++i)
+          if (outstanding[i]) mbar_drain(full_bar(i), issued_parity[i]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer (leader) ------------------------------
+    if (lane == 0 && leader) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t g_ctr = 0;
+      bool ok = true;
+      for (int t = pair; t < p.num_units && ok; t += npairs) {
+        const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+        const int ng = F.ch_ngemm[u.c];
+        for (int gi = 0; gi < ng && ok; ++gi, ++g_ctr) {
+          const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
+          if (!mbar_wait(tempty_bar(b), (use & 1u) ^ 1u, abort_flag, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t dtm = tmem_base + b * BN;
+          for (int kb = 0; kb < p.kblocks; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, abort_flag, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 32; ++kk) {
+              if constexpr (MX)
+                umma_mxf4_pair(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, tmem_base + kSfaCol,
+                               tmem_base + kSfbCol, (kb > 0 || kk > 0) ? 1u : 0u);
+              else
+                umma_f8f6f4_pair(dtm, sdesc(sa + kk * 32), sdesc(sb + kk * 32), p.idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit_pair_both(empty_bar(s));
+            if (++s == STAGES) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          umma_commit_pair_both(tfull_bar(b));
+        }
+      }
+      if (!ok) {
+        umma_commit_pair_self(drain_bar);
+        mbar_drain(drain_bar, 0);
+      }
+    }
+  } else {
+    // ------------------------------ epilogue (both CTAs) ------------------------------
+    const int e = warp - 2;
+    const int quarter = warp & 3;
+    const int half = e >> 2;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    const float wscale = __int_as_float((127 + F.e2) << 23);      // 2^e2: accumulator -> W
+    uint32_t g_ctr = 0;
+    bool ok = true;
+    for (int t = pair; t < p.num_units && ok; t += npairs) {
+      const Unit u = unit_coord(t, p.tiles_m, p.tiles_n);
+      const int g0 = F.ch_gemm0[u.c], ng = F.ch_ngemm[u.c];
+      const float mf = F.mf[u.c], invm = F.invm[u.c];
+      uint32_t acc16[C::HC / 2];             // running residue + 2048, 16 bits per column
+#pragma unroll
+      for (int i = 0; i < C::HC / 2; ++i) acc16[i] = 0x08000800u;
+      for (int gi = 0; gi < ng; ++gi, ++g_ctr) {
+        const uint32_t b = g_ctr & 1u, use = g_ctr >> 1;
+        if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
+        tc_fence_after();
+        fold_gemm<C::NCH, true>(acc16, tmem_base + lane_addr + b * BN + half * C::HC, mapa(tempty_bar(b), 0),
+                                F.g_lam[g0 + gi], wscale, mf, invm);
+      }
+      if (!ok) break;
+      store_unit<C::HC>(F, u.c, acc16, p.Y, p.ldy, p.m, p.n, u.tm * 2 * BM + (int)rank * BM + quarter * 32 + lane,
+                        u.tn * BN + half * C::HC, p.raw, p.acc);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();                           // neither CTA leaves while the pair may touch its memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kTmemCols);
   }
 }
 
@@ -860,12 +1104,20 @@ cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguo
 
 namespace {
 
+// Float-format GEMMs run one CTA per tile (gemm_fp_kernel). The CTA-pair
+// form (gemm_fp_pair_kernel) gives the same bits but was slower at 8192 on
+// one box: E4M3 GEMMs 10.07 against 9.75 ms, E2M1 12.29 against 11.35 ms.
+constexpr bool kFpPairs = false;
+
 template <bool MX>
 cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
                     const uint8_t* U, const uint8_t* V, uint16_t* Y, int64_t ldy, int raw, int32_t* status,
                     cudaStream_t st) {
   using C = Cfg<MX>;
-  const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + C::BN - 1) / C::BN;
+  using PC = PairCfg<MX>;
+  const bool pairs = kFpPairs && m_pad % (2 * BM) == 0;
+  const int tile_m = pairs ? 2 * BM : BM, tile_n = pairs ? PC::BN : C::BN;
+  const int64_t tiles_m = (m + tile_m - 1) / tile_m, tiles_n = (n + tile_n - 1) / tile_n;
   const int64_t units = tiles_m * tiles_n * f.nch;
   if (units > INT32_MAX || (int64_t)f.nplanes * m_pad > INT32_MAX || (int64_t)f.nplanes * n_pad > INT32_MAX)
     return cudaErrorInvalidValue;
@@ -874,13 +1126,12 @@ cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, in
   // B tiles of the last plane may run past its rows: the map's bound fills zeros;
   // elsewhere they read the next plane's rows into columns the epilogue drops
   if (!make_map8(&mapA, U, (int64_t)f.nplanes * m_pad, row_bytes, BM)) return cudaErrorInvalidValue;
-  if (!make_map8(&mapB, V, (int64_t)f.nplanes * n_pad, row_bytes, C::BN)) return cudaErrorInvalidValue;
+  if (!make_map8(&mapB, V, (int64_t)f.nplanes * n_pad, row_bytes, pairs ? PC::BNC : C::BN))
+    return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gemm_fp_kernel<MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
   if (e != cudaSuccess) return e;
   FpParams p;
   p.m = (int)m;
@@ -893,19 +1144,34 @@ cudaError_t gemm_fp(const OzFpTables& f, int64_t m, int64_t n, int64_t m_pad, in
   p.n_pad = (int)n_pad;
   p.raw = raw & kEpiRaw;
   p.acc = (raw & kEpiAccumulate) != 0;
+  const uint32_t mbits = (uint32_t)(tile_m >> 4) << 24, nbits = (uint32_t)(tile_n >> 3) << 17;
   if (MX) {
     // block-scaled: scale factor ids 0, A = B = E2M1 (1), both K-major, N >> 3,
     // UE8M0 scales (bit 23), M >> 4, K = 64 per instruction
-    p.idesc = (1u << 7) | (1u << 10) | ((uint32_t)(C::BN >> 3) << 17) | (1u << 23) | ((uint32_t)(BM >> 4) << 24);
+    p.idesc = (1u << 7) | (1u << 10) | nbits | (1u << 23) | mbits;
   } else {
     // D = F32, A and B of the format, both K-major, N >> 3, M >> 4
     const uint32_t code = f8f6f4_code(f.fmt);
     if (code == 0xffffffffu) return cudaErrorInvalidValue;
-    p.idesc = (1u << 4) | (code << 7) | (code << 10) | ((uint32_t)(C::BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    p.idesc = (1u << 4) | (code << 7) | (code << 10) | nbits | mbits;
   }
   p.Y = Y;
   p.ldy = ldy;
   p.status = status;
+  if (pairs) {
+    // as the INT8 pair kernel: each CTA of a pair claims all the shared memory a block may have
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int smem_bytes = smem_optin > PC::kSmemBytes ? smem_optin : PC::kSmemBytes;
+    e = cudaFuncSetAttribute(gemm_fp_pair_kernel<MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    const int64_t npairs = units < sms / 2 ? units : sms / 2;
+    gemm_fp_pair_kernel<MX><<<(unsigned)(2 * npairs), kThreads, smem_bytes, st>>>(mapA, mapB, f, p);
+    return cudaGetLastError();
+  }
+  e = cudaFuncSetAttribute(gemm_fp_kernel<MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e != cudaSuccess) return e;
   const int grid = (int)(units < sms ? units : sms);
   gemm_fp_kernel<MX><<<grid, kThreads, C::kSmemBytes, st>>>(mapA, mapB, f, p);
   return cudaGetLastError();
