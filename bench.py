@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--formats", nargs="+", default=["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"],
                     help="fp-sweep: float formats")
     ap.add_argument("--reps", type=int, default=5, help="sweeps: timed repetitions (median)")
+    ap.add_argument("--cooldown", type=float, default=2.0,
+                    help="sweeps: idle seconds before each row, so that every row starts below the power cap")
     ap.add_argument("--autograd-shapes", nargs="+", default=None,
                     help="autograd: m,k,n triples (default 4096,4096,4096 65536,256,256)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -880,6 +882,7 @@ def run_fp_sweep(args, rank, world, local):
             dg = 2.0 * n**3 / (_median_ms(lambda: Ad @ Bd, 2) * 1e-3) / 1e12
             for fmt in ["INT8"] + list(args.formats):
                 for bits in (0, 53):
+                    time.sleep(args.cooldown)
                     plan = oz.Plan(16, bits, n) if fmt == "INT8" else oz.PlanFP(fmt, n, bits)
                     ws = oz.workspace(plan, n, n, n)
                     C = torch.empty((n, n), dtype=torch.float64, device="cuda")
