@@ -401,10 +401,13 @@ __device__ __forceinline__ void fold_gemm(uint32_t (&acc16)[NCH * 16], uint32_t 
     uint32_t v[32];
     tmem_ld32(taddr0 + ch * 32, v);
     tmem_ld_wait();
-    if (ch == NCH - 1) {
+    if (ch == NCH - 1) {                  // one arrival per warp, after every lane's loads
       tc_fence_before();
-      if (PAIR) mbar_arrive_cluster(tempty);
-      else mbar_arrive(tempty);
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) {
+        if (PAIR) mbar_arrive_cluster(tempty);
+        else mbar_arrive(tempty);
+      }
     }
 #pragma unroll
     for (int w = 0; w < 16; ++w) {
@@ -521,7 +524,7 @@ gemm_fp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps * 32);
+      mbar_init(tempty_bar(b), kEpiWarps);        // one arrival per epilogue warp
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -737,7 +740,7 @@ gemm_fp_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 2 * kEpiWarps * 32);
+      mbar_init(tempty_bar(b), 2 * kEpiWarps);    // one arrival per epilogue warp of the pair
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;

@@ -208,6 +208,38 @@ __device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, in
   }
 }
 
+// The drain of a unit that is one slab (a kernel launched for K of at most
+// 1024 terms, unsplit): every chunk of this warp's columns is loaded first and
+// the accumulator released at once, so that the products of the unit after
+// next start while this warp forms the digits (W mod m reduced exactly, then
+// the CRT digit, or W mod m when raw), one byte per entry in acc8.
+template <int NCH, typename R>
+__device__ __forceinline__ void drain_one_slab(uint32_t taddr0, uint32_t (&acc8)[NCH * 8], float mf, float invm,
+                                               float invf, int raw, R release) {
+  uint32_t v[NCH][32];
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) tmem_ld32(taddr0 + ch * 32, v[ch]);
+  tmem_ld_wait();
+  tc_fence_before();
+  release();
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      uint32_t out[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float tv = __uint_as_float(v[ch][4 * w + j]);
+        const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
+        const float r = fmaf(-qf, mf, tv);                              // exact, |r| <= 120
+        out[j] = __float_as_uint(digit_of(r, mf, invm, invf, raw) + 8388608.0f);   // low byte
+      }
+      acc8[ch * 8 + w] =
+          __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
+    }
+  }
+}
+
 struct Params {
   int m, n, tiles_m, tiles_n, num_tiles, kblocks, m_pad, n_pad, raw;
   int acc;           // add into the digits already in Y, modulo m (blocked call)
@@ -236,6 +268,8 @@ __device__ __forceinline__ Unit unit_of(const Params& p, int u) {
   return w;
 }
 
+// ONE: every unit is one slab (K <= 1024, unsplit); see drain_one_slab.
+template <bool ONE>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ OzTables T, const Params p) {
@@ -374,6 +408,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, p.status)) { ok = false; break; }
         tc_fence_after();
+        if constexpr (ONE) {
+          const uint32_t tb = tempty_bar(b);
+          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, p.raw,
+                                    [&] { mbar_arrive(tb); });
+          continue;
+        }
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
@@ -553,7 +593,7 @@ struct PairGrouped {
 // EW epilogue warps (4, 8 or 16): every warp drains the 32 TMEM lanes of its
 // quarter (warp index mod 4), over CPW = 256 / (EW / 4) columns.
 // S: the unit scheduler (PairSingle or PairGrouped).
-template <int EW, typename S>
+template <int EW, typename S, bool ONE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__((2 + EW) * 32, 1)
 gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzTables T) {
   constexpr int CPW = 1024 / EW;            // columns per epilogue warp
@@ -704,6 +744,12 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, status)) { ok = false; break; }
         tc_fence_after();
+        if constexpr (ONE) {
+          const uint32_t tb = mapa(tempty_bar(b), 0);
+          drain_one_slab<CPW / 32>(tmem_base + lane_addr + b * 256 + cbase, acc8, mf, invm, invf, u.raw,
+                                   [&] { mbar_arrive_cluster(tb); });
+          continue;
+        }
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
@@ -776,6 +822,7 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
 // problem's descriptor gives its tensor maps (in global memory), padding, k
 // blocks and output. Roles and barriers as in gemm_tc_kernel.
 // ---------------------------------------------------------------------------
+template <bool ONE>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem* __restrict__ probs, int count,
                        int64_t total_units, int32_t* status) {
@@ -921,6 +968,12 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
         const uint32_t b = g & 1u, use = g >> 1;
         if (!mbar_wait(tfull_bar(b), use & 1u, abort_flag, status)) { ok = false; break; }
         tc_fence_after();
+        if constexpr (ONE) {
+          const uint32_t tb = tempty_bar(b);
+          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, 0,
+                                    [&] { mbar_arrive(tb); });
+          continue;
+        }
         const bool write_back = sl + 2 < nslabs;
         const bool last = sl + 1 == nslabs;
 #pragma unroll
@@ -1061,8 +1114,12 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const int smem_bytes = smem_optin > P_SMEM_BYTES ? smem_optin : P_SMEM_BYTES;
-  e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps, PairSingle>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  // every unit one slab (K <= 1024, unsplit): the kernel whose epilogue
+  // releases each accumulator before forming its digits
+  const bool one = k_pad <= (int64_t)kSlabBlocks * BK && split.nsplit <= 1;
+  auto kernel = one ? gemm_tc_pair_kernel<kPairEpiWarps, PairSingle, true>
+                    : gemm_tc_pair_kernel<kPairEpiWarps, PairSingle, false>;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   PairSingle sched;
   sched.mapA = mapA;
@@ -1084,8 +1141,7 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
   const int64_t units = num_tiles * p.nsplit;
   const int64_t pairs = units < sms / 2 ? units : sms / 2;
-  gemm_tc_pair_kernel<kPairEpiWarps, PairSingle>
-      <<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
+  kernel<<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
   return cudaGetLastError();
 }
 
@@ -1098,7 +1154,7 @@ bool group_maps_tc(OzGroupProblem* pr, int Q, bool pairs) {
 }
 
 cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
-                                   int32_t* status, cudaStream_t st, bool pairs) {
+                                   int32_t* status, cudaStream_t st, bool pairs, bool one_slab) {
   if (count == 0 || total_units == 0) return cudaSuccess;
   if (total_units > INT32_MAX) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
@@ -1112,8 +1168,9 @@ cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* prob
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const int smem_bytes = smem_optin > P_SMEM_BYTES ? smem_optin : P_SMEM_BYTES;
-    e = cudaFuncSetAttribute(gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    auto kernel = one_slab ? gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped, true>
+                           : gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped, false>;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
     PairGrouped sched;
     sched.probs = probs;
@@ -1121,14 +1178,14 @@ cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* prob
     sched.total = (int)total_units;
     sched.st = status;
     const int64_t pairs_n = total_units < sms / 2 ? total_units : sms / 2;
-    gemm_tc_pair_kernel<kPairEpiWarps, PairGrouped>
-        <<<(unsigned)(2 * pairs_n), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
+    kernel<<<(unsigned)(2 * pairs_n), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
     return cudaGetLastError();
   }
-  e = cudaFuncSetAttribute(gemm_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  auto kernel1 = one_slab ? gemm_tc_grouped_kernel<true> : gemm_tc_grouped_kernel<false>;
+  e = cudaFuncSetAttribute(kernel1, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   const int grid = (int)(total_units < sms ? total_units : sms);
-  gemm_tc_grouped_kernel<<<grid, kThreads, kSmemBytes, st>>>(t, probs, count, total_units, status);
+  kernel1<<<grid, kThreads, kSmemBytes, st>>>(t, probs, count, total_units, status);
   return cudaGetLastError();
 }
 
@@ -1153,7 +1210,9 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  const bool one = k_pad <= (int64_t)kSlabBlocks * BK && split.nsplit <= 1;
+  auto kernel = one ? gemm_tc_kernel<true> : gemm_tc_kernel<false>;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
   Params p;
   p.m = (int)m;
@@ -1172,7 +1231,7 @@ cudaError_t launch_gemm_tc_single(const OzTables& t, int64_t m, int64_t n, int64
   if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
   const int64_t units = num_tiles * p.nsplit;
   const int grid = (int)(units < sms ? units : sms);
-  gemm_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, t, p);
+  kernel<<<grid, kThreads, kSmemBytes, st>>>(mapA, mapB, t, p);
   return cudaGetLastError();
 }
 

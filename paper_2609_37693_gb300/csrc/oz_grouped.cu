@@ -51,6 +51,7 @@ struct Group {
   int first, count;                     // range of the device table
   int64_t total_rows, total_wrows, total_cm, total_sh, total_sc, total_units, total_rec;
   bool pairs;                           // GEMMs on CTA pairs (else one CTA per tile)
+  bool one_slab;                        // every product's k_pad at most 1024 (one slab per unit)
   oz::GroupMaps maps;                   // block -> problem (index from `first`) per phase
 };
 
@@ -254,6 +255,8 @@ extern "C" oz_status oz_group_create(oz_group* out, int count, const oz_plan* pl
     G.first = (int)table.size();
     G.count = (int)mem.size();
     G.pairs = group_uses_pairs(mem, mnk);
+    G.one_slab = true;
+    for (int i : mem) G.one_slab = G.one_slab && round_up(mnk[3 * i + 2], oz::kPadK) <= 1024;
     for (int i : mem) {
       const int64_t m = mnk[3 * i], n = mnk[3 * i + 1], k = mnk[3 * i + 2];
       const Part P = part_of(p, m, n, k);
@@ -390,7 +393,7 @@ extern "C" oz_status oz_group_run(oz_group g, void* stream) {
     // CTA all of its shared memory), so little is lost, and no two
     // tensor-memory users of this call run at once
     if (gi > 0) chk(cudaStreamWaitEvent(sa, g->events[3 + 3 * (gi - 1)], 0));
-    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, sa, G.pairs);
+    if (e == cudaSuccess) e = oz::launch_gemm_tc_grouped(T, probs, G.count, G.total_units, status, sa, G.pairs, G.one_slab);
     chk(cudaEventRecord(gemm_done, sa));
     if (e == cudaSuccess) e = oz::launch_reconstruct_grouped(T, probs, G.maps, G.total_rec, sa);
     chk(cudaEventRecord(done, sa));

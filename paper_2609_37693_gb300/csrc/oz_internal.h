@@ -249,9 +249,10 @@ cudaError_t launch_split_rows_grouped(const OzTables& t, const OzGroupProblem* p
 cudaError_t launch_split_cols_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
                                       int64_t total_cm, int64_t total_sh, int64_t total_sc, cudaStream_t st);
 // pairs: CTA pairs on 256 x 256 tiles (units Q ceil(m/256) tiles_n), else one
-// CTA per 128 x 256 tile (units Q tiles_m tiles_n)
+// CTA per 128 x 256 tile (units Q tiles_m tiles_n); one_slab: every problem's
+// k_pad is at most 1024 (each unit one slab)
 cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* probs, int count, int64_t total_units,
-                                   int32_t* status, cudaStream_t st, bool pairs);
+                                   int32_t* status, cudaStream_t st, bool pairs, bool one_slab);
 bool group_maps_tc(OzGroupProblem* pr, int Q, bool pairs);   // host: the TMA maps of a grouped problem's planes
 cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
                                        int64_t total_rec, cudaStream_t st);

@@ -176,6 +176,42 @@ __device__ __forceinline__ void store_residues(const OzTables& T, const Pieces<N
 // vector. Pass 1 finds the max bits; pass 2 re-reads the row (from L2) and
 // writes 8 consecutive entries per thread per plane.
 // ---------------------------------------------------------------------------
+// The largest |x| bit pattern over row[h], h = t, t + step, ... (t < step),
+// and whether any of those entries is not finite: 16-byte loads (two
+// entries) when the row is 16-byte aligned, four of them in flight per
+// iteration, so that a short row's maximum is not a chain of load latencies.
+__device__ __forceinline__ void row_absmax(const uint64_t* __restrict__ row, int64_t len, int t, int step,
+                                           uint64_t& mx, uint32_t& bad) {
+  auto fold = [&](uint64_t b) {
+    b &= kAbsMask;
+    bad |= (uint32_t)((b >> 52) == 0x7ff);
+    mx = b > mx ? b : mx;
+  };
+  if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const ulonglong2* r2 = reinterpret_cast<const ulonglong2*>(row);
+    const int64_t np = len >> 1;
+    int64_t p = t;
+    for (; p + 3 * (int64_t)step < np; p += 4 * (int64_t)step) {
+      ulonglong2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(r2 + p + u * step);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        fold(v[u].x);
+        fold(v[u].y);
+      }
+    }
+    for (; p < np; p += step) {
+      const ulonglong2 v = __ldg(r2 + p);
+      fold(v.x);
+      fold(v.y);
+    }
+    if ((len & 1) && t == 0) fold(__ldg(row + len - 1));
+  } else {
+    for (int64_t h = t; h < len; h += step) fold(__ldg(row + h));
+  }
+}
+
 template <bool kBF16, int NP, int QT>
 __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                           const double* __restrict__ X, int64_t ld, int64_t nvec_pad, int64_t k_pad,
@@ -193,13 +229,7 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
   } else {
     uint64_t mx = 0;
     uint32_t bad = 0;
-    if (live) {
-      for (int64_t h = tid; h < len; h += 256) {
-        uint64_t b = __ldg(row + h) & kAbsMask;
-        bad |= (uint32_t)((b >> 52) == 0x7ff);
-        mx = b > mx ? b : mx;
-      }
-    }
+    if (live) row_absmax(row, len, tid, 256, mx, bad);
     mx = warp_max_u64(mx);
     bad = __any_sync(0xffffffffu, bad);
     if ((tid & 31) == 0) red[tid >> 5] = mx | (bad ? (1ull << 63) : 0);
@@ -262,13 +292,7 @@ __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int
   } else {
     uint64_t mx = 0;
     uint32_t bad = 0;
-    if (live) {
-      for (int64_t h = lane; h < len; h += 32) {
-        uint64_t b = __ldg(row + h) & kAbsMask;
-        bad |= (uint32_t)((b >> 52) == 0x7ff);
-        mx = b > mx ? b : mx;
-      }
-    }
+    if (live) row_absmax(row, len, lane, 32, mx, bad);
     mx = warp_max_u64(mx);
     bad = __any_sync(0xffffffffu, bad);
     s = live ? shift_from_maxbits(bad ? 0 : mx, T.bits) : 0;
@@ -421,12 +445,7 @@ __global__ void __launch_bounds__(256) shifts_rows_kernel(int64_t nvec, int64_t 
   const uint64_t* row = reinterpret_cast<const uint64_t*>(X) + v * ld;
   uint64_t mx = 0;
   uint32_t bad = 0;
-#pragma unroll 4
-  for (int64_t h = lane; h < len; h += 32) {
-    const uint64_t b = __ldg(row + h) & kAbsMask;
-    bad |= (uint32_t)((b >> 52) == 0x7ff);
-    mx = b > mx ? b : mx;
-  }
+  row_absmax(row, len, lane, 32, mx, bad);
   mx = warp_max_u64(mx);
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) {
