@@ -210,9 +210,11 @@ __device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, in
 
 // The drain of a unit that is one slab (a kernel launched for K of at most
 // 1024 terms, unsplit): every chunk of this warp's columns is loaded first and
-// the accumulator released at once, so that the products of the unit after
-// next start while this warp forms the digits (W mod m reduced exactly, then
-// the CRT digit, or W mod m when raw), one byte per entry in acc8.
+// the accumulator released at once (one arrival per warp: each thread's
+// release-ordered arrival cost a memory barrier per unit), so that the
+// products of the unit after next start while this warp forms the digits
+// (W mod m reduced exactly, then the CRT digit, or W mod m when raw), one byte
+// per entry in acc8.
 template <int NCH, typename R>
 __device__ __forceinline__ void drain_one_slab(uint32_t taddr0, uint32_t (&acc8)[NCH * 8], float mf, float invm,
                                                float invf, int raw, R release) {
@@ -297,7 +299,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps * 32);
+      mbar_init(tempty_bar(b), ONE ? kEpiWarps : kEpiWarps * 32);   // one-slab: one arrival per warp
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -411,7 +413,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if constexpr (ONE) {
           const uint32_t tb = tempty_bar(b);
           drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, p.raw,
-                                    [&] { mbar_arrive(tb); });
+                                    [&] {
+                                      __syncwarp();
+                                      if (lane == 0) mbar_arrive(tb);
+                                    });
           continue;
         }
         const bool write_back = sl + 2 < nslabs;
@@ -624,7 +629,7 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 2 * EW * 32);
+      mbar_init(tempty_bar(b), ONE ? 2 * EW : 2 * EW * 32);        // one-slab: one arrival per warp
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -747,7 +752,10 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
         if constexpr (ONE) {
           const uint32_t tb = mapa(tempty_bar(b), 0);
           drain_one_slab<CPW / 32>(tmem_base + lane_addr + b * 256 + cbase, acc8, mf, invm, invf, u.raw,
-                                   [&] { mbar_arrive_cluster(tb); });
+                                   [&] {
+                                     __syncwarp();
+                                     if (lane == 0) mbar_arrive_cluster(tb);
+                                   });
           continue;
         }
         const bool write_back = sl + 2 < nslabs;
@@ -856,7 +864,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), kEpiWarps * 32);
+      mbar_init(tempty_bar(b), ONE ? kEpiWarps : kEpiWarps * 32);   // one-slab: one arrival per warp
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -971,7 +979,10 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
         if constexpr (ONE) {
           const uint32_t tb = tempty_bar(b);
           drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, 0,
-                                    [&] { mbar_arrive(tb); });
+                                    [&] {
+                                      __syncwarp();
+                                      if (lane == 0) mbar_arrive(tb);
+                                    });
           continue;
         }
         const bool write_back = sl + 2 < nslabs;

@@ -128,7 +128,8 @@ struct OzGroupProblem {
   int64_t unit_begin;   // GEMMs: Q * tiles_m * tiles_n units
   int64_t rec_begin;    // reconstruct: m * ceil(n/1024) blocks
   int tiles_m, tiles_n, kblocks;
-  int rec_tpr;          // reconstruct: threads per row chunk (32..256), 256 / rec_tpr rows per block
+  int rec_tpr;          // reconstruct: threads per row chunk (8..32), 256 / rec_tpr rows per block, each
+                        // thread 8 entries (the groups' kernel) or 4 (the pairs')
 };
 
 // the problem whose range [begin, next begin) holds index x (probs sorted by begin)
@@ -256,6 +257,9 @@ cudaError_t launch_gemm_tc_grouped(const OzTables& t, const OzGroupProblem* prob
 bool group_maps_tc(OzGroupProblem* pr, int Q, bool pairs);   // host: the TMA maps of a grouped problem's planes
 cudaError_t launch_reconstruct_grouped(const OzTables& t, const OzGroupProblem* probs, const GroupMaps& maps,
                                        int64_t total_rec, cudaStream_t st);
+// the grouped reconstruct's entries per thread for a plan's products: 8 (the
+// groups' kernel) when this holds, else 4 (the pairs' kernel)
+bool reconstruct_grouped_eight(const OzTables& t);
 // float-format path: planes of codes, 16-bit digits
 cudaError_t launch_split_fp(const OzTables& t, const OzFpTables& f, int contiguous, int64_t nvec, int64_t len,
                             const double* X, int64_t ld, int64_t nvec_pad, int64_t k_pad, int32_t* shifts,

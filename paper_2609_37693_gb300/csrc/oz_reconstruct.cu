@@ -775,31 +775,34 @@ __global__ void __launch_bounds__(256, 2) reconstruct_groups8_kernel(const __gri
 }
 
 // Grouped products: one block per task (256 / tpr rows of one column chunk
-// of 4 tpr entries of problem map[b], tpr = rec_tpr threads per row chunk, so
-// that short rows share a block), with the groups' sum. (A persistent form
-// with a task of lookahead, as reconstruct_groups_kernel, ran the 256-product
-// batch 3-8 % slower.)
+// of 8 tpr entries of problem map[b], tpr = rec_tpr threads per row chunk, so
+// that short rows share a block; eight entries per thread, as in
+// reconstruct_groups8_kernel), with the groups' sum. (A persistent form with a
+// task of lookahead, as reconstruct_groups_kernel, ran the 256-product batch
+// 3-8 % slower at four entries per thread.)
 template <int NT, int NP2, int NQ4>
 __global__ void __launch_bounds__(256) reconstruct_groups_grouped_kernel(const __grid_constant__ OzTables T,
                                                                          const OzGroupProblem* __restrict__ probs,
                                                                          const int32_t* __restrict__ map) {
   constexpr int Q = 3 * NT + 2 * NP2 + 4 * NQ4;
   __shared__ uint4 kP[16];
-  __shared__ uint32_t buf[Q * 256];
+  extern __shared__ uint32_t dbuf[];                   // [Q][256 threads][2 words]
   fill_kP(T, kP);
   __syncthreads();
   const int64_t b = blockIdx.x;
   const OzGroupProblem& P = probs[__ldg(map + b)];
   const int tpr = P.rec_tpr, rows = 256 / tpr;
-  const int64_t l = b - P.rec_begin, nch = (P.n + 4 * tpr - 1) / (4 * tpr);
+  const int64_t l = b - P.rec_begin, nch = (P.n + 8 * tpr - 1) / (8 * tpr);
   const int64_t i = (l / nch) * rows + threadIdx.x / tpr;
-  const int64_t j0 = ((l % nch) * tpr + threadIdx.x % tpr) * 4;
+  const int64_t j0 = ((l % nch) * tpr + threadIdx.x % tpr) * 8;
   if (i >= P.m || j0 >= P.n) return;
-  uint32_t* const mine = buf + threadIdx.x;
-  issue_digits<Q>(P.Y, P.m * P.ldy, P.ldy, i, j0, P.n, mine);
+  uint32_t* const mine = dbuf + 2 * threadIdx.x;
+  issue_digits8<Q>(P.Y, P.m * P.ldy, P.ldy, i, j0, P.n, mine);
   cp_async_commit();
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  rec4_groups<NT, NP2, NQ4>(T, kP, mine, i, j0, P.n, __ldg(P.s + i), P.t, P.C, P.ldc);
+  const int32_t si = __ldg(P.s + i);
+  rec4_groups<NT, NP2, NQ4, 512>(T, kP, mine, i, j0, P.n, si, P.t, P.C, P.ldc);
+  if (j0 + 4 < P.n) rec4_groups<NT, NP2, NQ4, 512>(T, kP, mine + 1, i, j0 + 4, P.n, si, P.t, P.C, P.ldc);
 }
 
 // Grouped: a block covers 256 / tpr rows of one column chunk of 4 tpr entries
@@ -925,6 +928,10 @@ cudaError_t with_shape(int key, F f) {
 
 }  // namespace
 
+// Whether the grouped reconstruct of a plan's products takes the groups'
+// kernel (eight entries per thread) rather than the pairs' (four).
+bool reconstruct_grouped_eight(const OzTables& T) { return group_shape(T) >= 0; }
+
 // 16-bit digits with P of five or six 32-bit limbs (widened float-format plans)
 cudaError_t launch_reconstruct16_wide(const OzTables& T, int64_t m, int64_t n, const uint16_t* Y, int64_t ldy,
                                       const int32_t* s, const int32_t* t, double* C, int64_t ldc, cudaStream_t st) {
@@ -1011,8 +1018,12 @@ cudaError_t launch_reconstruct_grouped(const OzTables& T, const OzGroupProblem* 
   const int shape = group_shape(T);
   if (shape >= 0) {
     return with_shape(shape, [&](auto nt, auto np2, auto nq4) {
-      reconstruct_groups_grouped_kernel<decltype(nt)::value, decltype(np2)::value, decltype(nq4)::value>
-          <<<(unsigned)total_rec, 256, 0, st>>>(T, probs, maps.rec);
+      constexpr int Q = 3 * decltype(nt)::value + 2 * decltype(np2)::value + 4 * decltype(nq4)::value;
+      auto kernel = reconstruct_groups_grouped_kernel<decltype(nt)::value, decltype(np2)::value, decltype(nq4)::value>;
+      const int smem = Q * 256 * 8;
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      kernel<<<(unsigned)total_rec, 256, smem, st>>>(T, probs, maps.rec);
       return cudaGetLastError();
     });
   }
