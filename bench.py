@@ -100,7 +100,12 @@ class ClockSampler:
         self.lines = []
         self.thread = None
 
-    def start(self):
+    def start(self, settle_s: float = 3.0):
+        """Start sampling and return once the first sample has arrived (at
+        most settle_s): nvidia-smi's start-up (its NVML initialisation) held
+        up the host's CUDA calls for tens of milliseconds in the first process
+        on a fresh machine, which a timed region begun right after start() paid
+        in full."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -110,6 +115,10 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t_end = time.time() + settle_s
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
+        time.sleep(0.05)
 
     def _read(self):
         for line in self.proc.stdout:

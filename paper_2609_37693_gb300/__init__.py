@@ -810,14 +810,14 @@ class GroupedGemm:
 
     def launches(self) -> int:
         """Kernels one run launches: per group of alike plans, the split of A
-        (one kernel for long rows, one for short rows of at most 1024 padded
+        (one kernel for long rows, one for short rows of at most 4096 padded
         entries), column maxima, shifts and split of B, the GEMMs and the
         Reconstruct."""
         groups = {}
         for p, (m, n, k) in zip(self.plans, self.shapes):
             g = groups.setdefault((p.q, p.bits, tuple(p.moduli)), set())
             if m and n and k:
-                g.add(round_up(k, 128) > 1024)
+                g.add(round_up(k, 128) > 4096)
         return sum(5 + len(kinds) for kinds in groups.values() if kinds)
 
     def capture(self, stream=None):

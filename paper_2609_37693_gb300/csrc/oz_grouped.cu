@@ -99,7 +99,9 @@ struct Blocks {
 
 Blocks blocks_of(const Part& P, int64_t m, int64_t n, int64_t k, int ept) {
   Blocks b;
-  const bool long_rows = P.k_pad > 1024;       // one block per row, else one warp per row
+  // one block per row, else one warp per row (eight rows per block: fewer,
+  // fuller blocks on the short and middling rows of a batch)
+  const bool long_rows = P.k_pad > 4096;
   b.rows = long_rows ? P.m_pad : 0;
   b.wrows = long_rows ? 0 : P.m_pad / 8;
   b.cm = ((n + 31) / 32) * ((k + 255) / 256);

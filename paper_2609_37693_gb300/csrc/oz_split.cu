@@ -276,8 +276,9 @@ __device__ __forceinline__ void split_row(const OzTables& T, int64_t v, int64_t 
   }
 }
 
-// The same for a short row (k_pad <= 1024): one warp per row, eight rows
-// per block; the row's maximum is a warp reduction.
+// The same for a short row (k_pad <= 1024 in one product's split, <= 4096
+// in the grouped one): one warp per row, eight rows per block; the row's
+// maximum is a warp reduction.
 template <bool kBF16, int NP, int QT>
 __device__ __forceinline__ void split_row_warp(const OzTables& T, int64_t v, int64_t nvec, int64_t len,
                                                const double* __restrict__ X, int64_t ld, int64_t nvec_pad,

@@ -75,9 +75,12 @@ def test_autotuner_picks_a_stream_count():
 
 def _edge_problems():
     """Uneven shapes with the edge cases of the grouped path: 1 x 1 x 1, one
-    row, one column, k = 0, k at a slab boundary, ragged tiles, Q = 14/15/16."""
+    row, one column, k = 0, k at a slab boundary, k on either side of the
+    split of A's switch from one warp per row to one block per row (4096),
+    ragged tiles, Q = 14/15/16."""
     shapes = [(1, 1, 1), (1, 300, 77), (300, 1, 77), (5, 7, 0), (130, 257, 1024), (129, 255, 1025),
-              (64, 64, 3), (700, 513, 900), (256, 256, 5000), (33, 1000, 837)]
+              (64, 64, 3), (700, 513, 900), (256, 256, 5000), (33, 1000, 837), (41, 70, 4096),
+              (9, 33, 4097)]
     As, Bs, Cs = [], [], []
     for i, (m, n, k) in enumerate(shapes):
         A, B = synth.phi_pair(m, n, k, 1.5, seed=300 + i)
