@@ -97,29 +97,50 @@ __device__ __forceinline__ ModConst<NP> mod_const(const OzTables& T, int q) {
   return c;
 }
 
-// Representative of a' nearest zero modulo one modulus, as an exact float in
-// [-m/2, m/2] (see the header); for an odd m it is below m/2 in magnitude.
-template <int NP>
-__device__ __forceinline__ float residue_any(const ModConst<NP>& c, const Pieces<NP>& P) {
-  float y = P.p[0];
-#pragma unroll
-  for (int i = 1; i < NP; ++i) y = fmaf(P.p[i], c.c[i - 1], y);
-  const float qf = fmaf(y, c.invm, 12582912.0f) - 12582912.0f;   // rint(y / m), exact
-  return fmaf(-qf, c.m, y);
-}
-
 // The tie of the even modulus (index 2): +m/2 becomes -m/2.
 __device__ __forceinline__ float fix_tie(const OzTables& T, float r) {
   const float h = T.halfm[2];
   return r == h ? -h : r;
 }
 
-// Representative in [-floor(m/2), ceil(m/2) - 1] of modulus q, q a
-// compile-time index after unrolling: only q = 2 takes the tie fix.
-template <int NP>
-__device__ __forceinline__ float residue_q(const OzTables& T, int q, const ModConst<NP>& c, const Pieces<NP>& P) {
-  const float r = residue_any(c, P);
-  return q == 2 ? fix_tie(T, r) : r;
+// Representatives of a' nearest zero modulo one modulus for EPT entries, as
+// exact floats in [-m/2, m/2] (see the header; below m/2 in magnitude for an
+// odd m): y = P0 + P1 c_1 + ..., q = rint(y / m) by one fma against the
+// rounding constant, r = y - q m. Two entries go through each packed fp32
+// operation (the f32x2 fma and add of sm_100 and later round each half as the
+// scalar operation would), so the issued instructions are half those of the
+// scalar chain and the results are the same bits.
+template <int NP, int EPT>
+__device__ __forceinline__ void residues_any(const ModConst<NP>& c, const Pieces<NP> (&P)[EPT], float (&r)[EPT]) {
+  static_assert(EPT % 2 == 0, "entries in pairs");
+  const float2 kC = make_float2(12582912.0f, 12582912.0f), kCn = make_float2(-12582912.0f, -12582912.0f);
+  const float2 inv = make_float2(c.invm, c.invm), nm = make_float2(-c.m, -c.m);
+  float2 ci[NP - 1];
+#pragma unroll
+  for (int i = 0; i < NP - 1; ++i) ci[i] = make_float2(c.c[i], c.c[i]);
+#pragma unroll
+  for (int e = 0; e < EPT; e += 2) {
+    float2 y = make_float2(P[e].p[0], P[e + 1].p[0]);
+#pragma unroll
+    for (int i = 1; i < NP; ++i) y = __ffma2_rn(make_float2(P[e].p[i], P[e + 1].p[i]), ci[i - 1], y);
+    const float2 qf = __fadd2_rn(__ffma2_rn(y, inv, kC), kCn);   // rint(y / m), exact
+    const float2 rr = __ffma2_rn(qf, nm, y);
+    r[e] = rr.x;
+    r[e + 1] = rr.y;
+  }
+}
+
+// Representatives in [-floor(m/2), ceil(m/2) - 1] of modulus q for EPT
+// entries, q a compile-time index after unrolling: only q = 2 takes the tie
+// fix.
+template <int NP, int EPT>
+__device__ __forceinline__ void residues_q(const OzTables& T, int q, const ModConst<NP>& c, const Pieces<NP> (&P)[EPT],
+                                           float (&r)[EPT]) {
+  residues_any<NP, EPT>(c, P, r);
+  if (q == 2) {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) r[e] = fix_tie(T, r[e]);
+  }
 }
 
 // bf16 bit pattern of the integers r (|r| < 2^8 needs at most 8 significand
@@ -150,8 +171,7 @@ __device__ __forceinline__ void store_residues(const OzTables& T, const Pieces<N
     if (QT > 0 || q < Q) {
       const ModConst<NP> mc = mod_const<NP>(T, q);
       float r[EPT];
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) r[e] = residue_q(T, q, mc, P[e]);
+      residues_q<NP, EPT>(T, q, mc, P, r);
       const int64_t o = (int64_t)q * plane + off;
       if (kBF16) {
         uint16_t* dst = static_cast<uint16_t*>(planes) + o;
@@ -490,8 +510,7 @@ __device__ __forceinline__ void split_cols_block(const OzTables& T, int64_t bx, 
     uint32_t* tb = tile[q & 1];
     const ModConst<NP> mc = mod_const<NP>(T, q);
     float r[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) r[e] = residue_any(mc, P[e]);
+    residues_any<NP, 16>(mc, P, r);
     if (q == 2) {                                    // block-uniform branch: the even modulus
 #pragma unroll
       for (int e = 0; e < 16; ++e) r[e] = fix_tie(T, r[e]);
@@ -570,8 +589,7 @@ __device__ __forceinline__ void split_cols_tile(const OzTables& T, int64_t j0, i
     if (QT > 0 || q < Q) {
       const ModConst<NP> mc = mod_const<NP>(T, q);
       float r[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) r[e] = residue_q(T, q, mc, P[e]);
+      residues_q<NP, 8>(T, q, mc, P, r);
       mine[q * (kColPlaneWords / 4)] =
           make_uint4(bf16_pair(r[0], r[1]), bf16_pair(r[2], r[3]), bf16_pair(r[4], r[5]), bf16_pair(r[6], r[7]));
     }
