@@ -154,17 +154,81 @@ __device__ __forceinline__ Coord tile_coord(int t, int tiles_m, int tiles_n) {
   return c;
 }
 
-// The last slab's value r (|r| <= 120, r == W mod m) as the byte the
-// epilogue stores: raw, W mod m in [0, m); else the CRT digit
-// (W mod m) (P/m)^-1 mod m, formed as r inv (|r inv| <= 120 * 238 < 2^15,
-// exact), one rint quotient and one sign correction into [0, m).
-__device__ __forceinline__ float digit_of(float r, float mf, float invm, float invf, int raw) {
-  float y = raw ? r : r * invf;
-  if (!raw) {
-    const float q2 = fmaf(y, invm, 12582912.0f) - 12582912.0f;
-    y = fmaf(-q2, mf, y);
+// The epilogue's arithmetic, two accumulator values per packed fp32
+// operation (the f32x2 fma, add and mul of sm_100 and later round each half
+// as the scalar operation would, so the results are those of the scalar form
+// at half the issued instructions). Per unit: the modulus m, fl(1/m), the
+// factor f of the digit ((P/m)^-1 mod m, or 1 for raw W mod m) and
+// bias = -1/2 + 1/(2m), each in both halves.
+struct EpiConst {
+  float2 invm, nm, f, bias;
+};
+
+__device__ __forceinline__ EpiConst epi_const(float mf, float invm, float f) {
+  const float b = fmaf(0.5f, invm, -0.5f);
+  return EpiConst{make_float2(invm, invm), make_float2(-mf, -mf), make_float2(f, f), make_float2(b, b)};
+}
+
+constexpr float kRint = 12582912.0f;      // 1.5 * 2^23: t + kRint - kRint = rint(t) for |t| < 2^22
+constexpr float kTwo23 = 8388608.0f;      // 2^23 + y, 0 <= y < 256: y in the low byte
+constexpr float kTwo23p128 = 8388736.0f;  // 2^23 + 128
+
+// r = t - m rint(t / m) for two accumulator values (|t| < 2^24): exact,
+// |r| <= 120.
+__device__ __forceinline__ float2 residue2(float2 t, const EpiConst& k) {
+  const float2 qf = __fadd2_rn(__ffma2_rn(t, k.invm, make_float2(kRint, kRint)), make_float2(-kRint, -kRint));
+  return __ffma2_rn(qf, k.nm, t);
+}
+
+// The byte of two residues r: y = r f mod m in [0, m), as 2^23 + y. r f is
+// an exact integer (|r f| <= 120 * 238 < 2^15), and floor(r f / m) =
+// rint(r f / m - 1/2 + 1/(2m)): the fraction of r f / m is a multiple of
+// 1/m, so the argument lies at least 1/(2m) from a half-integer, far beyond
+// the rounding of fl(1/m), of the bias and of the fma (together below 2^-14).
+// Equal to the balanced CRT digit moved into [0, m).
+__device__ __forceinline__ float2 digit2(float2 r, const EpiConst& k) {
+  const float2 y = __fmul2_rn(r, k.f);
+  const float2 q = __fadd2_rn(__fadd2_rn(__ffma2_rn(y, k.invm, k.bias), make_float2(kRint, kRint)),
+                              make_float2(-kRint, -kRint));
+  return __fadd2_rn(__ffma2_rn(q, k.nm, y), make_float2(kTwo23, kTwo23));
+}
+
+// A write-back slab: the 32 values of v reduced modulo m in place.
+__device__ __forceinline__ void residues32(uint32_t (&v)[32], const EpiConst& k) {
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    const float2 r = residue2(make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), k);
+    v[j] = __float_as_uint(r.x);
+    v[j + 1] = __float_as_uint(r.y);
   }
-  return y < 0.0f ? y + mf : y;
+}
+
+// Four values v[0..3] of a slab that is not written back, as four bytes:
+// the last slab's digits (after adding, when chain, the residue of the other
+// chain of slabs held as r + 128 in the bytes of a8), else r + 128.
+__device__ __forceinline__ uint32_t bytes4(const uint32_t* v, uint32_t a8, bool last, bool chain, const EpiConst& k) {
+  float2 t0 = make_float2(__uint_as_float(v[0]), __uint_as_float(v[1]));
+  float2 t1 = make_float2(__uint_as_float(v[2]), __uint_as_float(v[3]));
+  if (last && chain) {
+    const float2 nb = make_float2(-kTwo23p128, -kTwo23p128);
+    const float2 p0 = make_float2(__int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u)),
+                                  __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7541u)));
+    const float2 p1 = make_float2(__int_as_float(__byte_perm(a8, 0x4B000000u, 0x7542u)),
+                                  __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7543u)));
+    t0 = __fadd2_rn(t0, __fadd2_rn(p0, nb));
+    t1 = __fadd2_rn(t1, __fadd2_rn(p1, nb));
+  }
+  const float2 r0 = residue2(t0, k), r1 = residue2(t1, k);
+  float2 o0, o1;
+  if (last) {
+    o0 = digit2(r0, k);
+    o1 = digit2(r1, k);
+  } else {
+    o0 = __fadd2_rn(r0, make_float2(kTwo23p128, kTwo23p128));
+    o1 = __fadd2_rn(r1, make_float2(kTwo23p128, kTwo23p128));
+  }
+  return __byte_perm(__byte_perm(__float_as_uint(o0.x), __float_as_uint(o0.y), 0x0040u),
+                     __byte_perm(__float_as_uint(o1.x), __float_as_uint(o1.y), 0x0040u), 0x5410u);
 }
 
 // One thread's 128 digits of a tile row (one byte each, packed in words) to
@@ -216,8 +280,8 @@ __device__ __forceinline__ void store_digits(uint8_t* dst, const uint32_t* w, in
 // (W mod m reduced exactly, then the CRT digit, or W mod m when raw), one byte
 // per entry in acc8.
 template <int NCH, typename R>
-__device__ __forceinline__ void drain_one_slab(uint32_t taddr0, uint32_t (&acc8)[NCH * 8], float mf, float invm,
-                                               float invf, int raw, R release) {
+__device__ __forceinline__ void drain_one_slab(uint32_t taddr0, uint32_t (&acc8)[NCH * 8], const EpiConst& k,
+                                               R release) {
   uint32_t v[NCH][32];
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) tmem_ld32(taddr0 + ch * 32, v[ch]);
@@ -225,21 +289,9 @@ __device__ __forceinline__ void drain_one_slab(uint32_t taddr0, uint32_t (&acc8)
   tc_fence_before();
   release();
 #pragma unroll
-  for (int ch = 0; ch < NCH; ++ch) {
+  for (int ch = 0; ch < NCH; ++ch)
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      uint32_t out[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float tv = __uint_as_float(v[ch][4 * w + j]);
-        const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-        const float r = fmaf(-qf, mf, tv);                              // exact, |r| <= 120
-        out[j] = __float_as_uint(digit_of(r, mf, invm, invf, raw) + 8388608.0f);   // low byte
-      }
-      acc8[ch * 8 + w] =
-          __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
-    }
-  }
+    for (int w = 0; w < 8; ++w) acc8[ch * 8 + w] = bytes4(v[ch] + 4 * w, 0u, true, false, k);
 }
 
 struct Params {
@@ -400,9 +452,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const Unit u = unit_of(p, t);
       const Coord c = u.c;
       const int nslabs = u.nslabs;
-      const float mf = (float)T.m[c.q];
-      const float invm = T.invm[c.q];
-      const float invf = (float)T.inv[c.q];
+      const EpiConst k = epi_const((float)T.m[c.q], T.invm[c.q], p.raw ? 1.0f : (float)T.inv[c.q]);
       uint32_t acc8[CPW1 / 4];
 #pragma unroll
       for (int i = 0; i < CPW1 / 4; ++i) acc8[i] = 0x80808080u;
@@ -412,7 +462,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tc_fence_after();
         if constexpr (ONE) {
           const uint32_t tb = tempty_bar(b);
-          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, p.raw,
+          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, k,
                                     [&] {
                                       __syncwarp();
                                       if (lane == 0) mbar_arrive(tb);
@@ -428,33 +478,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           tmem_ld32(taddr, v);
           tmem_ld_wait();
           if (write_back) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float tv = __uint_as_float(v[j]);
-              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-              v[j] = __float_as_uint(fmaf(-qf, mf, tv));
-            }
+            residues32(v, k);
             tmem_st32(taddr, v);
           } else {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-              uint32_t out[4];
-              uint32_t& a8 = acc8[ch * 8 + w];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float tv = __uint_as_float(v[4 * w + j]);
-                if (last && nslabs > 1)
-                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
-                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                const float r = fmaf(-qf, mf, tv);
-                if (last) {
-                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, p.raw) + 8388608.0f);
-                } else {
-                  out[j] = __float_as_uint(r + 8388736.0f);
-                }
-              }
-              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
-            }
+            for (int w = 0; w < 8; ++w) acc8[ch * 8 + w] = bytes4(v + 4 * w, acc8[ch * 8 + w], last, nslabs > 1, k);
           }
         }
         if (write_back) tmem_st_wait();
@@ -739,9 +767,7 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
     for (int t = pair; t < num_units && ok; t += npairs) {
       const PairUnit u = sched.unit(t, pi);
       const int nslabs = u.nslabs;
-      const float mf = (float)T.m[u.q];
-      const float invm = T.invm[u.q];
-      const float invf = (float)T.inv[u.q];
+      const EpiConst k = epi_const((float)T.m[u.q], T.invm[u.q], u.raw ? 1.0f : (float)T.inv[u.q]);
       uint32_t acc8[CPW / 4];                // residue + 128 of the chain of slab nsl - 2, one byte per column
 #pragma unroll
       for (int i = 0; i < CPW / 4; ++i) acc8[i] = 0x80808080u;
@@ -751,7 +777,7 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
         tc_fence_after();
         if constexpr (ONE) {
           const uint32_t tb = mapa(tempty_bar(b), 0);
-          drain_one_slab<CPW / 32>(tmem_base + lane_addr + b * 256 + cbase, acc8, mf, invm, invf, u.raw,
+          drain_one_slab<CPW / 32>(tmem_base + lane_addr + b * 256 + cbase, acc8, k,
                                    [&] {
                                      __syncwarp();
                                      if (lane == 0) mbar_arrive_cluster(tb);
@@ -767,32 +793,11 @@ gemm_tc_pair_kernel(const __grid_constant__ S sched, const __grid_constant__ OzT
           tmem_ld32(taddr, v);
           tmem_ld_wait();
           if (write_back) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float tv = __uint_as_float(v[j]);
-              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;   // nearest quotient (+-1)
-              v[j] = __float_as_uint(fmaf(-qf, mf, tv));                     // exact, |r| <= 120
-            }
+            residues32(v, k);
             tmem_st32(taddr, v);
           } else {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-              uint32_t out[4];
-              uint32_t& a8 = acc8[ch * 8 + w];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float tv = __uint_as_float(v[4 * w + j]);
-                if (last && nslabs > 1)      // plus the residue of the other chain, r + 128 in a byte
-                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
-                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                const float r = fmaf(-qf, mf, tv);                          // exact, |r| <= 120
-                if (last)
-                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, u.raw) + 8388608.0f);   // low byte
-                else
-                  out[j] = __float_as_uint(r + 8388736.0f);                 // low byte = r + 128
-              }
-              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
-            }
+            for (int w = 0; w < 8; ++w) acc8[ch * 8 + w] = bytes4(v + 4 * w, acc8[ch * 8 + w], last, nslabs > 1, k);
           }
         }
         if (write_back) tmem_st_wait();
@@ -966,9 +971,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
         const OzGroupProblem& P = probs[pi];
       const Coord c = tile_coord((int)(t - P.unit_begin), P.tiles_m, P.tiles_n);
       const int nslabs = (P.kblocks + kSlabBlocks - 1) / kSlabBlocks;
-      const float mf = (float)T.m[c.q];
-      const float invm = T.invm[c.q];
-      const float invf = (float)T.inv[c.q];
+      const EpiConst k = epi_const((float)T.m[c.q], T.invm[c.q], (float)T.inv[c.q]);
       uint32_t acc8[CPW1 / 4];
 #pragma unroll
       for (int i = 0; i < CPW1 / 4; ++i) acc8[i] = 0x80808080u;
@@ -978,7 +981,7 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
         tc_fence_after();
         if constexpr (ONE) {
           const uint32_t tb = tempty_bar(b);
-          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, mf, invm, invf, 0,
+          drain_one_slab<CPW1 / 32>(tmem_base + lane_addr + b * BN + cbase, acc8, k,
                                     [&] {
                                       __syncwarp();
                                       if (lane == 0) mbar_arrive(tb);
@@ -994,33 +997,11 @@ gemm_tc_grouped_kernel(const __grid_constant__ OzTables T, const OzGroupProblem*
           tmem_ld32(taddr, v);
           tmem_ld_wait();
           if (write_back) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const float tv = __uint_as_float(v[j]);
-              const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-              v[j] = __float_as_uint(fmaf(-qf, mf, tv));
-            }
+            residues32(v, k);
             tmem_st32(taddr, v);
           } else {
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-              uint32_t out[4];
-              uint32_t& a8 = acc8[ch * 8 + w];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                float tv = __uint_as_float(v[4 * w + j]);
-                if (last && nslabs > 1)
-                  tv += __int_as_float(__byte_perm(a8, 0x4B000000u, 0x7540u + j)) - 8388736.0f;
-                const float qf = fmaf(tv, invm, 12582912.0f) - 12582912.0f;
-                const float r = fmaf(-qf, mf, tv);
-                if (last) {
-                  out[j] = __float_as_uint(digit_of(r, mf, invm, invf, 0) + 8388608.0f);   // the CRT digit
-                } else {
-                  out[j] = __float_as_uint(r + 8388736.0f);
-                }
-              }
-              a8 = __byte_perm(__byte_perm(out[0], out[1], 0x0040u), __byte_perm(out[2], out[3], 0x0040u), 0x5410u);
-            }
+            for (int w = 0; w < 8; ++w) acc8[ch * 8 + w] = bytes4(v + 4 * w, acc8[ch * 8 + w], last, nslabs > 1, k);
           }
         }
         if (write_back) tmem_st_wait();

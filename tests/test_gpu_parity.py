@@ -291,6 +291,43 @@ def test_dgemm_reports_nonfinite():
     assert oz.query_status(ws) == oz.OZ_OK
 
 
+@pytest.mark.parametrize("m,n,k", [(2000, 17, 1100), (33, 1000, 5000), (300, 300, 1025), (257, 129, 2048)])
+def test_dgemm_default_engine_long_rows(m, n, k):
+    """Products on the default engine with k past one slab (A's rows split one
+    block per row, B's columns split in place after their column maxima):
+    many rows and few columns, the reverse, k just past 1024; zero, tiny and
+    subnormal entries on both sides; bit for bit the oracle's product."""
+    plan = oz.Plan(16, 0, k, oz.OZ_ENGINE_TC)
+    A, B = synth.phi_pair(m, n, k, 1.5, seed=m + n + k)
+    A[1, :] = 0.0
+    B[:, min(3, n - 1)] = 0.0
+    A[2, :] *= 1e-300
+    B[:, n - 1] *= 1e-20
+    A[m - 1, k - 1] = 2.0**-1074
+    C = _dgemm(plan, A, B)
+    C_ref = oracle.dgemm(A, B, plan.moduli, plan.bits)
+    assert np.array_equal(_bits(C), _bits(C_ref))
+
+
+@pytest.mark.parametrize("side", ["A", "B"])
+def test_dgemm_reports_nonfinite_on_the_default_engine(side):
+    """A non-finite entry of A (found by the row split's maximum) or of B (by
+    the column maxima) sets the workspace status; the next clean call clears it."""
+    m, n, k = 64, 96, 1500
+    plan = oz.Plan(16, 0, k, oz.OZ_ENGINE_TC)
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=5)
+    if side == "A":
+        A[7, 1400] = np.inf
+    else:
+        B[1499, 90] = np.nan
+    ws = oz.workspace(plan, m, n, k)
+    oz.dgemm(_dev(A), _dev(B), plan, ws=ws)
+    assert oz.query_status(ws) == oz.OZ_ERR_NONFINITE
+    A, B = synth.phi_pair(m, n, k, 1.0, seed=5)
+    oz.dgemm(_dev(A), _dev(B), plan, ws=ws)
+    assert oz.query_status(ws) == oz.OZ_OK
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_full_size_8192_sampled_entries_and_error(engine):
     """m = n = k = 8192, Q = 16 (the headline size): sampled entries equal the
