@@ -409,22 +409,27 @@ __device__ __forceinline__ void fold_gemm(uint32_t (&acc16)[NCH * 16], uint32_t 
         else mbar_arrive(tempty);
       }
     }
+    // the two entries of a word of acc16 go through each packed fp32
+    // operation together (f32x2: each half rounded as the scalar form)
+    const float2 kC = make_float2(12582912.0f, 12582912.0f), kCn = make_float2(-12582912.0f, -12582912.0f);
+    const float2 ws2 = make_float2(wscale, wscale), inv2 = make_float2(invm, invm), nm2 = make_float2(-mf, -mf);
+    const float2 lam2 = make_float2(lam, lam), off2 = make_float2(8390656.0f, 8390656.0f);
+    const float2 noff2 = make_float2(-8390656.0f, -8390656.0f);
 #pragma unroll
     for (int w = 0; w < 16; ++w) {
-      uint32_t out[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        // previous residue r from its 16-bit field r + 2048
-        const float prev = __int_as_float(0x4B000000u | ((acc16[ch * 16 + w] >> (16 * j)) & 0xffffu)) - 8390656.0f;
-        const float W = __uint_as_float(v[2 * w + j]) * wscale;               // exact integer, |W| <= 2^24
-        const float wq = fmaf(W, invm, 12582912.0f) - 12582912.0f;
-        const float wm = fmaf(-wq, mf, W);                                   // W mod m, |wm| < 0.65 m
-        const float tsum = fmaf(lam, wm, prev);                              // exact: < 2^24
-        const float q2 = fmaf(tsum, invm, 12582912.0f) - 12582912.0f;
-        const float r = fmaf(-q2, mf, tsum);                                 // |r| < 0.51 m
-        out[j] = __float_as_uint(r + 8390656.0f) & 0xffffu;                  // r + 2048
-      }
-      acc16[ch * 16 + w] = out[0] | (out[1] << 16);
+      const uint32_t a = acc16[ch * 16 + w];
+      // previous residues r from their 16-bit fields r + 2048
+      const float2 prev = __fadd2_rn(make_float2(__int_as_float(__byte_perm(a, 0x4B000000u, 0x7410u)),
+                                                 __int_as_float(__byte_perm(a, 0x4B000000u, 0x7432u))),
+                                     noff2);
+      const float2 W = __fmul2_rn(make_float2(__uint_as_float(v[2 * w]), __uint_as_float(v[2 * w + 1])),
+                                  ws2);                                         // exact integers, |W| <= 2^24
+      const float2 wq = __fadd2_rn(__ffma2_rn(W, inv2, kC), kCn);
+      const float2 wm = __ffma2_rn(wq, nm2, W);                                  // W mod m, |wm| < 0.65 m
+      const float2 tsum = __ffma2_rn(lam2, wm, prev);                            // exact: < 2^24
+      const float2 q2 = __fadd2_rn(__ffma2_rn(tsum, inv2, kC), kCn);
+      const float2 o = __fadd2_rn(__ffma2_rn(q2, nm2, tsum), off2);              // |r| < 0.51 m; r + 2048
+      acc16[ch * 16 + w] = __byte_perm(__float_as_uint(o.x), __float_as_uint(o.y), 0x5410u);
     }
   }
 }
