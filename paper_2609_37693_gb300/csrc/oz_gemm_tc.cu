@@ -529,9 +529,13 @@ constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + kBarBytes + 1024;
 // full and empty barriers per stage, two tfull, two tempty, one drain: all below kHolderOff
 static_assert((2 * P_STAGES + 5) * 8 <= kHolderOff, "pair kernel barriers overlap the TMEM address");
 static_assert((2 * STAGES + 5) * 8 <= kHolderOff, "barriers overlap the TMEM address");
-// epilogue warps of the pair kernel (with four, one warp's drain of a slab
-// outlasts the slab's products)
+// Epilogue warps of the pair kernel: sixteen when every unit is one slab
+// (the epilogue then bounds the kernel) and for grouped products; four for a
+// product of several slabs, where fewer warps beside the MMA-issuing thread
+// leave it more issue slots: with the packed epilogue arithmetic one warp
+// drains its 256 columns of a slab well within the slab's products.
 constexpr int kPairEpiWarps = 16;
+constexpr int kPairEpiWarpsMulti = 4;
 
 // What a CTA pair needs to know about one unit of work: the tensor maps and
 // first plane rows of its 256 x 256 tile, its k-block range, its modulus and
@@ -1110,7 +1114,8 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   // releases each accumulator before forming its digits
   const bool one = k_pad <= (int64_t)kSlabBlocks * BK && split.nsplit <= 1;
   auto kernel = one ? gemm_tc_pair_kernel<kPairEpiWarps, PairSingle, true>
-                    : gemm_tc_pair_kernel<kPairEpiWarps, PairSingle, false>;
+                    : gemm_tc_pair_kernel<kPairEpiWarpsMulti, PairSingle, false>;
+  const int epi_warps = one ? kPairEpiWarps : kPairEpiWarpsMulti;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   PairSingle sched;
@@ -1133,7 +1138,7 @@ cudaError_t launch_gemm_tc(const OzTables& t, int64_t m, int64_t n, int64_t m_pa
   if (!set_split(&p, split, ysplit)) return cudaErrorInvalidValue;
   const int64_t units = num_tiles * p.nsplit;
   const int64_t pairs = units < sms / 2 ? units : sms / 2;
-  kernel<<<(unsigned)(2 * pairs), (2 + kPairEpiWarps) * 32, smem_bytes, st>>>(sched, t);
+  kernel<<<(unsigned)(2 * pairs), (2 + epi_warps) * 32, smem_bytes, st>>>(sched, t);
   return cudaGetLastError();
 }
 

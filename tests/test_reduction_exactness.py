@@ -79,22 +79,24 @@ def test_slab_drain_reduction_bounds_the_residue(m):
 @pytest.mark.parametrize("m", MODULI)
 def test_digit_step_lands_in_range(m):
     """The last slab's digit: from the balanced residue r of W (|r| <= 120),
-    y = r inv with inv = (P/m)^-1 mod m (|y| <= 120 * 238 < 2^15, exact in
-    fp32), then y - m rint(y fl(1/m)) and one correction by +m if negative.
-    Claim: the result is (W mod m) inv mod m in [0, m), for every r and every
-    coefficient below m (so for whatever (P/m)^-1 a plan has). The raw value
-    (W mod m in [0, m)) is r with the same correction."""
-    invm = float(np.float32(1.0) / np.float32(m))
+    y = r f with f = (P/m)^-1 mod m, or f = 1 for the raw value W mod m
+    (|y| <= 120 * 238 < 2^15, exact in fp32), then one floor quotient
+    q = rint(fl32(y fl(1/m) + bias)), bias = fl32(-1/2 + fl(1/m) / 2), by an
+    fma and the 1.5 * 2^23 rounding constant, and d = y - q m. Claim: d is
+    (W mod m) f mod m in [0, m), for every r and every f below m (so for
+    whatever (P/m)^-1 a plan has, and for raw). The emulation is exact: the
+    fma's product and sum are exact in float64 (39 significant bits), and
+    float64 -> float32 and rint both round to nearest even, as the GPU does."""
+    invm = np.float32(1.0) / np.float32(m)
+    bias = np.float32(0.5 * np.float64(invm) - 0.5)
     r = np.arange(-120, 121, dtype=np.int64)
-    raw = np.where(r < 0, r + m, r)
-    assert np.array_equal(raw, r % m)
-    for inv in range(m):
-        y = r * inv
-        q = np.rint(y.astype(np.float64) * invm).astype(np.int64)
+    for f in range(m):
+        y = r * f
+        t = (y.astype(np.float64) * np.float64(invm) + np.float64(bias)).astype(np.float32)
+        q = np.rint(t.astype(np.float64)).astype(np.int64)
         d = y - q * m
-        d = np.where(d < 0, d + m, d)
         assert d.min() >= 0 and d.max() < m
-        assert np.array_equal(d, (r * inv) % m)
+        assert np.array_equal(d, (r * f) % m)
 
 
 @pytest.mark.parametrize("fmt", ["E4M3", "E5M2", "E2M3", "E3M2", "E2M1"])
