@@ -88,7 +88,14 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    """nvidia-smi clock and throttle-reason samples, each stamped with the
+    host time it arrived. One sampler runs for a whole measurement: started
+    before the warm-up, it is summarised per timed region by the samples
+    that fall inside it (summary(t0, t1)). Starting nvidia-smi right before
+    a timed region stalled the host-operand pipeline's copies and kernels for
+    tens of milliseconds in the first process on a fresh machine, and
+    starting a second one mid-run did the same; a probe of the same sequence
+    without nvidia-smi never stalled."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -97,15 +104,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []            # (host time, csv line)
         self.thread = None
 
     def start(self, settle_s: float = 3.0):
         """Start sampling and return once the first sample has arrived (at
-        most settle_s): nvidia-smi's start-up (its NVML initialisation) held
-        up the host's CUDA calls for tens of milliseconds in the first process
-        on a fresh machine, which a timed region begun right after start() paid
-        in full."""
+        most settle_s)."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -118,25 +122,31 @@ class ClockSampler:
         t_end = time.time() + settle_s
         while not self.lines and time.time() < t_end and self.proc.poll() is None:
             time.sleep(0.01)
-        time.sleep(0.05)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, maximum clock, throttle reasons and peak power of
+        the samples that arrived in [t0, t1] (all samples when t0 is None);
+        a region shorter than the sampling period takes the first sample
+        after t0 (or the last one before it)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        if self.thread:
-            self.thread.join(timeout=2)
+        lines = list(self.lines)
+        if t0 is not None:
+            inside = [ln for t, ln in lines if t0 <= t <= t1]
+            if not inside:
+                after = [ln for t, ln in lines if t >= t0]
+                before = [ln for t, ln in lines if t < t0]
+                inside = after[:1] or before[-1:]
+            lines = inside
+        else:
+            lines = [ln for _, ln in lines]
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -152,6 +162,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm),
                 "power_w_max": max(power) if power else None}
+
+    def stop(self):
+        """End sampling; the summary of every sample taken."""
+        if self.proc is None:
+            return self.summary()
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        return self.summary()
 
 
 def operands(args, m, n, k, seed):
@@ -395,6 +418,10 @@ def run_ours(args, rank, world, local):
         if st != oz.OZ_OK:
             raise RuntimeError(f"oz_dgemm: {oz.oz_status_str(st)}")
 
+    # one clock sampler for the whole run, started before the warm-up (see
+    # ClockSampler); each timed region reads the samples inside it
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
@@ -425,22 +452,20 @@ def run_ours(args, rank, world, local):
             raise RuntimeError(f"result differs from native DGEMM by {rel_frob:.3e} (relative Frobenius)")
 
     # ---- timed region: K steps of oz_dgemm, inputs (1 GiB) larger than L2 ----
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    t_region = time.time()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = clocks.summary(t_region, time.time())
     if dist:
         dist.barrier()
     elapsed_ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
     elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     ms_per_step = elapsed_ms / args.steps
     flops = 2.0 * n**3
@@ -463,14 +488,13 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_steps = max(2, min(args.steps, 10))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
-    e2e_clocks = ClockSampler(local)
-    e2e_clocks.start()
+    t_region = time.time()
     ev[0].record(stream)
     for i in range(e2e_steps):
         hg(A_pin, B_pin, C_pin, stream)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    e2e_clk = e2e_clocks.stop()
+    e2e_clk = clocks.summary(t_region, time.time())
     e2e_step_ms = [round(ev[i].elapsed_time(ev[i + 1]), 3) for i in range(e2e_steps)]
     e2e_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]) / e2e_steps, dist, dev)
     e2e_value = throughput_tflops(flops, 1, e2e_ms, world)
@@ -508,6 +532,7 @@ def run_ours(args, rank, world, local):
         for i, key in enumerate(phase_ms):
             phase_ms[key] += ev[i].elapsed_time(ev[i + 1]) / reps
     phase_sum = sum(phase_ms.values())
+    clocks.stop()
 
     # ---- roofline of the dominant kernel (the residue GEMMs) ----
     peaks = load_peaks()
