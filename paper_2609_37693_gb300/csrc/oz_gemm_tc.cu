@@ -16,18 +16,20 @@
 //
 // Two kernels: gemm_tc_pair_kernel (the default; CTA pairs, cta_group::2,
 // 256 x 256 tiles, described before it) and gemm_tc_kernel (one CTA per
-// 128 x 256 tile). Both are persistent, one CTA per SM, 10 warps:
+// 128 x 256 tile). Both are persistent, one CTA per SM, 2 + E warps:
 //   warp 0      TMA producer: bf16 tiles, 128-byte swizzle, a ring of
 //               mbarrier-tracked shared-memory stages;
 //   warp 1      allocates all 512 TMEM columns (two 256-column FP32
 //               accumulators) and, from one thread, issues tcgen05.mma
 //               (K = 16) and tcgen05.commit;
-//   warps 2..9  epilogue: drain an accumulator with tcgen05.ld while the MMAs
-//               fill the other; each slab's sums are reduced modulo m and
-//               written back into the accumulator, on which the slab after
-//               next accumulates; the last two slabs of a tile give the CRT
-//               digit (or W mod m) of each entry, one byte, stored in 16-byte
-//               runs.
+//   warps 2..   E epilogue warps (16 in the one-CTA kernels; 4 or 16 in the
+//               pair kernel, see kPairEpiWarps): drain an accumulator with
+//               tcgen05.ld while the MMAs fill the other; each slab's sums
+//               are reduced modulo m and written back into the accumulator,
+//               on which the slab after next accumulates; the last two slabs
+//               of a tile give the CRT digit (or W mod m) of each entry, one
+//               byte, stored in 16-byte runs. Their arithmetic runs on packed
+//               f32x2 pairs.
 // Every wait is bounded (about 2 s of %globaltimer); a wait that runs out sets
 // bit 1 of the status word, makes every role stop issuing work, waits (again
 // bounded) for the copies and products already in flight, frees the tensor
