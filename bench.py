@@ -489,10 +489,13 @@ def run_ours(args, rank, world, local):
     e2e_steps = max(2, min(args.steps, 10))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
     t_region = time.time()
+    host_ms = []
     ev[0].record(stream)
     for i in range(e2e_steps):
+        h0 = time.perf_counter()
         hg(A_pin, B_pin, C_pin, stream)
         ev[i + 1].record(stream)
+        host_ms.append(round((time.perf_counter() - h0) * 1e3, 3))
     torch.cuda.synchronize()
     e2e_clk = clocks.summary(t_region, time.time())
     e2e_step_ms = [round(ev[i].elapsed_time(ev[i + 1]), 3) for i in range(e2e_steps)]
@@ -610,6 +613,7 @@ def run_ours(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n * n,
                     "d2h_bytes_per_step": 8 * n * n, "ms_per_step": e2e_ms, "step_ms": e2e_step_ms,
+                    "host_enqueue_ms": host_ms,
                     "copy_gbs": copy_gbs, "clocks": e2e_clk,
                     "api": "oz_dgemm_host (pinned host A, B, C; blocks of C overlap copies and phases)",
                     "block": [hg_rows, hg_cols], "host": host_binding,

@@ -22,6 +22,39 @@
 
 namespace {
 
+// The pipeline's events, created once per host thread and device and reused
+// by every call from that thread: a call records each event and enqueues the
+// waits on it before it returns, and a wait orders against the record made
+// before it, so the next call may record the same events again while this
+// call's work is still running. (Creating and destroying a dozen events per
+// call put driver work on the host path of every product.)
+struct EventPool {
+  int device = -1;
+  std::vector<cudaEvent_t> ev;
+  void release() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+  }
+  ~EventPool() { release(); }
+};
+thread_local EventPool t_events;
+
+// At least `count` events of the current device, or nullptr.
+std::vector<cudaEvent_t>* event_pool(size_t count) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (t_events.device != dev) {
+    t_events.release();
+    t_events.device = dev;
+  }
+  while (t_events.ev.size() < count) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    t_events.ev.push_back(e);
+  }
+  return &t_events.ev;
+}
+
 using oz::round_up;
 
 struct HostLayout {
@@ -123,21 +156,13 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   auto vj = [&](int64_t j) { return static_cast<void*>(ws + L.v + L.vplane * (size_t)j); };
 
   // events: start, B_j ready, A slot ready/free, C slot ready/free, end of both copy streams
-  std::vector<cudaEvent_t> evs;
-  auto mk = [&](cudaEvent_t* e) {
-    if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return false;
-    evs.push_back(*e);
-    return true;
-  };
-  auto cleanup = [&]() {
-    for (cudaEvent_t e : evs) cudaEventDestroy(e);
-  };
-  cudaEvent_t ev_start, ev_a_ready[2], ev_a_free[2], ev_c_ready[2], ev_c_free[2], ev_h_end, ev_d_end;
-  std::vector<cudaEvent_t> ev_b((size_t)nbj);
-  bool ok = mk(&ev_start) && mk(&ev_h_end) && mk(&ev_d_end);
-  for (int i = 0; i < 2 && ok; ++i) ok = mk(&ev_a_ready[i]) && mk(&ev_a_free[i]) && mk(&ev_c_ready[i]) && mk(&ev_c_free[i]);
-  for (int64_t j = 0; j < nbj && ok; ++j) ok = mk(&ev_b[(size_t)j]);
-  if (!ok) { cleanup(); return OZ_ERR_CUDA; }
+  std::vector<cudaEvent_t>* pool = event_pool((size_t)(11 + nbj));
+  if (!pool) return OZ_ERR_CUDA;
+  const cudaEvent_t* pe = pool->data();
+  const cudaEvent_t ev_start = pe[0], ev_h_end = pe[1], ev_d_end = pe[2];
+  const cudaEvent_t ev_a_ready[2] = {pe[3], pe[4]}, ev_a_free[2] = {pe[5], pe[6]};
+  const cudaEvent_t ev_c_ready[2] = {pe[7], pe[8]}, ev_c_free[2] = {pe[9], pe[10]};
+  const cudaEvent_t* ev_b = pe + 11;
 
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess && r != cudaSuccess) e = r; };
@@ -166,7 +191,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
     if (k > 0)
       chk(cudaMemcpy2DAsync(Bd + c0, (size_t)n * 8, B + c0, (size_t)ldb * 8, (size_t)cols_of(j) * 8, (size_t)k,
                             cudaMemcpyHostToDevice, sh));
-    chk(cudaEventRecord(ev_b[(size_t)j], sh));
+    chk(cudaEventRecord(ev_b[j], sh));
   }
   if (nbi > 1) copy_a(1);
 
@@ -198,7 +223,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
       uint8_t* Yj = Y + c0 * ybytes;
       if (k > 0) {
         if (i == 0) {
-          chk(cudaStreamWaitEvent(sc, ev_b[(size_t)j], 0));
+          chk(cudaStreamWaitEvent(sc, ev_b[j], 0));
           chk(fp ? oz::launch_split_fp(T, F, 0, nc, k, Bd + c0, n, L.w_pad, L.k_pad, t + c0,
                                        static_cast<uint8_t*>(vj(j)), flag, colmax + c0, sc)
                  : launch_split_b_chunk(nc, c0, vj(j)));
@@ -213,7 +238,7 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
                    : oz::launch_gemm_imma(T, nr, nc, L.k_pad, static_cast<const int8_t*>(U), L.chunk_pad * L.k_pad,
                                           static_cast<const int8_t*>(vj(j)), L.w_pad * L.k_pad, Yj, L.ldy, 0, sc));
       } else if (i == 0) {
-        chk(cudaStreamWaitEvent(sc, ev_b[(size_t)j], 0));
+        chk(cudaStreamWaitEvent(sc, ev_b[j], 0));
       }
       if (blk >= 2) chk(cudaStreamWaitEvent(sc, ev_c_free[cs], 0));      // copy-back of block blk-2 done
       if (k > 0)
@@ -234,6 +259,5 @@ extern "C" oz_status oz_dgemm_host(oz_plan plan, int64_t m, int64_t n, int64_t k
   chk(cudaEventRecord(ev_d_end, sd));
   chk(cudaStreamWaitEvent(sc, ev_h_end, 0));
   chk(cudaStreamWaitEvent(sc, ev_d_end, 0));
-  cleanup();
   return e == cudaSuccess ? OZ_OK : OZ_ERR_CUDA;
 }
