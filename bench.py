@@ -90,12 +90,10 @@ def dist_env():
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples, each stamped with the
     host time it arrived. One sampler runs for a whole measurement: started
-    before the warm-up, it is summarised per timed region by the samples
-    that fall inside it (summary(t0, t1)). Starting nvidia-smi right before
-    a timed region stalled the host-operand pipeline's copies and kernels for
-    tens of milliseconds in the first process on a fresh machine, and
-    starting a second one mid-run did the same; a probe of the same sequence
-    without nvidia-smi never stalled."""
+    before the warm-up (so that nvidia-smi's start-up falls outside every
+    timed region), it is summarised per timed region by the samples that
+    fall inside it (summary(t0, t1)), which reflect the region itself rather
+    than the idle moments around it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
