@@ -23,7 +23,9 @@
  *     memory during a product call. An INT8 plan owns a small table of
  *     constants in host memory; a float-format plan also owns a small device
  *     table of codes; a grouped product (oz_group_create) owns a few streams
- *     and events; oz_dgemm_host creates and destroys events per call.
+ *     and events; oz_dgemm_host keeps a pool of events per host thread and
+ *     device, created on first use and reused by every later call of that
+ *     thread (destroyed when the thread exits).
  *   - Calls are asynchronous on the given CUDA stream (a cudaStream_t passed as
  *     void*; NULL = the legacy default stream). Nothing synchronises the host
  *     except oz_query_status.
@@ -31,9 +33,9 @@
  *     traps. Argument errors are detected on the host before any launch.
  *     Non-finite input is detected on the device, leaves C unspecified, and is
  *     reported by the next oz_query_status on the same workspace.
- *   - Nothing is thread-local: a plan is immutable after creation and may be
- *     shared by threads; a workspace must not be used by two calls that
- *     overlap on the GPU.
+ *   - A plan is immutable after creation and may be shared by threads; a
+ *     workspace must not be used by two calls that overlap on the GPU. The
+ *     only per-thread state is oz_dgemm_host's event pool.
  */
 #ifndef OZ_H_
 #define OZ_H_
