@@ -62,3 +62,52 @@ def test_host_path_widened_budget():
     hg(Ah, Bh, Ch)
     torch.cuda.synchronize()
     assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, 70, what="host path, beta = 70")
+
+
+def test_host_path_back_to_back_calls_and_two_threads():
+    """The pipeline's events come from a per-thread pool reused by every call:
+    calls queued back to back on one thread (each recording the events the
+    previous call's work still waits on), and two threads with their own
+    streams and workspaces running at once, all give the oracle's product."""
+    import threading
+    plan = oz.Plan(16, 0, 1500, oz.OZ_ENGINE_TC)
+    m, n, k = 900, 700, 1500
+    ops = [synth.phi_pair(m, n, k, 1.0, seed=40 + i) for i in range(3)]
+    pinned = [(torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()) for A, B in ops]
+    outs = [torch.full((m, n), np.nan, dtype=torch.float64).pin_memory() for _ in ops]
+    hg = oz.HostGemm(plan, m, n, k, 256, cols_per_chunk=256)
+    for (Ah, Bh), Ch in zip(pinned, outs):           # queued without a synchronisation between them
+        hg(Ah, Bh, Ch)
+    torch.cuda.synchronize()
+    assert oz.query_status(hg.ws) == oz.OZ_OK
+    for (A, B), Ch in zip(ops, outs):
+        assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, plan.bits, what="back-to-back host calls", count=512)
+
+    results, errors = {}, []
+
+    def worker(t):
+        try:
+            torch.cuda.set_device(0)
+            stream = torch.cuda.Stream()
+            g = oz.HostGemm(plan, m, n, k, 256, cols_per_chunk=256)
+            Ah, Bh = pinned[t]
+            Cs = [torch.full((m, n), np.nan, dtype=torch.float64).pin_memory() for _ in range(2)]
+            for Ch in Cs:
+                g(Ah, Bh, Ch, stream)
+            stream.synchronize()
+            results[t] = (Cs, oz.query_status(g.ws, stream))
+        except Exception as e:  # noqa: BLE001 - reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=300)
+    assert not errors, errors
+    for t in range(2):
+        Cs, status = results[t]
+        assert status == oz.OZ_OK
+        A, B = ops[t]
+        for Ch in Cs:
+            assert_oracle_bits(Ch.numpy(), A, B, plan.moduli, plan.bits, what=f"host thread {t}", count=512)
