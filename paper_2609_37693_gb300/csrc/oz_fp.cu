@@ -692,7 +692,6 @@ struct PairCfg {
   static constexpr int STAGE_BYTES = A_BYTES + BNC * BK;
   static constexpr int STAGES = MX ? 7 : 6;
   static constexpr int kSmemBytes = STAGES * STAGE_BYTES + 256 + 1024;
-  static constexpr int KSTAGE = MX ? 2 * BK : BK;
 };
 
 __device__ __forceinline__ void umma_f8f6f4_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
